@@ -1,0 +1,71 @@
+/*
+ * FP64 kernel sums for the oracle (test infrastructure only; never part of the product path).
+ *
+ * One routine: for every target group g, for every target i of that group and every source j
+ * in the group's source ranges, add K(x_i, y_j) s_j to f_i, where K is the 3D Laplace kernel
+ * 1/(4 pi |x - y|) (Eq. 2, normalised by 4 pi), i.e. Eq. 1 restricted to the given pairs.
+ * Pairs with |x_i - y_j| == 0 exactly are skipped: that excludes self-interaction and
+ * coincident points.  With `grad` non-NULL the gradient with respect to the target position,
+ * -sum_j s_j (x_i - y_j) / (4 pi |x_i - y_j|^3), is accumulated as well.
+ *
+ * This is a plain double loop with no blocking; OpenMP only splits the groups between threads.
+ */
+#include <math.h>
+#include <stdint.h>
+
+#define INV4PI 0.079577471545947667884441881686257181  /* 1/(4 pi) */
+
+void oracle_grouped_sum(int64_t n_groups,
+                        const int64_t *t_off,      /* [n_groups+1]: targets of group g are t_off[g]..t_off[g+1]-1 */
+                        const double *tx,          /* [n_targets*3] target coordinates */
+                        const int64_t *r_off,      /* [n_groups+1]: source ranges of group g are r_off[g]..r_off[g+1]-1 */
+                        const int64_t *ranges,     /* [n_ranges*2]: (begin, end) into the source arrays */
+                        const double *sx,          /* [n_sources*3] source coordinates */
+                        const double *sq,          /* [n_sources] source densities */
+                        double *pot,               /* [n_targets], accumulated */
+                        double *grad)              /* [n_targets*3] or NULL, accumulated */
+{
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (g = 0; g < n_groups; ++g) {
+        for (int64_t i = t_off[g]; i < t_off[g + 1]; ++i) {
+            const double xi = tx[3 * i], yi = tx[3 * i + 1], zi = tx[3 * i + 2];
+            double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+            for (int64_t r = r_off[g]; r < r_off[g + 1]; ++r) {
+                for (int64_t j = ranges[2 * r]; j < ranges[2 * r + 1]; ++j) {
+                    const double dx = xi - sx[3 * j];
+                    const double dy = yi - sx[3 * j + 1];
+                    const double dz = zi - sx[3 * j + 2];
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 == 0.0) continue;
+                    const double rinv = 1.0 / sqrt(r2);
+                    const double w = sq[j] * rinv;
+                    f += w;
+                    if (grad) {
+                        const double w3 = w * rinv * rinv;
+                        gx -= w3 * dx;
+                        gy -= w3 * dy;
+                        gz -= w3 * dz;
+                    }
+                }
+            }
+            pot[i] += f * INV4PI;
+            if (grad) {
+                grad[3 * i] += gx * INV4PI;
+                grad[3 * i + 1] += gy * INV4PI;
+                grad[3 * i + 2] += gz * INV4PI;
+            }
+        }
+    }
+}
+
+/* Number of threads OpenMP would use (1 when built without OpenMP). */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,102 @@
+"""FP64 direct evaluation of the field sum (Eq. 1) with the 3D Laplace kernel (Eq. 2).
+
+The kernel is normalised as K(x, y) = 1 / (4 pi |x - y|).  The paper writes 1/|x - y|; the
+factor only scales every result, so relative errors are unaffected.  Pairs at distance exactly
+zero are skipped (self-interaction and coincident points).
+
+Two independent formulations are kept so that each pins the other:
+  * `direct_numpy`: dense NumPy broadcasting in chunks of targets;
+  * `grouped_sum` / `direct_c`: the plain C double loop in csrc/oracle_sum.c.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+INV4PI = 1.0 / (4.0 * np.pi)
+
+_lib = None
+
+
+def _native():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        p = ctypes.c_void_p
+        lib.oracle_grouped_sum.argtypes = [ctypes.c_int64, p, p, p, p, p, p, p, p]
+        lib.oracle_grouped_sum.restype = None
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """Threads the C helper uses (OpenMP), for reporting the CPU baseline."""
+    return int(_native().oracle_num_threads())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def direct_numpy(targets, sources, charges, gradient=True, chunk=2048):
+    """phi_i = sum_j K(x_i, y_j) s_j and its gradient, by dense broadcasting (FP64)."""
+    x = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+    y = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
+    s = np.asarray(charges, dtype=np.float64).reshape(-1)
+    pot = np.zeros(len(x))
+    grad = np.zeros((len(x), 3)) if gradient else None
+    for a in range(0, len(x), chunk):
+        d = x[a:a + chunk, None, :] - y[None, :, :]          # x_i - y_j
+        r2 = np.einsum("ijk,ijk->ij", d, d)
+        with np.errstate(divide="ignore"):
+            rinv = np.where(r2 > 0.0, 1.0 / np.sqrt(np.where(r2 > 0.0, r2, 1.0)), 0.0)
+        w = rinv * s[None, :]
+        pot[a:a + chunk] = w.sum(axis=1) * INV4PI
+        if gradient:
+            w3 = w * rinv * rinv
+            grad[a:a + chunk] = -np.einsum("ij,ijk->ik", w3, d) * INV4PI
+    return pot, grad
+
+
+def grouped_sum(t_off, tx, r_off, ranges, sx, sq, gradient=True, pot=None, grad=None):
+    """Accumulate kernel sums over (target group, source ranges) with the C helper (FP64).
+
+    t_off[g]:t_off[g+1] are the targets of group g; ranges[r_off[g]:r_off[g+1]] are its
+    (begin, end) source index ranges.  Returns (pot, grad) accumulated into the given arrays.
+    """
+    t_off = np.ascontiguousarray(t_off, dtype=np.int64)
+    tx = np.ascontiguousarray(tx, dtype=np.float64).reshape(-1, 3)
+    r_off = np.ascontiguousarray(r_off, dtype=np.int64)
+    ranges = np.ascontiguousarray(ranges, dtype=np.int64).reshape(-1, 2)
+    sx = np.ascontiguousarray(sx, dtype=np.float64).reshape(-1, 3)
+    sq = np.ascontiguousarray(sq, dtype=np.float64).reshape(-1)
+    n_groups = len(t_off) - 1
+    assert len(r_off) == n_groups + 1
+    if pot is None:
+        pot = np.zeros(len(tx))
+    if gradient and grad is None:
+        grad = np.zeros((len(tx), 3))
+    assert pot.dtype == np.float64 and pot.flags.c_contiguous
+    if gradient:
+        assert grad.dtype == np.float64 and grad.flags.c_contiguous
+    _native().oracle_grouped_sum(n_groups, _ptr(t_off), _ptr(tx), _ptr(r_off), _ptr(ranges),
+                                 _ptr(sx), _ptr(sq), _ptr(pot), _ptr(grad) if gradient else None)
+    return pot, (grad if gradient else None)
+
+
+def direct_c(targets, sources, charges, gradient=True):
+    """Eq. 1 at the given targets from all sources, with the C helper (FP64)."""
+    tx = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+    n_s = len(np.asarray(sources).reshape(-1, 3))
+    return grouped_sum([0, len(tx)], tx, [0, 1], [[0, n_s]], sources, charges, gradient)
+
+
+def direct_self(points, charges, gradient=True, sample=None):
+    """Field at the points themselves (targets = sources), optionally only at `sample` indices."""
+    x = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    t = x if sample is None else x[np.asarray(sample)]
+    return direct_c(t, x, charges, gradient)
