@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark: kiFMM points/s (potentials + gradients) on the 8,388,608-point unit-sphere
+workload at p = 6, depth 7, on one GB300, through the C ABI of libfmm.
+
+One step = one pass of the whole evaluation path over the synthetic batch: the octree build
+(Morton keys, radix sort, leaves, levels, lists) followed by fmm_evaluate (S2U, U2U, VLI, D2D,
+D2T, ULI) with potentials and gradients.  The operators come from the one-time FP64 precompute
+(independent of the points), done before timing.  Inputs are resident in HBM when the timed
+region starts; L2 (129 MB) is flushed between steps by writing a 256 MB buffer outside the
+timed events.  `e2e` repeats the step through the same C entry points with pinned host
+buffers, host<->device copies included.
+
+Default: 1 GPU, 3 warm-up steps, 10 timed steps, then the FP64 CPU oracle on a bounded sample
+(the cpu_baseline leg).  `--impl reference` times only that oracle (the reference arm).
+Under torchrun with N > 1 every rank runs an independent replica (the path has no exchange
+step on one GPU per process); value = all ranks' points / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synth import WORKLOADS, SEED_SAMPLE, sample_indices, sphere_points, charges  # noqa: E402
+
+METRIC = "kiFMM points/sec (potential+gradient) at N=8M, p=6, rel err ≤1e-5 vs FP64"
+UNIT = "points/s"
+FLOPS_PER_PAIR = 20          # conventional count for a potential+gradient Laplace interaction
+SAMPLE_N = 524_288           # CPU sample: same sphere distribution, depth 5 -> ~112 points/leaf
+SAMPLE_DEPTH = 5
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def source_digest(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2604_19243_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, digest):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_digest") != digest:
+        return None
+    return rec.get("bytes_per_launch_full")
+
+
+def cpu_baseline_sample(p):
+    """The FP64 oracle kiFMM on a bounded sample of the same workload family."""
+    from oracle import direct, kifmm
+    x = sphere_points(SAMPLE_N)
+    q = charges(SAMPLE_N, "u01")
+    t0 = time.perf_counter()
+    kifmm.evaluate(x.astype(np.float64), q.astype(np.float64), p, SAMPLE_DEPTH, (-1, -1, -1), 2.0,
+                   pinv_rtol=1e-7, gradient=True)
+    dt = time.perf_counter() - t0
+    return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": direct.num_threads(),
+            "host_cpus": os.cpu_count(), "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"FP64 oracle kiFMM (p={p}, potentials+gradients, tree and operators "
+                      f"included) on {SAMPLE_N:,} points of the same unit-sphere distribution at "
+                      f"depth {SAMPLE_DEPTH} (~112 points per leaf, as in the full workload)"}
+
+
+def accuracy_check(w, x, q, phi, grad, m=256):
+    """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum."""
+    from oracle import direct
+    idx = sample_indices(w.n, m, SEED_SAMPLE)
+    x64 = x.astype(np.float64)
+    p_ref, g_ref = direct.direct_self(x64, q.astype(np.float64), sample=idx)
+    e_p = float(np.linalg.norm(phi[idx] - p_ref) / np.linalg.norm(p_ref))
+    e_g = float(np.linalg.norm(grad[idx] - g_ref) / np.linalg.norm(g_ref))
+    return {"phi": e_p, "grad": e_g, "targets": int(m),
+            "reference": "FP64 direct sum (Eq. 1) at seeded sampled targets"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline_sample(w.p)
+        if i >= args.warmup:
+            times.append(info["seconds"])
+    mean_s = sum(times) / len(times)
+    value = SAMPLE_N / mean_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "p": w.p,
+                                            "depth": w.depth, "dist": w.dist},
+            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
+                             "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere8m_p6_d7", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_2604_19243_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    fp64 = args.precision == "fp64"
+    tdt = torch.float64 if fp64 else torch.float32
+    x_np, q_np = w.points(), w.charges()
+    x = torch.from_numpy(x_np).to(dev, tdt)
+    q = torch.from_numpy(q_np).to(dev, tdt)
+    phi = torch.empty(w.n, device=dev, dtype=tdt)
+    grad = torch.empty(w.n, 3, device=dev, dtype=tdt)
+    fmm = pkg.FMM(p=w.p, depth=w.depth, precision=args.precision, domain=(w.origin, w.side),
+                  stream=stream.cuda_stream)
+    fmm.precompute()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        fmm.build_tree(x)
+        fmm.evaluate_into(q, phi, grad)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    info = fmm.info()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or "0"
+    clocks = ClockSampler(gpu_index)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phases = []
+    launches0 = pkg.kernel_launches()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        phases.append(fmm.timings())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = pkg.kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t)
+    value = w.n * args.steps * ws / total_s
+    ms_per_step = total_s / args.steps * 1e3
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    xh = torch.from_numpy(x_np).to(tdt).pin_memory()
+    qh = torch.from_numpy(q_np).to(tdt).pin_memory()
+    ph = torch.empty(w.n, dtype=tdt).pin_memory()
+    gh = torch.empty(w.n, 3, dtype=tdt).pin_memory()
+    for _ in range(2):
+        fmm.build_tree(xh)
+        fmm.evaluate_into(qh, ph, gh)
+    torch.cuda.synchronize()
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fmm.build_tree(xh)
+        fmm.evaluate_into(qh, ph, gh)     # host outputs: returns after the device-to-host copy
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_value = w.n / (sum(e2e_s) / len(e2e_s)) * ws
+    es = 8 if fp64 else 4
+    h2d = w.n * 3 * es + w.n * es
+    d2h = w.n * es + w.n * 3 * es
+
+    # adjoint timing (reported beside the metric, not part of the step)
+    fmm.build_tree(x)
+    g_adj = torch.empty_like(phi)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    psi, _ = fmm.adjoint(q)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    adjoint_ms = a0.elapsed_time(a1)
+    fmm.evaluate_into(q, phi, grad)
+    torch.cuda.synchronize()
+
+    # roofline of the dominant kernel
+    peaks, peak_src = read_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tf = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    near_ms = statistics.median(p["near"] for p in phases)
+    m2l_ms = statistics.median(p["m2l"] for p in phases)
+    up_ms = statistics.median(p["upward"] for p in phases)
+    down_ms = statistics.median(p["downward"] for p in phases)
+    pairs = info["p2p_pairs"]
+    p2p = {"bound": "alu", "achieved": pairs * FLOPS_PER_PAIR / (near_ms * 1e-3) / 1e12,
+           "peak": fp32_peak_tf, "unit": "TFLOP/s",
+           "kernel": "p2p_kernel (ULI near field)",
+           "peak_basis": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz "
+                         f"(max SM clock, {peak_src} peaks file); {FLOPS_PER_PAIR} flops per pair",
+           "pairs": pairs, "ms": near_ms}
+    p2p["frac"] = p2p["achieved"] / p2p["peak"]
+    p2p["traffic"] = recorded_traffic("p2p_kernel", source_digest("p2p.cu"))
+    # M2L algorithmic flops: compress + stencil products over the real V pairs + decompress
+    kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"]
+    vpairs = 0
+    m2l_flops = 0.0
+    for level in range(2, w.depth + 1):
+        nl = info["n_boxes"][level]
+        lv = fmm.export_level(level, lists=True)
+        nv = len(lv["v_idx"])
+        vpairs += nv
+        m2l_flops += 2.0 * kin * ns * nl + 2.0 * kout * kin * nv
+    tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3")
+    if tensor:
+        mult = {"bf16x3": 3, "bf16x6": 6, "tf32x3": 3}[args.precision]
+        base = float(peaks["bf16_tflops_sustained"]) * (0.5 if args.precision == "tf32x3" else 1.0)
+        m2l = {"bound": "tensor", "achieved": mult * m2l_flops / (m2l_ms * 1e-3) / 1e12,
+               "peak": base, "unit": "TFLOP/s",
+               "peak_basis": f"{peak_src} bf16 sustained" + (" x 1/2 (tf32 nominal ratio)"
+                                                           if args.precision == "tf32x3" else ""),
+               "split_products": mult}
+    else:
+        m2l = {"bound": "alu", "achieved": m2l_flops / (m2l_ms * 1e-3) / 1e12,
+               "peak": fp32_peak_tf if not fp64 else None, "unit": "TFLOP/s",
+               "peak_basis": "FP32 FMA pipe (SIMT contraction)"}
+    m2l.update({"kernel": "M2L phase: compress + stencil GEMMs, all levels", "ms": m2l_ms,
+                "v_pairs": vpairs, "algorithmic_flops": m2l_flops})
+    m2l["frac"] = (m2l["achieved"] / m2l["peak"]) if m2l["peak"] else None
+    m2l["traffic"] = None
+    dominant, other = (p2p, m2l) if near_ms >= m2l_ms else (m2l, p2p)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
+                       "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                       "step": "build_tree + evaluate(potential+gradient)",
+                       "parallelism": f"replicas x{ws}"},
+            "phases_ms": {"near_p2p": near_ms, "upward": up_ms, "m2l": m2l_ms,
+                          "downward": down_ms,
+                          "evaluate_total": statistics.median(p["total"] for p in phases),
+                          "build_tree": ms_per_step - statistics.median(p["total"] for p in phases),
+                          "adjoint": adjoint_ms},
+            "roofline": dominant, "roofline_other": other,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["accuracy"] = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
+                                          grad.cpu().numpy().astype(np.float64))
+        line["cpu_baseline"] = cpu_baseline_sample(w.p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fmm.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

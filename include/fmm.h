@@ -1,0 +1,179 @@
+/*
+ * fmm.h - C ABI of libfmm: a kernel-independent fast multipole method (kiFMM) for the 3D
+ * Laplace kernel K(x, y) = 1 / (4 pi |x - y|) over a Morton-keyed uniform octree, evaluated on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * What is computed (the paper's problem statement, Section 1, Eq. 1 with the kernel of Eq. 2
+ * normalised by 4 pi): for N points x_i that are both sources and targets, given in arbitrary
+ * order (Section 2.3), and densities s_j,
+ *     phi_i = sum_{j != i} K(x_i, x_j) s_j,   grad_i = grad_x phi(x_i),
+ * approximated by Algorithm 1 (uniform branches: S2U, U2U, VLI, D2D, D2T, ULI).  A built tree
+ * can be re-used with new densities (Section 3.1, step 6).
+ *
+ * Calling conventions shared by every entry point:
+ *  - Status codes only; nothing throws across the ABI.  After an error, fmm_last_error(ctx)
+ *    returns a message; the context stays usable unless the status is FMM_ECUDA.
+ *  - All GPU work is ordered on the CUDA stream given to fmm_create (NULL = legacy default).
+ *  - Array arguments may be device pointers or host pointers (pageable or pinned); the library
+ *    detects which with cudaPointerGetAttributes.  With device pointers a call returns as soon
+ *    as its work is enqueued; with host pointers it copies through library-owned device
+ *    buffers and returns after the results are back in host memory.
+ *  - Floating-point arrays are float (4 bytes) unless the context's precision is FMM_FP64,
+ *    in which case they are double.  Coordinates are N x 3 row-major (x0 y0 z0 x1 y1 z1 ...).
+ *  - The caller owns every array it passes; the library keeps no caller pointer after a call
+ *    returns.  The library owns the tree, the operators and all workspaces (allocated with
+ *    cudaMalloc by fmm_build_tree and fmm_precompute, released by fmm_destroy).
+ *  - One context must not be used by two host threads at the same time.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx fmm_ctx;
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_EINVAL = 1,        /* bad argument (null pointer, size, option out of range, NaN input) */
+    FMM_ENOMEM = 2,        /* a device or host allocation failed */
+    FMM_ECUDA = 3,         /* a CUDA call or kernel failed; the context should be destroyed */
+    FMM_ESTATE = 4,        /* call out of order (e.g. evaluate before build_tree/precompute) */
+    FMM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    FMM_EUNSUPPORTED = 6   /* option combination not available in this build */
+} fmm_status;
+
+/* Arithmetic of the surface contractions (U2U, VLI, D2D and the check-to-equivalent steps).
+ * The near field (ULI), the S2U check potentials and D2T always run in FP32 SIMT arithmetic,
+ * except under FMM_FP64 where everything is FP64. */
+typedef enum {
+    FMM_FP32 = 0,          /* FP32 SIMT everywhere */
+    FMM_FP64 = 1,          /* FP64 SIMT everywhere; inputs and outputs are double */
+    FMM_TF32X3 = 2,        /* contractions on tcgen05 tensor cores, 3 TF32 products (big/small split) */
+    FMM_BF16X3 = 3,        /* contractions on tcgen05 tensor cores, 3 BF16 products (hi/lo split) */
+    FMM_BF16X6 = 4         /* contractions on tcgen05 tensor cores, 6 BF16 products (hi/mid/lo split) */
+} fmm_precision;
+
+typedef struct {
+    int order_p;           /* expansion order p >= 2; each box vector has 6(p-1)^2+2 entries
+                              (Section 4, global portion).  Supported: 2..10. */
+    int depth;             /* uniform tree depth d, 0..10 (level 0 = root, d = leaves; Section 2.1) */
+    int precision;         /* an fmm_precision value */
+    double svd_rtol;       /* M2L operator compression: keep singular values >= svd_rtol * sigma_1 */
+    double pinv_rtol;      /* check-to-equivalent pseudo-inverse cutoff relative to sigma_1 */
+    int with_gradient;     /* nonzero: fmm_evaluate may be asked for gradients */
+    int has_domain;        /* nonzero: use origin/side below as the bounding cube */
+    double origin[3];      /* bounding cube corner (has_domain) */
+    double side;           /* bounding cube side > 0 (has_domain) */
+} fmm_options;
+
+/* Part selectors for fmm_evaluate_parts (Section 1, Eq. 3: near field + far field). */
+#define FMM_PART_NEAR 1    /* ULI: direct sums over the U lists */
+#define FMM_PART_FAR 2     /* S2U, U2U, VLI, D2D, D2T */
+#define FMM_PART_ALL 3
+
+/* Tree and operator sizes, filled by fmm_get_tree_info. */
+typedef struct {
+    int64_t n_points;
+    int32_t depth;
+    int32_t n_surface;         /* 6(p-1)^2+2 */
+    int32_t m2l_rank_in;       /* rank of the compressed M2L on the source side (0 before precompute) */
+    int32_t m2l_rank_out;      /* rank on the target side (0 before precompute) */
+    int64_t n_boxes[11];       /* non-empty boxes per level 0..depth */
+    int64_t n_u_entries;       /* total length of all U lists */
+    int64_t p2p_pairs;         /* sum over leaves of |leaf| * sum_{a in U(leaf)} |a| */
+    double origin[3];          /* the bounding cube actually used */
+    double side;
+} fmm_tree_info;
+
+/* Fill *opt with defaults: p = 6, depth = 4, FMM_FP32, svd_rtol = 1e-6, pinv_rtol = 1e-7,
+ * with_gradient = 1, no domain (the cube is taken from the points). */
+fmm_status fmm_default_options(fmm_options *opt);
+
+/* Create a context bound to the current CUDA device and `cuda_stream` (a cudaStream_t, may be
+ * NULL).  Validates the options (EINVAL) and allocates nothing on the device. */
+fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out);
+
+/* Build the octree over n points (Section 2.1): Morton keys at depth d, a stable radix sort,
+ * leaf ranges, per-level box tables and the U lists; V lists are stencil lookups (Section 2.2).
+ * xyz: n x 3 coordinates (float, or double under FMM_FP64), host or device.
+ * Errors: EINVAL for n <= 0, n > 2^31 - 1 or a non-finite coordinate; ENOMEM. */
+fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n);
+
+/* Host FP64 precompute of every operator (check-to-equivalent pseudo-inverses, U2U, D2D,
+ * the 316 M2L operators and their SVD compression) and upload in the context's precision.
+ * Independent of the points; may be called before or after fmm_build_tree. */
+fmm_status fmm_precompute(fmm_ctx *ctx);
+
+/* phi = A q (Algorithm 1), and grad phi if `grad` is non-NULL (requires with_gradient).
+ * q: n densities; phi: n outputs; grad: n x 3 outputs; all in the input order of the points.
+ * Errors: ESTATE before fmm_build_tree and fmm_precompute; EINVAL for null q/phi. */
+fmm_status fmm_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad);
+
+/* As fmm_evaluate, restricted to the parts in `parts` (FMM_PART_NEAR | FMM_PART_FAR). */
+fmm_status fmm_evaluate_parts(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts);
+
+/* psi = A^T g: the transpose of the map q -> phi computed by fmm_evaluate (the FMM is not
+ * exactly symmetric), by running every step of Algorithm 1 transposed in reverse order.
+ * If grad_psi is non-NULL it receives grad phi_g(x_i), the gradient of the potential generated
+ * by densities g (a forward pass); with it, d/dx_k of a loss L(phi) is
+ * g_k grad phi_q(x_k) + q_k grad phi_g(x_k) with g = dL/dphi and the tree held fixed.
+ * Same argument rules and errors as fmm_evaluate. */
+fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi);
+
+/* Sizes of the built tree and operators.  ESTATE before fmm_build_tree. */
+fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info);
+
+/* Copy the tree to host arrays (any pointer may be NULL to skip it):
+ *  perm[n]                  sorted position -> input index (stable sort by leaf key)
+ *  leaf_keys[n_leaf]        Morton keys of the non-empty leaves, ascending
+ *  leaf_offsets[n_leaf+1]   points of leaf b are sorted positions leaf_offsets[b] .. [b+1]-1
+ *  u_offsets[n_leaf+1], u_idx[n_u_entries]  U lists (CSR), leaf indices ascending
+ * Morton keys interleave x, y, z bits with x most significant in every triple. */
+fmm_status fmm_export_tree(fmm_ctx *ctx, int64_t *perm, uint64_t *leaf_keys,
+                           int64_t *leaf_offsets, int64_t *u_offsets, int64_t *u_idx);
+
+/* Copy one level's boxes and V lists to host arrays (pointers may be NULL):
+ *  keys[n_boxes[level]]     ascending Morton keys of the level's non-empty boxes
+ *  v_offsets[n+1], v_idx[], v_tvec[]   V lists (CSR) for level >= 2, box indices ascending;
+ *  v_tvec holds the transfer-vector index t in [0, 316): (source - target) in box units, in
+ *  the enumeration of [-3,3]^3 minus [-1,1]^3 with x slowest and z fastest.
+ * *n_v_entries receives the total V length (call once with v_idx = NULL to size the arrays).
+ * The V lists are built on the device for this call and freed before it returns. */
+fmm_status fmm_export_level(fmm_ctx *ctx, int level, uint64_t *keys, int64_t *v_offsets,
+                            int64_t *v_idx, int32_t *v_tvec, int64_t *n_v_entries);
+
+/* Copy the check potentials of the last fmm_evaluate (with its far field) at `level` in [2, d]
+ * to host memory: n_boxes[level] x n_surface values, row-major, float or double.
+ *  kind 0 (upward): row b approximates sum_{j in b} K(x^{uc}_b, x_j) s_j, the potential of the
+ *          sources inside box b on its upward check surface (exact at the leaf level);
+ *  kind 1 (downward): row b approximates the potential on b's downward check surface of the
+ *          sources outside b's colleagues and b itself (its far field, Section 1 Eq. 3).
+ * The surfaces: centre c_b + alpha r_b g, g the order-p grid on the boundary of [-1,1]^3 in
+ * lexicographic order, alpha = 2.95 (upward check) or 1.05 (downward check), r_b the half-width.
+ * Errors: ESTATE without such an evaluation; EINVAL for a bad level or kind. */
+fmm_status fmm_export_check(fmm_ctx *ctx, int level, int kind, void *host_out);
+
+/* Milliseconds spent in each phase of the last fmm_evaluate or fmm_adjoint, measured with CUDA
+ * events on the context's stream: [0] near field (the ULI kernel alone), [1] upward pass
+ * (S2U and U2U), [2] VLI (M2L compress and stencil products, all levels), [3] downward pass
+ * (decompress, D2D, closing, D2T), [4] whole call.  n <= 5 values are written. */
+fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n);
+
+/* Number of CUDA kernels this library has launched in the process so far (all contexts). */
+long long fmm_kernel_launches(void);
+
+/* Message for the last failed call on ctx ("" if none).  Never NULL. */
+const char *fmm_last_error(const fmm_ctx *ctx);
+
+/* Release every device and host resource of ctx (waits for its stream).  NULL is allowed. */
+void fmm_destroy(fmm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H */

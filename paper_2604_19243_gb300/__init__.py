@@ -1,0 +1,254 @@
+"""Python binding of libfmm, a GB300 (sm_103a) kernel-independent FMM for the 3D Laplace kernel.
+
+Argument marshalling only: every step of the FMM runs in the CUDA library behind the C ABI of
+include/fmm.h.  Importing this package does not build anything; call
+`paper_2604_19243_gb300.build.build()` first.  If the library is missing, every call raises.
+
+    fmm = FMM(p=6, depth=5, precision="fp32", domain=((0, 0, 0), 1.0))
+    fmm.build_tree(x)            # x: (N, 3) float32 torch tensor (CUDA or CPU) or NumPy array
+    fmm.precompute()
+    phi, grad = fmm.evaluate(q)  # same device and dtype as q
+    psi = fmm.adjoint(g)         # the transpose of q -> phi
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfmm.so")
+
+PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
+STATUS = {0: "FMM_OK", 1: "FMM_EINVAL", 2: "FMM_ENOMEM", 3: "FMM_ECUDA", 4: "FMM_ESTATE",
+          5: "FMM_ETIMEOUT", 6: "FMM_EUNSUPPORTED"}
+PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
+
+# C entry points declared in include/fmm.h (checked by the export test)
+ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
+                "fmm_evaluate", "fmm_evaluate_parts", "fmm_adjoint", "fmm_get_tree_info",
+                "fmm_export_tree", "fmm_export_level", "fmm_export_check", "fmm_last_timings",
+                "fmm_kernel_launches", "fmm_last_error", "fmm_destroy")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("order_p", ctypes.c_int), ("depth", ctypes.c_int), ("precision", ctypes.c_int),
+                ("svd_rtol", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
+                ("with_gradient", ctypes.c_int), ("has_domain", ctypes.c_int),
+                ("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("n_surface", ctypes.c_int32), ("m2l_rank_in", ctypes.c_int32),
+                ("m2l_rank_out", ctypes.c_int32), ("n_boxes", ctypes.c_int64 * 11),
+                ("n_u_entries", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libfmm (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfmm is not built ({LIB_PATH} missing); run "
+                               "paper_2604_19243_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sigs = {
+            "fmm_default_options": [ctypes.POINTER(Options)],
+            "fmm_create": [ctypes.POINTER(Options), vp, ctypes.POINTER(vp)],
+            "fmm_build_tree": [vp, vp, i64],
+            "fmm_precompute": [vp],
+            "fmm_evaluate": [vp, vp, vp, vp],
+            "fmm_evaluate_parts": [vp, vp, vp, vp, i32],
+            "fmm_adjoint": [vp, vp, vp, vp],
+            "fmm_get_tree_info": [vp, ctypes.POINTER(TreeInfo)],
+            "fmm_export_tree": [vp, vp, vp, vp, vp, vp],
+            "fmm_export_level": [vp, i32, vp, vp, vp, vp, vp],
+            "fmm_export_check": [vp, i32, i32, vp],
+            "fmm_last_timings": [vp, vp, i32],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.fmm_kernel_launches.argtypes = []
+        L.fmm_kernel_launches.restype = ctypes.c_longlong
+        L.fmm_last_error.argtypes = [vp]
+        L.fmm_last_error.restype = ctypes.c_char_p
+        L.fmm_destroy.argtypes = [vp]
+        L.fmm_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or NumPy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def kernel_launches():
+    """Kernels launched by libfmm in this process so far."""
+    return int(lib().fmm_kernel_launches())
+
+
+class FMM:
+    """One FMM context: a tree over a point set and the operators of one expansion order."""
+
+    def __init__(self, p=6, depth=4, precision="fp32", svd_rtol=1e-6, pinv_rtol=1e-7,
+                 with_gradient=True, domain=None, stream=None):
+        L = lib()
+        opt = Options()
+        L.fmm_default_options(ctypes.byref(opt))
+        opt.order_p, opt.depth = p, depth
+        opt.precision = PRECISIONS[precision]
+        opt.svd_rtol, opt.pinv_rtol = svd_rtol, pinv_rtol
+        opt.with_gradient = int(with_gradient)
+        if domain is not None:
+            opt.has_domain = 1
+            for a in range(3):
+                opt.origin[a] = float(domain[0][a])
+            opt.side = float(domain[1])
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        self._ctx = ctypes.c_void_p()
+        st = L.fmm_create(ctypes.byref(opt), ctypes.c_void_p(stream), ctypes.byref(self._ctx))
+        if st != 0:
+            raise FmmError(st, "fmm_create rejected the options")
+        self.p, self.depth, self.precision = p, depth, precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.n = 0
+
+    def _check(self, st):
+        if st != 0:
+            raise FmmError(st, lib().fmm_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            lib().fmm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- marshalling helpers ------------------------------------------------------------
+    def _like(self, ref, shape):
+        if isinstance(ref, np.ndarray):
+            return np.empty(shape, dtype=self.dtype)
+        import torch
+        return torch.empty(shape, dtype=ref.dtype, device=ref.device)
+
+    def _as_input(self, a):
+        if isinstance(a, np.ndarray):
+            return np.ascontiguousarray(a, dtype=self.dtype)
+        import torch
+        want = torch.float64 if self.dtype == np.float64 else torch.float32
+        return a.detach().to(want).contiguous()
+
+    # -- C entry points -----------------------------------------------------------------
+    def build_tree(self, x):
+        x = self._as_input(x)
+        self.n = int(x.shape[0])
+        self._check(lib().fmm_build_tree(self._ctx, _ptr(x), self.n))
+        return self
+
+    def precompute(self):
+        self._check(lib().fmm_precompute(self._ctx))
+        return self
+
+    def evaluate(self, q, gradient=True, parts=PART_ALL):
+        q = self._as_input(q)
+        phi = self._like(q, (self.n,))
+        grad = self._like(q, (self.n, 3)) if gradient else None
+        self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+        return phi, grad
+
+    def evaluate_into(self, q, phi, grad=None, parts=PART_ALL):
+        """fmm_evaluate_parts on caller-owned arrays (host or device, contiguous)."""
+        self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+
+    def adjoint(self, g, gradient=False):
+        g = self._as_input(g)
+        psi = self._like(g, (self.n,))
+        grad = self._like(g, (self.n, 3)) if gradient else None
+        self._check(lib().fmm_adjoint(self._ctx, _ptr(g), _ptr(psi), _ptr(grad)))
+        return psi, grad
+
+    def info(self):
+        ti = TreeInfo()
+        self._check(lib().fmm_get_tree_info(self._ctx, ctypes.byref(ti)))
+        return {"n_points": ti.n_points, "depth": ti.depth, "n_surface": ti.n_surface,
+                "m2l_rank_in": ti.m2l_rank_in, "m2l_rank_out": ti.m2l_rank_out,
+                "n_boxes": list(ti.n_boxes)[: ti.depth + 1], "n_u_entries": ti.n_u_entries,
+                "p2p_pairs": ti.p2p_pairs, "origin": list(ti.origin), "side": ti.side}
+
+    def export_tree(self):
+        inf = self.info()
+        nl = inf["n_boxes"][inf["depth"]]
+        perm = np.empty(self.n, np.int64)
+        keys = np.empty(nl, np.uint64)
+        loff = np.empty(nl + 1, np.int64)
+        uoff = np.empty(nl + 1, np.int64)
+        uidx = np.empty(inf["n_u_entries"], np.int64)
+        self._check(lib().fmm_export_tree(self._ctx, _ptr(perm), _ptr(keys), _ptr(loff),
+                                          _ptr(uoff), _ptr(uidx)))
+        return {"perm": perm, "leaf_keys": keys, "leaf_offsets": loff, "u_offsets": uoff,
+                "u_idx": uidx}
+
+    def export_level(self, level, lists=True):
+        inf = self.info()
+        nb = inf["n_boxes"][level]
+        keys = np.empty(nb, np.uint64)
+        if not lists:
+            self._check(lib().fmm_export_level(self._ctx, level, _ptr(keys), None, None, None, None))
+            return {"keys": keys}
+        cnt = ctypes.c_int64()
+        off = np.empty(nb + 1, np.int64)
+        self._check(lib().fmm_export_level(self._ctx, level, _ptr(keys), _ptr(off), None, None,
+                                           ctypes.addressof(cnt)))
+        idx = np.empty(cnt.value, np.int64)
+        tv = np.empty(cnt.value, np.int32)
+        self._check(lib().fmm_export_level(self._ctx, level, None, None, _ptr(idx), _ptr(tv),
+                                           ctypes.addressof(cnt)))
+        return {"keys": keys, "v_offsets": off, "v_idx": idx, "v_tvec": tv}
+
+    def export_check(self, level, kind="upward"):
+        """Check potentials of the last evaluate at `level` (n_boxes x n_surface)."""
+        inf = self.info()
+        out = np.empty((inf["n_boxes"][level], inf["n_surface"]), dtype=self.dtype)
+        self._check(lib().fmm_export_check(self._ctx, level, {"upward": 0, "downward": 1}[kind],
+                                           _ptr(out)))
+        return out
+
+    def timings(self):
+        """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""
+        ms = np.zeros(5, np.float64)
+        self._check(lib().fmm_last_timings(self._ctx, _ptr(ms), 5))
+        return dict(zip(("near", "upward", "m2l", "downward", "total"), ms.tolist()))
+
+
+from .autograd import FmmFunction, fmm_energy  # noqa: E402,F401

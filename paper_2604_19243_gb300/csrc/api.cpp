@@ -1,0 +1,516 @@
+// C ABI of libfmm (include/fmm.h): argument checks, context state, host/device staging and the
+// order of the evaluation steps.  No C++ exception crosses this boundary.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fmm_internal.h"
+
+using namespace fmm;
+
+namespace fmm {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace fmm
+
+namespace {
+
+fmm_status fail(fmm_ctx *ctx, fmm_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+fmm_status cuda_fail(fmm_ctx *ctx, cudaError_t e, const char *where) {
+    cudaGetLastError();   // clear a non-sticky error
+    return fail(ctx, FMM_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                                    cudaGetErrorString(e) + ")");
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_size(const fmm_ctx *ctx) { return ctx->fp64 ? sizeof(double) : sizeof(float); }
+
+template <typename P>
+void free_async(P *&p, cudaStream_t s) {
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+void free_workspace(fmm_ctx *ctx) {
+    cudaStream_t s = ctx->stream;
+    free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
+    free_async(ctx->Yc, s), free_async(ctx->Dq, s);
+    free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
+    free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
+    free_async(ctx->stage_in, s), free_async(ctx->stage_out, s), free_async(ctx->stage_grad, s);
+    for (int l = 0; l <= kMaxDepth; ++l)
+        for (TileSet *ts : {&ctx->tiles_plain[l], &ctx->tiles_cls[l]}) {
+            free_async(ts->tiles, s), free_async(ts->masks, s);
+            ts->host.clear();
+            ts->ntiles = 0;
+        }
+    ctx->have_ws = false;
+    ctx->ws_bytes = 0;
+}
+
+void free_tree(fmm_ctx *ctx) {
+    free_workspace(ctx);
+    cudaStream_t s = ctx->stream;
+    free_async(ctx->pts, s), free_async(ctx->perm, s), free_async(ctx->leaf_off, s);
+    free_async(ctx->u_off, s), free_async(ctx->u_idx, s), free_async(ctx->p2p_order, s);
+    free_async(ctx->class_slots, s), free_async(ctx->class_delta, s);
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        LevelTables &L = ctx->lev[l];
+        free_async(L.keys, s), free_async(L.parent, s), free_async(L.child, s);
+        free_async(L.dense, s), free_async(L.cls_rows, s);
+        L = LevelTables{};
+    }
+    ctx->have_tree = false;
+    ctx->n = 0;
+    ctx->nleaf = 0;
+}
+
+void free_ops(fmm_ctx *ctx) {
+    cudaStreamSynchronize(ctx->stream);
+    for (void *p : ctx->op_allocs) cudaFree(p);
+    ctx->op_allocs.clear();
+    tc_free(ctx);
+    ctx->fwd = OpSet{};
+    ctx->adj = OpSet{};
+    ctx->grid_dev = nullptr;
+    ctx->have_ops = false;
+}
+
+fmm_status ensure_workspace(fmm_ctx *ctx) {
+    if (ctx->have_ws) return FMM_OK;
+    cudaStream_t s = ctx->stream;
+    const size_t es = elem_size(ctx);
+    const int nsp = ctx->nsp;
+    const int kw = std::max(std::max(ctx->fwd.kinp, ctx->fwd.koutp), 16);
+    ctx->ws_kw = kw;
+    const int64_t rows = ctx->total_rows, nl = ctx->nleaf, n = ctx->n;
+    struct A {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {&ctx->Uc, (size_t)rows * nsp * es},   {&ctx->Dc, (size_t)rows * nsp * es},
+        {&ctx->Ut, (size_t)rows * kw * es},    {&ctx->Ct, (size_t)rows * kw * es},
+        {&ctx->Yc, (size_t)nl * ctx->fwd.rclp * es},
+        {&ctx->Dq, (size_t)nl * nsp * es},     {&ctx->near_phi, (size_t)n * es},
+        {&ctx->near_grad, (size_t)n * 3 * es}, {&ctx->far_phi, (size_t)n * es},
+        {&ctx->far_grad, (size_t)n * 3 * es},
+    };
+    size_t total = 0;
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMallocAsync(a.p, std::max<size_t>(a.bytes, 16), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(ctx);
+            return fail(ctx, FMM_ENOMEM, "workspace allocation of " + std::to_string(a.bytes) + " bytes failed");
+        }
+        total += a.bytes;
+    }
+    // rows that no step writes (levels 0-1, unused padding) must read as zero
+    for (void **p : {&ctx->Uc, &ctx->Dc, &ctx->Ut, &ctx->Ct}) {
+        size_t b = (p == &ctx->Uc || p == &ctx->Dc) ? (size_t)rows * nsp * es : (size_t)rows * kw * es;
+        cudaMemsetAsync(*p, 0, b, s);
+    }
+    cudaError_t e = build_tiles(ctx, ctx->tensor ? 128 : 64);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile construction");
+    ctx->ws_bytes = total;
+    ctx->have_ws = true;
+    return FMM_OK;
+}
+
+// device view of a caller array: either the pointer itself or a staging buffer
+struct Staged {
+    void *dev = nullptr;
+    bool host = false;
+};
+
+fmm_status stage(fmm_ctx *ctx, const void *p, size_t bytes, bool copy_in, void **slot, Staged *out) {
+    out->host = !is_device_ptr(p);
+    if (!out->host) {
+        out->dev = const_cast<void *>(p);
+        return FMM_OK;
+    }
+    if (!*slot) {
+        if (cudaMallocAsync(slot, std::max<size_t>(bytes, 16), ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FMM_ENOMEM, "staging allocation failed");
+        }
+    }
+    out->dev = *slot;
+    if (copy_in) {
+        cudaError_t e = cudaMemcpyAsync(*slot, p, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+    }
+    return FMM_OK;
+}
+
+template <typename T>
+fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts, bool adjoint) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n;
+    Staged sq, sphi, sgrad;
+    fmm_status st;
+    if ((st = stage(ctx, q, n * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
+    if ((st = stage(ctx, phi, n * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
+    if (grad && (st = stage(ctx, grad, 3 * n * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
+    cudaError_t e;
+    cudaEventRecord(ctx->ev[0], s);
+    if ((e = launch_gather_points<T>((const T *)sq.dev, ctx->perm, ctx->pts, n, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "gather");
+    cudaEventRecord(ctx->ev[7], s);
+    const bool near = parts & FMM_PART_NEAR;
+    const bool far = (parts & FMM_PART_FAR) && ctx->opt.depth >= 2;
+    T *ng = (grad && !adjoint) ? (T *)ctx->near_grad : nullptr;
+    T *fg = (grad && !adjoint) ? (T *)ctx->far_grad : nullptr;
+    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "near field");
+    cudaEventRecord(ctx->ev[1], s);
+    if (far) {
+        e = run_far<T>(ctx, adjoint, (T *)ctx->far_phi, fg, s);
+        if (e == cudaErrorNotSupported)
+            return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "far field");
+    } else {
+        cudaEventRecord(ctx->ev[2], s), cudaEventRecord(ctx->ev[3], s), cudaEventRecord(ctx->ev[4], s);
+    }
+    cudaEventRecord(ctx->ev[5], s);
+    e = launch_scatter<T>(near ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
+                          far ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
+                          (T *)sphi.dev, (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter");
+    cudaEventRecord(ctx->ev[6], s);
+    if (sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if (grad && !adjoint && sgrad.host &&
+        (e = cudaMemcpyAsync(grad, sgrad.dev, 3 * n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if (sq.host || sphi.host || (grad && sgrad.host)) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    }
+    ctx->last_adjoint = adjoint;
+    ctx->last_far = far;
+    return FMM_OK;
+}
+
+fmm_status check_ready(fmm_ctx *ctx, const void *q, const void *phi) {
+    if (!ctx) return FMM_EINVAL;
+    if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
+    if (!ctx->have_ops) return fail(ctx, FMM_ESTATE, "fmm_precompute has not been called");
+    if (!q || !phi) return fail(ctx, FMM_EINVAL, "null density or output pointer");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    return ensure_workspace(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status fmm_default_options(fmm_options *opt) {
+    if (!opt) return FMM_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->order_p = 6;
+    opt->depth = 4;
+    opt->precision = FMM_FP32;
+    opt->svd_rtol = 1e-6;
+    opt->pinv_rtol = 1e-7;
+    opt->with_gradient = 1;
+    opt->has_domain = 0;
+    opt->side = 1.0;
+    return FMM_OK;
+}
+
+fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) {
+    if (!opt || !out) return FMM_EINVAL;
+    *out = nullptr;
+    if (opt->order_p < 2 || opt->order_p > 10) return FMM_EINVAL;
+    if (opt->depth < 0 || opt->depth > kMaxDepth) return FMM_EINVAL;
+    if (opt->precision < FMM_FP32 || opt->precision > FMM_BF16X6) return FMM_EINVAL;
+    if (!(opt->svd_rtol > 0 && opt->svd_rtol < 1) || !(opt->pinv_rtol > 0 && opt->pinv_rtol < 1))
+        return FMM_EINVAL;
+    if (opt->has_domain) {
+        if (!(std::isfinite(opt->side) && opt->side > 0)) return FMM_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(opt->origin[a])) return FMM_EINVAL;
+    }
+    fmm_ctx *ctx = new (std::nothrow) fmm_ctx();
+    if (!ctx) return FMM_ENOMEM;
+    ctx->opt = *opt;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->fp64 = opt->precision == FMM_FP64;
+    ctx->tensor = opt->precision == FMM_TF32X3 || opt->precision == FMM_BF16X3 || opt->precision == FMM_BF16X6;
+    ctx->ns = 6 * (opt->order_p - 1) * (opt->order_p - 1) + 2;
+    ctx->nsp = round_up(ctx->ns, 16);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return FMM_ECUDA;
+    }
+    for (auto &e : ctx->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : ctx->ev)
+                if (x) cudaEventDestroy(x);
+            delete ctx;
+            return FMM_ECUDA;
+        }
+    }
+    *out = ctx;
+    return FMM_OK;
+}
+
+fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n) {
+    if (!ctx) return FMM_EINVAL;
+    if (!xyz) return fail(ctx, FMM_EINVAL, "null coordinate pointer");
+    if (n <= 0 || n > 2147483647LL) return fail(ctx, FMM_EINVAL, "n must be in [1, 2^31 - 1]");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    free_tree(ctx);
+    ctx->n = n;
+    const size_t bytes = (size_t)n * 3 * elem_size(ctx);
+    void *dev = const_cast<void *>(xyz);
+    void *tmp = nullptr;
+    if (!is_device_ptr(xyz)) {
+        if (cudaMallocAsync(&tmp, bytes, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FMM_ENOMEM, "staging allocation failed");
+        }
+        cudaError_t e = cudaMemcpyAsync(tmp, xyz, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+        dev = tmp;
+    }
+    cudaError_t e = build_tree(ctx, dev);
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (e == cudaErrorInvalidValue) {
+        free_tree(ctx);
+        return fail(ctx, FMM_EINVAL, "non-finite coordinate");
+    }
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        free_tree(ctx);
+        return fail(ctx, FMM_ENOMEM, "tree allocation failed");
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tree build");
+    ctx->have_tree = true;
+    return FMM_OK;
+}
+
+fmm_status fmm_precompute(fmm_ctx *ctx) {
+    if (!ctx) return FMM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    if (ctx->have_ops) return FMM_OK;
+    std::string err;
+    const HostOps *h = nullptr;
+    try {
+        h = host_operators(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, &err);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, FMM_ENOMEM, "host memory exhausted in precompute");
+    } catch (...) {
+        return fail(ctx, FMM_EINVAL, "precompute failed");
+    }
+    if (!h) return fail(ctx, FMM_EINVAL, "precompute failed: " + err);
+    ctx->host_ops = const_cast<HostOps *>(h);
+    cudaError_t e;
+    try {
+        e = upload_operators(ctx);
+    } catch (const std::bad_alloc &) {
+        free_ops(ctx);
+        return fail(ctx, FMM_ENOMEM, "host memory exhausted in operator upload");
+    }
+    if (e == cudaErrorNotSupported) {
+        free_ops(ctx);
+        return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
+    }
+    if (e != cudaSuccess) {
+        free_ops(ctx);
+        return cuda_fail(ctx, e, "operator upload");
+    }
+    free_workspace(ctx);   // operator ranks size the workspaces
+    ctx->have_ops = true;
+    return FMM_OK;
+}
+
+fmm_status fmm_evaluate_parts(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts) {
+    fmm_status st = check_ready(ctx, q, phi);
+    if (st != FMM_OK) return st;
+    if (grad && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
+    if (parts < 1 || parts > FMM_PART_ALL) return fail(ctx, FMM_EINVAL, "parts must be a nonempty subset of near|far");
+    return ctx->fp64 ? run_evaluate<double>(ctx, q, phi, grad, parts, false)
+                     : run_evaluate<float>(ctx, q, phi, grad, parts, false);
+}
+
+fmm_status fmm_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad) {
+    return fmm_evaluate_parts(ctx, q, phi, grad, FMM_PART_ALL);
+}
+
+fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
+    fmm_status st = check_ready(ctx, g, psi);
+    if (st != FMM_OK) return st;
+    if (grad_psi && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
+    st = ctx->fp64 ? run_evaluate<double>(ctx, g, psi, nullptr, FMM_PART_ALL, true)
+                   : run_evaluate<float>(ctx, g, psi, nullptr, FMM_PART_ALL, true);
+    if (st != FMM_OK || !grad_psi) return st;
+    // grad phi_g: a forward pass with densities g, potentials into scratch
+    void *scratch = ctx->far_phi;   // sorted-order buffer reused as the discarded potential
+    const size_t es = elem_size(ctx);
+    void *tmp = nullptr;
+    if (cudaMallocAsync(&tmp, (size_t)ctx->n * es, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FMM_ENOMEM, "scratch allocation failed");
+    }
+    (void)scratch;
+    st = ctx->fp64 ? run_evaluate<double>(ctx, g, tmp, grad_psi, FMM_PART_ALL, false)
+                   : run_evaluate<float>(ctx, g, tmp, grad_psi, FMM_PART_ALL, false);
+    cudaFreeAsync(tmp, ctx->stream);
+    if (st == FMM_OK) ctx->last_adjoint = true;
+    return st;
+}
+
+fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
+    if (!ctx || !info) return FMM_EINVAL;
+    if (!ctx->have_tree) return FMM_ESTATE;
+    std::memset(info, 0, sizeof(*info));
+    info->n_points = ctx->n;
+    info->depth = ctx->opt.depth;
+    info->n_surface = ctx->ns;
+    info->m2l_rank_in = ctx->have_ops ? ctx->fwd.kin : 0;
+    info->m2l_rank_out = ctx->have_ops ? ctx->fwd.kout : 0;
+    for (int l = 0; l <= ctx->opt.depth; ++l) info->n_boxes[l] = ctx->lev[l].n;
+    info->n_u_entries = ctx->n_u;
+    info->p2p_pairs = ctx->p2p_pairs;
+    for (int a = 0; a < 3; ++a) info->origin[a] = ctx->origin[a];
+    info->side = ctx->side;
+    return FMM_OK;
+}
+
+fmm_status fmm_export_tree(fmm_ctx *ctx, int64_t *perm, uint64_t *leaf_keys, int64_t *leaf_offsets,
+                           int64_t *u_offsets, int64_t *u_idx) {
+    if (!ctx) return FMM_EINVAL;
+    if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
+    cudaStream_t s = ctx->stream;
+    const int d = ctx->opt.depth;
+    auto copy_i32 = [&](const int *src, int64_t count, int64_t *dst) -> cudaError_t {
+        std::vector<int> h(count);
+        cudaError_t e = cudaMemcpyAsync(h.data(), src, count * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int64_t i = 0; i < count; ++i) dst[i] = h[i];
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (perm && e == cudaSuccess) e = copy_i32(ctx->perm, ctx->n, perm);
+    if (leaf_offsets && e == cudaSuccess) e = copy_i32(ctx->leaf_off, ctx->nleaf + 1, leaf_offsets);
+    if (u_offsets && e == cudaSuccess) e = copy_i32(ctx->u_off, ctx->nleaf + 1, u_offsets);
+    if (u_idx && e == cudaSuccess) e = copy_i32(ctx->u_idx, ctx->n_u, u_idx);
+    if (leaf_keys && e == cudaSuccess) {
+        std::vector<uint32_t> h(ctx->nleaf);
+        e = cudaMemcpyAsync(h.data(), ctx->lev[d].keys, ctx->nleaf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int i = 0; i < ctx->nleaf; ++i) leaf_keys[i] = h[i];
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export");
+    return FMM_OK;
+}
+
+fmm_status fmm_export_level(fmm_ctx *ctx, int level, uint64_t *keys, int64_t *v_offsets, int64_t *v_idx,
+                            int32_t *v_tvec, int64_t *n_v_entries) {
+    if (!ctx) return FMM_EINVAL;
+    if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
+    if (level < 0 || level > ctx->opt.depth) return fail(ctx, FMM_EINVAL, "level out of range");
+    cudaStream_t s = ctx->stream;
+    const LevelTables &L = ctx->lev[level];
+    cudaError_t e = cudaSuccess;
+    if (keys) {
+        std::vector<uint32_t> h(L.n);
+        e = cudaMemcpyAsync(h.data(), L.keys, L.n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int64_t i = 0; i < L.n; ++i) keys[i] = h[i];
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export");
+    if (level < 2) {
+        if (v_offsets)
+            for (int64_t i = 0; i <= L.n; ++i) v_offsets[i] = 0;
+        if (n_v_entries) *n_v_entries = 0;
+        return FMM_OK;
+    }
+    if (v_offsets || v_idx || v_tvec || n_v_entries) {
+        try {
+            e = export_v_lists(ctx, level, v_offsets, v_idx, v_tvec, n_v_entries);
+        } catch (const std::bad_alloc &) {
+            return fail(ctx, FMM_ENOMEM, "host memory exhausted in export");
+        }
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(ctx, FMM_ENOMEM, "device memory exhausted in export");
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "V-list export");
+    }
+    return FMM_OK;
+}
+
+fmm_status fmm_export_check(fmm_ctx *ctx, int level, int kind, void *host_out) {
+    if (!ctx || !host_out) return FMM_EINVAL;
+    if (!ctx->have_ws || ctx->last_adjoint || !ctx->last_far)
+        return fail(ctx, FMM_ESTATE, "no forward far-field evaluation to export");
+    if (level < 2 || level > ctx->opt.depth) return fail(ctx, FMM_EINVAL, "level must be in [2, depth]");
+    if (kind != 0 && kind != 1) return fail(ctx, FMM_EINVAL, "kind must be 0 (upward) or 1 (downward)");
+    const size_t es = elem_size(ctx);
+    const LevelTables &L = ctx->lev[level];
+    const void *src = kind == 0 ? ctx->Uc : ctx->Dc;
+    std::vector<unsigned char> h((size_t)L.n * ctx->nsp * es);
+    cudaError_t e = cudaMemcpyAsync(h.data(), (const unsigned char *)src + (size_t)L.row_base * ctx->nsp * es,
+                                    h.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export");
+    for (int64_t b = 0; b < L.n; ++b)
+        std::memcpy((unsigned char *)host_out + (size_t)b * ctx->ns * es, h.data() + (size_t)b * ctx->nsp * es,
+                    ctx->ns * es);
+    return FMM_OK;
+}
+
+fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n) {
+    if (!ctx || !ms || n < 0) return FMM_EINVAL;
+    if (cudaEventSynchronize(ctx->ev[6]) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "timings");
+    float t[5] = {};
+    cudaEventElapsedTime(&t[0], ctx->ev[7], ctx->ev[1]);
+    cudaEventElapsedTime(&t[1], ctx->ev[1], ctx->ev[3]);
+    cudaEventElapsedTime(&t[2], ctx->ev[3], ctx->ev[4]);
+    cudaEventElapsedTime(&t[3], ctx->ev[4], ctx->ev[5]);
+    cudaEventElapsedTime(&t[4], ctx->ev[0], ctx->ev[6]);
+    cudaGetLastError();
+    for (int i = 0; i < n && i < 5; ++i) ms[i] = t[i];
+    return FMM_OK;
+}
+
+long long fmm_kernel_launches(void) { return launches(); }
+
+const char *fmm_last_error(const fmm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void fmm_destroy(fmm_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_tree(ctx);
+    free_ops(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

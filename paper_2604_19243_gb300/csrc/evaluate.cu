@@ -1,0 +1,227 @@
+// Evaluation pipeline (Algorithm 1, uniform branches) and its transpose.
+//
+// Forward, with boxes holding check potentials (fmm_internal.h):
+//   S2U   U_d  = K(uc, y) s                          leaf check kernel
+//   U2U   U_l  = sum_c A_c U_{l+1}[child_c]          l = d-1 .. 2 (levels 0-1 take no part)
+//   VLI   Ut_l = Vi^T U_l ; Ct_l[b] = sum_t C_t Ut_l[b + t] ; D_l = Uo Ct_l   l = 2 .. d
+//   D2D   D_l += B_c D_{l-1}[parent]                 fused with the VLI decompress, l >= 3
+//   D2T   d = r_d (V S^-1)(U^T D_d) ; f = K(x, de) d
+//   ULI   f += near-field sums                       independent of the rest (Section 2.2)
+// Adjoint (psi = A^T g): the same sequence with every operator transposed and the roles of the
+// upward and downward arrays exchanged: D2T^T is the leaf check kernel on the 2.95 surface,
+// the closing pseudo-inverse is applied transposed, D2D^T gathers children like U2U, the VLI
+// runs with C_{-t}^T, U2U^T gathers the parent like D2D and S2U^T evaluates the 2.95 surface
+// at the points like D2T.  ULI is symmetric.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "devutil.cuh"
+#include "gemm_common.cuh"
+
+namespace fmm {
+
+GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c) {
+    GemmDev g{};
+    g.mode = c.mode;
+    g.accumulate = c.accumulate;
+    g.n_out = c.n_out;
+    g.level = c.level;
+    g.alpha = (float)c.alpha;
+    g.alpha_d = c.alpha;
+    g.X0 = c.X0, g.ldx0 = c.ldx0, g.k0 = c.k0;
+    g.W0 = c.W0, g.w_stride = c.w_stride;
+    g.X1 = c.X1, g.ldx1 = c.ldx1, g.k1 = c.k1;
+    for (int i = 0; i < 8; ++i) g.W1[i] = c.W1_by_cls ? c.W1_by_cls[i] : nullptr;
+    g.Y = c.Y, g.ldy = c.ldy;
+    const LevelTables &L = ctx->lev[c.level];
+    const bool cls = c.mode == GM_STENCIL || c.mode == GM_PARENT2;
+    g.rows = cls ? L.cls_rows : nullptr;
+    g.child = L.child;
+    g.parent = L.parent;
+    g.keys = L.keys;
+    g.dense = L.dense;
+    g.class_slots = ctx->class_slots;
+    g.class_delta = ctx->class_delta;
+    return g;
+}
+
+namespace {
+
+template <typename T>
+cudaError_t gemm(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream_t s) {
+    if (ctx->tensor) return gemm_tc(ctx, c, op_id, s);
+    return gemm_simt<T>(ctx, c, s);
+}
+
+template <typename T>
+T *rows_at(void *base, const fmm_ctx *ctx, int level, int ld) {
+    return (T *)base + (size_t)ctx->lev[level].row_base * ld;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
+    const OpSet &o = adjoint ? ctx->adj : ctx->fwd;
+    const int d = ctx->opt.depth;
+    const int nsp = ctx->nsp;
+    const int kw = ctx->ws_kw;   // row stride of Ut / Ct
+    void *A = adjoint ? ctx->Dc : ctx->Uc;   // upward-side array of this direction
+    void *B = adjoint ? ctx->Uc : ctx->Dc;   // downward-side array
+    const T *grid = (const T *)ctx->grid_dev;
+    const double r_leaf = ctx->side / (double)(1 << d) * 0.5;
+    const int dir = adjoint ? 1 : 0;
+
+    // leaf stage
+    if (!adjoint) {
+        FMM_CUDA_TRY(launch_leaf_check<T>(ctx, grid, rows_at<T>(A, ctx, d, nsp), s));
+    } else {
+        FMM_CUDA_TRY(launch_leaf_check<T>(ctx, grid, (T *)ctx->Dq, s));
+        GemmCall c1;
+        c1.mode = GM_IDENTITY, c1.level = d, c1.n_out = o.rclp;
+        c1.X0 = ctx->Dq, c1.ldx0 = nsp, c1.k0 = nsp, c1.W0 = o.close1;
+        c1.Y = ctx->Yc, c1.ldy = o.rclp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c1, OP_CLOSE1 + dir * OP_COUNT, s));
+        GemmCall c2;
+        c2.mode = GM_IDENTITY, c2.level = d, c2.n_out = nsp, c2.alpha = r_leaf;
+        c2.X0 = ctx->Yc, c2.ldx0 = o.rclp, c2.k0 = o.rclp, c2.W0 = o.close2;
+        c2.Y = rows_at<T>(A, ctx, d, nsp), c2.ldy = nsp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c2, OP_CLOSE2 + dir * OP_COUNT, s));
+    }
+    cudaEventRecord(ctx->ev[2], s);
+    // upward sweep
+    for (int l = d - 1; l >= 2; --l) {
+        GemmCall c;
+        c.mode = GM_CHILDREN, c.level = l, c.n_out = nsp;
+        c.X0 = rows_at<T>(A, ctx, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
+        c.W0 = o.up[0], c.w_stride = (int64_t)nsp * nsp;
+        c.Y = rows_at<T>(A, ctx, l, nsp), c.ldy = nsp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_UP + dir * OP_COUNT, s));
+    }
+    cudaEventRecord(ctx->ev[3], s);
+    // VLI
+    for (int l = 2; l <= d; ++l) {
+        GemmCall c;
+        c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
+        c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
+        c.Y = rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;
+        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, s));
+        GemmCall st;
+        st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
+        st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
+        st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
+        st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
+        FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, s));
+    }
+    cudaEventRecord(ctx->ev[4], s);
+    // downward sweep: decompress fused with the parent's contribution
+    for (int l = 2; l <= d; ++l) {
+        GemmCall c;
+        c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
+        c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = o.decompress;
+        if (l >= 3) {
+            c.X1 = rows_at<T>(B, ctx, l - 1, nsp), c.ldx1 = nsp, c.k1 = nsp;
+            c.W1_by_cls = o.down;
+        }
+        c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_DECOMPRESS + dir * OP_COUNT, s));
+    }
+    // leaf output
+    if (!adjoint) {
+        GemmCall c1;
+        c1.mode = GM_IDENTITY, c1.level = d, c1.n_out = o.rclp;
+        c1.X0 = rows_at<T>(B, ctx, d, nsp), c1.ldx0 = nsp, c1.k0 = nsp, c1.W0 = o.close1;
+        c1.Y = ctx->Yc, c1.ldy = o.rclp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c1, OP_CLOSE1, s));
+        GemmCall c2;
+        c2.mode = GM_IDENTITY, c2.level = d, c2.n_out = nsp, c2.alpha = r_leaf;
+        c2.X0 = ctx->Yc, c2.ldx0 = o.rclp, c2.k0 = o.rclp, c2.W0 = o.close2;
+        c2.Y = ctx->Dq, c2.ldy = nsp;
+        FMM_CUDA_TRY(gemm<T>(ctx, c2, OP_CLOSE2, s));
+        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, (const T *)ctx->Dq, nsp, (T)1, far_phi, far_grad, s));
+    } else {
+        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, rows_at<T>(B, ctx, d, nsp), nsp, (T)1, far_phi,
+                                         nullptr, s));
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t run_far<float>(fmm_ctx *, bool, float *, float *, cudaStream_t);
+template cudaError_t run_far<double>(fmm_ctx *, bool, double *, double *, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// operator upload (SIMT layouts: row-major, zero padded)
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+cudaError_t upload_padded(fmm_ctx *ctx, const std::vector<double> &w, int rows, int cols,
+                          int rows_p, int cols_p, int count, void **out) {
+    std::vector<T> h((size_t)count * rows_p * cols_p, (T)0);
+    for (int m = 0; m < count; ++m)
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j)
+                h[(size_t)m * rows_p * cols_p + (size_t)i * cols_p + j] =
+                    (T)w[(size_t)m * rows * cols + (size_t)i * cols + j];
+    void *p = nullptr;
+    FMM_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(T)));
+    ctx->op_allocs.push_back(p);
+    FMM_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *out = p;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, OpSet &o) {
+    const int ns = h.ns, nsp = round_up(ns, 16);
+    o.ns = ns, o.nsp = nsp;
+    o.kin = adjoint ? h.kout : h.kin;
+    o.kout = adjoint ? h.kin : h.kout;
+    o.kinp = round_up(o.kin, 16), o.koutp = round_up(o.kout, 16);
+    o.rcl = h.rcl, o.rclp = round_up(h.rcl, 16);
+    const auto &up = adjoint ? h.a_up : h.up;
+    const auto &down = adjoint ? h.a_down : h.down;
+    // the 8 U2U operators contiguous so that W0 + c * nsp * nsp addresses octant c
+    std::vector<double> ups;
+    for (int c = 0; c < 8; ++c) ups.insert(ups.end(), up[c].begin(), up[c].end());
+    FMM_CUDA_TRY(upload_padded<T>(ctx, ups, ns, ns, nsp, nsp, 8, &o.up[0]));
+    for (int c = 1; c < 8; ++c) o.up[c] = (T *)o.up[0] + (size_t)c * nsp * nsp;
+    for (int c = 0; c < 8; ++c) FMM_CUDA_TRY(upload_padded<T>(ctx, down[c], ns, ns, nsp, nsp, 1, &o.down[c]));
+    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_compress : h.compress, o.kin, ns, o.kinp, nsp, 1, &o.compress));
+    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_stencil : h.stencil, o.kout, o.kin, o.koutp, o.kinp,
+                                  kNumTransfer, &o.stencil));
+    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_decompress : h.decompress, ns, o.kout, nsp, o.koutp, 1,
+                                  &o.decompress));
+    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close1 : h.close1, h.rcl, ns, o.rclp, nsp, 1, &o.close1));
+    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close2 : h.close2, ns, h.rcl, nsp, o.rclp, 1, &o.close2));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t upload_operators(fmm_ctx *ctx) {
+    const HostOps &h = *ctx->host_ops;
+    if (ctx->fp64) {
+        FMM_CUDA_TRY(upload_set<double>(ctx, h, false, ctx->fwd));
+        FMM_CUDA_TRY(upload_set<double>(ctx, h, true, ctx->adj));
+    } else {
+        FMM_CUDA_TRY(upload_set<float>(ctx, h, false, ctx->fwd));
+        FMM_CUDA_TRY(upload_set<float>(ctx, h, true, ctx->adj));
+    }
+    if (ctx->tensor) FMM_CUDA_TRY(tc_upload_operators(ctx));
+    // unit surface grid in the storage type
+    std::vector<double> g = surface_grid(ctx->opt.order_p);
+    size_t bytes = g.size() * (ctx->fp64 ? sizeof(double) : sizeof(float));
+    FMM_CUDA_TRY(cudaMalloc(&ctx->grid_dev, bytes));
+    ctx->op_allocs.push_back(ctx->grid_dev);
+    if (ctx->fp64) {
+        FMM_CUDA_TRY(cudaMemcpy(ctx->grid_dev, g.data(), bytes, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(g.begin(), g.end());
+        FMM_CUDA_TRY(cudaMemcpy(ctx->grid_dev, f.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fmm

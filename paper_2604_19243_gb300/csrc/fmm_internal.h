@@ -1,0 +1,239 @@
+// Internal declarations of libfmm (not part of the C ABI).
+//
+// Representation.  Every box carries *check potentials* instead of equivalent densities:
+//   U_l[b] = potential on the upward-check surface of box b due to the sources inside b,
+//   D_l[b] = potential on the downward-check surface of b due to the sources far from b.
+// The kiFMM operators of Table 1 then become products "evaluation o pseudo-inverse" formed in
+// FP64 on the host, which are smooth and bounded, so they can be applied in FP32 or in split
+// BF16/TF32 without the rounding amplification an explicit pseudo-inverse would cause:
+//   U2U  U_P  = sum_c A_c U_c,        A_c = K(uc_P, ue_c) pinv(K(uc_c, ue_c))
+//   VLI  D_b += sum_{a in V(b)} T_t U_a,  T_t = K(dc_b, ue_a) pinv(K(uc_a, ue_a)) ~ Uo C_t Vi^T
+//   D2D  D_c += B_c D_P,              B_c = K(dc_c, de_P) pinv(K(dc_P, de_P))
+//   D2T  d_b  = pinv(K(dc_b, de_b)) D_b  (factored: (V S^-1)(U^T D_b)), f += K(x, de_b) d_b
+// All of these are level-invariant in units of the box half-width (K is homogeneous of degree
+// -1); only the leaf closing carries the factor r_leaf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+constexpr int kMaxDepth = 10;
+constexpr int kNumTransfer = 316;     // [-3,3]^3 minus [-1,1]^3
+constexpr int kClassSlots = 189;      // transfer vectors with adjacent parents, per octant
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Operators of one direction (forward or adjoint) in one arithmetic, device-resident.
+// Row-major [rows x cols] with cols padded: a matrix applied to a padded row vector.
+struct OpSet {
+    // host-side shapes
+    int ns = 0, nsp = 0;        // surface size and its padding to 16
+    int kin = 0, kinp = 0;      // M2L compressed source rank (Vi^T: kin x ns)
+    int kout = 0, koutp = 0;    // M2L compressed target rank (Uo: ns x kout)
+    int rcl = 0, rclp = 0;      // leaf-closing rank
+    // Device pointers (element type = the context's storage type for SIMT; split planes for
+    // tensor-core arithmetic live in TcOps).
+    void *up[8] = {};           // U2U (children -> parent) per octant: [nsp x nsp]
+    void *down[8] = {};         // D2D (parent -> child) per child octant: [nsp x nsp]
+    void *compress = nullptr;   // [kinp x nsp]
+    void *stencil = nullptr;    // [316][koutp x kinp]
+    void *decompress = nullptr; // [nsp x koutp]
+    void *close1 = nullptr;     // [rclp x nsp]  (U^T)          forward: applied before D2T
+    void *close2 = nullptr;     // [nsp x rclp]  (V S^-1)
+};
+
+// Split operand planes for the tcgen05 GEMMs, laid out in the tensor-core K-major core-matrix
+// order (see gemm_tc.cu).  Planes: BF16x3 -> {hi, lo}; BF16x6 -> {hi, mid, lo}; TF32x3 ->
+// {big, small}.
+struct TcMat {
+    void *planes[3] = {};
+    int rows = 0, cols = 0;     // padded N x K
+    int nplanes = 0;
+};
+
+struct TcOpSet {
+    TcMat up[8], down[8], compress, decompress, close1, close2;
+    TcMat stencil[kNumTransfer];
+};
+
+struct HostOps;  // FP64 host operators (precompute.cpp)
+
+// Tile of output rows for the GEMM kernels: rows [row0, row0+nrows) of a level's row list,
+// all of one child octant class `cls` (or -1 when not class-ordered); `mask` indexes the
+// 6-word active-transfer bitmask of the tile (stencil GEMMs only).
+struct Tile {
+    int row0, nrows, cls, mask;
+};
+
+struct LevelTables {
+    int64_t n = 0;              // non-empty boxes
+    uint32_t *keys = nullptr;   // ascending Morton keys
+    int *parent = nullptr;      // index into level-1
+    int *child = nullptr;       // [n x 8] index into level+1, -1 if empty
+    int *dense = nullptr;       // [8^l] key -> index or -1 (levels >= 2)
+    int *cls_rows = nullptr;    // box indices ordered by octant (stable)
+    int cls_off[9] = {};        // host copy: class c rows are cls_rows[cls_off[c] .. cls_off[c+1])
+    int64_t row_base = 0;       // first row of this level in the all-level arrays
+};
+
+struct TileSet {                // tiles of one level for one tile height
+    int ntiles = 0;
+    Tile *tiles = nullptr;      // device
+    uint32_t *masks = nullptr;  // device [ntiles x 6] (stencil active-slot bits)
+    std::vector<Tile> host;
+};
+
+}  // namespace fmm
+
+struct fmm_ctx {
+    fmm_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool fp64 = false;
+    bool tensor = false;        // tcgen05 contractions
+    int ns = 0, nsp = 0;
+
+    // tree
+    bool have_tree = false;
+    int64_t n = 0;
+    double origin[3] = {0, 0, 0};
+    double side = 1.0;
+    int nleaf = 0;
+    void *pts = nullptr;        // sorted (x, y, z, q) as float4 or double4
+    int *perm = nullptr;        // sorted position -> input index
+    int *leaf_off = nullptr;    // [nleaf+1]
+    int *u_off = nullptr, *u_idx = nullptr;
+    int64_t n_u = 0;
+    int64_t p2p_pairs = 0;
+    fmm::LevelTables lev[fmm::kMaxDepth + 1];
+    int64_t total_rows = 0;     // sum of boxes over levels
+    // tiles per level: [0] plain order (children gather), [1] class order with stencil masks
+    fmm::TileSet tiles_plain[fmm::kMaxDepth + 1];
+    fmm::TileSet tiles_cls[fmm::kMaxDepth + 1];
+    int tile_m = 0;             // tile height the tile sets were built for
+    int *class_slots = nullptr; // device [8][189] transfer index of each slot
+    int *class_delta = nullptr; // device [8][189] packed (dx, dy, dz) of each slot
+    // P2P schedule: leaves in decreasing work order
+    int *p2p_order = nullptr;
+
+    // evaluate workspaces (allocated with the tree once operators are known)
+    bool have_ws = false;
+    void *Uc = nullptr, *Dc = nullptr;   // [total_rows x nsp] upward / downward check potentials
+    void *Ut = nullptr, *Ct = nullptr;   // [total_rows x ws_kw] compressed M2L vectors
+    void *Yc = nullptr;                  // [nleaf x rclp] closing intermediate
+    void *Dq = nullptr;                  // [nleaf x nsp] leaf equivalent densities
+    void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
+    void *far_phi = nullptr, *far_grad = nullptr;
+    size_t ws_bytes = 0;
+    int ws_kw = 0;
+    void *grid_dev = nullptr;            // unit surface grid [ns x 3] in the storage type
+    // host-pointer staging
+    void *stage_in = nullptr, *stage_out = nullptr, *stage_grad = nullptr;
+
+    // operators
+    bool have_ops = false;
+    fmm::HostOps *host_ops = nullptr;
+    fmm::OpSet fwd, adj;
+    fmm::TcOpSet *tc_fwd = nullptr, *tc_adj = nullptr;
+    std::vector<void *> op_allocs;
+
+    bool last_adjoint = false;  // what the last evaluation left in the workspaces
+    bool last_far = false;
+
+    // timings
+    cudaEvent_t ev[8] = {};
+    float last_ms[5] = {};
+    int *dev_flag = nullptr;    // device error flag (bounded waits, bounds checks)
+};
+
+namespace fmm {
+
+// Process-wide count of kernels launched by the library (every launch site calls it).
+void count_launch();
+long long launches();
+
+// ---- precompute.cpp ----
+struct HostOps {
+    int p = 0, ns = 0;
+    int kin = 0, kout = 0, rcl = 0;
+    std::vector<double> surf_inner, surf_outer;       // [ns x 3] unit grids scaled by alpha
+    std::vector<double> up[8], down[8];               // [ns x ns]
+    std::vector<double> compress;                     // [kin x ns]   Vi^T
+    std::vector<double> stencil;                      // [316][kout x kin]
+    std::vector<double> decompress;                   // [ns x kout]  Uo
+    std::vector<double> close1, close2;               // [rcl x ns], [ns x rcl] (unit box)
+    // adjoint (transposes)
+    std::vector<double> a_up[8], a_down[8], a_compress, a_stencil, a_decompress, a_close1,
+        a_close2;
+};
+// Build (or fetch from the process-wide cache) the FP64 operators for (p, pinv_rtol, svd_rtol).
+const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err);
+// Unit surface grid of order p (lexicographic), [n x 3] in [-1,1]^3.
+std::vector<double> surface_grid(int p);
+
+// ---- tree.cu ----
+cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz);
+cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, int32_t *tv,
+                           int64_t *count);
+cudaError_t build_tiles(fmm_ctx *ctx, int tile_m);
+
+// ---- kernels ----
+// Point kernels (p2p.cu).  T = float or double.
+template <typename T>
+cudaError_t launch_gather_points(const T *q_in, const int *perm, void *pts, int64_t n,
+                                 cudaStream_t s);
+// phi[perm[i]] = near_phi[i] + far_phi[i] (either may be null), same for grad if non-null
+template <typename T>
+cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_phi,
+                           const T *far_grad, const int *perm, T *phi, T *grad, int64_t n,
+                           cudaStream_t s);
+// ULI near field in sorted order (phi written, grad written if non-null)
+template <typename T>
+cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
+// check potentials on the 2.95 surface of every leaf from its own points -> rows [nleaf x nsp]
+template <typename T>
+cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s);
+// potentials (and gradients) at the points of every leaf from densities on its 2.95 surface
+template <typename T>
+cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
+                             T *phi, T *grad, cudaStream_t s);
+
+// Generic gathered GEMM (gemm_simt.cu / gemm_tc.cu): Y[rows] (+)= alpha sum_seg W_seg X[src(row,seg)].
+enum GatherMode { GM_IDENTITY = 0, GM_CHILDREN = 1, GM_PARENT2 = 2, GM_STENCIL = 3 };
+// operator ids (tensor-core operand planes); the adjoint set adds OP_COUNT
+enum OpId { OP_UP = 0, OP_COMPRESS, OP_STENCIL, OP_DECOMPRESS, OP_CLOSE1, OP_CLOSE2, OP_COUNT };
+struct GemmCall {
+    int mode = GM_IDENTITY;
+    int level = 0;               // level of the output rows
+    int accumulate = 0;          // Y += ... instead of Y = ...
+    int n_out = 0;               // padded N (columns of Y, rows of W)
+    double alpha = 1.0;
+    // segment 0 (and the only one for IDENTITY / STENCIL); CHILDREN uses W0 + c * w_stride,
+    // STENCIL uses W0 + t * w_stride
+    const void *X0 = nullptr; int ldx0 = 0; int k0 = 0;   // input rows, padded K
+    const void *W0 = nullptr; int64_t w_stride = 0;
+    // segment 1 (PARENT2 only): X1 rows of the parent level, W chosen by child octant class
+    const void *X1 = nullptr; int ldx1 = 0; int k1 = 0;
+    void *const *W1_by_cls = nullptr;                     // array of 8 device pointers
+    void *Y = nullptr; int ldy = 0;
+};
+template <typename T>
+cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &g, cudaStream_t s);
+cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &g, int op_id, cudaStream_t s);
+cudaError_t tc_upload_operators(fmm_ctx *ctx);
+void tc_free(fmm_ctx *ctx);
+
+// ---- evaluate.cu ----
+cudaError_t upload_operators(fmm_ctx *ctx);
+template <typename T>
+cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s);
+
+}  // namespace fmm

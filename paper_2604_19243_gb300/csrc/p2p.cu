@@ -1,0 +1,366 @@
+// Point kernels of the kiFMM (Algorithm 1): the near-field ULI sums (step 3c), the S2U check
+// potentials of the leaves (step 1a, before the pseudo-inverse) and the D2T evaluation of the
+// leaves' far field (step 3b).  Points live in Morton order as (x, y, z, q) vectors.
+//
+// Kernel: K(x, y) = 1/(4 pi |x - y|) (Eq. 2 normalised by 4 pi); the gradient with respect to
+// the target is (y - x) q / (4 pi |x - y|^3).  Pairs at distance zero are skipped (the self
+// interaction and coincident points, which share a leaf).
+#include <algorithm>
+
+#include "devutil.cuh"
+#include "fmm_internal.h"
+
+namespace fmm {
+namespace {
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+template <typename T> __device__ inline T rsqrt_t(T x);
+template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <typename T> __host__ __device__ constexpr T inv4pi() { return (T)0.079577471545947667884441881686257181; }
+
+// ---------------------------------------------------------------------------------------
+// ULI: one CTA per target leaf; every thread owns R targets and one slice of the sources.
+// ---------------------------------------------------------------------------------------
+constexpr int kP2PThreads = 128;
+constexpr int kP2PChunk = 2048;     // sources staged per pass (32 KB as float4)
+
+// one (target, source) interaction; `checked` skips pairs at distance zero
+template <typename T, bool checked>
+__device__ __forceinline__ void interact(const typename Vec4<T>::type &sp, T xi, T yi, T zi,
+                                         T &pot, T &gx, T &gy, T &gz) {
+    const T dx = sp.x - xi, dy = sp.y - yi, dz = sp.z - zi;
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    T rinv = rsqrt_t<T>(r2);
+    if (checked) rinv = r2 > (T)0 ? rinv : (T)0;
+    const T qr = sp.w * rinv;
+    pot += qr;
+    const T qr3 = qr * rinv * rinv;
+    gx += qr3 * dx;
+    gy += qr3 * dy;
+    gz += qr3 * dz;
+}
+
+template <typename T, int R, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads)
+p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
+           const int *__restrict__ u_off, const int *__restrict__ u_idx,
+           const int *__restrict__ order, T *__restrict__ phi, T *__restrict__ grad) {
+    using P = typename Vec4<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    P *src = reinterpret_cast<P *>(smem_raw);                         // [kP2PChunk]
+    __shared__ int rbeg[27], rlen[27];
+    __shared__ int nranges, self_len;
+
+    const int b = order[blockIdx.x];
+    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    const int nt = t1 - t0;
+    // range list: the target leaf first (the only one that can hold a zero distance)
+    if (threadIdx.x == 0) {
+        int k = 0;
+        rbeg[k] = t0;
+        rlen[k++] = nt;
+        for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
+            int a = u_idx[e];
+            if (a == b) continue;
+            rbeg[k] = leaf_off[a];
+            rlen[k++] = leaf_off[a + 1] - leaf_off[a];
+        }
+        nranges = k;
+        self_len = nt;
+    }
+    __syncthreads();
+    int total = 0;
+    for (int k = 0; k < nranges; ++k) total += rlen[k];
+
+    // thread layout for this leaf: TS target threads (multiple of 32) x S source slices
+    int slots = (min(nt, kP2PThreads * R) + R - 1) / R;
+    int TS = min(kP2PThreads, (slots + 31) & ~31);
+    int S = kP2PThreads / TS;
+    const int j = threadIdx.x % TS, sidx = threadIdx.x / TS;
+
+    for (int tbase = t0; tbase < t1; tbase += TS * R) {
+        T xi[R], yi[R], zi[R], pot[R], gx[R], gy[R], gz[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int i = tbase + j + r * TS;
+            P p = pts[min(i, t1 - 1)];
+            xi[r] = p.x, yi[r] = p.y, zi[r] = p.z;
+            pot[r] = gx[r] = gy[r] = gz[r] = (T)0;
+        }
+        for (int c0 = 0; c0 < total; c0 += kP2PChunk) {
+            const int c1 = min(total, c0 + kP2PChunk);
+            __syncthreads();
+            // stage sources [c0, c1) of the concatenated ranges
+            int pos = 0;
+            for (int k = 0; k < nranges; ++k) {
+                int lo = max(pos, c0), hi = min(pos + rlen[k], c1);
+                for (int e = lo + (int)threadIdx.x; e < hi; e += kP2PThreads)
+                    src[e - c0] = pts[rbeg[k] + (e - pos)];
+                pos += rlen[k];
+            }
+            __syncthreads();
+            const int n = c1 - c0;
+            const int per = (n + S - 1) / S;
+            const int s0 = sidx * per, s1 = min(n, s0 + per);
+            const int chk_end = min(s1, max(s0, self_len - c0));     // [s0, chk_end) may hold self
+            for (int e = s0; e < chk_end; ++e) {
+                const P sp = src[e];
+#pragma unroll
+                for (int r = 0; r < R; ++r) interact<T, true>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+            }
+            int e = chk_end;
+            for (; e + 4 <= s1; e += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const P sp = src[e + u];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+                }
+            }
+            for (; e < s1; ++e) {
+                const P sp = src[e];
+#pragma unroll
+                for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+            }
+        }
+        // reduce the S source slices
+        if (S > 1) {
+            __syncthreads();
+            T *red = reinterpret_cast<T *>(smem_raw);   // [S][TS*R][4]
+            for (int r = 0; r < R; ++r) {
+                T *o = red + ((size_t)sidx * TS * R + j + r * TS) * 4;
+                o[0] = pot[r], o[1] = gx[r], o[2] = gy[r], o[3] = gz[r];
+            }
+            __syncthreads();
+            if (sidx == 0) {
+                for (int s = 1; s < S; ++s)
+                    for (int r = 0; r < R; ++r) {
+                        const T *o = red + ((size_t)s * TS * R + j + r * TS) * 4;
+                        pot[r] += o[0], gx[r] += o[1], gy[r] += o[2], gz[r] += o[3];
+                    }
+            }
+        }
+        if (sidx == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int i = tbase + j + r * TS;
+                if (i < t1) {
+                    phi[i] = pot[r] * inv4pi<T>();
+                    if (GRAD) {
+                        grad[3 * (int64_t)i] = gx[r] * inv4pi<T>();
+                        grad[3 * (int64_t)i + 1] = gy[r] * inv4pi<T>();
+                        grad[3 * (int64_t)i + 2] = gz[r] * inv4pi<T>();
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// S2U check potentials: row b = K(x^{uc}_b, y_b) s_b on the 2.95 surface of leaf b.
+// ---------------------------------------------------------------------------------------
+constexpr int kLeafThreads = 128;
+constexpr int kLeafChunk = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads)
+leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
+                  const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns, int nsp,
+                  double ox, double oy, double oz, double width, double radius,
+                  T *__restrict__ out) {
+    using P = typename Vec4<T>::type;
+    __shared__ P src[kLeafChunk];
+    const int b = blockIdx.x;
+    const int s0 = leaf_off[b], s1 = leaf_off[b + 1];
+    int ax, ay, az;
+    demorton3(keys[b], ax, ay, az);
+    const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
+                 cz = oz + (az + 0.5) * width;
+    for (int i0 = 0; i0 < nsp; i0 += kLeafThreads) {
+        const int i = i0 + threadIdx.x;
+        T px = 0, py = 0, pz = 0;
+        if (i < ns) {
+            px = (T)(cx + radius * (double)grid[3 * i]);
+            py = (T)(cy + radius * (double)grid[3 * i + 1]);
+            pz = (T)(cz + radius * (double)grid[3 * i + 2]);
+        }
+        T acc = 0;
+        for (int c0 = s0; c0 < s1; c0 += kLeafChunk) {
+            const int c1 = min(s1, c0 + kLeafChunk);
+            __syncthreads();
+            for (int e = c0 + threadIdx.x; e < c1; e += kLeafThreads) src[e - c0] = pts[e];
+            __syncthreads();
+            if (i < ns)
+                for (int e = 0; e < c1 - c0; ++e) {
+                    const P sp = src[e];
+                    const T dx = sp.x - px, dy = sp.y - py, dz = sp.z - pz;
+                    acc += sp.w * rsqrt_t<T>(dx * dx + dy * dy + dz * dz);
+                }
+        }
+        if (i < nsp) out[(int64_t)b * nsp + i] = i < ns ? acc * inv4pi<T>() : (T)0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// D2T: potentials (and gradients) at the points of leaf b from densities on its 2.95 surface.
+// ---------------------------------------------------------------------------------------
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(kLeafThreads)
+leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
+                 const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns,
+                 const T *__restrict__ dens, int ldd, T scale, double ox, double oy, double oz,
+                 double width, double radius, T *__restrict__ phi, T *__restrict__ grad) {
+    using P = typename Vec4<T>::type;
+    extern __shared__ unsigned char smem_raw[];
+    P *src = reinterpret_cast<P *>(smem_raw);    // [ns]
+    const int b = blockIdx.x;
+    int ax, ay, az;
+    demorton3(keys[b], ax, ay, az);
+    const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
+                 cz = oz + (az + 0.5) * width;
+    for (int j = threadIdx.x; j < ns; j += kLeafThreads) {
+        P p;
+        p.x = (T)(cx + radius * (double)grid[3 * j]);
+        p.y = (T)(cy + radius * (double)grid[3 * j + 1]);
+        p.z = (T)(cz + radius * (double)grid[3 * j + 2]);
+        p.w = dens[(int64_t)b * ldd + j];
+        src[j] = p;
+    }
+    __syncthreads();
+    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    for (int i = t0 + threadIdx.x; i < t1; i += kLeafThreads) {
+        const P x = pts[i];
+        T pot = 0, gx = 0, gy = 0, gz = 0;
+        for (int e = 0; e < ns; ++e) interact<T, false>(src[e], x.x, x.y, x.z, pot, gx, gy, gz);
+        const T f = scale * inv4pi<T>();
+        phi[i] = pot * f;
+        if (GRAD) {
+            grad[3 * (int64_t)i] = gx * f;
+            grad[3 * (int64_t)i + 1] = gy * f;
+            grad[3 * (int64_t)i + 2] = gz * f;
+        }
+    }
+}
+
+template <typename T>
+__global__ void gather_q_kernel(const T *__restrict__ q, const int *__restrict__ perm,
+                                typename Vec4<T>::type *__restrict__ pts, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) pts[i].w = q[perm[i]];
+}
+
+template <typename T>
+__global__ void scatter_kernel(const T *__restrict__ near_phi, const T *__restrict__ near_grad,
+                               const T *__restrict__ far_phi, const T *__restrict__ far_grad,
+                               const int *__restrict__ perm, T *__restrict__ phi,
+                               T *__restrict__ grad, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int o = perm[i];
+    T v = 0;
+    if (near_phi) v += near_phi[i];
+    if (far_phi) v += far_phi[i];
+    phi[o] = v;
+    if (grad) {
+        for (int a = 0; a < 3; ++a) {
+            T g = 0;
+            if (near_grad) g += near_grad[3 * i + a];
+            if (far_grad) g += far_grad[3 * i + a];
+            grad[3 * (int64_t)o + a] = g;
+        }
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_gather_points(const T *q_in, const int *perm, void *pts, int64_t n,
+                                 cudaStream_t s) {
+    gather_q_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(q_in, perm, (typename Vec4<T>::type *)pts, n); count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_phi,
+                           const T *far_grad, const int *perm, T *phi, T *grad, int64_t n,
+                           cudaStream_t s) {
+    scatter_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(near_phi, near_grad, far_phi, far_grad,
+                                                         perm, phi, grad, n); count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
+    if (ctx->nleaf == 0) return cudaSuccess;
+    using P = typename Vec4<T>::type;
+    constexpr int R = 2;
+    size_t smem = std::max(sizeof(P) * kP2PChunk, sizeof(T) * 4 * kP2PThreads * R * 4);
+    const P *pts = (const P *)ctx->pts;
+    if (grad) {
+        auto k = p2p_kernel<T, R, true>;
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<ctx->nleaf, kP2PThreads, smem, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                ctx->p2p_order, phi, grad); count_launch();
+    } else {
+        auto k = p2p_kernel<T, R, false>;
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<ctx->nleaf, kP2PThreads, smem, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                ctx->p2p_order, phi, nullptr); count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s) {
+    if (ctx->nleaf == 0) return cudaSuccess;
+    const int d = ctx->opt.depth;
+    const double width = ctx->side / (double)(1 << d);
+    const double radius = 2.95 * 0.5 * width;
+    leaf_check_kernel<T><<<ctx->nleaf, kLeafThreads, 0, s>>>(
+        (const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns,
+        ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out); count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
+                             T *phi, T *grad, cudaStream_t s) {
+    if (ctx->nleaf == 0) return cudaSuccess;
+    const int d = ctx->opt.depth;
+    const double width = ctx->side / (double)(1 << d);
+    const double radius = 2.95 * 0.5 * width;
+    using P = typename Vec4<T>::type;
+    size_t smem = sizeof(P) * ctx->ns;
+    if (grad)
+        leaf_eval_kernel<T, true><<<ctx->nleaf, kLeafThreads, smem, s>>>(
+            (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
+            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, grad);
+    else
+        leaf_eval_kernel<T, false><<<ctx->nleaf, kLeafThreads, smem, s>>>(
+            (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
+            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+#define FMM_INST(T)                                                                                \
+    template cudaError_t launch_gather_points<T>(const T *, const int *, void *, int64_t, cudaStream_t); \
+    template cudaError_t launch_scatter<T>(const T *, const T *, const T *, const T *, const int *,   \
+                                           T *, T *, int64_t, cudaStream_t);                        \
+    template cudaError_t launch_p2p<T>(const fmm_ctx *, T *, T *, cudaStream_t);                    \
+    template cudaError_t launch_leaf_check<T>(const fmm_ctx *, const T *, T *, cudaStream_t);       \
+    template cudaError_t launch_leaf_eval<T>(const fmm_ctx *, const T *, const T *, int, T, T *, T *, \
+                                             cudaStream_t);
+FMM_INST(float)
+FMM_INST(double)
+#undef FMM_INST
+
+}  // namespace fmm

@@ -1,0 +1,404 @@
+// Host FP64 precompute of the kiFMM operators (the one place FP64 is used on the fast path's
+// behalf).  Everything is built once per (p, pinv_rtol, svd_rtol) in units of the box
+// half-width and cached for the life of the process.
+//
+// Operators (Table 1 of the paper, algebraic kiFMM of Section 2.1), with the box data held as
+// check potentials (see fmm_internal.h):
+//   UC2E = pinv(K(uc, ue)), DC2E = pinv(K(dc, de)) on the unit box (truncated SVD);
+//   A_c  = K(uc_P, ue_c) * (1/2) UC2E       U2U, child half-width 1/2
+//   B_c  = K(dc_c, de_P) * DC2E             D2D
+//   T_t  = K(dc_0, ue_{2 t}) * UC2E         VLI for transfer vector t (316 of them; the
+//                                           translational symmetry of Section 2.2)
+//   T_t ~ Uo C_t Vi^T with Uo, Vi from the SVDs of [T_1 ... T_316] and [T_1; ...; T_316]
+//   close: DC2E = (V S^-1)(U^T) kept factored.
+// Surfaces: a surface of order p around a box of centre c and half-width r is the grid
+// c + alpha r (2 idx/(p-1) - 1), idx in {0..p-1}^3 with an index at 0 or p-1 (lexicographic),
+// 6(p-1)^2+2 points (Section 4, global portion); alpha = 1.05 for the upward-equivalent and
+// downward-check surfaces, 2.95 for the upward-check and downward-equivalent surfaces.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+
+#include "fmm_internal.h"
+
+namespace fmm {
+namespace {
+
+constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
+constexpr double kAlphaInner = 1.05;
+constexpr double kAlphaOuter = 2.95;
+
+using Mat = std::vector<double>;  // row-major
+
+int hw_threads() {
+    unsigned n = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(n, 32u));
+}
+
+template <class F>
+void parallel_for(int n, F f) {
+    int nt = std::min(hw_threads(), n);
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (int i = t; i < n; i += nt) f(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+// C[m x n] = A[m x k] * B[k x n]
+Mat matmul(const Mat &a, const Mat &b, int m, int k, int n) {
+    Mat c((size_t)m * n, 0.0);
+    for (int i = 0; i < m; ++i) {
+        double *ci = &c[(size_t)i * n];
+        for (int l = 0; l < k; ++l) {
+            const double ail = a[(size_t)i * k + l];
+            if (ail == 0.0) continue;
+            const double *bl = &b[(size_t)l * n];
+            for (int j = 0; j < n; ++j) ci[j] += ail * bl[j];
+        }
+    }
+    return c;
+}
+
+Mat transpose(const Mat &a, int m, int n) {
+    Mat t((size_t)m * n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) t[(size_t)j * m + i] = a[(size_t)i * n + j];
+    return t;
+}
+
+Mat scaled_surface(const std::vector<double> &grid, double cx, double cy, double cz, double r,
+                   double alpha) {
+    Mat s(grid.size());
+    for (size_t i = 0; i < grid.size() / 3; ++i) {
+        s[3 * i] = cx + alpha * r * grid[3 * i];
+        s[3 * i + 1] = cy + alpha * r * grid[3 * i + 1];
+        s[3 * i + 2] = cz + alpha * r * grid[3 * i + 2];
+    }
+    return s;
+}
+
+// K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised); 0 where the points coincide.
+Mat kernel_matrix(const Mat &x, const Mat &y) {
+    int m = (int)x.size() / 3, n = (int)y.size() / 3;
+    Mat k((size_t)m * n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            double dx = x[3 * i] - y[3 * j], dy = x[3 * i + 1] - y[3 * j + 1],
+                   dz = x[3 * i + 2] - y[3 * j + 2];
+            double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+            k[(size_t)i * n + j] = r > 0.0 ? kInv4Pi / r : 0.0;
+        }
+    return k;
+}
+
+// One-sided (Hestenes) Jacobi SVD of a square n x n matrix: A = U diag(s) V^T, s descending.
+void jacobi_svd(const Mat &a_in, int n, Mat &u, std::vector<double> &s, Mat &v) {
+    // work on columns: store A^T rows = A columns for contiguous access
+    Mat w = transpose(a_in, n, n);   // w[j*n + i] = A[i][j]
+    Mat vt((size_t)n * n, 0.0);      // vt[j*n + i] = V[i][j]
+    for (int i = 0; i < n; ++i) vt[(size_t)i * n + i] = 1.0;
+    const double tol = 1e-15;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double *cp = &w[(size_t)p * n], *cq = &w[(size_t)q * n];
+                double alpha = 0, beta = 0, gamma = 0;
+                for (int i = 0; i < n; ++i) {
+                    alpha += cp[i] * cp[i];
+                    beta += cq[i] * cq[i];
+                    gamma += cp[i] * cq[i];
+                }
+                if (gamma == 0.0) continue;
+                double rel = std::fabs(gamma) / std::sqrt(alpha * beta);
+                if (!(rel > tol)) continue;
+                off = std::max(off, rel);
+                double zeta = (beta - alpha) / (2.0 * gamma);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < n; ++i) {
+                    double x = cp[i], y = cq[i];
+                    cp[i] = c * x - sn * y;
+                    cq[i] = sn * x + c * y;
+                }
+                double *vp = &vt[(size_t)p * n], *vq = &vt[(size_t)q * n];
+                for (int i = 0; i < n; ++i) {
+                    double x = vp[i], y = vq[i];
+                    vp[i] = c * x - sn * y;
+                    vq[i] = sn * x + c * y;
+                }
+            }
+        }
+        if (off <= tol) break;
+    }
+    std::vector<double> norms(n);
+    for (int j = 0; j < n; ++j) {
+        double acc = 0;
+        for (int i = 0; i < n; ++i) acc += w[(size_t)j * n + i] * w[(size_t)j * n + i];
+        norms[j] = std::sqrt(acc);
+    }
+    std::vector<int> order(n);
+    for (int j = 0; j < n; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return norms[a] > norms[b]; });
+    u.assign((size_t)n * n, 0.0);
+    v.assign((size_t)n * n, 0.0);
+    s.assign(n, 0.0);
+    for (int jj = 0; jj < n; ++jj) {
+        int j = order[jj];
+        s[jj] = norms[j];
+        for (int i = 0; i < n; ++i) {
+            u[(size_t)i * n + jj] = norms[j] > 0 ? w[(size_t)j * n + i] / norms[j] : 0.0;
+            v[(size_t)i * n + jj] = vt[(size_t)j * n + i];
+        }
+    }
+}
+
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix: G = Q diag(l) Q^T, l descending.
+void jacobi_eig(const Mat &g_in, int n, Mat &q, std::vector<double> &lam) {
+    Mat a = g_in;
+    Mat qt((size_t)n * n, 0.0);  // rows are eigenvectors
+    for (int i = 0; i < n; ++i) qt[(size_t)i * n + i] = 1.0;
+    double scale = 0;
+    for (int i = 0; i < n; ++i) scale = std::max(scale, std::fabs(a[(size_t)i * n + i]));
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < n; ++p)
+            for (int r = p + 1; r < n; ++r) off = std::max(off, std::fabs(a[(size_t)p * n + r]));
+        if (off <= 1e-17 * scale) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int r = p + 1; r < n; ++r) {
+                double apr = a[(size_t)p * n + r];
+                if (std::fabs(apr) <= 1e-19 * scale) continue;
+                double app = a[(size_t)p * n + p], arr = a[(size_t)r * n + r];
+                double theta = (arr - app) / (2.0 * apr);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, r
+                    double akp = a[(size_t)k * n + p], akr = a[(size_t)k * n + r];
+                    a[(size_t)k * n + p] = c * akp - s * akr;
+                    a[(size_t)k * n + r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, r
+                    double apk = a[(size_t)p * n + k], ark = a[(size_t)r * n + k];
+                    a[(size_t)p * n + k] = c * apk - s * ark;
+                    a[(size_t)r * n + k] = s * apk + c * ark;
+                }
+                double *qp = &qt[(size_t)p * n], *qr = &qt[(size_t)r * n];
+                for (int k = 0; k < n; ++k) {
+                    double x = qp[k], y = qr[k];
+                    qp[k] = c * x - s * y;
+                    qr[k] = s * x + c * y;
+                }
+            }
+        }
+    }
+    std::vector<int> order(n);
+    for (int j = 0; j < n; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return a[(size_t)x * n + x] > a[(size_t)y * n + y]; });
+    q.assign((size_t)n * n, 0.0);
+    lam.assign(n, 0.0);
+    for (int jj = 0; jj < n; ++jj) {
+        int j = order[jj];
+        lam[jj] = a[(size_t)j * n + j];
+        for (int k = 0; k < n; ++k) q[(size_t)k * n + jj] = qt[(size_t)j * n + k];
+    }
+}
+
+// Truncated pseudo-inverse factors of a square matrix: pinv = (V S^-1)[:, :r] (U[:, :r])^T.
+void pinv_factors(const Mat &a, int n, double rtol, Mat &vsinv, Mat &ut, int &rank) {
+    Mat u, v;
+    std::vector<double> s;
+    jacobi_svd(a, n, u, s, v);
+    rank = 0;
+    while (rank < n && s[rank] >= rtol * s[0] && s[rank] > 0) ++rank;
+    vsinv.assign((size_t)n * rank, 0.0);
+    ut.assign((size_t)rank * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < rank; ++j) vsinv[(size_t)i * rank + j] = v[(size_t)i * n + j] / s[j];
+    for (int j = 0; j < rank; ++j)
+        for (int i = 0; i < n; ++i) ut[(size_t)j * n + i] = u[(size_t)i * n + j];
+}
+
+void transfer_vector(int t, int &dx, int &dy, int &dz) {
+    int k = 0;
+    for (int i = -3; i <= 3; ++i)
+        for (int j = -3; j <= 3; ++j)
+            for (int l = -3; l <= 3; ++l) {
+                if (std::max(std::abs(i), std::max(std::abs(j), std::abs(l))) <= 1) continue;
+                if (k == t) {
+                    dx = i, dy = j, dz = l;
+                    return;
+                }
+                ++k;
+            }
+}
+
+int transfer_index_of(int dx, int dy, int dz) {
+    int k = 0;
+    for (int i = -3; i <= 3; ++i)
+        for (int j = -3; j <= 3; ++j)
+            for (int l = -3; l <= 3; ++l) {
+                if (std::max(std::abs(i), std::max(std::abs(j), std::abs(l))) <= 1) continue;
+                if (i == dx && j == dy && l == dz) return k;
+                ++k;
+            }
+    return -1;
+}
+
+std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::string *err) {
+    auto h = std::make_unique<HostOps>();
+    h->p = p;
+    std::vector<double> grid = surface_grid(p);
+    const int ns = (int)grid.size() / 3;
+    h->ns = ns;
+    Mat ue = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaInner);   // upward equivalent
+    Mat uc = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaOuter);   // upward check
+    Mat dc = ue;                                                // downward check (1.05)
+    Mat de = uc;                                                // downward equivalent (2.95)
+    h->surf_inner = ue;
+    h->surf_outer = uc;
+
+    // check-to-equivalent pseudo-inverses on the unit box
+    Mat uc_vs, uc_ut, dc_vs, dc_ut;
+    int r_uc = 0, r_dc = 0;
+    pinv_factors(kernel_matrix(uc, ue), ns, pinv_rtol, uc_vs, uc_ut, r_uc);
+    pinv_factors(kernel_matrix(dc, de), ns, pinv_rtol, dc_vs, dc_ut, r_dc);
+    Mat uc2e = matmul(uc_vs, uc_ut, ns, r_uc, ns);
+    Mat dc2e = matmul(dc_vs, dc_ut, ns, r_dc, ns);
+    h->rcl = r_dc;
+    h->close1 = dc_ut;   // [r_dc x ns]
+    h->close2 = dc_vs;   // [ns x r_dc]
+
+    // U2U and D2D per octant (child half-width 1/2, centre offset +-1/2 per axis, x bit first)
+    for (int c = 0; c < 8; ++c) {
+        double cx = ((c >> 2) & 1) ? 0.5 : -0.5, cy = ((c >> 1) & 1) ? 0.5 : -0.5,
+               cz = (c & 1) ? 0.5 : -0.5;
+        Mat child_ue = scaled_surface(grid, cx, cy, cz, 0.5, kAlphaInner);
+        Mat child_dc = child_ue;
+        Mat kk = kernel_matrix(uc, child_ue);
+        Mat half_uc2e = uc2e;
+        for (auto &x : half_uc2e) x *= 0.5;      // pinv at half-width 1/2 = (1/2) pinv at 1
+        h->up[c] = matmul(kk, half_uc2e, ns, ns, ns);
+        h->down[c] = matmul(kernel_matrix(child_dc, de), dc2e, ns, ns, ns);
+    }
+
+    // M2L operators T_t = K(dc_0, ue_{2t}) UC2E and their SVD compression
+    std::vector<Mat> T(kNumTransfer);
+    parallel_for(kNumTransfer, [&](int t) {
+        int dx, dy, dz;
+        transfer_vector(t, dx, dy, dz);
+        Mat src = scaled_surface(grid, 2.0 * dx, 2.0 * dy, 2.0 * dz, 1.0, kAlphaInner);
+        T[t] = matmul(kernel_matrix(dc, src), uc2e, ns, ns, ns);
+    });
+    // Gram matrices of the fat [T_1 .. T_316] (left) and tall [T_1; ..; T_316] (right) stacks
+    int nt = hw_threads();
+    std::vector<Mat> gl(nt, Mat((size_t)ns * ns, 0.0)), gr(nt, Mat((size_t)ns * ns, 0.0));
+    parallel_for(nt, [&](int w) {
+        for (int t = w; t < kNumTransfer; t += nt) {
+            const Mat &a = T[t];
+            Mat at = transpose(a, ns, ns);
+            Mat l = matmul(a, at, ns, ns, ns), r = matmul(at, a, ns, ns, ns);
+            for (size_t i = 0; i < l.size(); ++i) {
+                gl[w][i] += l[i];
+                gr[w][i] += r[i];
+            }
+        }
+    });
+    for (int w = 1; w < nt; ++w)
+        for (size_t i = 0; i < gl[0].size(); ++i) {
+            gl[0][i] += gl[w][i];
+            gr[0][i] += gr[w][i];
+        }
+    Mat ql, qr;
+    std::vector<double> ll, lr;
+    jacobi_eig(gl[0], ns, ql, ll);
+    jacobi_eig(gr[0], ns, qr, lr);
+    // sigma_i >= svd_rtol * sigma_1  <=>  lambda_i >= svd_rtol^2 * lambda_1
+    auto rank_of = [&](const std::vector<double> &l) {
+        int k = 0;
+        while (k < ns && l[k] > 0 && l[k] >= svd_rtol * svd_rtol * l[0]) ++k;
+        return std::max(k, 1);
+    };
+    int kout = rank_of(ll), kin = rank_of(lr);
+    h->kout = kout;
+    h->kin = kin;
+    Mat uo((size_t)ns * kout), vi((size_t)ns * kin);
+    for (int i = 0; i < ns; ++i) {
+        for (int j = 0; j < kout; ++j) uo[(size_t)i * kout + j] = ql[(size_t)i * ns + j];
+        for (int j = 0; j < kin; ++j) vi[(size_t)i * kin + j] = qr[(size_t)i * ns + j];
+    }
+    h->decompress = uo;                       // [ns x kout]
+    h->compress = transpose(vi, ns, kin);     // [kin x ns]
+    Mat uot = transpose(uo, ns, kout);
+    h->stencil.assign((size_t)kNumTransfer * kout * kin, 0.0);
+    parallel_for(kNumTransfer, [&](int t) {
+        Mat tv = matmul(T[t], vi, ns, ns, kin);            // ns x kin
+        Mat c = matmul(uot, tv, kout, ns, kin);            // kout x kin
+        std::copy(c.begin(), c.end(), h->stencil.begin() + (size_t)t * kout * kin);
+    });
+
+    // adjoint operators: transposes, with the stencil re-indexed by the opposite vector
+    for (int c = 0; c < 8; ++c) {
+        h->a_up[c] = transpose(h->down[c], ns, ns);   // children gather of D2D^T
+        h->a_down[c] = transpose(h->up[c], ns, ns);   // parent gather of U2U^T
+    }
+    h->a_compress = uot;                              // [kout x ns]
+    h->a_decompress = vi;                             // [ns x kin]
+    h->a_stencil.assign((size_t)kNumTransfer * kin * kout, 0.0);
+    for (int t = 0; t < kNumTransfer; ++t) {
+        int dx, dy, dz;
+        transfer_vector(t, dx, dy, dz);
+        int tn = transfer_index_of(-dx, -dy, -dz);
+        const double *c = &h->stencil[(size_t)tn * kout * kin];
+        double *o = &h->a_stencil[(size_t)t * kin * kout];
+        for (int i = 0; i < kout; ++i)
+            for (int j = 0; j < kin; ++j) o[(size_t)j * kout + i] = c[(size_t)i * kin + j];
+    }
+    h->a_close1 = transpose(dc_vs, ns, r_dc);         // [r_dc x ns] = (V S^-1)^T
+    h->a_close2 = transpose(dc_ut, r_dc, ns);         // [ns x r_dc] = U
+    (void)err;
+    return h;
+}
+
+}  // namespace
+
+std::vector<double> surface_grid(int p) {
+    std::vector<double> g;
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                bool on = i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1;
+                if (!on) continue;
+                g.push_back(2.0 * i / (p - 1) - 1.0);
+                g.push_back(2.0 * j / (p - 1) - 1.0);
+                g.push_back(2.0 * k / (p - 1) - 1.0);
+            }
+    return g;
+}
+
+const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, double, double>, std::unique_ptr<HostOps>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(p, pinv_rtol, svd_rtol);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second.get();
+    auto h = build(p, pinv_rtol, svd_rtol, err);
+    if (!h) return nullptr;
+    const HostOps *ptr = h.get();
+    cache.emplace(key, std::move(h));
+    return ptr;
+}
+
+}  // namespace fmm

@@ -1,0 +1,761 @@
+// Octree construction on the GPU (Section 2.1 of the paper, uniform refinement):
+//   1. bounding cube (given, or from the points' extent),
+//   2. Morton key of every point at depth d,
+//   3. stable LSD radix sort of (key, input index),
+//   4. leaf run-lengths, the non-empty boxes of every level, parent/child tables,
+//   5. dense key -> box tables (the GPU stand-in for the hashing of non-empty keys: with a
+//      uniform tree a direct-address table of 8^l entries is cheaper than a hash),
+//   6. U lists of the leaves (colleagues plus self, Table 1), and for the VLI the boxes of each
+//      level ordered by child octant with per-tile masks of the transfer vectors that occur
+//      (the stencil existence checks of Section 2.2).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "devutil.cuh"
+#include "fmm_internal.h"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------------------
+// exclusive scan (three-phase: block scans, scan of block sums, add-back)
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+template <typename T>
+__global__ void scan_blocks(T *d, int64_t n, T *block_sums) {
+    __shared__ T warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T run = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t k = base + i;
+        T x = k < n ? d[k] : (T)0;
+        v[i] = run;
+        run += x;
+    }
+    // inclusive scan of per-thread totals within the warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < kScanThreads / 32 ? warp_tot[lane] : (T)0;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    T excl = inc - run + (warp > 0 ? warp_tot[warp - 1] : (T)0);
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t k = base + i;
+        if (k < n) d[k] = v[i] + excl;
+    }
+    if (threadIdx.x == kScanThreads - 1 && block_sums) block_sums[blockIdx.x] = excl + run;
+}
+
+template <typename T>
+__global__ void scan_add(T *d, int64_t n, const T *offsets) {
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    const T add = offsets[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanBlock; i += kScanThreads) {
+        int64_t k = base + i;
+        if (k < n) d[k] += add;
+    }
+}
+
+template <typename T>
+__global__ void scan_total(const T *d_scanned, const T *d_orig_last, int64_t n, T *total) {
+    // total = scanned[n-1] + original last value (saved before the scan)
+    *total = n > 0 ? d_scanned[n - 1] + *d_orig_last : (T)0;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t exclusive_scan(T *d, int64_t n, T *d_total, cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) FMM_CUDA_TRY(cudaMemsetAsync(d_total, 0, sizeof(T), s));
+        return cudaSuccess;
+    }
+    Scratch<T> last;
+    if (d_total) {
+        FMM_CUDA_TRY(last.alloc(1, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(last.p, d + n - 1, sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 1) {
+        scan_blocks<T><<<1, kScanThreads, 0, s>>>(d, n, nullptr); count_launch();
+    } else {
+        Scratch<T> sums;
+        FMM_CUDA_TRY(sums.alloc(nb, s));
+        scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums.p); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        FMM_CUDA_TRY(exclusive_scan<T>(sums.p, nb, nullptr, s));
+        scan_add<T><<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums.p); count_launch();
+    }
+    FMM_CUDA_TRY(cudaGetLastError());
+    if (d_total) {
+        scan_total<T><<<1, 1, 0, s>>>(d, last.p, n, d_total); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+template cudaError_t exclusive_scan<int>(int *, int64_t, int *, cudaStream_t);
+template cudaError_t exclusive_scan<long long>(long long *, int64_t, long long *, cudaStream_t);
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// domain and Morton keys
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void extent_kernel(const T *xyz, int64_t n, double *minmax /*[6]*/, int *bad) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nonfinite = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            double v = (double)xyz[3 * i + a];
+            if (!isfinite(v)) nonfinite = 1;
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    nonfinite = __any_sync(0xffffffffu, nonfinite);
+    if ((threadIdx.x & 31) == 0) {
+        // doubles have no native atomicMin; order-preserving map to signed 64-bit integers
+        for (int a = 0; a < 3; ++a) {
+            long long l = __double_as_longlong(lo[a]), h = __double_as_longlong(hi[a]);
+            l = l >= 0 ? l : (l ^ 0x7fffffffffffffffLL);
+            h = h >= 0 ? h : (h ^ 0x7fffffffffffffffLL);
+            atomicMin((long long *)&minmax[a], l);
+            atomicMax((long long *)&minmax[3 + a], h);
+        }
+        if (nonfinite) atomicOr(bad, 1);
+    }
+}
+
+long long ordered_bits(double v) {
+    long long l;
+    memcpy(&l, &v, sizeof(l));
+    return l >= 0 ? l : (l ^ 0x7fffffffffffffffLL);
+}
+double from_ordered_bits(long long l) {
+    l = l >= 0 ? l : (l ^ 0x7fffffffffffffffLL);
+    double v;
+    memcpy(&v, &l, sizeof(v));
+    return v;
+}
+
+// anchor a = min(max(floor((x - o) * scale), 0), 2^d - 1), every FP64 operation rounded
+// separately (no fused multiply-add) so that the host oracle reproduces it bit for bit.
+template <typename T>
+__global__ void morton_kernel(const T *xyz, int64_t n, double ox, double oy, double oz,
+                              double scale, int depth, uint32_t *keys, int *idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double o[3] = {ox, oy, oz};
+    const double amax = (double)((1 << depth) - 1);
+    uint32_t a[3];
+    for (int k = 0; k < 3; ++k) {
+        double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + k], o[k]), scale);
+        t = floor(t);
+        t = fmin(fmax(t, 0.0), amax);
+        a[k] = (uint32_t)t;
+    }
+    keys[i] = morton3(a[0], a[1], a[2]);
+    idx[i] = (int)i;
+}
+
+// ---------------------------------------------------------------------------------------
+// stable LSD radix sort of (uint32 key, int value), 8-bit digits
+// ---------------------------------------------------------------------------------------
+constexpr int kSortWarps = 8;
+constexpr int kSortThreads = kSortWarps * 32;
+constexpr int kSortRounds = 16;                         // 32-key rounds per warp
+constexpr int kSortWarpItems = 32 * kSortRounds;        // 512 keys per warp
+constexpr int kSortTile = kSortWarps * kSortWarpItems;  // 4096 keys per tile
+
+__global__ void radix_hist(const uint32_t *keys, int64_t n, int shift, int ntiles, int *hist) {
+    __shared__ int cnt[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+        int64_t k = base + i;
+        if (k < n) atomicAdd(&cnt[(keys[k] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
+}
+
+__global__ void radix_scatter(const uint32_t *keys, const int *vals, int64_t n, int shift,
+                              int ntiles, const int *offs, uint32_t *keys_out, int *vals_out) {
+    __shared__ int wcnt[kSortWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSortWarpItems;
+    // per-warp digit counts
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t k = wbase + r * 32 + lane;
+        if (k < n) atomicAdd(&wcnt[warp][(keys[k] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    // turn counts into starting positions: tile offset of the digit + earlier warps
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        int run = offs[(int64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < kSortWarps; ++w) {
+            int c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t k = wbase + r * 32 + lane;
+        bool valid = k < n;
+        uint32_t key = valid ? keys[k] : 0u;
+        int digit = valid ? (int)((key >> shift) & 255u) : 256 + lane;   // invalid lanes unique
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        int rank = __popc(peers & lt);
+        int pos = valid ? wcnt[warp][digit] + rank : 0;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[warp][digit] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            keys_out[pos] = key;
+            vals_out[pos] = vals[k];
+        }
+    }
+}
+
+// Stable sort of (keys, vals) by the low `bits` bits of the keys.  Results end in (keys, vals).
+cudaError_t radix_sort(uint32_t *keys, int *vals, int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    Scratch<uint32_t> k2;
+    Scratch<int> v2, hist;
+    FMM_CUDA_TRY(k2.alloc(n, s));
+    FMM_CUDA_TRY(v2.alloc(n, s));
+    FMM_CUDA_TRY(hist.alloc((size_t)256 * ntiles, s));
+    uint32_t *ka = keys, *kb = k2.p;
+    int *va = vals, *vb = v2.p;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist.p); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        FMM_CUDA_TRY(exclusive_scan<int>(hist.p, (int64_t)256 * ntiles, nullptr, s));
+        radix_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, shift, ntiles, hist.p, kb, vb); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(keys, ka, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(vals, va, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------------------
+// leaves, levels and tables
+// ---------------------------------------------------------------------------------------
+
+template <typename T, typename P>
+__global__ void gather_sorted_points(const T *xyz, const int *perm, int64_t n, P *pts) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j = perm[i];
+    P p;
+    p.x = xyz[3 * j];
+    p.y = xyz[3 * j + 1];
+    p.z = xyz[3 * j + 2];
+    p.w = 0;
+    pts[i] = p;
+}
+
+// flag[i] = 1 where a new run of (keys >> shift) starts
+__global__ void run_flags(const uint32_t *keys, int64_t n, int shift, int *flags) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+}
+
+// After an exclusive scan of the flags: runs get contiguous ids.  For every run start record
+// its position (offsets) and key; for every element record its run id (optional).  The
+// exclusive scan counts the starts strictly before i, so an element that does not start a run
+// sees its own run's start too and its id is the scanned value minus one.
+__global__ void run_compact(const uint32_t *keys, const int *flags_scanned, int64_t n, int shift,
+                            int *run_start, uint32_t *run_key, int *elem_run) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool start = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift));
+    const int id = flags_scanned[i] - (start ? 0 : 1);
+    if (start) {
+        if (run_start) run_start[id] = (int)i;
+        run_key[id] = keys[i] >> shift;
+    }
+    if (elem_run) elem_run[i] = id;
+}
+
+__global__ void set_last(int *arr, int64_t pos, int value) { arr[pos] = value; }
+
+__global__ void fill_child(const uint32_t *keys, const int *parent, int64_t n, int *child) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    child[(int64_t)parent[i] * 8 + (keys[i] & 7u)] = (int)i;
+}
+
+__global__ void fill_dense(const uint32_t *keys, int64_t n, int *dense) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dense[keys[i]] = (int)i;
+}
+
+// U list of every leaf: its non-empty colleagues and itself, ascending box index (= Morton).
+__global__ void u_count(const uint32_t *keys, int nleaf, const int *dense, int depth, int *cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    int ax, ay, az;
+    demorton3(keys[b], ax, ay, az);
+    int c = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz)
+                c += dense_find(dense, depth, ax + dx, ay + dy, az + dz) >= 0;
+    cnt[b] = c;
+}
+
+__global__ void u_fill(const uint32_t *keys, int nleaf, const int *dense, int depth,
+                       const int *off, int *idx) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    int ax, ay, az;
+    demorton3(keys[b], ax, ay, az);
+    int list[27];
+    int c = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int j = dense_find(dense, depth, ax + dx, ay + dy, az + dz);
+                if (j >= 0) {
+                    int k = c++;   // insertion sort, ascending
+                    while (k > 0 && list[k - 1] > j) {
+                        list[k] = list[k - 1];
+                        --k;
+                    }
+                    list[k] = j;
+                }
+            }
+    for (int k = 0; k < c; ++k) idx[off[b] + k] = list[k];
+}
+
+// work of each leaf for the P2P: |leaf| * sum_{a in U(leaf)} |a|
+__global__ void p2p_work(const int *leaf_off, const int *u_off, const int *u_idx, int nleaf,
+                         uint32_t *work_key, int *order, unsigned long long *total) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    long long src = 0;
+    for (int k = u_off[b]; k < u_off[b + 1]; ++k) {
+        int a = u_idx[k];
+        src += leaf_off[a + 1] - leaf_off[a];
+    }
+    long long w = src * (long long)(leaf_off[b + 1] - leaf_off[b]);
+    atomicAdd(total, (unsigned long long)w);
+    // descending work order through an ascending sort of the complement (clamped to 32 bits)
+    unsigned long long wc = w > 0xffffffffLL ? 0xffffffffULL : (unsigned long long)w;
+    work_key[b] = 0xffffffffu - (uint32_t)wc;
+    order[b] = b;
+}
+
+__global__ void octant_keys(const uint32_t *keys, int64_t n, uint32_t *oct, int *idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    oct[i] = keys[i] & 7u;
+    idx[i] = (int)i;
+}
+
+// Class slot table: for child octant c, the 189 transfer indices t (ascending) whose source
+// box has a parent adjacent to (or equal to) the target's parent.
+void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas) {
+    slots.assign(8 * kClassSlots, -1);
+    deltas.assign(8 * kClassSlots, 0);
+    for (int c = 0; c < 8; ++c) {
+        int b[3] = {(c >> 2) & 1, (c >> 1) & 1, c & 1};
+        int k = 0, t = 0;
+        for (int i = -3; i <= 3; ++i)
+            for (int j = -3; j <= 3; ++j)
+                for (int l = -3; l <= 3; ++l) {
+                    if (std::max(std::abs(i), std::max(std::abs(j), std::abs(l))) <= 1) continue;
+                    int d[3] = {i, j, l};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a) {
+                        int q = b[a] + d[a];   // (2P + b + d) >> 1 - P = (b + d) >> 1
+                        int pd = q >= 0 ? q / 2 : -((-q + 1) / 2);
+                        if (pd < -1 || pd > 1) ok = false;
+                    }
+                    if (ok) {
+                        deltas[c * kClassSlots + k] = pack_delta(i, j, l);
+                        slots[c * kClassSlots + k++] = t;
+                    }
+                    ++t;
+                }
+    }
+}
+
+// Per tile: bit s of masks[tile*6 + s/32] is set when some row of the tile has a non-empty
+// source box for class slot s.
+__global__ void tile_masks(const Tile *tiles, int ntiles, const int *cls_rows, const uint32_t *keys,
+                           const int *dense, int level, const int *class_delta, uint32_t *masks) {
+    __shared__ uint32_t m[6];
+    __shared__ int dlt[kClassSlots][3];
+    const int tid = blockIdx.x;
+    if (tid >= ntiles) return;
+    Tile tl = tiles[tid];
+    if (threadIdx.x < 6) m[threadIdx.x] = 0;
+    for (int s = threadIdx.x; s < kClassSlots; s += blockDim.x) {
+        int dx, dy, dz;
+        unpack_delta(class_delta[tl.cls * kClassSlots + s], dx, dy, dz);
+        dlt[s][0] = dx, dlt[s][1] = dy, dlt[s][2] = dz;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < tl.nrows * kClassSlots; w += blockDim.x) {
+        int r = w / kClassSlots, s = w % kClassSlots;
+        int box = cls_rows[tl.row0 + r];
+        int ax, ay, az;
+        demorton3(keys[box], ax, ay, az);
+        if (dense_find(dense, level, ax + dlt[s][0], ay + dlt[s][1], az + dlt[s][2]) >= 0)
+            atomicOr(&m[s >> 5], 1u << (s & 31));
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) masks[tid * 6 + threadIdx.x] = m[threadIdx.x];
+}
+
+// V lists for export: count, then fill sorted ascending by source index.
+__global__ void v_count(const uint32_t *keys, int64_t n, const int *dense, int level,
+                        const int *class_delta, long long *cnt) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    uint32_t k = keys[b];
+    int ax, ay, az;
+    demorton3(k, ax, ay, az);
+    int c = k & 7u;
+    long long total = 0;
+    for (int s = 0; s < kClassSlots; ++s) {
+        int dx, dy, dz;
+        unpack_delta(class_delta[c * kClassSlots + s], dx, dy, dz);
+        total += dense_find(dense, level, ax + dx, ay + dy, az + dz) >= 0;
+    }
+    cnt[b] = total;
+}
+
+__global__ void v_fill(const uint32_t *keys, int64_t n, const int *dense, int level,
+                       const int *class_slots, const int *class_delta, const long long *off,
+                       int *idx, int *tv) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    uint32_t k = keys[b];
+    int ax, ay, az;
+    demorton3(k, ax, ay, az);
+    int c = k & 7u;
+    long long o = off[b], m = 0;
+    for (int s = 0; s < kClassSlots; ++s) {
+        int t = class_slots[c * kClassSlots + s];
+        int dx, dy, dz;
+        unpack_delta(class_delta[c * kClassSlots + s], dx, dy, dz);
+        int j = dense_find(dense, level, ax + dx, ay + dy, az + dz);
+        if (j < 0) continue;
+        // insertion into the sorted output segment
+        long long q = o + m++;
+        while (q > o && idx[q - 1] > j) {
+            idx[q] = idx[q - 1];
+            tv[q] = tv[q - 1];
+            --q;
+        }
+        idx[q] = j;
+        tv[q] = t;
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// build
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+static cudaError_t build_tree_t(fmm_ctx *ctx, const T *xyz) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n;
+    const int depth = ctx->opt.depth;
+    // 1. bounding cube
+    if (ctx->opt.has_domain) {
+        for (int a = 0; a < 3; ++a) ctx->origin[a] = ctx->opt.origin[a];
+        ctx->side = ctx->opt.side;
+    }
+    {
+        Scratch<double> mm;
+        Scratch<int> bad;
+        FMM_CUDA_TRY(mm.alloc(6, s));
+        FMM_CUDA_TRY(bad.alloc(1, s));
+        long long init[6];
+        for (int a = 0; a < 3; ++a) {
+            init[a] = ordered_bits(INFINITY);
+            init[3 + a] = ordered_bits(-INFINITY);
+        }
+        FMM_CUDA_TRY(cudaMemcpyAsync(mm.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        FMM_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+        extent_kernel<T><<<std::min<unsigned>(blocks_for(n, 256), 1024), 256, 0, s>>>(xyz, n, mm.p, bad.p); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        long long res[6];
+        int hbad = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(res, mm.p, sizeof(res), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad) return cudaErrorInvalidValue;   // mapped to FMM_EINVAL by the caller
+        if (!ctx->opt.has_domain) {
+            double ext = 0;
+            for (int a = 0; a < 3; ++a) {
+                double lo = from_ordered_bits(res[a]), hi = from_ordered_bits(res[3 + a]);
+                ctx->origin[a] = lo;
+                ext = std::max(ext, hi - lo);
+            }
+            ctx->side = ext > 0 ? ext * (1.0 + std::ldexp(1.0, -20)) : 1.0;
+        }
+    }
+    const double scale = std::ldexp(1.0, depth) / ctx->side;
+    // 2-3. keys and stable sort
+    Scratch<uint32_t> keys;
+    FMM_CUDA_TRY(keys.alloc(n, s));
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->perm, n * sizeof(int), s));
+    morton_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ctx->origin[0], ctx->origin[1],
+                                                          ctx->origin[2], scale, depth, keys.p, ctx->perm); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    FMM_CUDA_TRY(radix_sort(keys.p, ctx->perm, n, 3 * depth, s));
+    // sorted points (x, y, z, q=0)
+    const size_t psz = ctx->fp64 ? sizeof(double4) : sizeof(float4);
+    FMM_CUDA_TRY(cudaMallocAsync(&ctx->pts, n * psz, s));
+    if (ctx->fp64)
+        gather_sorted_points<T, double4><<<blocks_for(n, 256), 256, 0, s>>>(xyz, ctx->perm, n, (double4 *)ctx->pts);
+    else
+        gather_sorted_points<T, float4><<<blocks_for(n, 256), 256, 0, s>>>(xyz, ctx->perm, n, (float4 *)ctx->pts);
+    count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    // 4. leaves
+    Scratch<int> flags;
+    Scratch<int> dtot;
+    FMM_CUDA_TRY(flags.alloc(n, s));
+    FMM_CUDA_TRY(dtot.alloc(1, s));
+    run_flags<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, n, 0, flags.p); count_launch();
+    FMM_CUDA_TRY(exclusive_scan<int>(flags.p, n, dtot.p, s));
+    int nleaf = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&nleaf, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    ctx->nleaf = nleaf;
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->leaf_off, (nleaf + 1) * sizeof(int), s));
+    LevelTables &L = ctx->lev[depth];
+    L.n = nleaf;
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&L.keys, nleaf * sizeof(uint32_t), s));
+    run_compact<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, flags.p, n, 0, ctx->leaf_off, L.keys, nullptr); count_launch();
+    set_last<<<1, 1, 0, s>>>(ctx->leaf_off, nleaf, (int)n); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    // levels d-1 .. 0: unique parents of the sorted child keys
+    for (int l = depth; l >= 1; --l) {
+        LevelTables &C = ctx->lev[l], &P = ctx->lev[l - 1];
+        Scratch<int> f;
+        FMM_CUDA_TRY(f.alloc(C.n, s));
+        run_flags<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, C.n, 3, f.p); count_launch();
+        FMM_CUDA_TRY(exclusive_scan<int>(f.p, C.n, dtot.p, s));
+        int np = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(&np, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        P.n = np;
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&P.keys, np * sizeof(uint32_t), s));
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&C.parent, C.n * sizeof(int), s));
+        run_compact<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, f.p, C.n, 3, nullptr, P.keys, C.parent); count_launch();
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&P.child, (size_t)np * 8 * sizeof(int), s));
+        FMM_CUDA_TRY(cudaMemsetAsync(P.child, 0xff, (size_t)np * 8 * sizeof(int), s));
+        fill_child<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, C.parent, C.n, P.child); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    // 5. dense tables, row bases
+    int64_t rows = 0;
+    for (int l = 0; l <= depth; ++l) {
+        LevelTables &T_ = ctx->lev[l];
+        T_.row_base = rows;
+        rows += T_.n;
+        size_t sz = (size_t)1 << (3 * l);
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&T_.dense, sz * sizeof(int), s));
+        FMM_CUDA_TRY(cudaMemsetAsync(T_.dense, 0xff, sz * sizeof(int), s));
+        fill_dense<<<blocks_for(T_.n, 256), 256, 0, s>>>(T_.keys, T_.n, T_.dense); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    ctx->total_rows = rows;
+    // 6. U lists
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->u_off, (nleaf + 1) * sizeof(int), s));
+    u_count<<<blocks_for(nleaf, 128), 128, 0, s>>>(L.keys, nleaf, L.dense, depth, ctx->u_off); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    FMM_CUDA_TRY(exclusive_scan<int>(ctx->u_off, nleaf, dtot.p, s));
+    int nu = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&nu, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    ctx->n_u = nu;
+    set_last<<<1, 1, 0, s>>>(ctx->u_off, nleaf, nu); count_launch();
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->u_idx, std::max(nu, 1) * sizeof(int), s));
+    u_fill<<<blocks_for(nleaf, 128), 128, 0, s>>>(L.keys, nleaf, L.dense, depth, ctx->u_off, ctx->u_idx); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    // P2P schedule (decreasing work) and the total pair count
+    {
+        Scratch<uint32_t> wk;
+        Scratch<unsigned long long> tot;
+        FMM_CUDA_TRY(wk.alloc(nleaf, s));
+        FMM_CUDA_TRY(tot.alloc(1, s));
+        FMM_CUDA_TRY(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->p2p_order, nleaf * sizeof(int), s));
+        p2p_work<<<blocks_for(nleaf, 256), 256, 0, s>>>(ctx->leaf_off, ctx->u_off, ctx->u_idx, nleaf,
+                                                          wk.p, ctx->p2p_order, tot.p); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        FMM_CUDA_TRY(radix_sort(wk.p, ctx->p2p_order, nleaf, 32, s));
+        unsigned long long h = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(&h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        ctx->p2p_pairs = (int64_t)h;
+    }
+    // class (octant) order per level >= 1
+    for (int l = 1; l <= depth; ++l) {
+        LevelTables &T_ = ctx->lev[l];
+        Scratch<uint32_t> oct;
+        FMM_CUDA_TRY(oct.alloc(T_.n, s));
+        FMM_CUDA_TRY(cudaMallocAsync((void **)&T_.cls_rows, T_.n * sizeof(int), s));
+        octant_keys<<<blocks_for(T_.n, 256), 256, 0, s>>>(T_.keys, T_.n, oct.p, T_.cls_rows); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        FMM_CUDA_TRY(radix_sort(oct.p, T_.cls_rows, T_.n, 3, s));
+        std::vector<uint32_t> h(T_.n);
+        FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), oct.p, T_.n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int c = 0; c <= 8; ++c)
+            T_.cls_off[c] = (int)(std::lower_bound(h.begin(), h.end(), (uint32_t)c) - h.begin());
+    }
+    std::vector<int> slots, deltas;
+    class_slot_table(slots, deltas);
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->class_slots, slots.size() * sizeof(int), s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(ctx->class_slots, slots.data(), slots.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->class_delta, deltas.size() * sizeof(int), s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(ctx->class_delta, deltas.data(), deltas.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    return cudaSuccess;
+}
+
+cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz) {
+    if (ctx->fp64) return build_tree_t<double>(ctx, (const double *)d_xyz);
+    return build_tree_t<float>(ctx, (const float *)d_xyz);
+}
+
+cudaError_t build_tiles(fmm_ctx *ctx, int tile_m) {
+    cudaStream_t s = ctx->stream;
+    const int depth = ctx->opt.depth;
+    for (int l = 0; l <= depth; ++l) {
+        for (TileSet *ts : {&ctx->tiles_plain[l], &ctx->tiles_cls[l]}) {
+            if (ts->tiles) cudaFreeAsync(ts->tiles, s);
+            if (ts->masks) cudaFreeAsync(ts->masks, s);
+            ts->tiles = nullptr;
+            ts->masks = nullptr;
+            ts->host.clear();
+            ts->ntiles = 0;
+        }
+        LevelTables &T_ = ctx->lev[l];
+        // plain order
+        TileSet &pl = ctx->tiles_plain[l];
+        for (int64_t r = 0; r < T_.n; r += tile_m)
+            pl.host.push_back(Tile{(int)r, (int)std::min<int64_t>(tile_m, T_.n - r), -1, 0});
+        // class order
+        TileSet &cl = ctx->tiles_cls[l];
+        if (l >= 1)
+            for (int c = 0; c < 8; ++c)
+                for (int r = T_.cls_off[c]; r < T_.cls_off[c + 1]; r += tile_m)
+                    cl.host.push_back(Tile{r, std::min(tile_m, T_.cls_off[c + 1] - r), c, (int)cl.host.size()});
+        for (TileSet *ts : {&pl, &cl}) {
+            ts->ntiles = (int)ts->host.size();
+            if (!ts->ntiles) continue;
+            FMM_CUDA_TRY(cudaMallocAsync((void **)&ts->tiles, ts->ntiles * sizeof(Tile), s));
+            FMM_CUDA_TRY(cudaMemcpyAsync(ts->tiles, ts->host.data(), ts->ntiles * sizeof(Tile),
+                                         cudaMemcpyHostToDevice, s));
+        }
+        if (l >= 2 && cl.ntiles) {
+            FMM_CUDA_TRY(cudaMallocAsync((void **)&cl.masks, (size_t)cl.ntiles * 6 * sizeof(uint32_t), s));
+            tile_masks<<<cl.ntiles, 256, 0, s>>>(cl.tiles, cl.ntiles, T_.cls_rows, T_.keys, T_.dense, l,
+                                                 ctx->class_delta, cl.masks); count_launch();
+            FMM_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    ctx->tile_m = tile_m;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, int32_t *tv,
+                           int64_t *count) {
+    cudaStream_t s = ctx->stream;
+    LevelTables &T_ = ctx->lev[level];
+    const int64_t n = T_.n;
+    Scratch<long long> o;
+    Scratch<long long> tot;
+    FMM_CUDA_TRY(o.alloc(n + 1, s));
+    FMM_CUDA_TRY(tot.alloc(1, s));
+    v_count<<<blocks_for(n, 128), 128, 0, s>>>(T_.keys, n, T_.dense, level, ctx->class_delta, o.p); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    FMM_CUDA_TRY(exclusive_scan<long long>(o.p, n, tot.p, s));
+    long long total = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&total, tot.p, sizeof(total), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (count) *count = total;
+    std::vector<long long> ho(n + 1);
+    FMM_CUDA_TRY(cudaMemcpyAsync(ho.data(), o.p, n * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    ho[n] = total;
+    if (off)
+        for (int64_t i = 0; i <= n; ++i) off[i] = ho[i];
+    if (idx || tv) {
+        Scratch<int> di, dt;
+        FMM_CUDA_TRY(di.alloc(total, s));
+        FMM_CUDA_TRY(dt.alloc(total, s));
+        v_fill<<<blocks_for(n, 128), 128, 0, s>>>(T_.keys, n, T_.dense, level, ctx->class_slots,
+                                                   ctx->class_delta, o.p, di.p, dt.p); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        std::vector<int> hi(total), ht(total);
+        FMM_CUDA_TRY(cudaMemcpyAsync(hi.data(), di.p, total * sizeof(int), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(ht.data(), dt.p, total * sizeof(int), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (long long i = 0; i < total; ++i) {
+            if (idx) idx[i] = hi[i];
+            if (tv) tv[i] = ht[i];
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fmm
