@@ -37,8 +37,8 @@ from synth import WORKLOADS, SEED_SAMPLE, sample_indices, sphere_points, charges
 METRIC = "kiFMM points/sec (potential+gradient) at N=8M, p=6, rel err ≤1e-5 vs FP64"
 UNIT = "points/s"
 FLOPS_PER_PAIR = 20          # conventional count for a potential+gradient Laplace interaction
-SAMPLE_N = 524_288           # CPU sample: same sphere distribution, depth 5 -> ~112 points/leaf
-SAMPLE_DEPTH = 5
+SAMPLE_N = 2_097_152         # CPU sample: same sphere distribution, depth 6 -> ~112 points/leaf
+SAMPLE_DEPTH = 6
 
 
 def read_peaks():

@@ -163,6 +163,12 @@ fmm_status fmm_export_check(fmm_ctx *ctx, int level, int kind, void *host_out);
  * (decompress, D2D, closing, D2T), [4] whole call.  n <= 5 values are written. */
 fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n);
 
+/* Wait for all work of ctx and report device-side failures since the last fmm_sync:
+ * FMM_ETIMEOUT if a tensor-core kernel's bounded wait on a shared-memory barrier expired (the
+ * kernel then skipped its remaining work, so the outputs of those calls are invalid); FMM_ECUDA
+ * for a CUDA error.  Calls with host pointers already synchronize but do not read the flag. */
+fmm_status fmm_sync(fmm_ctx *ctx);
+
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long fmm_kernel_launches(void);
 

@@ -29,7 +29,7 @@ PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
 ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
                 "fmm_evaluate", "fmm_evaluate_parts", "fmm_adjoint", "fmm_get_tree_info",
                 "fmm_export_tree", "fmm_export_level", "fmm_export_check", "fmm_last_timings",
-                "fmm_kernel_launches", "fmm_last_error", "fmm_destroy")
+                "fmm_sync", "fmm_kernel_launches", "fmm_last_error", "fmm_destroy")
 
 
 class Options(ctypes.Structure):
@@ -78,6 +78,7 @@ def lib():
             "fmm_export_level": [vp, i32, vp, vp, vp, vp, vp],
             "fmm_export_check": [vp, i32, i32, vp],
             "fmm_last_timings": [vp, vp, i32],
+            "fmm_sync": [vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -243,6 +244,10 @@ class FMM:
         self._check(lib().fmm_export_check(self._ctx, level, {"upward": 0, "downward": 1}[kind],
                                            _ptr(out)))
         return out
+
+    def sync(self):
+        """Wait for the context's stream; raises if a kernel reported a device-side failure."""
+        self._check(lib().fmm_sync(self._ctx))
 
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""

@@ -326,6 +326,13 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     if (!h) return fail(ctx, FMM_EINVAL, "precompute failed: " + err);
     ctx->host_ops = const_cast<HostOps *>(h);
     cudaError_t e;
+    if (!ctx->dev_flag) {
+        if (cudaMalloc((void **)&ctx->dev_flag, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FMM_ENOMEM, "flag allocation failed");
+        }
+        if ((e = cudaMemset(ctx->dev_flag, 0, sizeof(int))) != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    }
     try {
         e = upload_operators(ctx);
     } catch (const std::bad_alloc &) {
@@ -509,8 +516,25 @@ void fmm_destroy(fmm_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->dev_flag) cudaFree(ctx->dev_flag);
     cudaGetLastError();
     delete ctx;
+}
+
+fmm_status fmm_sync(fmm_ctx *ctx) {
+    if (!ctx) return FMM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    if (!ctx->dev_flag) return FMM_OK;
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, e, "flag read");
+    if (flag) {
+        cudaMemset(ctx->dev_flag, 0, sizeof(int));
+        return fail(ctx, (fmm_status)flag, "a kernel gave up waiting on the device (bounded wait expired); "
+                                           "results of the calls since the last fmm_sync are invalid");
+    }
+    return FMM_OK;
 }
 
 }  // extern "C"

@@ -48,9 +48,13 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c) {
 
 namespace {
 
+// Tensor-core contractions in the split-precision modes, except the leaf closing: its second
+// factor (V S^-1) carries the inverse singular values of the check-to-equivalent map and stays
+// in FP32 so that its rounding is attenuated by the D2T evaluation as analysed for FP32.
 template <typename T>
 cudaError_t gemm(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream_t s) {
-    if (ctx->tensor) return gemm_tc(ctx, c, op_id, s);
+    const int op = op_id % OP_COUNT;
+    if (ctx->tensor && op != OP_CLOSE1 && op != OP_CLOSE2) return gemm_tc(ctx, c, op_id, s);
     return gemm_simt<T>(ctx, c, s);
 }
 

@@ -49,18 +49,20 @@ struct OpSet {
     void *close2 = nullptr;     // [nsp x rclp]  (V S^-1)
 };
 
-// Split operand planes for the tcgen05 GEMMs, laid out in the tensor-core K-major core-matrix
-// order (see gemm_tc.cu).  Planes: BF16x3 -> {hi, lo}; BF16x6 -> {hi, mid, lo}; TF32x3 ->
-// {big, small}.
+// Split operand planes for the tcgen05 GEMMs (gemm_tc.cu): planes[0] holds `count` operators,
+// each `bytes` long, in the stage layout [K chunk][plane][rows x 128 B, SWIZZLE_128B].  Planes:
+// BF16x3 {hi, lo}; BF16x6 {hi, lo, third}; TF32x3 {big, small}.
 struct TcMat {
-    void *planes[3] = {};
+    void *planes[1] = {};
     int rows = 0, cols = 0;     // padded N x K
     int nplanes = 0;
+    size_t bytes = 0;           // one operator
 };
 
 struct TcOpSet {
-    TcMat up[8], down[8], compress, decompress, close1, close2;
-    TcMat stencil[kNumTransfer];
+    TcMat up;                   // 8 operators (children octants)
+    TcMat down[8], compress, decompress;
+    TcMat stencil;              // 316 operators
 };
 
 struct HostOps;  // FP64 host operators (precompute.cpp)

@@ -10,17 +10,22 @@ namespace {
 
 constexpr int BM = 64, BN = 32, BK = 16, THREADS = 128;   // 4 x 4 outputs per thread
 
+// A tile of the level's row list may be taller than BM (the tensor-core tiles are 128 rows):
+// blockIdx.x enumerates (tile, BM-row slice) pairs, `subs` slices per tile.
 template <typename T>
-__global__ void __launch_bounds__(THREADS) gemm_simt_kernel(GemmDev g) {
+__global__ void __launch_bounds__(THREADS) gemm_simt_kernel(GemmDev g, int subs) {
     __shared__ T As[BK][BM + 4];
     __shared__ T Ws[BK][BN + 4];
     __shared__ int src[BM];
     __shared__ int box[BM];
-    const Tile t = g.tiles[blockIdx.x];
+    const Tile t = g.tiles[blockIdx.x / subs];
+    const int r_off = (blockIdx.x % subs) * BM;     // first tile row of this slice
+    const int nrows = min(BM, t.nrows - r_off);     // may be <= 0 for a short tile
     const int n0 = blockIdx.y * BN;
     const int tid = threadIdx.x;
     const int tr = tid / 8, tc = tid % 8;          // 16 x 8 thread grid -> rows tr*4.., cols tc*4..
-    if (tid < BM) box[tid] = tid < t.nrows ? gemm_row_box(g, t, tid) : -1;
+    if (nrows <= 0) return;
+    if (tid < BM) box[tid] = tid < nrows ? gemm_row_box(g, t, r_off + tid) : -1;
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(THREADS) gemm_simt_kernel(GemmDev g) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int r = tr * 4 + i;
-        if (r >= t.nrows) continue;
+        if (r >= nrows) continue;
         int b = box[r];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -94,8 +99,9 @@ cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &c, cudaStream_t s) {
     if (ts.ntiles == 0) return cudaSuccess;
     g.tiles = ts.tiles;
     g.masks = ts.masks;
-    dim3 grid(ts.ntiles, (c.n_out + BN - 1) / BN);
-    gemm_simt_kernel<T><<<grid, THREADS, 0, s>>>(g); count_launch();
+    const int subs = (ctx->tile_m + BM - 1) / BM;
+    dim3 grid(ts.ntiles * subs, (c.n_out + BN - 1) / BN);
+    gemm_simt_kernel<T><<<grid, THREADS, 0, s>>>(g, subs); count_launch();
     return cudaGetLastError();
 }
 

@@ -1,8 +1,656 @@
-// Tensor-core (tcgen05) form of the gathered GEMM: not built yet.
-#include "fmm_internal.h"
+// Tensor-core (tcgen05, sm_103a) form of the gathered GEMM of gemm_common.cuh, with split-
+// precision operands: the FP32 inputs are split into BF16 (hi, lo[, mid]) or TF32 (big, small)
+// planes and the products a_i b_j with i + j below the split order are accumulated in FP32 in
+// tensor memory.  This carries the surface contractions and the M2L (VLI) of the FMM.
+//
+// Layout.  One CTA computes a 128-row tile (M = 128 boxes) for all N output columns.  The K
+// dimension of every segment is cut into chunks of one 128-byte swizzle atom (64 BF16 or 32
+// TF32 values).  A stage holds the A planes (128 rows x 128 B each, K-major, SWIZZLE_128B:
+// 16-byte unit j of row r sits at (j ^ (r % 8)) * 16 within the row's 128 bytes, rows 128 B
+// apart, 8-row groups 1024 B apart) and the B planes (N rows, same layout).  B (the operator) is
+// stored in global memory already in this layout, chunk by chunk, so one bulk copy per stage
+// moves it; A rows are gathered by the producer warps, split and written with st.shared.
+//
+// Warp roles (256 threads, two warps per SM sub-partition so that the accumulator warps can hold
+// 160 FP32 partial sums in registers): warps 0-3 gather A and issue the B copy (warp 0 also owns
+// the tensor memory allocation); warps 4-7 drain the tensor memory accumulators (warp w owns TMEM
+// lanes 32(w-4).. = tile rows) into FP32 registers and write Y; lane 0 of warp 4 issues every
+// tcgen05.mma.
+//
+// Accumulation.  The tensor core adds an MMA's products into the FP32 accumulator with
+// truncation, so a long chain of MMAs into one accumulator drifts toward zero by about one
+// half-ulp per step.  Every stage (at most 4 k-steps x the split products) therefore gets a
+// fresh accumulator (two alternate in tensor memory) and its partial sum is added, correctly
+// rounded, into registers of the accumulator warps.  A CTA covers at most 160 output columns;
+// wider outputs are split over blockIdx.y.
+//
+// Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel records an error
+// code in a device flag, stops producing/issuing, still releases its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gemm_common.cuh"
 
 namespace fmm {
-cudaError_t gemm_tc(const fmm_ctx *, const GemmCall &, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_upload_operators(fmm_ctx *) { return cudaErrorNotSupported; }
-void tc_free(fmm_ctx *) {}
+
+constexpr int kTcThreads = 256;           // 4 producer warps, 4 accumulator warps (one issues MMAs)
+constexpr int kTcRows = 128;
+constexpr int kTcMaxN = 160;               // output columns per CTA (wider N: several CTAs)
+constexpr int kAtomBytes = 128;            // one swizzle atom row
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+struct TcDev {
+    GemmDev g;                      // gather description (W fields unused)
+    const unsigned char *Wt0;       // tensor-core operand of segment 0 (or of segment index * stride)
+    long long wt_stride;            // bytes between consecutive operators (CHILDREN, STENCIL)
+    const unsigned char *Wt1[8];    // PARENT2 segment 1 by class
+    int nplanes;                    // 2 (x3) or 3 (x6)
+    int tf32;                       // 1: kind::tf32 planes (4-byte); 0: BF16 planes (2-byte)
+    int nprod;                      // products per k-step
+    int prod_a[6], prod_b[6];       // plane pairs
+    int nstages;
+    int ncta;                       // output columns per CTA (grid.y splits wider N)
+    int tmem_cols;
+    int *err;                       // device error flag
+};
+
+namespace {
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until the barrier's phase with the given parity has completed; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    uint32_t done = 0;
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = global_ns();
+        else if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// K-major, SWIZZLE_128B shared-memory matrix descriptor: start address, LBO = 16 B (unused for
+// this layout), SBO = 1024 B between 8-row groups, version 1, layout type 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D = F32, A/B format (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128).
+__device__ __forceinline__ uint32_t make_idesc(int n, int fmt) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- splits
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_val(uint32_t b) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
+}
+__device__ __forceinline__ uint32_t tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r & 0xffffe000u;   // keep the 10 explicit mantissa bits only
+}
+
+// ---------------------------------------------------------------- work list helpers
+struct SegInfo {
+    const float *X;
+    int ldx, K;
+    const unsigned char *Wt;
+    int nchunks;
+};
+
+__device__ __forceinline__ SegInfo seg_info(const TcDev &p, const Tile &t, int seg, int chunk_elems) {
+    SegInfo s;
+    const GemmDev &g = p.g;
+    const bool second = g.mode == GM_PARENT2 && seg == 1;
+    s.X = (const float *)(second ? g.X1 : g.X0);
+    s.ldx = second ? g.ldx1 : g.ldx0;
+    s.K = second ? g.k1 : g.k0;
+    s.Wt = second ? p.Wt1[t.cls] : p.Wt0 + gemm_w_index(g, t, seg) * p.wt_stride;
+    s.nchunks = (s.K + chunk_elems - 1) / chunk_elems;
+    return s;
+}
+
+}  // namespace
+
+template <bool TF32>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_constant__ TcDev p) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int box[kTcRows];
+    __shared__ uint32_t mask[6];
+    __shared__ int abort_flag;
+
+    const GemmDev &g = p.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const Tile t = g.tiles[blockIdx.x];
+    const int n_lo = blockIdx.y * p.ncta;                 // this CTA's output columns
+    const int N = min(p.ncta, g.n_out - n_lo);            // multiple of 16
+    constexpr int esz = TF32 ? 4 : 2;                     // bytes per plane element
+    constexpr int chunk_elems = kAtomBytes / esz;         // K values per stage
+    const int a_plane_bytes = kTcRows * kAtomBytes;       // 16 KB
+    const int b_plane_bytes = N * kAtomBytes;
+    const int stage_bytes = p.nplanes * (a_plane_bytes + p.ncta * kAtomBytes);
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    if (tid == 0) {
+        for (int s = 0; s < p.nstages; ++s) {
+            mbar_init(&full_bar[s], 4 + 1);   // 4 producer warps + the B copy's expect_tx arrive
+            mbar_init(&empty_bar[s], 1);      // tcgen05.commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull_bar[b], 1);      // tcgen05.commit
+            mbar_init(&tempty_bar[b], 4);     // the 4 accumulator warps
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 6) mask[tid] = g.mode == GM_STENCIL ? g.masks[(size_t)t.mask * 6 + tid] : 0xffffffffu;
+    if (tid < kTcRows) box[tid] = tid < t.nrows ? gemm_row_box(g, t, tid) : -1;
+    if (warp == 0) tmem_alloc(&tmem_base, p.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int nseg = gemm_nseg(g);
+    auto active = [&](int seg) { return g.mode != GM_STENCIL || ((mask[seg >> 5] >> (seg & 31)) & 1u); };
+    // number of stage items (segment chunks) of the tile
+    int n_items = 0;
+    for (int seg = 0; seg < nseg; ++seg)
+        if (active(seg)) n_items += (gemm_seg_k(g, seg) + chunk_elems - 1) / chunk_elems;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------ producers
+        int item = 0;
+        bool ok = true;
+        for (int seg = 0; seg < nseg && ok; ++seg) {
+            if (!active(seg)) continue;
+            const SegInfo si = seg_info(p, t, seg, chunk_elems);
+            // source row of this warp's rows (row 32 * warp + lane), shared by shuffles
+            const int my_src = box[tid] >= 0 ? gemm_src_row(g, t, box[tid], seg) : -1;
+            for (int c = 0; c < si.nchunks; ++c, ++item) {
+                const int stage = item % p.nstages;
+                if (item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (*(volatile int *)&abort_flag) { ok = false; break; }
+                unsigned char *sa = base + (size_t)stage * stage_bytes;
+                unsigned char *sb = sa + p.nplanes * a_plane_bytes;
+                if (tid == 0) {
+                    // rows [n_lo, n_lo + N) of every plane of chunk c: contiguous per plane
+                    mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    const size_t plane_full = (size_t)g.n_out * kAtomBytes;
+                    for (int pl = 0; pl < p.nplanes; ++pl)
+                        bulk_g2s(sb + pl * b_plane_bytes,
+                                 si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
+                                 (uint32_t)b_plane_bytes, &full_bar[stage]);
+                }
+                // gather: each warp covers its 32 rows; lanes split a row into 16-byte pieces.
+                // All loads of the warp are issued before any is used (memory-level parallelism).
+                const int k0 = c * chunk_elems;
+                const int kval = min(chunk_elems, si.K - k0);       // valid K values in this chunk
+                constexpr int per_row = chunk_elems / 4;            // float4 loads per row
+                constexpr int rows_per_pass = 32 / per_row;
+                constexpr int passes = 32 / rows_per_pass;
+                const int my_row_in_pass = lane / per_row, my_q = lane % per_row;
+                const int k = my_q * 4;                             // first of 4 values
+                float4 vbuf[passes];
+#pragma unroll
+                for (int ps = 0; ps < passes; ++ps) {
+                    const int r = warp * 32 + ps * rows_per_pass + my_row_in_pass;
+                    const int sr = __shfl_sync(0xffffffffu, my_src, r - warp * 32);
+                    vbuf[ps] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (sr >= 0 && k < kval)
+                        vbuf[ps] = __ldg(reinterpret_cast<const float4 *>(si.X + (size_t)sr * si.ldx + k0 + k));
+                }
+#pragma unroll
+                for (int ps = 0; ps < passes; ++ps) {
+                    const int r = warp * 32 + ps * rows_per_pass + my_row_in_pass;
+                    const float x[4] = {vbuf[ps].x, vbuf[ps].y, vbuf[ps].z, vbuf[ps].w};
+                    const int rowoff = (r >> 3) * 1024 + (r & 7) * 128;
+                    if (!TF32) {
+                        // 4 BF16 values = 8 bytes: half of a 16-byte unit
+                        const int unit = k >> 3, half = (k >> 2) & 1;
+                        const int off = rowoff + ((unit ^ (r & 7)) << 4) + half * 8;
+                        uint32_t hb[4], lb[4], mb[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            hb[i] = bf16_bits(x[i]);
+                            const float r1 = x[i] - bf16_val(hb[i]);
+                            lb[i] = bf16_bits(r1);
+                            mb[i] = bf16_bits(r1 - bf16_val(lb[i]));
+                        }
+                        // plane order: 0 = hi, 1 = lo, 2 = third term
+                        *reinterpret_cast<uint2 *>(sa + off) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+                        *reinterpret_cast<uint2 *>(sa + a_plane_bytes + off) =
+                            make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+                        if (p.nplanes == 3)
+                            *reinterpret_cast<uint2 *>(sa + 2 * a_plane_bytes + off) =
+                                make_uint2(mb[0] | (mb[1] << 16), mb[2] | (mb[3] << 16));
+                    } else {
+                        // 4 TF32 values = one 16-byte unit
+                        const int unit = k >> 2;
+                        const int off = rowoff + ((unit ^ (r & 7)) << 4);
+                        uint32_t bb[4], ss[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            bb[i] = tf32_round(x[i]);
+                            ss[i] = tf32_round(x[i] - __uint_as_float(bb[i]));
+                        }
+                        *reinterpret_cast<uint4 *>(sa + off) = make_uint4(bb[0], bb[1], bb[2], bb[3]);
+                        *reinterpret_cast<uint4 *>(sa + a_plane_bytes + off) = make_uint4(ss[0], ss[1], ss[2], ss[3]);
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[stage]);
+            }
+        }
+        if (!ok) {
+            atomicExch(p.err, FMM_ETIMEOUT);
+            *(volatile int *)&abort_flag = 1;
+        }
+    } else {
+        // ------------------------------------------------------------ accumulators / epilogue
+        // Each stage item's products land in one of two TMEM accumulators; these warps add the
+        // item's partial sums (32 rows each) into FP32 registers, so that no TMEM accumulator
+        // takes more than one stage of tensor-core additions.  Lane 0 of warp 4 also issues the
+        // MMAs: it issues item i, then the warp drains item i - 1 while item i runs.
+        const int q = warp - 4;                           // TMEM lane quarter
+        const bool issuer = warp == 4;
+        float acc[kTcMaxN];
+#pragma unroll
+        for (int i = 0; i < kTcMaxN; ++i) acc[i] = 0.f;
+        bool ok = true;
+        // MMA issue state (lane 0 of warp 4)
+        const uint32_t idesc = make_idesc(N, TF32 ? 2 : 1);
+        int seg = 0, chunk = 0;
+        SegInfo si{};
+        if (issuer) {
+            while (seg < nseg && !active(seg)) ++seg;
+            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
+        }
+        auto drain = [&](int item) -> bool {
+            const int b = item & 1;
+            if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1)) return false;
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.ncta);
+            // 32 columns per load
+#pragma unroll
+            for (int n0 = 0; n0 < kTcMaxN; n0 += 32) {
+                if (n0 < N) {
+                    uint32_t v[32];
+                    tmem_ld32(ta + (uint32_t)n0, v);
+                    tmem_wait_ld();
+                    // N is a multiple of 16: the upper half of the last load may be past N
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (n0 + i < kTcMaxN && (i < 16 || n0 + 16 < N)) acc[n0 + i] += __uint_as_float(v[i]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty_bar[b]);
+            return true;
+        };
+        for (int item = 0; item < n_items && ok; ++item) {
+            if (issuer) {
+                int good = 1;
+                if (lane == 0) {
+                    const int stage = item % p.nstages, b = item & 1;
+                    if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1) ||
+                        (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1)) ||
+                        *(volatile int *)&abort_flag) {
+                        good = 0;
+                    } else {
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(base + (size_t)stage * stage_bytes);
+                        const uint32_t sb = sa + p.nplanes * a_plane_bytes;
+                        const uint32_t dt = tmem + (uint32_t)(b * p.ncta);
+                        const int kval = min(chunk_elems, si.K - chunk * chunk_elems);
+                        const int ksteps = min(kAtomBytes / 32, (kval * esz + 31) / 32);
+                        uint32_t accum = 0;
+                        for (int pr = 0; pr < p.nprod; ++pr) {
+                            for (int ks = 0; ks < ksteps; ++ks) {
+                                const uint64_t ad = sw128_desc(sa + p.prod_a[pr] * a_plane_bytes + ks * 32);
+                                const uint64_t bd = sw128_desc(sb + p.prod_b[pr] * b_plane_bytes + ks * 32);
+                                if (TF32) mma_tf32(dt, ad, bd, idesc, accum);
+                                else mma_bf16(dt, ad, bd, idesc, accum);
+                                accum = 1;
+                            }
+                        }
+                        mma_commit(&empty_bar[stage]);
+                        mma_commit(&tfull_bar[b]);
+                        // advance to the next stage item
+                        if (++chunk == si.nchunks) {
+                            chunk = 0;
+                            ++seg;
+                            while (seg < nseg && !active(seg)) ++seg;
+                            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
+                        }
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, good, 0) != 0;
+                if (ok && item >= 1) ok = drain(item - 1);
+            } else {
+                ok = drain(item);
+            }
+        }
+        if (ok && issuer && n_items >= 1) ok = drain(n_items - 1);
+        if (!ok) {
+            atomicExch(p.err, FMM_ETIMEOUT);
+            *(volatile int *)&abort_flag = 1;
+        } else {
+            const int row = q * 32 + lane;
+            const int b = row < t.nrows ? box[row] : -1;
+            if (b >= 0) {
+                float *y = (float *)g.Y + (size_t)b * g.ldy + n_lo;
+#pragma unroll
+                for (int n0 = 0; n0 < kTcMaxN; n0 += 4) {
+                    if (n0 < N) {
+                        float4 o = make_float4(g.alpha * acc[n0], g.alpha * acc[n0 + 1], g.alpha * acc[n0 + 2],
+                                               g.alpha * acc[n0 + 3]);
+                        if (g.accumulate) {
+                            const float4 old = *reinterpret_cast<const float4 *>(y + n0);
+                            o.x += old.x, o.y += old.y, o.z += old.z, o.w += old.w;
+                        }
+                        *reinterpret_cast<float4 *>(y + n0) = o;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, p.tmem_cols);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side: operand planes and launch
+// ---------------------------------------------------------------------------------------
+namespace {
+
+int planes_of(int prec) { return prec == FMM_BF16X6 ? 3 : 2; }
+
+uint16_t host_bf16(float x) {   // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+float host_bf16_val(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+uint32_t host_tf32(float x) {   // round to nearest (ties away), 10 explicit mantissa bits
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x1000u;
+    return u & 0xffffe000u;
+}
+float host_f(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+}  // namespace
+
+// rows x cols FP64 (row-major) -> the split planes of the padded rows_p x cols_p operand, in
+// the stage layout [chunk][plane][rows_p x 128 B, SWIZZLE_128B], appended to `out`.
+static void tc_pack(int prec, const double *w, int rows, int cols, int rows_p, int cols_p,
+                    std::vector<unsigned char> &out) {
+    const bool tf32 = prec == FMM_TF32X3;
+    const int np = planes_of(prec);
+    const int esz = tf32 ? 4 : 2;
+    const int ce = kAtomBytes / esz;
+    const int nchunks = (cols_p + ce - 1) / ce;
+    const size_t plane_bytes = (size_t)rows_p * kAtomBytes;
+    const size_t base = out.size();
+    out.resize(base + (size_t)nchunks * np * plane_bytes, 0);
+    unsigned char *h = out.data() + base;
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) {
+            const double x = w[(size_t)r * cols + c];
+            const int chunk = c / ce, kin = c % ce;
+            const int unit = (kin * esz) >> 4, within = (kin * esz) & 15;
+            const size_t off = (size_t)(r >> 3) * 1024 + (r & 7) * 128 + ((unit ^ (r & 7)) << 4) + within;
+            unsigned char *dst = h + (size_t)chunk * np * plane_bytes + off;
+            if (tf32) {
+                const uint32_t b = host_tf32((float)x);
+                const uint32_t sm = host_tf32((float)(x - (double)host_f(b)));
+                std::memcpy(dst, &b, 4);
+                std::memcpy(dst + plane_bytes, &sm, 4);
+            } else {
+                const uint16_t b0 = host_bf16((float)x);
+                const double r1 = x - (double)host_bf16_val(b0);
+                const uint16_t b1 = host_bf16((float)r1);
+                const double r2 = r1 - (double)host_bf16_val(b1);
+                const uint16_t b2 = host_bf16((float)r2);
+                const uint16_t v[3] = {b0, b1, b2};
+                for (int pl = 0; pl < np; ++pl) std::memcpy(dst + pl * plane_bytes, &v[pl], 2);
+            }
+        }
+}
+
+// `count` operators of rows x cols (consecutive in w) packed into one allocation
+static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int rows, int cols,
+                                  int rows_p, int cols_p, TcMat *out) {
+    std::vector<unsigned char> h;
+    for (int k = 0; k < count; ++k)
+        tc_pack(ctx->opt.precision, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h);
+    void *d = nullptr;
+    FMM_CUDA_TRY(cudaMalloc(&d, h.size()));
+    ctx->op_allocs.push_back(d);
+    FMM_CUDA_TRY(cudaMemcpy(d, h.data(), h.size(), cudaMemcpyHostToDevice));
+    out->planes[0] = d;
+    out->rows = rows_p;
+    out->cols = cols_p;
+    out->nplanes = planes_of(ctx->opt.precision);
+    out->bytes = h.size() / count;   // bytes of one operator (the stride)
+    return cudaSuccess;
+}
+
+static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, const OpSet &o, TcOpSet &t) {
+    const int ns = h.ns, nsp = o.nsp;
+    const auto &U = adjoint ? h.a_up : h.up;
+    const auto &D = adjoint ? h.a_down : h.down;
+    std::vector<double> ups;
+    for (int c = 0; c < 8; ++c) ups.insert(ups.end(), U[c].begin(), U[c].end());
+    FMM_CUDA_TRY(tc_upload_many(ctx, ups.data(), 8, ns, ns, nsp, nsp, &t.up));
+    for (int c = 0; c < 8; ++c) FMM_CUDA_TRY(tc_upload_many(ctx, D[c].data(), 1, ns, ns, nsp, nsp, &t.down[c]));
+    FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_compress : h.compress).data(), 1, o.kin, ns, o.kinp, nsp,
+                                &t.compress));
+    FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_decompress : h.decompress).data(), 1, ns, o.kout, nsp,
+                                o.koutp, &t.decompress));
+    FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_stencil : h.stencil).data(), kNumTransfer, o.kout, o.kin,
+                                o.koutp, o.kinp, &t.stencil));
+    return cudaSuccess;
+}
+
+cudaError_t tc_upload_operators(fmm_ctx *ctx) {
+    ctx->tc_fwd = new TcOpSet();
+    ctx->tc_adj = new TcOpSet();
+    FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops, false, ctx->fwd, *ctx->tc_fwd));
+    FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops, true, ctx->adj, *ctx->tc_adj));
+    return cudaSuccess;
+}
+
+void tc_free(fmm_ctx *ctx) {
+    delete ctx->tc_fwd;
+    delete ctx->tc_adj;
+    ctx->tc_fwd = ctx->tc_adj = nullptr;
+}
+
+GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c);
+
+cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream_t s) {
+    const bool adj = op_id >= OP_COUNT;
+    const int op = op_id % OP_COUNT;
+    const TcOpSet &T = adj ? *ctx->tc_adj : *ctx->tc_fwd;
+    TcDev p{};
+    p.g = make_gemm_dev(ctx, c);
+    const TileSet &ts = (c.mode == GM_STENCIL || c.mode == GM_PARENT2) ? ctx->tiles_cls[c.level]
+                                                                       : ctx->tiles_plain[c.level];
+    if (ts.ntiles == 0) return cudaSuccess;
+    p.g.tiles = ts.tiles;
+    p.g.masks = ts.masks;
+    switch (op) {
+        case OP_UP: p.Wt0 = (const unsigned char *)T.up.planes[0]; p.wt_stride = (long long)T.up.bytes; break;
+        case OP_COMPRESS: p.Wt0 = (const unsigned char *)T.compress.planes[0]; break;
+        case OP_STENCIL: p.Wt0 = (const unsigned char *)T.stencil.planes[0]; p.wt_stride = (long long)T.stencil.bytes; break;
+        case OP_DECOMPRESS:
+            p.Wt0 = (const unsigned char *)T.decompress.planes[0];
+            for (int k = 0; k < 8; ++k) p.Wt1[k] = (const unsigned char *)T.down[k].planes[0];
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    const int prec = ctx->opt.precision;
+    p.tf32 = prec == FMM_TF32X3;
+    p.nplanes = planes_of(prec);
+    if (prec == FMM_BF16X6) {
+        const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+        p.nprod = 6;
+        for (int i = 0; i < 6; ++i) p.prod_a[i] = a[i], p.prod_b[i] = b[i];
+    } else {
+        const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+        p.nprod = 3;
+        for (int i = 0; i < 3; ++i) p.prod_a[i] = a[i], p.prod_b[i] = b[i];
+    }
+    if (c.n_out % 16 != 0 || (c.k0 % 16) != 0 || (c.X1 && c.k1 % 16 != 0)) return cudaErrorInvalidValue;
+    const int nsplit = (c.n_out + kTcMaxN - 1) / kTcMaxN;
+    p.ncta = round_up((c.n_out + nsplit - 1) / nsplit, 16);
+    const int stage_bytes = p.nplanes * (kTcRows + p.ncta) * kAtomBytes;
+    const int budget = 227 * 1024 - 2048;
+    p.nstages = std::min(4, budget / stage_bytes);
+    if (p.nstages < 2) return cudaErrorInvalidValue;
+    // two accumulators of ncta columns; the drain reads 32 columns at a time, so the last read
+    // of the second accumulator may extend 16 columns past it: keep that inside the allocation
+    int cols = 32;
+    while (cols < 2 * p.ncta + 16) cols <<= 1;
+    p.tmem_cols = cols;
+    p.err = ctx->dev_flag;
+    const size_t smem = (size_t)p.nstages * stage_bytes + 1024;
+    auto kern = p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(ts.ntiles, (c.n_out + p.ncta - 1) / p.ncta), kTcThreads, smem, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fmm
