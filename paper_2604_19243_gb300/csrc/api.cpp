@@ -52,6 +52,7 @@ void free_async(P *&p, cudaStream_t s) {
 void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
+    free_async(ctx->UtP, s);
     free_async(ctx->Yc, s), free_async(ctx->Dq, s);
     free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
     free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
@@ -113,6 +114,16 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         {&ctx->near_grad, (size_t)n * 3 * es}, {&ctx->far_phi, (size_t)n * es},
         {&ctx->far_grad, (size_t)n * 3 * es},
     };
+    if (ctx->tensor) {
+        const int np = ctx->opt.precision == FMM_BF16X6 ? 3 : 2;
+        const size_t pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
+        ctx->utp_plane = (long long)((size_t)rows * kw * pesz + 256) / 256 * 256;
+        if (cudaMallocAsync(&ctx->UtP, (size_t)ctx->utp_plane * np, s) != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(ctx);
+            return fail(ctx, FMM_ENOMEM, "workspace allocation failed (split planes)");
+        }
+    }
     size_t total = 0;
     for (auto &a : allocs) {
         cudaError_t e = cudaMallocAsync(a.p, std::max<size_t>(a.bytes, 16), s);
@@ -179,9 +190,12 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     const bool far = (parts & FMM_PART_FAR) && ctx->opt.depth >= 2;
     T *ng = (grad && !adjoint) ? (T *)ctx->near_grad : nullptr;
     T *fg = (grad && !adjoint) ? (T *)ctx->far_grad : nullptr;
-    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, s)) != cudaSuccess)
+    // the near field (ULI) runs on a side stream, concurrently with the far field
+    cudaStream_t ns = ctx->aux[kMaxDepth + 1];
+    cudaStreamWaitEvent(ns, ctx->ev[7], 0);
+    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, ns)) != cudaSuccess)
         return cuda_fail(ctx, e, "near field");
-    cudaEventRecord(ctx->ev[1], s);
+    cudaEventRecord(ctx->ev[1], ns);
     if (far) {
         e = run_far<T>(ctx, adjoint, (T *)ctx->far_phi, fg, s);
         if (e == cudaErrorNotSupported)
@@ -191,6 +205,7 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
         cudaEventRecord(ctx->ev[2], s), cudaEventRecord(ctx->ev[3], s), cudaEventRecord(ctx->ev[4], s);
     }
     cudaEventRecord(ctx->ev[5], s);
+    cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
     e = launch_scatter<T>(near ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
                           far ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
                           (T *)sphi.dev, (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
@@ -262,14 +277,17 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
         delete ctx;
         return FMM_ECUDA;
     }
-    for (auto &e : ctx->ev) {
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaGetLastError();
-            for (auto &x : ctx->ev)
-                if (x) cudaEventDestroy(x);
-            delete ctx;
-            return FMM_ECUDA;
-        }
+    bool okc = true;
+    for (auto &e : ctx->ev) okc = okc && cudaEventCreate(&e) == cudaSuccess;
+    for (int k = 0; k < kMaxDepth + 2; ++k) {
+        okc = okc && cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking) == cudaSuccess;
+        okc = okc && cudaEventCreateWithFlags(&ctx->fork_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        okc = okc && cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!okc) {
+        cudaGetLastError();
+        fmm_destroy(ctx);
+        return FMM_ECUDA;
     }
     *out = ctx;
     return FMM_OK;
@@ -516,6 +534,11 @@ void fmm_destroy(fmm_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (int k = 0; k < kMaxDepth + 2; ++k) {
+        if (ctx->aux[k]) cudaStreamSynchronize(ctx->aux[k]), cudaStreamDestroy(ctx->aux[k]);
+        if (ctx->fork_ev[k]) cudaEventDestroy(ctx->fork_ev[k]);
+        if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+    }
     if (ctx->dev_flag) cudaFree(ctx->dev_flag);
     cudaGetLastError();
     delete ctx;

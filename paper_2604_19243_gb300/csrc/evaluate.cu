@@ -105,22 +105,40 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
     }
     cudaEventRecord(ctx->ev[3], s);
     // VLI
+    // VLI of every level on its own stream (levels are independent once the upward pass is
+    // done); the downward sweep below waits for each level's VLI just before using it.
+    // Tensor-core modes pass the compressed vectors between the two GEMMs as split planes, so
+    // that the stencil copies its source rows instead of converting them itself.
+    const int pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
+    FMM_CUDA_TRY(cudaEventRecord(ctx->fork_ev[0], s));
     for (int l = 2; l <= d; ++l) {
+        cudaStream_t ls = ctx->aux[l];
+        FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
         GemmCall c;
         c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
         c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
         c.Y = rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;
-        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, s));
+        unsigned char *planes = nullptr;
+        if (ctx->tensor) {
+            planes = (unsigned char *)ctx->UtP + (size_t)ctx->lev[l].row_base * kw * pesz;
+            c.Yp = planes, c.yp_ld = kw, c.yp_plane = ctx->utp_plane;
+        }
+        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, ls));
         GemmCall st;
         st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
         st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
         st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
         st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
-        FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, s));
+        if (ctx->tensor) {
+            st.Xp = planes, st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
+        }
+        FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, ls));
+        FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
     }
-    cudaEventRecord(ctx->ev[4], s);
     // downward sweep: decompress fused with the parent's contribution
     for (int l = 2; l <= d; ++l) {
+        FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
+        if (l == d) cudaEventRecord(ctx->ev[4], s);
         GemmCall c;
         c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
         c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = o.decompress;

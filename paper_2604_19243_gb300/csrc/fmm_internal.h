@@ -130,6 +130,8 @@ struct fmm_ctx {
     bool have_ws = false;
     void *Uc = nullptr, *Dc = nullptr;   // [total_rows x nsp] upward / downward check potentials
     void *Ut = nullptr, *Ct = nullptr;   // [total_rows x ws_kw] compressed M2L vectors
+    void *UtP = nullptr;                 // tensor-core modes: Ut as split planes [plane][rows x ws_kw]
+    long long utp_plane = 0;             // bytes per plane
     void *Yc = nullptr;                  // [nleaf x rclp] closing intermediate
     void *Dq = nullptr;                  // [nleaf x nsp] leaf equivalent densities
     void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
@@ -149,6 +151,11 @@ struct fmm_ctx {
 
     bool last_adjoint = false;  // what the last evaluation left in the workspaces
     bool last_far = false;
+
+    // concurrency: side streams for the near field and the per-level VLI (Section 2.2: the ULI is
+    // independent of the far field and the VLI of different levels are independent)
+    cudaStream_t aux[fmm::kMaxDepth + 2] = {};
+    cudaEvent_t fork_ev[fmm::kMaxDepth + 2] = {}, join_ev[fmm::kMaxDepth + 2] = {};
 
     // timings
     cudaEvent_t ev[8] = {};
@@ -226,6 +233,11 @@ struct GemmCall {
     const void *X1 = nullptr; int ldx1 = 0; int k1 = 0;
     void *const *W1_by_cls = nullptr;                     // array of 8 device pointers
     void *Y = nullptr; int ldy = 0;
+    // tensor-core only: A rows read from split planes through TMA row gathers (segment 0), and/or
+    // the output written as split planes instead of FP32 Y.  Plane p of row r, column k is at
+    // byte (r * ld + k) * esize + p * plane within the buffer (esize 2 for BF16, 4 for TF32).
+    const void *Xp = nullptr; int xp_ld = 0; int xp_rows = 0; long long xp_plane = 0;
+    void *Yp = nullptr; int yp_ld = 0; long long yp_plane = 0;
 };
 template <typename T>
 cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &g, cudaStream_t s);

@@ -15,7 +15,7 @@
 // 160 FP32 partial sums in registers): warps 0-3 gather A and issue the B copy (warp 0 also owns
 // the tensor memory allocation); warps 4-7 drain the tensor memory accumulators (warp w owns TMEM
 // lanes 32(w-4).. = tile rows) into FP32 registers and write Y; lane 0 of warp 4 issues every
-// tcgen05.mma.
+// tcgen05.mma (item i), after which its warp drains item i - 1 while item i runs.
 //
 // Accumulation.  The tensor core adds an MMA's products into the FP32 accumulator with
 // truncation, so a long chain of MMAs into one accumulator drifts toward zero by about one
@@ -55,6 +55,13 @@ struct TcDev {
     int ncta;                       // output columns per CTA (grid.y splits wider N)
     int tmem_cols;
     int *err;                       // device error flag
+    int a_planes;                   // A rows arrive pre-split from xp (cp.async copies)
+    const unsigned char *xp;        // split planes of the A rows
+    long long xp_plane;             // bytes between planes
+    int xp_ld;                      // row stride in elements
+    unsigned char *yp;              // split-plane output (instead of FP32 Y) if non-null
+    long long yp_plane;             // bytes between output planes
+    int yp_ld;                      // output row stride in elements
 };
 
 namespace {
@@ -110,6 +117,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// arrive on the barrier once all of this thread's earlier cp.async copies have completed
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -218,6 +236,7 @@ __device__ __forceinline__ SegInfo seg_info(const TcDev &p, const Tile &t, int s
     return s;
 }
 
+
 }  // namespace
 
 template <bool TF32>
@@ -226,6 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     __shared__ uint64_t full_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int box[kTcRows];
+    __shared__ int srcs[2][kTcRows];
     __shared__ uint32_t mask[6];
     __shared__ int abort_flag;
 
@@ -243,7 +263,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
 
     if (tid == 0) {
         for (int s = 0; s < p.nstages; ++s) {
-            mbar_init(&full_bar[s], 4 + 1);   // 4 producer warps + the B copy's expect_tx arrive
+            // register gather: 4 producer warps + the B copy's expect_tx arrive;
+            // plane copies: 128 cp.async arrivals + the B copy's expect_tx arrive
+            mbar_init(&full_bar[s], p.a_planes ? 128 + 1 : 4 + 1);
             mbar_init(&empty_bar[s], 1);      // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
@@ -260,6 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    const uint32_t idesc = make_idesc(N, TF32 ? 2 : 1);
     const int nseg = gemm_nseg(g);
     auto active = [&](int seg) { return g.mode != GM_STENCIL || ((mask[seg >> 5] >> (seg & 31)) & 1u); };
     // number of stage items (segment chunks) of the tile
@@ -267,7 +290,69 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     for (int seg = 0; seg < nseg; ++seg)
         if (active(seg)) n_items += (gemm_seg_k(g, seg) + chunk_elems - 1) / chunk_elems;
 
-    if (warp < 4) {
+    if (warp < 4 && p.a_planes) {
+        // ------------------------------------------------------------ producers, split planes
+        // The source rows are already split into planes in global memory, so the producers only
+        // copy: every thread issues 16-byte cp.async copies straight into the swizzled stage
+        // (8 lanes per row, 4 rows per warp instruction, zero fill for missing rows and for K
+        // past the segment), then arrives on the stage barrier when its copies have landed.
+        // Thread 0 adds the operator's bulk copy.  Copies of several stages stay in flight.
+        // Every producer thread runs the same segment loop and the same named barrier per active
+        // segment whatever happens; after a failed (bounded) wait it only skips its copies.
+        int item = 0, sidx = 0;
+        bool ok = true;
+        for (int seg = 0; seg < nseg; ++seg) {
+            if (!active(seg)) continue;
+            const SegInfo si = seg_info(p, t, seg, chunk_elems);
+            srcs[sidx][tid] = box[tid] >= 0 ? gemm_src_row(g, t, box[tid], seg) : -1;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int *rs = srcs[sidx];
+            const int unit = lane & 7;
+            for (int c = 0; c < si.nchunks; ++c, ++item) {
+                const int stage = item % p.nstages;
+                if (!ok) continue;
+                if ((item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1)) ||
+                    *(volatile int *)&abort_flag) {
+                    ok = false;
+                    continue;
+                }
+                unsigned char *sa = base + (size_t)stage * stage_bytes;
+                unsigned char *sb = sa + p.nplanes * a_plane_bytes;
+                if (tid == 0) {
+                    mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    const size_t plane_full = (size_t)g.n_out * kAtomBytes;
+                    for (int pl = 0; pl < p.nplanes; ++pl)
+                        bulk_g2s(sb + pl * b_plane_bytes,
+                                 si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
+                                 (uint32_t)b_plane_bytes, &full_bar[stage]);
+                }
+                const int k0 = c * chunk_elems;
+                const int kval = min(chunk_elems, si.K - k0);
+                const int valid_units = (kval * esz + 15) / 16;
+                const bool unit_ok = unit < valid_units;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int r = warp * 32 + j * 4 + (lane >> 3);
+                    const int sr = rs[r];
+                    const bool have = unit_ok && sr >= 0;
+                    const size_t elem = (size_t)(have ? sr : 0) * p.xp_ld + k0 + unit * (16 / esz);
+                    const int dst_off = r * kAtomBytes + ((unit ^ (r & 7)) << 4);
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl) {
+                        if (pl < p.nplanes)
+                            cp_async16(sa + pl * a_plane_bytes + dst_off, p.xp + pl * p.xp_plane + elem * esz,
+                                       have ? 16 : 0);
+                    }
+                }
+                cp_async_arrive(&full_bar[stage]);
+            }
+            sidx ^= 1;
+        }
+        if (!ok) {
+            atomicExch(p.err, FMM_ETIMEOUT);
+            *(volatile int *)&abort_flag = 1;
+        }
+    } else if (warp < 4) {
         // ------------------------------------------------------------ producers
         int item = 0;
         bool ok = true;
@@ -363,28 +448,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         // ------------------------------------------------------------ accumulators / epilogue
         // Each stage item's products land in one of two TMEM accumulators; these warps add the
         // item's partial sums (32 rows each) into FP32 registers, so that no TMEM accumulator
-        // takes more than one stage of tensor-core additions.  Lane 0 of warp 4 also issues the
-        // MMAs: it issues item i, then the warp drains item i - 1 while item i runs.
+        // takes more than one stage of tensor-core additions.
         const int q = warp - 4;                           // TMEM lane quarter
         const bool issuer = warp == 4;
         float acc[kTcMaxN];
 #pragma unroll
         for (int i = 0; i < kTcMaxN; ++i) acc[i] = 0.f;
         bool ok = true;
-        // MMA issue state (lane 0 of warp 4)
-        const uint32_t idesc = make_idesc(N, TF32 ? 2 : 1);
-        int seg = 0, chunk = 0;
-        SegInfo si{};
-        if (issuer) {
-            while (seg < nseg && !active(seg)) ++seg;
-            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
-        }
         auto drain = [&](int item) -> bool {
             const int b = item & 1;
             if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1)) return false;
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.ncta);
-            // 32 columns per load
 #pragma unroll
             for (int n0 = 0; n0 < kTcMaxN; n0 += 32) {
                 if (n0 < N) {
@@ -402,8 +477,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             if (lane == 0) mbar_arrive(&tempty_bar[b]);
             return true;
         };
-        for (int item = 0; item < n_items && ok; ++item) {
-            if (issuer) {
+        if (!issuer) {
+            for (int item = 0; item < n_items && ok; ++item) ok = drain(item);
+        } else {
+            // lane 0 issues item i; the whole warp then drains item i - 1 while item i runs
+            int seg = 0, chunk = 0;
+            while (seg < nseg && !active(seg)) ++seg;
+            SegInfo si{};
+            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
+            for (int item = 0; item < n_items && ok; ++item) {
                 int good = 1;
                 if (lane == 0) {
                     const int stage = item % p.nstages, b = item & 1;
@@ -413,6 +495,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                         good = 0;
                     } else {
                         tc_fence_after();
+                        fence_proxy_async();   // cp.async / st.shared writes (generic proxy) -> tcgen05.mma
                         const uint32_t sa = smem_u32(base + (size_t)stage * stage_bytes);
                         const uint32_t sb = sa + p.nplanes * a_plane_bytes;
                         const uint32_t dt = tmem + (uint32_t)(b * p.ncta);
@@ -430,7 +513,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                         }
                         mma_commit(&empty_bar[stage]);
                         mma_commit(&tfull_bar[b]);
-                        // advance to the next stage item
                         if (++chunk == si.nchunks) {
                             chunk = 0;
                             ++seg;
@@ -441,18 +523,61 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 }
                 ok = __shfl_sync(0xffffffffu, good, 0) != 0;
                 if (ok && item >= 1) ok = drain(item - 1);
-            } else {
-                ok = drain(item);
             }
+            if (ok && n_items >= 1) ok = drain(n_items - 1);
         }
-        if (ok && issuer && n_items >= 1) ok = drain(n_items - 1);
         if (!ok) {
             atomicExch(p.err, FMM_ETIMEOUT);
             *(volatile int *)&abort_flag = 1;
         } else {
             const int row = q * 32 + lane;
             const int b = row < t.nrows ? box[row] : -1;
-            if (b >= 0) {
+            if (b >= 0 && p.yp) {
+                // split planes for a later tensor-core gather (BF16 hi/lo[/third] or TF32 big/small)
+#pragma unroll
+                for (int n0 = 0; n0 < kTcMaxN; n0 += 8) {
+                    if (n0 < N) {
+                        const size_t e = (size_t)b * p.yp_ld + n_lo + n0;
+                        if (!TF32) {
+                            uint32_t w[3][4];
+#pragma unroll
+                            for (int i = 0; i < 8; i += 2) {
+                                uint32_t h[2], l[2], m[2];
+#pragma unroll
+                                for (int j = 0; j < 2; ++j) {
+                                    const float x = g.alpha * acc[n0 + i + j];
+                                    h[j] = bf16_bits(x);
+                                    const float r1 = x - bf16_val(h[j]);
+                                    l[j] = bf16_bits(r1);
+                                    m[j] = bf16_bits(r1 - bf16_val(l[j]));
+                                }
+                                w[0][i / 2] = h[0] | (h[1] << 16);
+                                w[1][i / 2] = l[0] | (l[1] << 16);
+                                w[2][i / 2] = m[0] | (m[1] << 16);
+                            }
+#pragma unroll
+                            for (int pl = 0; pl < 3; ++pl)
+                                if (pl < p.nplanes)
+                                    *reinterpret_cast<uint4 *>(p.yp + pl * p.yp_plane + e * 2) =
+                                        make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+                        } else {
+                            uint32_t bb[8], ss[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float x = g.alpha * acc[n0 + i];
+                                bb[i] = tf32_round(x);
+                                ss[i] = tf32_round(x - __uint_as_float(bb[i]));
+                            }
+                            uint4 *d0 = reinterpret_cast<uint4 *>(p.yp + e * 4);
+                            uint4 *d1 = reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 4);
+                            d0[0] = make_uint4(bb[0], bb[1], bb[2], bb[3]);
+                            d0[1] = make_uint4(bb[4], bb[5], bb[6], bb[7]);
+                            d1[0] = make_uint4(ss[0], ss[1], ss[2], ss[3]);
+                            d1[1] = make_uint4(ss[4], ss[5], ss[6], ss[7]);
+                        }
+                    }
+                }
+            } else if (b >= 0) {
                 float *y = (float *)g.Y + (size_t)b * g.ldy + n_lo;
 #pragma unroll
                 for (int n0 = 0; n0 < kTcMaxN; n0 += 4) {
@@ -645,6 +770,21 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     while (cols < 2 * p.ncta + 16) cols <<= 1;
     p.tmem_cols = cols;
     p.err = ctx->dev_flag;
+    if (c.Xp) {
+        // A rows from split planes: K of the segment must be the planes' width
+        if (c.mode != GM_STENCIL && c.mode != GM_IDENTITY) return cudaErrorInvalidValue;
+        if (((uintptr_t)c.Xp & 15) || ((c.xp_ld * (p.tf32 ? 4 : 2)) & 15) || (c.xp_plane & 15))
+            return cudaErrorInvalidValue;
+        p.a_planes = 1;
+        p.xp = (const unsigned char *)c.Xp;
+        p.xp_plane = c.xp_plane;
+        p.xp_ld = c.xp_ld;
+    }
+    if (c.Yp) {
+        p.yp = (unsigned char *)c.Yp;
+        p.yp_plane = c.yp_plane;
+        p.yp_ld = c.yp_ld;
+    }
     const size_t smem = (size_t)p.nstages * stage_bytes + 1024;
     auto kern = p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
     FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
