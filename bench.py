@@ -185,7 +185,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere8m_p6_d7", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="bf16x3",
+    ap.add_argument("--precision", default="bf16x6",
                     choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -24,10 +24,14 @@ template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x)
 template <typename T> __host__ __device__ constexpr T inv4pi() { return (T)0.079577471545947667884441881686257181; }
 
 // ---------------------------------------------------------------------------------------
-// ULI: one CTA per target leaf; every thread owns R targets and one slice of the sources.
+// ULI: one CTA (4 warps) per target leaf.  The leaf's targets are cut into chunks of 32 (one
+// target per lane).  Each warp holds R chunks at once, so every source read from shared memory
+// serves R targets per lane, and works through one of S slices of the sources; R and S are
+// chosen per leaf so that the four warps stay busy with little padding (Section 2.2: the ULI is
+// the compute-bound kernel the method leans on).
 // ---------------------------------------------------------------------------------------
 constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 2048;     // sources staged per pass (32 KB as float4)
+constexpr int kP2PChunk = 1024;     // sources staged per pass (16 KB as float4)
 
 // one (target, source) interaction; `checked` skips pairs at distance zero
 template <typename T, bool checked>
@@ -45,119 +49,140 @@ __device__ __forceinline__ void interact(const typename Vec4<T>::type &sp, T xi,
     gz += qr3 * dz;
 }
 
+struct P2PRanges {
+    int beg[27], len[27];
+    int n, total, self_len;
+};
+
+// One round: chunks [cbase, cbase + nch) of the leaf with R chunks per warp group and S source
+// slices (4 / S groups of S warps).
 template <typename T, int R, bool GRAD>
+__device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restrict__ pts,
+                                          typename Vec4<T>::type *src, T *red, const P2PRanges &rg,
+                                          int t0, int t1, int cbase, int nch, int S, T *__restrict__ phi,
+                                          T *__restrict__ grad) {
+    using P = typename Vec4<T>::type;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = warp / S, slice = warp % S;
+    T xi[R], yi[R], zi[R], pot[R], gx[R], gy[R], gz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = t0 + (cbase + grp * R + r) * 32 + lane;
+        const P p = pts[min(i, t1 - 1)];
+        xi[r] = p.x, yi[r] = p.y, zi[r] = p.z;
+        pot[r] = gx[r] = gy[r] = gz[r] = (T)0;
+    }
+    for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
+        const int c1 = min(rg.total, c0 + kP2PChunk);
+        __syncthreads();
+        int pos = 0;
+        for (int k = 0; k < rg.n; ++k) {
+            const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
+            for (int e = lo + (int)threadIdx.x; e < hi; e += kP2PThreads) src[e - c0] = pts[rg.beg[k] + (e - pos)];
+            pos += rg.len[k];
+        }
+        __syncthreads();
+        const int n = c1 - c0;
+        const int per = (n + S - 1) / S;
+        const int s0 = slice * per, s1 = min(n, s0 + per);
+        const int chk_end = min(s1, max(s0, rg.self_len - c0));     // [s0, chk_end) may hold self
+        for (int e = s0; e < chk_end; ++e) {
+            const P sp = src[e];
+#pragma unroll
+            for (int r = 0; r < R; ++r) interact<T, true>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+        }
+        int e = chk_end;
+        for (; e + 4 <= s1; e += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const P sp = src[e + u];
+#pragma unroll
+                for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+            }
+        }
+        for (; e < s1; ++e) {
+            const P sp = src[e];
+#pragma unroll
+            for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+        }
+    }
+    if (S > 1) {   // reduce the S slices of every group
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T *o = red + ((size_t)(warp * R + r) * 32 + lane) * 4;
+            o[0] = pot[r], o[1] = gx[r], o[2] = gy[r], o[3] = gz[r];
+        }
+        __syncthreads();
+        if (slice == 0)
+            for (int sl = 1; sl < S; ++sl)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T *o = red + ((size_t)((warp + sl) * R + r) * 32 + lane) * 4;
+                    pot[r] += o[0], gx[r] += o[1], gy[r] += o[2], gz[r] += o[3];
+                }
+    }
+    if (slice == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ch = grp * R + r;
+            const int i = t0 + (cbase + ch) * 32 + lane;
+            if (ch < nch && i < t1) {
+                phi[i] = pot[r] * inv4pi<T>();
+                if (GRAD) {
+                    grad[3 * (int64_t)i] = gx[r] * inv4pi<T>();
+                    grad[3 * (int64_t)i + 1] = gy[r] * inv4pi<T>();
+                    grad[3 * (int64_t)i + 2] = gz[r] * inv4pi<T>();
+                }
+            }
+        }
+    }
+    __syncthreads();   // src / red are reused by the next round
+}
+
+template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kP2PThreads)
 p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
            const int *__restrict__ u_off, const int *__restrict__ u_idx,
            const int *__restrict__ order, T *__restrict__ phi, T *__restrict__ grad) {
     using P = typename Vec4<T>::type;
-    extern __shared__ unsigned char smem_raw[];
-    P *src = reinterpret_cast<P *>(smem_raw);                         // [kP2PChunk]
-    __shared__ int rbeg[27], rlen[27];
-    __shared__ int nranges, self_len;
+    __shared__ __align__(16) unsigned char smem_raw[kP2PChunk * sizeof(P)];
+    __shared__ P2PRanges rg;
+    P *src = reinterpret_cast<P *>(smem_raw);
+    T *red = reinterpret_cast<T *>(smem_raw);   // [4 warps][R][32][4] after the sources are used
 
     const int b = order[blockIdx.x];
     const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
     const int nt = t1 - t0;
     // range list: the target leaf first (the only one that can hold a zero distance)
     if (threadIdx.x == 0) {
-        int k = 0;
-        rbeg[k] = t0;
-        rlen[k++] = nt;
+        int k = 0, tot = nt;
+        rg.beg[k] = t0;
+        rg.len[k++] = nt;
         for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
-            int a = u_idx[e];
+            const int a = u_idx[e];
             if (a == b) continue;
-            rbeg[k] = leaf_off[a];
-            rlen[k++] = leaf_off[a + 1] - leaf_off[a];
+            rg.beg[k] = leaf_off[a];
+            rg.len[k] = leaf_off[a + 1] - leaf_off[a];
+            tot += rg.len[k++];
         }
-        nranges = k;
-        self_len = nt;
+        rg.n = k;
+        rg.total = tot;
+        rg.self_len = nt;
     }
     __syncthreads();
-    int total = 0;
-    for (int k = 0; k < nranges; ++k) total += rlen[k];
-
-    // thread layout for this leaf: TS target threads (multiple of 32) x S source slices
-    int slots = (min(nt, kP2PThreads * R) + R - 1) / R;
-    int TS = min(kP2PThreads, (slots + 31) & ~31);
-    int S = kP2PThreads / TS;
-    const int j = threadIdx.x % TS, sidx = threadIdx.x / TS;
-
-    for (int tbase = t0; tbase < t1; tbase += TS * R) {
-        T xi[R], yi[R], zi[R], pot[R], gx[R], gy[R], gz[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int i = tbase + j + r * TS;
-            P p = pts[min(i, t1 - 1)];
-            xi[r] = p.x, yi[r] = p.y, zi[r] = p.z;
-            pot[r] = gx[r] = gy[r] = gz[r] = (T)0;
-        }
-        for (int c0 = 0; c0 < total; c0 += kP2PChunk) {
-            const int c1 = min(total, c0 + kP2PChunk);
-            __syncthreads();
-            // stage sources [c0, c1) of the concatenated ranges
-            int pos = 0;
-            for (int k = 0; k < nranges; ++k) {
-                int lo = max(pos, c0), hi = min(pos + rlen[k], c1);
-                for (int e = lo + (int)threadIdx.x; e < hi; e += kP2PThreads)
-                    src[e - c0] = pts[rbeg[k] + (e - pos)];
-                pos += rlen[k];
-            }
-            __syncthreads();
-            const int n = c1 - c0;
-            const int per = (n + S - 1) / S;
-            const int s0 = sidx * per, s1 = min(n, s0 + per);
-            const int chk_end = min(s1, max(s0, self_len - c0));     // [s0, chk_end) may hold self
-            for (int e = s0; e < chk_end; ++e) {
-                const P sp = src[e];
-#pragma unroll
-                for (int r = 0; r < R; ++r) interact<T, true>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
-            }
-            int e = chk_end;
-            for (; e + 4 <= s1; e += 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const P sp = src[e + u];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
-                }
-            }
-            for (; e < s1; ++e) {
-                const P sp = src[e];
-#pragma unroll
-                for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
-            }
-        }
-        // reduce the S source slices
-        if (S > 1) {
-            __syncthreads();
-            T *red = reinterpret_cast<T *>(smem_raw);   // [S][TS*R][4]
-            for (int r = 0; r < R; ++r) {
-                T *o = red + ((size_t)sidx * TS * R + j + r * TS) * 4;
-                o[0] = pot[r], o[1] = gx[r], o[2] = gy[r], o[3] = gz[r];
-            }
-            __syncthreads();
-            if (sidx == 0) {
-                for (int s = 1; s < S; ++s)
-                    for (int r = 0; r < R; ++r) {
-                        const T *o = red + ((size_t)s * TS * R + j + r * TS) * 4;
-                        pot[r] += o[0], gx[r] += o[1], gy[r] += o[2], gz[r] += o[3];
-                    }
-            }
-        }
-        if (sidx == 0) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                int i = tbase + j + r * TS;
-                if (i < t1) {
-                    phi[i] = pot[r] * inv4pi<T>();
-                    if (GRAD) {
-                        grad[3 * (int64_t)i] = gx[r] * inv4pi<T>();
-                        grad[3 * (int64_t)i + 1] = gy[r] * inv4pi<T>();
-                        grad[3 * (int64_t)i + 2] = gz[r] * inv4pi<T>();
-                    }
-                }
-            }
+    const int C = (nt + 31) / 32;   // target chunks
+    for (int cbase = 0; cbase < C; cbase += 16) {
+        const int nch = min(16, C - cbase);
+        int R, S;
+        if (nch <= 4) R = nch, S = 4;
+        else if (nch <= 8) R = (nch + 1) / 2, S = 2;
+        else R = (nch + 3) / 4, S = 1;
+        switch (R) {
+            case 1: p2p_round<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 2: p2p_round<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 3: p2p_round<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            default: p2p_round<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
         }
     }
 }
@@ -301,20 +326,14 @@ template <typename T>
 cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     if (ctx->nleaf == 0) return cudaSuccess;
     using P = typename Vec4<T>::type;
-    constexpr int R = 2;
-    size_t smem = std::max(sizeof(P) * kP2PChunk, sizeof(T) * 4 * kP2PThreads * R * 4);
     const P *pts = (const P *)ctx->pts;
-    if (grad) {
-        auto k = p2p_kernel<T, R, true>;
-        FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<ctx->nleaf, kP2PThreads, smem, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                ctx->p2p_order, phi, grad); count_launch();
-    } else {
-        auto k = p2p_kernel<T, R, false>;
-        FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<ctx->nleaf, kP2PThreads, smem, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                ctx->p2p_order, phi, nullptr); count_launch();
-    }
+    if (grad)
+        p2p_kernel<T, true><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                                ctx->p2p_order, phi, grad);
+    else
+        p2p_kernel<T, false><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                                 ctx->p2p_order, phi, nullptr);
+    count_launch();
     return cudaGetLastError();
 }
 
