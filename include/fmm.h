@@ -169,6 +169,25 @@ fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n);
  * for a CUDA error.  Calls with host pointers already synchronize but do not read the flag. */
 fmm_status fmm_sync(fmm_ctx *ctx);
 
+/* Morton keys and stable sort of n points, allocating nothing.  The paper has no counterpart:
+ * this entry point is for callers that cannot let a library allocate device memory, because
+ * one allocator owns all of their device memory or because they reserve their whole budget at
+ * start-up.  It performs the first step of fmm_build_tree (the leaf key of every point at
+ * `depth` in the cube [origin, origin + side)^3, computed as fmm_build_tree does, and a stable
+ * sort by key) on caller-owned device arrays:
+ *   xyz[n x 3]  float coordinates (device);  perm[n]  receives the input index of each sorted
+ *   position;  keys[n]  receives the sorted Morton keys (x bit most significant per triple).
+ * Its scratch is a file-scope device array of 8,651,008 bytes (every GPU that loads the library
+ * holds it until the process exits), so n is limited to 1,048,576: larger n, n <= 0, a
+ * depth outside 0..10, a non-positive side or a non-finite origin return FMM_EINVAL.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call shares the array: calls that
+ * overlap on the GPU (different streams, or different threads on one device) race and must be
+ * serialised by the caller.  Work is enqueued on `cuda_stream`; the call returns without
+ * waiting.  FMM_ECUDA reports a CUDA failure. */
+fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int depth, const double origin[3],
+                                   double side, int32_t *perm, uint32_t *keys, void *cuda_stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long fmm_kernel_launches(void);
 

@@ -29,7 +29,8 @@ PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
 ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
                 "fmm_evaluate", "fmm_evaluate_parts", "fmm_adjoint", "fmm_get_tree_info",
                 "fmm_export_tree", "fmm_export_level", "fmm_export_check", "fmm_last_timings",
-                "fmm_sync", "fmm_kernel_launches", "fmm_last_error", "fmm_destroy")
+                "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches", "fmm_last_error",
+                "fmm_destroy")
 
 
 class Options(ctypes.Structure):
@@ -79,6 +80,7 @@ def lib():
             "fmm_export_check": [vp, i32, i32, vp],
             "fmm_last_timings": [vp, vp, i32],
             "fmm_sync": [vp],
+            "fmm_sort_points_noalloc": [vp, i64, i32, vp, ctypes.c_double, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)

@@ -10,6 +10,7 @@
 //      (the stencil existence checks of Section 2.2).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "devutil.cuh"
@@ -759,3 +760,105 @@ cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, 
 }
 
 }  // namespace fmm
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free point sort (fmm_sort_points_noalloc).  The paper has no counterpart: this is
+// for callers that cannot let a library allocate device memory (their device memory is owned
+// by one allocator or reserved in full at start-up).  Its scratch lives in one file-scope
+// device array shared by every call, sized for kNoAllocMaxPoints points.
+// ---------------------------------------------------------------------------------------
+namespace fmm {
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 1 << 20;
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxPoints + kSortTile - 1) / kSortTile;   // radix tiles
+constexpr int64_t kNoAllocHist = 256 * kNoAllocTiles;                                // digit counts
+constexpr int64_t kNoAllocSums = (kNoAllocHist + kScanBlock - 1) / kScanBlock;      // scan blocks
+constexpr size_t kNoAllocBytes =
+    (size_t)kNoAllocMaxPoints * (sizeof(uint32_t) + sizeof(int)) + (size_t)(kNoAllocHist + kNoAllocSums) * sizeof(int);
+
+// keys copy | values copy | digit counts | scan block sums.  Every pass overwrites the part it
+// reads, so nothing has to be cleared between calls.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        FMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+// Exclusive scan of n <= kScanBlock * kScanBlock ints with the given block-sum buffer.
+cudaError_t scan_fixed(int *d, int64_t n, int *sums, cudaStream_t s) {
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 1) {
+        scan_blocks<int><<<1, kScanThreads, 0, s>>>(d, n, nullptr); count_launch();
+        return cudaGetLastError();
+    }
+    scan_blocks<int><<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums); count_launch();
+    scan_blocks<int><<<1, kScanThreads, 0, s>>>(sums, nb, nullptr); count_launch();
+    scan_add<int><<<(unsigned)nb, kScanThreads, 0, s>>>(d, n, sums); count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace fmm
+
+extern "C" fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int depth, const double origin[3],
+                                              double side, int32_t *perm, uint32_t *keys, void *cuda_stream) {
+    using namespace fmm;
+    if (!xyz || !perm || !keys || !origin) return FMM_EINVAL;
+    if (n <= 0 || n > kNoAllocMaxPoints) return FMM_EINVAL;   // beyond the scratch array's size
+    if (depth < 0 || depth > kMaxDepth) return FMM_EINVAL;
+    if (!(side > 0) || !std::isfinite(side)) return FMM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin[a])) return FMM_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char *base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return FMM_ECUDA;
+    }
+    uint32_t *k2 = (uint32_t *)base;
+    int *v2 = (int *)(base + (size_t)kNoAllocMaxPoints * sizeof(uint32_t));
+    int *hist = v2 + kNoAllocMaxPoints;
+    int *sums = hist + kNoAllocHist;
+    const double scale = std::ldexp(1.0, depth) / side;
+    morton_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, origin[0], origin[1], origin[2], scale, depth,
+                                                           keys, perm);
+    count_launch();
+    // stable LSD radix sort of (keys, perm), 8-bit digits, ping-ponging with the scratch copies
+    const int bits = 3 * depth;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t *ka = keys, *kb = k2;
+    int *va = perm, *vb = v2;
+    for (int pass = 0; pass < (bits + 7) / 8 && n > 1; ++pass) {
+        radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, 8 * pass, ntiles, hist); count_launch();
+        if (scan_fixed(hist, (int64_t)256 * ntiles, sums, s) != cudaSuccess) return FMM_ECUDA;
+        radix_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, n, 8 * pass, ntiles, hist, kb, vb); count_launch();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        if (cudaMemcpyAsync(keys, ka, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(perm, va, n * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return FMM_ECUDA;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return FMM_ECUDA;
+    return FMM_OK;
+}
