@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("order_p", ctypes.c_int), ("depth", ctypes.c_int), ("precision", ctypes.c_int),
                 ("svd_rtol", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("with_gradient", ctypes.c_int), ("has_domain", ctypes.c_int),
-                ("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
+                ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
+                ("mean_free", ctypes.c_int)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -116,7 +117,7 @@ class FMM:
     """One FMM context: a tree over a point set and the operators of one expansion order."""
 
     def __init__(self, p=6, depth=4, precision="fp32", svd_rtol=1e-6, pinv_rtol=1e-7,
-                 with_gradient=True, domain=None, stream=None):
+                 with_gradient=True, domain=None, stream=None, mean_free=False):
         L = lib()
         opt = Options()
         L.fmm_default_options(ctypes.byref(opt))
@@ -124,6 +125,7 @@ class FMM:
         opt.precision = PRECISIONS[precision]
         opt.svd_rtol, opt.pinv_rtol = svd_rtol, pinv_rtol
         opt.with_gradient = int(with_gradient)
+        opt.mean_free = int(mean_free)
         if domain is not None:
             opt.has_domain = 1
             for a in range(3):

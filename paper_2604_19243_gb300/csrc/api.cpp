@@ -53,7 +53,7 @@ void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
     free_async(ctx->UtP, s);
-    free_async(ctx->Yc, s), free_async(ctx->Dq, s);
+    free_async(ctx->Yc, s), free_async(ctx->Dq, s), free_async(ctx->Cmean, s);
     free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
     free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
     free_async(ctx->stage_in, s), free_async(ctx->stage_out, s), free_async(ctx->stage_grad, s);
@@ -108,9 +108,12 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         size_t bytes;
     } allocs[] = {
         {&ctx->Uc, (size_t)rows * nsp * es},   {&ctx->Dc, (size_t)rows * nsp * es},
-        {&ctx->Ut, (size_t)rows * kw * es},    {&ctx->Ct, (size_t)rows * kw * es},
+        // tensor-core modes hand the compressed vectors over as split planes (UtP) instead
+        {&ctx->Ut, ctx->tensor ? (size_t)16 : (size_t)rows * kw * es},
+        {&ctx->Ct, (size_t)rows * kw * es},
         {&ctx->Yc, (size_t)nl * ctx->fwd.rclp * es},
-        {&ctx->Dq, (size_t)nl * nsp * es},     {&ctx->near_phi, (size_t)n * es},
+        {&ctx->Dq, (size_t)nl * nsp * es},     {&ctx->Cmean, (size_t)rows * sizeof(double)},
+        {&ctx->near_phi, (size_t)n * es},
         {&ctx->near_grad, (size_t)n * 3 * es}, {&ctx->far_phi, (size_t)n * es},
         {&ctx->far_grad, (size_t)n * 3 * es},
     };
@@ -137,6 +140,7 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     // rows that no step writes (levels 0-1, unused padding) must read as zero
     for (void **p : {&ctx->Uc, &ctx->Dc, &ctx->Ut, &ctx->Ct}) {
         size_t b = (p == &ctx->Uc || p == &ctx->Dc) ? (size_t)rows * nsp * es : (size_t)rows * kw * es;
+        if (p == &ctx->Ut && ctx->tensor) b = 16;
         cudaMemsetAsync(*p, 0, b, s);
     }
     cudaError_t e = build_tiles(ctx, ctx->tensor ? 128 : 64);
@@ -248,6 +252,7 @@ fmm_status fmm_default_options(fmm_options *opt) {
     opt->with_gradient = 1;
     opt->has_domain = 0;
     opt->side = 1.0;
+    opt->mean_free = 0;
     return FMM_OK;
 }
 
@@ -499,11 +504,23 @@ fmm_status fmm_export_check(fmm_ctx *ctx, int level, int kind, void *host_out) {
     std::vector<unsigned char> h((size_t)L.n * ctx->nsp * es);
     cudaError_t e = cudaMemcpyAsync(h.data(), (const unsigned char *)src + (size_t)L.row_base * ctx->nsp * es,
                                     h.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    // downward rows are stored without their per-box mean (carried separately): add it back
+    const bool add_mean = kind == 1 && ctx->opt.mean_free;
+    std::vector<double> cm(add_mean ? L.n : 0);
+    if (e == cudaSuccess && add_mean)
+        e = cudaMemcpyAsync(cm.data(), (const double *)ctx->Cmean + L.row_base, L.n * sizeof(double),
+                            cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "export");
-    for (int64_t b = 0; b < L.n; ++b)
-        std::memcpy((unsigned char *)host_out + (size_t)b * ctx->ns * es, h.data() + (size_t)b * ctx->nsp * es,
-                    ctx->ns * es);
+    for (int64_t b = 0; b < L.n; ++b) {
+        unsigned char *dst = (unsigned char *)host_out + (size_t)b * ctx->ns * es;
+        std::memcpy(dst, h.data() + (size_t)b * ctx->nsp * es, ctx->ns * es);
+        if (add_mean)
+            for (int j = 0; j < ctx->ns; ++j) {
+                if (ctx->fp64) ((double *)dst)[j] += cm[b];
+                else ((float *)dst)[j] = (float)((double)((float *)dst)[j] + cm[b]);
+            }
+    }
     return FMM_OK;
 }
 

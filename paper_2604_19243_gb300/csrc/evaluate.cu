@@ -48,6 +48,27 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c) {
 
 namespace {
 
+// Option mean_free.  Downward check potentials carry the whole far-field potential, whose size
+// is that of the potential itself while the gradients at a leaf depend only on its variation
+// across the leaf.  Taking the per-box mean off after every downward step keeps the stored
+// values at the size of that variation, so their rounding no longer grows into gradient error
+// as boxes shrink.  A constant potential has zero gradient and D2D maps it onto itself up to the
+// operators' fit error, so the means are carried down the tree separately (FP64) and added back
+// to the leaf potentials only.
+template <typename T>
+__global__ void remove_mean_kernel(T *__restrict__ D, int n, int ns, int ld, const int *__restrict__ parent,
+                                   const double *__restrict__ c_parent, double *__restrict__ c_out) {
+    const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (b >= n) return;
+    T *row = D + (size_t)b * ld;
+    double sum = 0;
+    for (int j = lane; j < ns; j += 32) sum += (double)row[j];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const double m = sum / ns;
+    for (int j = lane; j < ns; j += 32) row[j] = (T)((double)row[j] - m);
+    if (lane == 0) c_out[b] = m + (c_parent ? c_parent[parent[b]] : 0.0);
+}
+
 // Tensor-core contractions in the split-precision modes, except the leaf closing: its second
 // factor (V S^-1) carries the inverse singular values of the check-to-equivalent map and stays
 // in FP32 so that its rounding is attenuated by the D2T evaluation as analysed for FP32.
@@ -148,6 +169,15 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         }
         c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
         FMM_CUDA_TRY(gemm<T>(ctx, c, OP_DECOMPRESS + dir * OP_COUNT, s));
+        if (!adjoint && ctx->opt.mean_free) {
+            const LevelTables &L = ctx->lev[l];
+            double *cm = (double *)ctx->Cmean;
+            remove_mean_kernel<T><<<(unsigned)((L.n + 7) / 8), 256, 0, s>>>(
+                rows_at<T>(B, ctx, l, nsp), (int)L.n, ctx->ns, nsp, L.parent,
+                l >= 3 ? cm + ctx->lev[l - 1].row_base : nullptr, cm + L.row_base);
+            count_launch();
+            FMM_CUDA_TRY(cudaGetLastError());
+        }
     }
     // leaf output
     if (!adjoint) {
@@ -161,10 +191,12 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         c2.X0 = ctx->Yc, c2.ldx0 = o.rclp, c2.k0 = o.rclp, c2.W0 = o.close2;
         c2.Y = ctx->Dq, c2.ldy = nsp;
         FMM_CUDA_TRY(gemm<T>(ctx, c2, OP_CLOSE2, s));
-        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, (const T *)ctx->Dq, nsp, (T)1, far_phi, far_grad, s));
+        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, (const T *)ctx->Dq, nsp, (T)1, far_phi, far_grad, s,
+                                         ctx->opt.mean_free ? (const double *)ctx->Cmean + ctx->lev[d].row_base
+                                                            : nullptr));
     } else {
         FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, rows_at<T>(B, ctx, d, nsp), nsp, (T)1, far_phi,
-                                         nullptr, s));
+                                         nullptr, s, nullptr));
     }
     return cudaSuccess;
 }

@@ -134,6 +134,7 @@ struct fmm_ctx {
     long long utp_plane = 0;             // bytes per plane
     void *Yc = nullptr;                  // [nleaf x rclp] closing intermediate
     void *Dq = nullptr;                  // [nleaf x nsp] leaf equivalent densities
+    void *Cmean = nullptr;               // [total_rows] FP64 constant part of the downward check potentials
     void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
     void *far_phi = nullptr, *far_grad = nullptr;
     size_t ws_bytes = 0;
@@ -211,9 +212,10 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
 template <typename T>
 cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s);
 // potentials (and gradients) at the points of every leaf from densities on its 2.95 surface
+// shift (nullable): per-leaf constant added to the potentials (not the gradients)
 template <typename T>
 cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
-                             T *phi, T *grad, cudaStream_t s);
+                             T *phi, T *grad, cudaStream_t s, const double *shift);
 
 // Generic gathered GEMM (gemm_simt.cu / gemm_tc.cu): Y[rows] (+)= alpha sum_seg W_seg X[src(row,seg)].
 enum GatherMode { GM_IDENTITY = 0, GM_CHILDREN = 1, GM_PARENT2 = 2, GM_STENCIL = 3 };

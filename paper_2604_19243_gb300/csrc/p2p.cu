@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(kLeafThreads)
 leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
                  const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns,
                  const T *__restrict__ dens, int ldd, T scale, double ox, double oy, double oz,
-                 double width, double radius, T *__restrict__ phi, T *__restrict__ grad) {
+                 double width, double radius, T *__restrict__ phi, T *__restrict__ grad,
+                 const double *__restrict__ shift) {
     using P = typename Vec4<T>::type;
     extern __shared__ unsigned char smem_raw[];
     P *src = reinterpret_cast<P *>(smem_raw);    // [ns]
@@ -264,7 +265,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
         T pot = 0, gx = 0, gy = 0, gz = 0;
         for (int e = 0; e < ns; ++e) interact<T, false>(src[e], x.x, x.y, x.z, pot, gx, gy, gz);
         const T f = scale * inv4pi<T>();
-        phi[i] = pot * f;
+        phi[i] = pot * f + (shift ? (T)shift[b] : (T)0);   // the leaf's constant potential part
         if (GRAD) {
             grad[3 * (int64_t)i] = gx * f;
             grad[3 * (int64_t)i + 1] = gy * f;
@@ -351,7 +352,7 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
 
 template <typename T>
 cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
-                             T *phi, T *grad, cudaStream_t s) {
+                             T *phi, T *grad, cudaStream_t s, const double *shift) {
     if (ctx->nleaf == 0) return cudaSuccess;
     const int d = ctx->opt.depth;
     const double width = ctx->side / (double)(1 << d);
@@ -361,11 +362,11 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     if (grad)
         leaf_eval_kernel<T, true><<<ctx->nleaf, kLeafThreads, smem, s>>>(
             (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
-            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, grad);
+            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, grad, shift);
     else
         leaf_eval_kernel<T, false><<<ctx->nleaf, kLeafThreads, smem, s>>>(
             (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
-            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, nullptr);
+            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, nullptr, shift);
     count_launch();
     return cudaGetLastError();
 }
@@ -377,7 +378,7 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     template cudaError_t launch_p2p<T>(const fmm_ctx *, T *, T *, cudaStream_t);                    \
     template cudaError_t launch_leaf_check<T>(const fmm_ctx *, const T *, T *, cudaStream_t);       \
     template cudaError_t launch_leaf_eval<T>(const fmm_ctx *, const T *, const T *, int, T, T *, T *, \
-                                             cudaStream_t);
+                                             cudaStream_t, const double *);
 FMM_INST(float)
 FMM_INST(double)
 #undef FMM_INST

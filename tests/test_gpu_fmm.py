@@ -175,3 +175,20 @@ def test_check_potentials_per_level(precision):
             ex_d.append(direct.direct_c(ctr[b] + 1.05 * r * grid, xs[far], qs[far], False)[0])
         assert rel(up[boxes], np.array(ex_u)) < 1e-5, level
         assert rel(dn[boxes], np.array(ex_d)) < 1e-5, level
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x6"])
+def test_mean_free_option(precision):
+    # p = 8, two points per leaf: the option keeps FP32 gradients near FP64 quality, and differs
+    # from the textbook kiFMM only by the constant-field fit error (~1e-7 at this order)
+    n, p, depth = 65_536, 8, 5
+    x, q = cube_points(n, seed=7), charges(n, "u01")
+    idx = np.arange(0, n, 37)
+    ref = _oracle(x, q, p, depth, CUBE, sample=idx)
+    dp, dg = direct.direct_self(x.astype(np.float64), q.astype(np.float64), sample=idx)
+    f = make_fmm(x, p, depth, precision, CUBE, mean_free=True)
+    phi, grad = run(f, q)
+    # measured: FP32 7.1e-7 / 1.05e-5, against 4e-5 for the gradient without the option
+    assert rel(phi[idx], ref.phi) < 1e-5 and rel(grad[idx], ref.grad) < 3e-5
+    assert rel(grad[idx], dg) < 3e-5
+    f.sync()

@@ -1,0 +1,93 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+
+The oracle computes sampled outputs one by one: its kiFMM runs the whole upward pass and then
+the downward pass only along the sampled leaves' ancestors (exact same arithmetic as a full
+run, pinned in test_oracle_kifmm.test_sampled_equals_full); the largest case is checked against
+the FP64 direct sum at sampled targets, with the p = 8 truncation error inside the bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2604_19243_gb300 as pkg
+from oracle import direct, kifmm
+from synth import WORKLOADS, sample_indices, charges
+from gpu_helpers import PINV_RTOL, make_fmm, rel, run
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _sampled(w, precision, m=64):
+    x, q = w.points(), w.charges()
+    f = make_fmm(x, w.p, w.depth, precision, (w.origin, w.side))
+    phi, grad = run(f, q)
+    f.sync()
+    f.close()
+    idx = sample_indices(w.n, m)
+    ref = kifmm.evaluate(x.astype(np.float64), q.astype(np.float64), w.p, w.depth, w.origin, w.side,
+                         pinv_rtol=PINV_RTOL, sample=idx)
+    return rel(phi[idx], ref.phi), rel(grad[idx], ref.grad)
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "fp32"])
+def test_sphere8m_against_oracle_sampled(precision):
+    e_phi, e_grad = _sampled(WORKLOADS["sphere8m_p6_d7"], precision)
+    assert e_phi < 1e-5 and e_grad < 1e-4, (e_phi, e_grad)
+
+
+def test_cube1m_against_oracle_sampled():
+    e_phi, e_grad = _sampled(WORKLOADS["cube1m_p6_d5"], "fp32")
+    assert e_phi < 1e-5 and e_grad < 1e-4, (e_phi, e_grad)
+
+
+def test_cube262k_full_and_autograd():
+    w = WORKLOADS["cube262k_p6_d4"]
+    x, q = w.points(), w.charges()
+    f = make_fmm(x, w.p, w.depth, "fp32", (w.origin, w.side))
+    phi, grad = run(f, q)
+    ref = kifmm.evaluate(x.astype(np.float64), q.astype(np.float64), w.p, w.depth, w.origin, w.side,
+                         pinv_rtol=PINV_RTOL)
+    assert rel(phi, ref.phi) < 1e-5 and rel(grad, ref.grad) < 1e-4
+    # E = 1/2 q . phi: dE/dq is (phi + A^T q)/2, dE/dx_k = q_k grad phi(x_k)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    qt = torch.from_numpy(q).cuda().requires_grad_(True)
+    pkg.fmm_energy(qt, xt, f).backward()
+    adj = kifmm.adjoint(x.astype(np.float64), q.astype(np.float64), w.p, w.depth, w.origin, w.side,
+                        pinv_rtol=PINV_RTOL)
+    assert rel(qt.grad.cpu().numpy(), 0.5 * (ref.phi + adj)) < 1e-5
+    assert rel(xt.grad.cpu().numpy(), q.astype(np.float64)[:, None] * ref.grad) < 1e-4
+    # central differences of the FP64 direct-sum energy at a few coordinates (Richardson)
+    xs, q64 = x.astype(np.float64), q.astype(np.float64)
+    dx = xt.grad.cpu().numpy().astype(np.float64)
+    for k in (17, 131_072, 262_000):
+        others = np.delete(np.arange(w.n), k)
+        for a in range(3):
+            def fd(h):
+                t = np.repeat(xs[k:k + 1], 2, axis=0)
+                t[0, a] += h
+                t[1, a] -= h
+                p, _ = direct.direct_c(t, xs[others], q64[others], gradient=False)
+                return q64[k] * (p[0] - p[1]) / (2 * h)
+            rich = (4 * fd(5e-4) - fd(1e-3)) / 3
+            assert dx[k, a] == pytest.approx(rich, rel=2e-3, abs=1e-3 * np.abs(dx).max())
+    f.close()
+
+
+def test_cube33m_p8_d8_against_direct_and_adjoint():
+    # Depth 8 with two points per leaf: the far field carries nearly all of every gradient, and
+    # with the textbook representation the FP32 rounding of the large downward potentials grows
+    # by 2x per level (measured 2e-4 against the direct sum).  The mean-free option removes it.
+    w = WORKLOADS["cube33m_p8_d8"]
+    x, q = w.points(), w.charges()
+    f = make_fmm(x, w.p, w.depth, "bf16x6", (w.origin, w.side), mean_free=True)
+    phi, grad = run(f, q)
+    g = charges(w.n, "normal", seed=2)
+    psi, _ = f.adjoint(torch.from_numpy(g).cuda())
+    f.sync()
+    psi = psi.cpu().numpy().astype(np.float64)
+    idx = sample_indices(w.n, 64)
+    dp, dg = direct.direct_self(x.astype(np.float64), q.astype(np.float64), sample=idx)
+    assert rel(phi[idx], dp) < 1e-5 and rel(grad[idx], dg) < 1e-4
+    g64, q64 = g.astype(np.float64), q.astype(np.float64)
+    assert abs(g64 @ phi - psi @ q64) / (np.linalg.norm(g64) * np.linalg.norm(phi)) < 1e-5
+    f.close()
