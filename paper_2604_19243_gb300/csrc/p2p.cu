@@ -6,6 +6,7 @@
 // the target is (y - x) q / (4 pi |x - y|^3).  Pairs at distance zero are skipped (the self
 // interaction and coincident points, which share a leaf).
 #include <algorithm>
+#include <type_traits>
 
 #include "devutil.cuh"
 #include "fmm_internal.h"
@@ -140,6 +141,148 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
     __syncthreads();   // src / red are reused by the next round
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 form on pairs of sources.  The two-wide FP32 instructions of sm_100 and later (add, mul
+// and fma on float2) do the arithmetic of two (target, source) pairs in one issue slot, so the
+// 13 FP32 operations of a pair cost 6.5 issue slots instead of 13 and the FP32 pipe, not the
+// instruction issue, bounds the sum.  Sources are staged per pair (j, k) as two float4,
+// [x_j x_k y_j y_k] [z_j z_k q_j q_k]; a chunk with an odd count is padded with a zero charge,
+// and that last pair takes the checked path.  Targets are held negated so that one add forms
+// y - x.
+// ---------------------------------------------------------------------------------------
+template <bool checked>
+__device__ __forceinline__ void interact2(const float4 &a, const float4 &b, float2 nx, float2 ny,
+                                          float2 nz, float2 &pot, float2 &gx, float2 &gy, float2 &gz) {
+    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+    const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (checked) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 qr = __fmul2_rn(make_float2(b.z, b.w), ri);
+    pot = __fadd2_rn(pot, qr);
+    const float2 qr3 = __fmul2_rn(__fmul2_rn(qr, ri), ri);
+    gx = __ffma2_rn(qr3, dx, gx);
+    gy = __ffma2_rn(qr3, dy, gy);
+    gz = __ffma2_rn(qr3, dz, gz);
+}
+
+template <int R, bool checked>
+__device__ __forceinline__ void pair_step(const float4 *__restrict__ sp, int e, const float2 *nx,
+                                          const float2 *ny, const float2 *nz, float2 *pot, float2 *gx,
+                                          float2 *gy, float2 *gz) {
+    const float4 a = sp[2 * e], b = sp[2 * e + 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) interact2<checked>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r]);
+}
+
+template <int R, bool GRAD>
+__device__ __forceinline__ void p2p_round_f32(const float4 *__restrict__ pts, float4 *src, float *red,
+                                              const P2PRanges &rg, int t0, int t1, int cbase, int nch,
+                                              int S, float *__restrict__ phi, float *__restrict__ grad) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = warp / S, slice = warp % S;
+    float2 nx[R], ny[R], nz[R], pot[R], gx[R], gy[R], gz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = t0 + (cbase + grp * R + r) * 32 + lane;
+        const float4 p = pts[min(i, t1 - 1)];
+        nx[r] = make_float2(-p.x, -p.x), ny[r] = make_float2(-p.y, -p.y), nz[r] = make_float2(-p.z, -p.z);
+        pot[r] = gx[r] = gy[r] = gz[r] = make_float2(0.f, 0.f);
+    }
+    float *sf = reinterpret_cast<float *>(src);
+    for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
+        const int c1 = min(rg.total, c0 + kP2PChunk);
+        const int n = c1 - c0;
+        __syncthreads();
+        int pos = 0;
+        for (int k = 0; k < rg.n; ++k) {
+            const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
+            for (int e = lo + (int)threadIdx.x; e < hi; e += kP2PThreads) {
+                const float4 v = pts[rg.beg[k] + (e - pos)];
+                const int j = e - c0;
+                float *o = sf + 8 * (j >> 1) + (j & 1);
+                o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
+            }
+            pos += rg.len[k];
+        }
+        if ((n & 1) && threadIdx.x == 0) {   // zero-charge partner of the last source
+            float *o = sf + 8 * (n >> 1) + 1;
+            o[0] = 0.f, o[2] = 0.f, o[4] = 0.f, o[6] = 0.f;
+        }
+        __syncthreads();
+        const int np = (n + 1) >> 1;
+        const int per = (np + S - 1) / S;
+        const int q0 = min(np, slice * per), q1 = min(np, q0 + per);
+        const int self_pairs = (max(0, min(n, rg.self_len - c0)) + 1) >> 1;   // pairs that may hold a target
+        const int qc = min(q1, max(q0, self_pairs));
+        const bool tail = (n & 1) && q1 == np && np - 1 >= qc;              // padded pair, not yet checked
+        const int qu = tail ? q1 - 1 : q1;
+        for (int e = q0; e < qc; ++e) pair_step<R, true>(src, e, nx, ny, nz, pot, gx, gy, gz);
+        int e = qc;
+        for (; e + 4 <= qu; e += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pair_step<R, false>(src, e + u, nx, ny, nz, pot, gx, gy, gz);
+        }
+        for (; e < qu; ++e) pair_step<R, false>(src, e, nx, ny, nz, pot, gx, gy, gz);
+        if (tail) pair_step<R, true>(src, np - 1, nx, ny, nz, pot, gx, gy, gz);
+    }
+    float sp[R], sx[R], sy[R], sz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        sp[r] = pot[r].x + pot[r].y, sx[r] = gx[r].x + gx[r].y;
+        sy[r] = gy[r].x + gy[r].y, sz[r] = gz[r].x + gz[r].y;
+    }
+    if (S > 1) {   // reduce the S slices of every group
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float *o = red + ((size_t)(warp * R + r) * 32 + lane) * 4;
+            o[0] = sp[r], o[1] = sx[r], o[2] = sy[r], o[3] = sz[r];
+        }
+        __syncthreads();
+        if (slice == 0)
+            for (int sl = 1; sl < S; ++sl)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float *o = red + ((size_t)((warp + sl) * R + r) * 32 + lane) * 4;
+                    sp[r] += o[0], sx[r] += o[1], sy[r] += o[2], sz[r] += o[3];
+                }
+    }
+    if (slice == 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ch = grp * R + r;
+            const int i = t0 + (cbase + ch) * 32 + lane;
+            if (ch < nch && i < t1) {
+                phi[i] = sp[r] * inv4pi<float>();
+                if (GRAD) {
+                    grad[3 * (int64_t)i] = sx[r] * inv4pi<float>();
+                    grad[3 * (int64_t)i + 1] = sy[r] * inv4pi<float>();
+                    grad[3 * (int64_t)i + 2] = sz[r] * inv4pi<float>();
+                }
+            }
+        }
+    }
+    __syncthreads();   // src / red are reused by the next round
+}
+
+template <typename T, int R, bool GRAD>
+__device__ __forceinline__ void p2p_round_any(const typename Vec4<T>::type *__restrict__ pts,
+                                              typename Vec4<T>::type *src, T *red, const P2PRanges &rg,
+                                              int t0, int t1, int cbase, int nch, int S,
+                                              T *__restrict__ phi, T *__restrict__ grad) {
+    if constexpr (std::is_same<T, float>::value)
+        p2p_round_f32<R, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad);
+    else
+        p2p_round<T, R, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad);
+}
+
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kP2PThreads)
 p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
@@ -179,10 +322,10 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
         else if (nch <= 8) R = (nch + 1) / 2, S = 2;
         else R = (nch + 3) / 4, S = 1;
         switch (R) {
-            case 1: p2p_round<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 2: p2p_round<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 3: p2p_round<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            default: p2p_round<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 1: p2p_round_any<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 2: p2p_round_any<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 3: p2p_round_any<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            default: p2p_round_any<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
         }
     }
 }
