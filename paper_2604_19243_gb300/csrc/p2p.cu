@@ -146,9 +146,8 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
 // and fma on float2) do the arithmetic of two (target, source) pairs in one issue slot, so the
 // 13 FP32 operations of a pair cost 6.5 issue slots instead of 13 and the FP32 pipe, not the
 // instruction issue, bounds the sum.  Sources are staged per pair (j, k) as two float4,
-// [x_j x_k y_j y_k] [z_j z_k q_j q_k]; a chunk with an odd count is padded with a zero charge,
-// and that last pair takes the checked path.  Targets are held negated so that one add forms
-// y - x.
+// [x_j x_k y_j y_k] [z_j z_k q_j q_k], padded with zero charges to an even number of pairs.
+// Targets are held negated so that one add forms y - x.
 // ---------------------------------------------------------------------------------------
 template <bool checked>
 __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, float2 nx, float2 ny,
@@ -181,106 +180,150 @@ __device__ __forceinline__ void pair_step(const float4 *__restrict__ sp, int e, 
     for (int r = 0; r < R; ++r) interact2<checked>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r]);
 }
 
-template <int R, bool GRAD>
-__device__ __forceinline__ void p2p_round_f32(const float4 *__restrict__ pts, float4 *src, float *red,
-                                              const P2PRanges &rg, int t0, int t1, int cbase, int nch,
-                                              int S, float *__restrict__ phi, float *__restrict__ grad) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = warp / S, slice = warp % S;
-    float2 nx[R], ny[R], nz[R], pot[R], gx[R], gy[R], gz[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = t0 + (cbase + grp * R + r) * 32 + lane;
-        const float4 p = pts[min(i, t1 - 1)];
-        nx[r] = make_float2(-p.x, -p.x), ny[r] = make_float2(-p.y, -p.y), nz[r] = make_float2(-p.z, -p.z);
-        pot[r] = gx[r] = gy[r] = gz[r] = make_float2(0.f, 0.f);
+// FP32 ULI kernel.  Targets go to half-warps 16 at a time (the padding of a leaf's last group
+// is then 6.7% of the sphere workload's pairs instead of 14% with whole warps), and the work of
+// a leaf, (groups of targets) x (source pairs), is cut into four equal contiguous ranges, one
+// per warp, so no warp waits on another for more than one pair step.  The two half-warps of a
+// warp always walk the same pair indices: they hold two target groups, or, for a leaf with an
+// odd number of groups, the two halves of the sources of its last group.  A range may start or
+// end inside a group's sweep; the partial sums go to shared memory and are added up per target
+// in a fixed order, so the results do not depend on timing.
+constexpr int kSub = 16;                        // targets per half-warp
+constexpr int kRoundSub = 16;                   // target groups per round
+constexpr int kRoundT = kSub * kRoundSub;       // 256 targets per round
+constexpr int kSlots = kRoundSub / 2 + 4;       // partial-sum slots: one per (unit, warp) piece
+
+__device__ __forceinline__ void build_ranges(P2PRanges &rg, int b, const int *__restrict__ leaf_off,
+                                             const int *__restrict__ u_off, const int *__restrict__ u_idx) {
+    // the target leaf first (the only one that can hold a zero distance), then its U list
+    const int t0 = leaf_off[b], nt = leaf_off[b + 1] - t0;
+    int k = 0, tot = nt;
+    rg.beg[k] = t0;
+    rg.len[k++] = nt;
+    for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
+        const int a = u_idx[e];
+        if (a == b) continue;
+        rg.beg[k] = leaf_off[a];
+        rg.len[k] = leaf_off[a + 1] - leaf_off[a];
+        tot += rg.len[k++];
     }
-    float *sf = reinterpret_cast<float *>(src);
-    for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
-        const int c1 = min(rg.total, c0 + kP2PChunk);
-        const int n = c1 - c0;
-        __syncthreads();
-        int pos = 0;
-        for (int k = 0; k < rg.n; ++k) {
-            const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
-            for (int e = lo + (int)threadIdx.x; e < hi; e += kP2PThreads) {
-                const float4 v = pts[rg.beg[k] + (e - pos)];
-                const int j = e - c0;
-                float *o = sf + 8 * (j >> 1) + (j & 1);
-                o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
-            }
-            pos += rg.len[k];
-        }
-        if ((n & 1) && threadIdx.x == 0) {   // zero-charge partner of the last source
-            float *o = sf + 8 * (n >> 1) + 1;
-            o[0] = 0.f, o[2] = 0.f, o[4] = 0.f, o[6] = 0.f;
-        }
-        __syncthreads();
-        const int np = (n + 1) >> 1;
-        const int per = (np + S - 1) / S;
-        const int q0 = min(np, slice * per), q1 = min(np, q0 + per);
-        const int self_pairs = (max(0, min(n, rg.self_len - c0)) + 1) >> 1;   // pairs that may hold a target
-        const int qc = min(q1, max(q0, self_pairs));
-        const bool tail = (n & 1) && q1 == np && np - 1 >= qc;              // padded pair, not yet checked
-        const int qu = tail ? q1 - 1 : q1;
-        for (int e = q0; e < qc; ++e) pair_step<R, true>(src, e, nx, ny, nz, pot, gx, gy, gz);
-        int e = qc;
-        for (; e + 4 <= qu; e += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) pair_step<R, false>(src, e + u, nx, ny, nz, pot, gx, gy, gz);
-        }
-        for (; e < qu; ++e) pair_step<R, false>(src, e, nx, ny, nz, pot, gx, gy, gz);
-        if (tail) pair_step<R, true>(src, np - 1, nx, ny, nz, pot, gx, gy, gz);
-    }
-    float sp[R], sx[R], sy[R], sz[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        sp[r] = pot[r].x + pot[r].y, sx[r] = gx[r].x + gx[r].y;
-        sy[r] = gy[r].x + gy[r].y, sz[r] = gz[r].x + gz[r].y;
-    }
-    if (S > 1) {   // reduce the S slices of every group
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float *o = red + ((size_t)(warp * R + r) * 32 + lane) * 4;
-            o[0] = sp[r], o[1] = sx[r], o[2] = sy[r], o[3] = sz[r];
-        }
-        __syncthreads();
-        if (slice == 0)
-            for (int sl = 1; sl < S; ++sl)
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float *o = red + ((size_t)((warp + sl) * R + r) * 32 + lane) * 4;
-                    sp[r] += o[0], sx[r] += o[1], sy[r] += o[2], sz[r] += o[3];
-                }
-    }
-    if (slice == 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int ch = grp * R + r;
-            const int i = t0 + (cbase + ch) * 32 + lane;
-            if (ch < nch && i < t1) {
-                phi[i] = sp[r] * inv4pi<float>();
-                if (GRAD) {
-                    grad[3 * (int64_t)i] = sx[r] * inv4pi<float>();
-                    grad[3 * (int64_t)i + 1] = sy[r] * inv4pi<float>();
-                    grad[3 * (int64_t)i + 2] = sz[r] * inv4pi<float>();
-                }
-            }
-        }
-    }
-    __syncthreads();   // src / red are reused by the next round
+    rg.n = k;
+    rg.total = tot;
+    rg.self_len = nt;
 }
 
-template <typename T, int R, bool GRAD>
-__device__ __forceinline__ void p2p_round_any(const typename Vec4<T>::type *__restrict__ pts,
-                                              typename Vec4<T>::type *src, T *red, const P2PRanges &rg,
-                                              int t0, int t1, int cbase, int nch, int S,
-                                              T *__restrict__ phi, T *__restrict__ grad) {
-    if constexpr (std::is_same<T, float>::value)
-        p2p_round_f32<R, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad);
-    else
-        p2p_round<T, R, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad);
+template <bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads)
+p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
+               const int *__restrict__ u_off, const int *__restrict__ u_idx,
+               const int *__restrict__ order, float *__restrict__ phi, float *__restrict__ grad) {
+    __shared__ __align__(16) float4 src[kP2PChunk];       // sources, pair layout
+    __shared__ __align__(16) float4 tgt[kRoundT];
+    __shared__ __align__(16) float4 acc[kRoundT];         // (pot, gx, gy, gz) per target
+    __shared__ __align__(16) float4 part[kSlots * 32];
+    __shared__ P2PRanges rg;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
+    const int b = order[blockIdx.x];
+    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    if (tid == 0) build_ranges(rg, b, leaf_off, u_off, u_idx);
+    const int groups = (t1 - t0 + kSub - 1) / kSub;
+    float *sf = reinterpret_cast<float *>(src);
+    for (int gb = 0; gb < groups; gb += kRoundSub) {
+        const int m = min(kRoundSub, groups - gb), mt = m * kSub, tb = t0 + gb * kSub;
+        __syncthreads();   // rg ready; tgt / acc of the previous round consumed
+        for (int j = tid; j < mt; j += kP2PThreads) {
+            tgt[j] = pts[min(tb + j, t1 - 1)];
+            acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int npair = m >> 1;                          // units holding two groups
+        for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
+            const int c1 = min(rg.total, c0 + kP2PChunk), n = c1 - c0;
+            const int L = (((n + 1) >> 1) + 1) & ~1;      // source pairs, even
+            __syncthreads();
+            int pos = 0;
+            for (int k = 0; k < rg.n; ++k) {
+                const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
+                for (int e = lo + tid; e < hi; e += kP2PThreads) {
+                    const float4 v = pts[rg.beg[k] + (e - pos)];
+                    const int j = e - c0;
+                    float *o = sf + 8 * (j >> 1) + (j & 1);
+                    o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
+                }
+                pos += rg.len[k];
+            }
+            for (int j = n + tid; j < 2 * L; j += kP2PThreads) {   // zero charges up to 2L
+                float *o = sf + 8 * (j >> 1) + (j & 1);
+                o[0] = 0.f, o[2] = 0.f, o[4] = 0.f, o[6] = 0.f;
+            }
+            __syncthreads();
+            const int T = npair * L + (m & 1) * (L >> 1);
+            const int self_pairs = (max(0, min(n, rg.self_len - c0)) + 1) >> 1;
+            const int pad_pair = n >> 1, pad_split = max(0, pad_pair - (L >> 1));
+            const int W = (T + 3) >> 2;
+            int at = warp * W;
+            const int end = min(T, at + W);
+            while (at < end) {
+                int u, e0, e1, g, soff;
+                if (at < npair * L) {
+                    u = at / L, e0 = at - u * L, e1 = min(L, e0 + (end - at));
+                    g = 2 * u + half, soff = 0;
+                } else {
+                    u = npair, e0 = at - npair * L, e1 = min(L >> 1, e0 + (end - at));
+                    g = m - 1, soff = half * (L >> 1);
+                }
+                const float4 t = tgt[g * kSub + hl];
+                const float2 nx = make_float2(-t.x, -t.x), ny = make_float2(-t.y, -t.y),
+                             nz = make_float2(-t.z, -t.z);
+                float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+                const float4 *sp = src + 2 * soff;
+                // checked: pairs that may hold a target (the leaf's own points lead the list)
+                // or a padding charge at the origin; the bounds are the same for both halves
+                const int ce = min(e1, max(e0, self_pairs)), ue = max(ce, min(e1, u == npair ? pad_split : pad_pair));
+                for (int e = e0; e < ce; ++e) pair_step<1, true>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                int e = ce;
+                for (; e + 4 <= ue; e += 4) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) pair_step<1, false>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                }
+                for (; e < ue; ++e) pair_step<1, false>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                for (e = ue; e < e1; ++e) pair_step<1, true>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                part[(u + warp) * 32 + lane] =
+                    make_float4(pot.x + pot.y, gx.x + gx.y, gy.x + gy.y, gz.x + gz.y);
+                at += e1 - e0;
+            }
+            __syncthreads();
+            for (int j = tid; j < mt; j += kP2PThreads) {   // fixed-order sum of the pieces
+                const int g = j / kSub, h = j % kSub;
+                const bool two = g < 2 * npair;
+                const int u = two ? g >> 1 : npair;
+                const int start = two ? u * L : npair * L, len = two ? L : (L >> 1);
+                float4 s = acc[j];
+                for (int w = start / W; w <= (start + len - 1) / W; ++w) {
+                    const float4 *pp = part + (u + w) * 32;
+                    const float4 a = two ? pp[(g & 1) * kSub + h] : pp[h];
+                    s.x += a.x, s.y += a.y, s.z += a.z, s.w += a.w;
+                    if (!two) {
+                        const float4 c = pp[kSub + h];
+                        s.x += c.x, s.y += c.y, s.z += c.z, s.w += c.w;
+                    }
+                }
+                acc[j] = s;
+            }
+        }
+        // acc[j] is read back by the thread that wrote it
+        for (int j = tid; j < mt; j += kP2PThreads) {
+            const int i = tb + j;
+            if (i < t1) {
+                const float4 s = acc[j];
+                phi[i] = s.x * inv4pi<float>();
+                if (GRAD) {
+                    grad[3 * (int64_t)i] = s.y * inv4pi<float>();
+                    grad[3 * (int64_t)i + 1] = s.z * inv4pi<float>();
+                    grad[3 * (int64_t)i + 2] = s.w * inv4pi<float>();
+                }
+            }
+        }
+    }
 }
 
 template <typename T, bool GRAD>
@@ -297,22 +340,7 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
     const int b = order[blockIdx.x];
     const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
     const int nt = t1 - t0;
-    // range list: the target leaf first (the only one that can hold a zero distance)
-    if (threadIdx.x == 0) {
-        int k = 0, tot = nt;
-        rg.beg[k] = t0;
-        rg.len[k++] = nt;
-        for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
-            const int a = u_idx[e];
-            if (a == b) continue;
-            rg.beg[k] = leaf_off[a];
-            rg.len[k] = leaf_off[a + 1] - leaf_off[a];
-            tot += rg.len[k++];
-        }
-        rg.n = k;
-        rg.total = tot;
-        rg.self_len = nt;
-    }
+    if (threadIdx.x == 0) build_ranges(rg, b, leaf_off, u_off, u_idx);
     __syncthreads();
     const int C = (nt + 31) / 32;   // target chunks
     for (int cbase = 0; cbase < C; cbase += 16) {
@@ -322,10 +350,10 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
         else if (nch <= 8) R = (nch + 1) / 2, S = 2;
         else R = (nch + 3) / 4, S = 1;
         switch (R) {
-            case 1: p2p_round_any<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 2: p2p_round_any<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 3: p2p_round_any<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            default: p2p_round_any<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 1: p2p_round<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 2: p2p_round<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 3: p2p_round<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            default: p2p_round<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
         }
     }
 }
@@ -471,12 +499,20 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     if (ctx->nleaf == 0) return cudaSuccess;
     using P = typename Vec4<T>::type;
     const P *pts = (const P *)ctx->pts;
-    if (grad)
+    if constexpr (std::is_same<T, float>::value) {
+        if (grad)
+            p2p_f32_kernel<true><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                                    ctx->p2p_order, phi, grad);
+        else
+            p2p_f32_kernel<false><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
+                                                                     ctx->p2p_order, phi, nullptr);
+    } else if (grad) {
         p2p_kernel<T, true><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
                                                                 ctx->p2p_order, phi, grad);
-    else
+    } else {
         p2p_kernel<T, false><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
                                                                  ctx->p2p_order, phi, nullptr);
+    }
     count_launch();
     return cudaGetLastError();
 }
