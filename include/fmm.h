@@ -167,9 +167,12 @@ fmm_status fmm_export_level(fmm_ctx *ctx, int level, uint64_t *keys, int64_t *v_
 fmm_status fmm_export_check(fmm_ctx *ctx, int level, int kind, void *host_out);
 
 /* Milliseconds spent in each phase of the last fmm_evaluate or fmm_adjoint, measured with CUDA
- * events on the context's stream: [0] near field (the ULI kernel alone), [1] upward pass
- * (S2U and U2U), [2] VLI (M2L compress and stencil products, all levels), [3] downward pass
- * (decompress, D2D, closing, D2T), [4] whole call.  n <= 5 values are written. */
+ * events: [0] near field (the ULI kernel, on the side stream it runs on), [1] upward pass (S2U
+ * and U2U), [2] VLI (M2L compress and stencil products of all levels, with the downward steps
+ * of the levels above the leaves that overlap them), [3] the leaf level's downward step and
+ * D2T, [4] whole call.  [1] to [3] are consecutive on the far-field stream; the near field runs
+ * concurrently with them at a lower stream priority, so [0] + [1] + [2] + [3] may exceed [4].
+ * n <= 5 values are written. */
 fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n);
 
 /* Wait for all work of ctx and report device-side failures since the last fmm_sync:

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,6 +15,44 @@
 using namespace fmm;
 
 namespace fmm {
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&g_pool[dev], &props)) != cudaSuccess) {
+                g_pool[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = UINT64_MAX;
+            if ((e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+                return e;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_trim() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool[dev]) cudaMemPoolTrimTo(g_pool[dev], 0);
+}
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
@@ -67,12 +106,11 @@ void free_workspace(fmm_ctx *ctx) {
     ctx->ws_bytes = 0;
 }
 
+// The workspaces outlive the tree: a new tree reuses them when it fits (see ensure_workspace).
 void free_tree(fmm_ctx *ctx) {
-    free_workspace(ctx);
     cudaStream_t s = ctx->stream;
     free_async(ctx->pts, s), free_async(ctx->perm, s), free_async(ctx->leaf_off, s);
     free_async(ctx->u_off, s), free_async(ctx->u_idx, s), free_async(ctx->p2p_order, s);
-    free_async(ctx->class_slots, s), free_async(ctx->class_delta, s);
     for (int l = 0; l <= kMaxDepth; ++l) {
         LevelTables &L = ctx->lev[l];
         free_async(L.keys, s), free_async(L.parent, s), free_async(L.child, s);
@@ -80,6 +118,8 @@ void free_tree(fmm_ctx *ctx) {
         L = LevelTables{};
     }
     ctx->have_tree = false;
+    ctx->tiles_ok = false;
+    ctx->last_far = false;
     ctx->n = 0;
     ctx->nleaf = 0;
 }
@@ -95,14 +135,27 @@ void free_ops(fmm_ctx *ctx) {
     ctx->have_ops = false;
 }
 
+// Workspaces sized for the current tree, kept across trees while they fit (rows of levels 0
+// and 1 and padding columns are zeroed once when allocated and never written or read by the
+// passes); the tiles of the VLI and the level sweeps are rebuilt for every tree.
 fmm_status ensure_workspace(fmm_ctx *ctx) {
-    if (ctx->have_ws) return FMM_OK;
+    const int64_t need_rows = ctx->total_rows, need_nl = ctx->nleaf, need_n = ctx->n;
+    if (ctx->have_ws && (need_rows > ctx->ws_rows || need_nl > ctx->ws_nleaf || need_n > ctx->ws_n))
+        free_workspace(ctx);
+    if (ctx->have_ws) {
+        if (!ctx->tiles_ok) {
+            cudaError_t e = build_tiles(ctx, ctx->tensor ? 128 : 64);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "tile construction");
+            ctx->tiles_ok = true;
+        }
+        return FMM_OK;
+    }
     cudaStream_t s = ctx->stream;
     const size_t es = elem_size(ctx);
     const int nsp = ctx->nsp;
     const int kw = std::max(std::max(ctx->fwd.kinp, ctx->fwd.koutp), 16);
     ctx->ws_kw = kw;
-    const int64_t rows = ctx->total_rows, nl = ctx->nleaf, n = ctx->n;
+    const int64_t rows = need_rows, nl = need_nl, n = need_n;
     struct A {
         void **p;
         size_t bytes;
@@ -121,7 +174,7 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         const int np = ctx->opt.precision == FMM_BF16X6 ? 3 : 2;
         const size_t pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
         ctx->utp_plane = (long long)((size_t)rows * kw * pesz + 256) / 256 * 256;
-        if (cudaMallocAsync(&ctx->UtP, (size_t)ctx->utp_plane * np, s) != cudaSuccess) {
+        if (pool_alloc(&ctx->UtP, (size_t)ctx->utp_plane * np, s) != cudaSuccess) {
             cudaGetLastError();
             free_workspace(ctx);
             return fail(ctx, FMM_ENOMEM, "workspace allocation failed (split planes)");
@@ -129,7 +182,7 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     }
     size_t total = 0;
     for (auto &a : allocs) {
-        cudaError_t e = cudaMallocAsync(a.p, std::max<size_t>(a.bytes, 16), s);
+        cudaError_t e = pool_alloc(a.p, std::max<size_t>(a.bytes, 16), s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_workspace(ctx);
@@ -145,7 +198,9 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     }
     cudaError_t e = build_tiles(ctx, ctx->tensor ? 128 : 64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile construction");
+    ctx->tiles_ok = true;
     ctx->ws_bytes = total;
+    ctx->ws_rows = rows, ctx->ws_nleaf = nl, ctx->ws_n = n;
     ctx->have_ws = true;
     return FMM_OK;
 }
@@ -163,7 +218,7 @@ fmm_status stage(fmm_ctx *ctx, const void *p, size_t bytes, bool copy_in, void *
         return FMM_OK;
     }
     if (!*slot) {
-        if (cudaMallocAsync(slot, std::max<size_t>(bytes, 16), ctx->stream) != cudaSuccess) {
+        if (pool_alloc(slot, std::max<size_t>(bytes, 16), ctx->stream) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, FMM_ENOMEM, "staging allocation failed");
         }
@@ -194,21 +249,23 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     const bool far = (parts & FMM_PART_FAR) && ctx->opt.depth >= 2;
     T *ng = (grad && !adjoint) ? (T *)ctx->near_grad : nullptr;
     T *fg = (grad && !adjoint) ? (T *)ctx->far_grad : nullptr;
-    // the near field (ULI) runs on a side stream, concurrently with the far field
-    cudaStream_t ns = ctx->aux[kMaxDepth + 1];
+    // the near field (ULI) and the far field run on two side streams, concurrently
+    cudaStream_t ns = ctx->aux[kMaxDepth + 1], fs = ctx->aux[0];
     cudaStreamWaitEvent(ns, ctx->ev[7], 0);
-    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, ns)) != cudaSuccess)
-        return cuda_fail(ctx, e, "near field");
-    cudaEventRecord(ctx->ev[1], ns);
+    cudaStreamWaitEvent(fs, ctx->ev[7], 0);
     if (far) {
-        e = run_far<T>(ctx, adjoint, (T *)ctx->far_phi, fg, s);
+        e = run_far<T>(ctx, adjoint, (T *)ctx->far_phi, fg, fs);
         if (e == cudaErrorNotSupported)
             return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "far field");
     } else {
-        cudaEventRecord(ctx->ev[2], s), cudaEventRecord(ctx->ev[3], s), cudaEventRecord(ctx->ev[4], s);
+        cudaEventRecord(ctx->ev[2], fs), cudaEventRecord(ctx->ev[3], fs), cudaEventRecord(ctx->ev[4], fs);
     }
-    cudaEventRecord(ctx->ev[5], s);
+    cudaEventRecord(ctx->ev[5], fs);
+    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, ns)) != cudaSuccess)
+        return cuda_fail(ctx, e, "near field");
+    cudaEventRecord(ctx->ev[1], ns);
+    cudaStreamWaitEvent(s, ctx->ev[5], 0);   // join the far field
     cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
     e = launch_scatter<T>(near ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
                           far ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
@@ -284,8 +341,15 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     }
     bool okc = true;
     for (auto &e : ctx->ev) okc = okc && cudaEventCreate(&e) == cudaSuccess;
+    // Far-field streams (aux[0] for the level sweeps, aux[2..] for the VLI of each level) at
+    // the highest priority, the near field (aux[kMaxDepth + 1]) at the lowest: the far field's
+    // dependent chain of small launches then takes SMs first and the near-field kernel fills
+    // whatever it leaves idle.
+    int prio_lo = 0, prio_hi = 0;
+    okc = okc && cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess;
     for (int k = 0; k < kMaxDepth + 2; ++k) {
-        okc = okc && cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking) == cudaSuccess;
+        const int prio = k == kMaxDepth + 1 ? prio_lo : prio_hi;
+        okc = okc && cudaStreamCreateWithPriority(&ctx->aux[k], cudaStreamNonBlocking, prio) == cudaSuccess;
         okc = okc && cudaEventCreateWithFlags(&ctx->fork_ev[k], cudaEventDisableTiming) == cudaSuccess;
         okc = okc && cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
     }
@@ -309,7 +373,7 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n) {
     void *dev = const_cast<void *>(xyz);
     void *tmp = nullptr;
     if (!is_device_ptr(xyz)) {
-        if (cudaMallocAsync(&tmp, bytes, ctx->stream) != cudaSuccess) {
+        if (pool_alloc(&tmp, bytes, ctx->stream) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, FMM_ENOMEM, "staging allocation failed");
         }
@@ -399,7 +463,7 @@ fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
     void *scratch = ctx->far_phi;   // sorted-order buffer reused as the discarded potential
     const size_t es = elem_size(ctx);
     void *tmp = nullptr;
-    if (cudaMallocAsync(&tmp, (size_t)ctx->n * es, ctx->stream) != cudaSuccess) {
+    if (pool_alloc(&tmp, (size_t)ctx->n * es, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, FMM_ENOMEM, "scratch allocation failed");
     }
@@ -423,6 +487,15 @@ fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
     for (int l = 0; l <= ctx->opt.depth; ++l) info->n_boxes[l] = ctx->lev[l].n;
     info->n_u_entries = ctx->n_u;
     info->p2p_pairs = ctx->p2p_pairs;
+    if (ctx->p2p_pairs < 0 && ctx->dev_pairs) {   // computed on the device by the last build
+        unsigned long long h = 0;
+        if (cudaMemcpyAsync(&h, ctx->dev_pairs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return FMM_ECUDA;
+        }
+        info->p2p_pairs = (int64_t)h;
+    }
     for (int a = 0; a < 3; ++a) info->origin[a] = ctx->origin[a];
     info->side = ctx->side;
     return FMM_OK;
@@ -529,7 +602,7 @@ fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n) {
     if (cudaEventSynchronize(ctx->ev[6]) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "timings");
     float t[5] = {};
     cudaEventElapsedTime(&t[0], ctx->ev[7], ctx->ev[1]);
-    cudaEventElapsedTime(&t[1], ctx->ev[1], ctx->ev[3]);
+    cudaEventElapsedTime(&t[1], ctx->ev[7], ctx->ev[3]);
     cudaEventElapsedTime(&t[2], ctx->ev[3], ctx->ev[4]);
     cudaEventElapsedTime(&t[3], ctx->ev[4], ctx->ev[5]);
     cudaEventElapsedTime(&t[4], ctx->ev[0], ctx->ev[6]);
@@ -547,8 +620,17 @@ void fmm_destroy(fmm_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     free_tree(ctx);
+    free_workspace(ctx);
     free_ops(ctx);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->class_slots) cudaFree(ctx->class_slots);
+    if (ctx->class_delta) cudaFree(ctx->class_delta);
+    if (ctx->dev_counts) cudaFree(ctx->dev_counts);
+    if (ctx->dev_pairs) cudaFree(ctx->dev_pairs);
+    if (ctx->host_counts) cudaFreeHost(ctx->host_counts);
+    if (ctx->host_tiles) cudaFreeHost(ctx->host_tiles);
+    if (ctx->tiles_ev) cudaEventDestroy(ctx->tiles_ev);
+    pool_trim();
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     for (int k = 0; k < kMaxDepth + 2; ++k) {

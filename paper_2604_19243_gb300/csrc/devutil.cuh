@@ -15,7 +15,14 @@
 
 namespace fmm {
 
-// Stream-ordered temporary buffer (cudaMallocAsync / cudaFreeAsync).
+// Stream-ordered allocation from a per-device memory pool that keeps freed memory cached
+// (release threshold at its maximum): repeated tree builds and evaluations then reuse device
+// memory instead of mapping it again after every synchronisation.  Freed with cudaFreeAsync.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+// Return the cached, unused memory of the current device's pool to the driver.
+void pool_trim();
+
+// Stream-ordered temporary buffer (pool_alloc / cudaFreeAsync).
 template <typename T>
 struct Scratch {
     T *p = nullptr;
@@ -23,7 +30,7 @@ struct Scratch {
     cudaError_t alloc(size_t n, cudaStream_t st) {
         s = st;
         if (n == 0) n = 1;
-        return cudaMallocAsync((void **)&p, n * sizeof(T), st);
+        return pool_alloc((void **)&p, n * sizeof(T), st);
     }
     ~Scratch() {
         if (p) cudaFreeAsync(p, s);

@@ -25,6 +25,10 @@
 namespace fmm {
 
 constexpr int kMaxDepth = 10;
+// device count array of the tree build: boxes per level, U-list entries, a non-finite
+// coordinate flag, boxes per child octant per level
+constexpr int kCntLevel = 0, kCntU = kMaxDepth + 1, kCntBad = kMaxDepth + 2, kCntOct = kMaxDepth + 3;
+constexpr int kCntSize = kCntOct + 8 * (kMaxDepth + 1);
 constexpr int kNumTransfer = 316;     // [-3,3]^3 minus [-1,1]^3
 constexpr int kClassSlots = 189;      // transfer vectors with adjacent parents, per octant
 
@@ -74,6 +78,11 @@ struct Tile {
     int row0, nrows, cls, mask;
 };
 
+// Stream-ordered allocation from the library's per-device pool (memory is kept cached for
+// reuse); freed with cudaFreeAsync.  pool_trim returns the unused memory to the driver.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_trim();
+
 struct LevelTables {
     int64_t n = 0;              // non-empty boxes
     uint32_t *keys = nullptr;   // ascending Morton keys
@@ -121,13 +130,21 @@ struct fmm_ctx {
     fmm::TileSet tiles_plain[fmm::kMaxDepth + 1];
     fmm::TileSet tiles_cls[fmm::kMaxDepth + 1];
     int tile_m = 0;             // tile height the tile sets were built for
-    int *class_slots = nullptr; // device [8][189] transfer index of each slot
-    int *class_delta = nullptr; // device [8][189] packed (dx, dy, dz) of each slot
+    int *class_slots = nullptr; // device [8][189] transfer index of each slot (per context)
+    int *class_delta = nullptr; // device [8][189] packed (dx, dy, dz) of each slot (per context)
+    // counts the tree build produces on the device, read back once per build (layout: kCnt*)
+    int *dev_counts = nullptr, *host_counts = nullptr;   // device / pinned host [kCntSize]
+    unsigned long long *dev_pairs = nullptr;              // device: near-field pair count
+    fmm::Tile *host_tiles = nullptr;                      // pinned staging of the tile lists
+    size_t host_tiles_cap = 0;
+    cudaEvent_t tiles_ev = nullptr;                       // completion of the last tile copies
     // P2P schedule: leaves in decreasing work order
     int *p2p_order = nullptr;
 
     // evaluate workspaces (allocated with the tree once operators are known)
     bool have_ws = false;
+    bool tiles_ok = false;          // tiles of the current tree built
+    int64_t ws_rows = 0, ws_nleaf = 0, ws_n = 0;   // capacity of the workspaces
     void *Uc = nullptr, *Dc = nullptr;   // [total_rows x nsp] upward / downward check potentials
     void *Ut = nullptr, *Ct = nullptr;   // [total_rows x ws_kw] compressed M2L vectors
     void *UtP = nullptr;                 // tensor-core modes: Ut as split planes [plane][rows x ws_kw]

@@ -168,15 +168,17 @@ double from_ordered_bits(long long l) {
 
 // anchor a = min(max(floor((x - o) * scale), 0), 2^d - 1), every FP64 operation rounded
 // separately (no fused multiply-add) so that the host oracle reproduces it bit for bit.
+// A non-finite coordinate sets *bad (when given).
 template <typename T>
 __global__ void morton_kernel(const T *xyz, int64_t n, double ox, double oy, double oz,
-                              double scale, int depth, uint32_t *keys, int *idx) {
+                              double scale, int depth, uint32_t *keys, int *idx, int *bad) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double o[3] = {ox, oy, oz};
     const double amax = (double)((1 << depth) - 1);
     uint32_t a[3];
     for (int k = 0; k < 3; ++k) {
+        if (bad && !isfinite((double)xyz[3 * i + k])) *bad = 1;
         double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + k], o[k]), scale);
         t = floor(t);
         t = fmin(fmax(t, 0.0), amax);
@@ -296,21 +298,26 @@ __global__ void gather_sorted_points(const T *xyz, const int *perm, int64_t n, P
     pts[i] = p;
 }
 
-// flag[i] = 1 where a new run of (keys >> shift) starts
-__global__ void run_flags(const uint32_t *keys, int64_t n, int shift, int *flags) {
+// Kernels below take the element count either from the host (`cnt` null) or from device
+// memory (`cnt`), with `n` then an upper bound that sizes the grid: the tree build runs from
+// the keys to the U lists without reading a count back.
+__device__ __forceinline__ int64_t count_of(const int *cnt, int64_t n) { return cnt ? (int64_t)*cnt : n; }
+
+// flag[i] = 1 where a new run of (keys >> shift) starts; 0 past the count (up to n)
+__global__ void run_flags(const uint32_t *keys, int64_t n, const int *cnt, int shift, int *flags) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    flags[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+    flags[i] = (i < count_of(cnt, n) && (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift))) ? 1 : 0;
 }
 
 // After an exclusive scan of the flags: runs get contiguous ids.  For every run start record
 // its position (offsets) and key; for every element record its run id (optional).  The
 // exclusive scan counts the starts strictly before i, so an element that does not start a run
 // sees its own run's start too and its id is the scanned value minus one.
-__global__ void run_compact(const uint32_t *keys, const int *flags_scanned, int64_t n, int shift,
-                            int *run_start, uint32_t *run_key, int *elem_run) {
+__global__ void run_compact(const uint32_t *keys, const int *flags_scanned, int64_t n, const int *cnt,
+                            int shift, int *run_start, uint32_t *run_key, int *elem_run) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= count_of(cnt, n)) return;
     const bool start = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift));
     const int id = flags_scanned[i] - (start ? 0 : 1);
     if (start) {
@@ -320,24 +327,43 @@ __global__ void run_compact(const uint32_t *keys, const int *flags_scanned, int6
     if (elem_run) elem_run[i] = id;
 }
 
-__global__ void set_last(int *arr, int64_t pos, int value) { arr[pos] = value; }
+// arr[pos] = value, pos from the device when given there
+__global__ void set_last(int *arr, const int *pos_dev, int64_t pos, const int *value_dev, int value) {
+    arr[pos_dev ? *pos_dev : pos] = value_dev ? *value_dev : value;
+}
 
-__global__ void fill_child(const uint32_t *keys, const int *parent, int64_t n, int *child) {
+__global__ void fill_child(const uint32_t *keys, const int *parent, int64_t n, const int *cnt, int *child) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= count_of(cnt, n)) return;
     child[(int64_t)parent[i] * 8 + (keys[i] & 7u)] = (int)i;
 }
 
-__global__ void fill_dense(const uint32_t *keys, int64_t n, int *dense) {
+__global__ void fill_dense(const uint32_t *keys, int64_t n, const int *cnt, int *dense) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= count_of(cnt, n)) return;
     dense[keys[i]] = (int)i;
 }
 
+// boxes per child octant (key & 7) of one level
+__global__ void octant_hist(const uint32_t *keys, int64_t n, const int *cnt, int *hist8) {
+    __shared__ int h[8];
+    if (threadIdx.x < 8) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t c = count_of(cnt, n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[keys[i] & 7u], 1);
+    __syncthreads();
+    if (threadIdx.x < 8 && h[threadIdx.x]) atomicAdd(&hist8[threadIdx.x], h[threadIdx.x]);
+}
+
 // U list of every leaf: its non-empty colleagues and itself, ascending box index (= Morton).
-__global__ void u_count(const uint32_t *keys, int nleaf, const int *dense, int depth, int *cnt) {
+__global__ void u_count(const uint32_t *keys, int nbound, const int *nleaf, const int *dense, int depth, int *cnt) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nleaf) return;
+    if (b >= nbound) return;
+    if (b >= *nleaf) {
+        cnt[b] = 0;
+        return;
+    }
     int ax, ay, az;
     demorton3(keys[b], ax, ay, az);
     int c = 0;
@@ -507,168 +533,176 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t
 // build
 // ---------------------------------------------------------------------------------------
 
+// Per-context constant tables and count buffers (allocated on the first build).
+static cudaError_t ensure_build_buffers(fmm_ctx *ctx) {
+    if (!ctx->dev_counts) FMM_CUDA_TRY(cudaMalloc((void **)&ctx->dev_counts, kCntSize * sizeof(int)));
+    if (!ctx->host_counts) FMM_CUDA_TRY(cudaMallocHost((void **)&ctx->host_counts, kCntSize * sizeof(int)));
+    if (!ctx->dev_pairs) FMM_CUDA_TRY(cudaMalloc((void **)&ctx->dev_pairs, sizeof(unsigned long long)));
+    if (!ctx->class_slots) {
+        std::vector<int> slots, deltas;
+        class_slot_table(slots, deltas);
+        FMM_CUDA_TRY(cudaMalloc((void **)&ctx->class_slots, slots.size() * sizeof(int)));
+        FMM_CUDA_TRY(cudaMalloc((void **)&ctx->class_delta, deltas.size() * sizeof(int)));
+        FMM_CUDA_TRY(cudaMemcpy(ctx->class_slots, slots.data(), slots.size() * sizeof(int), cudaMemcpyHostToDevice));
+        FMM_CUDA_TRY(cudaMemcpy(ctx->class_delta, deltas.data(), deltas.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return cudaSuccess;
+}
+
+// The build runs on the device from the coordinates to the U-list offsets with every box
+// count kept in device memory (arrays sized by the bound min(n, 8^l) of level l), then reads
+// all counts back in one copy; the remaining steps are sized on the host and stay
+// stream-ordered, so that a build waits on the device once (twice without a given domain).
 template <typename T>
 static cudaError_t build_tree_t(fmm_ctx *ctx, const T *xyz) {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n;
     const int depth = ctx->opt.depth;
+    FMM_CUDA_TRY(ensure_build_buffers(ctx));
+    int *cnt = ctx->dev_counts;
+    FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, kCntSize * sizeof(int), s));
+    FMM_CUDA_TRY(cudaMemsetAsync(ctx->dev_pairs, 0, sizeof(unsigned long long), s));
     // 1. bounding cube
     if (ctx->opt.has_domain) {
         for (int a = 0; a < 3; ++a) ctx->origin[a] = ctx->opt.origin[a];
         ctx->side = ctx->opt.side;
-    }
-    {
+    } else {
         Scratch<double> mm;
-        Scratch<int> bad;
         FMM_CUDA_TRY(mm.alloc(6, s));
-        FMM_CUDA_TRY(bad.alloc(1, s));
         long long init[6];
         for (int a = 0; a < 3; ++a) {
             init[a] = ordered_bits(INFINITY);
             init[3 + a] = ordered_bits(-INFINITY);
         }
         FMM_CUDA_TRY(cudaMemcpyAsync(mm.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
-        FMM_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-        extent_kernel<T><<<std::min<unsigned>(blocks_for(n, 256), 1024), 256, 0, s>>>(xyz, n, mm.p, bad.p); count_launch();
+        extent_kernel<T><<<std::min<unsigned>(blocks_for(n, 256), 1024), 256, 0, s>>>(xyz, n, mm.p, cnt + kCntBad); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
         long long res[6];
-        int hbad = 0;
         FMM_CUDA_TRY(cudaMemcpyAsync(res, mm.p, sizeof(res), cudaMemcpyDeviceToHost, s));
-        FMM_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         FMM_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hbad) return cudaErrorInvalidValue;   // mapped to FMM_EINVAL by the caller
-        if (!ctx->opt.has_domain) {
-            double ext = 0;
-            for (int a = 0; a < 3; ++a) {
-                double lo = from_ordered_bits(res[a]), hi = from_ordered_bits(res[3 + a]);
-                ctx->origin[a] = lo;
-                ext = std::max(ext, hi - lo);
-            }
-            ctx->side = ext > 0 ? ext * (1.0 + std::ldexp(1.0, -20)) : 1.0;
+        double ext = 0;
+        for (int a = 0; a < 3; ++a) {
+            double lo = from_ordered_bits(res[a]), hi = from_ordered_bits(res[3 + a]);
+            ctx->origin[a] = std::isfinite(lo) ? lo : 0.0;
+            if (std::isfinite(hi - lo)) ext = std::max(ext, hi - lo);
         }
+        ctx->side = ext > 0 ? ext * (1.0 + std::ldexp(1.0, -20)) : 1.0;
     }
     const double scale = std::ldexp(1.0, depth) / ctx->side;
+    auto bound = [&](int l) { return std::min<int64_t>(n, (int64_t)1 << (3 * l)); };
     // 2-3. keys and stable sort
     Scratch<uint32_t> keys;
     FMM_CUDA_TRY(keys.alloc(n, s));
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->perm, n * sizeof(int), s));
-    morton_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ctx->origin[0], ctx->origin[1],
-                                                          ctx->origin[2], scale, depth, keys.p, ctx->perm); count_launch();
+    FMM_CUDA_TRY(pool_alloc((void **)&ctx->perm, n * sizeof(int), s));
+    morton_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ctx->origin[0], ctx->origin[1], ctx->origin[2],
+                                                          scale, depth, keys.p, ctx->perm, cnt + kCntBad); count_launch();
     FMM_CUDA_TRY(cudaGetLastError());
     FMM_CUDA_TRY(radix_sort(keys.p, ctx->perm, n, 3 * depth, s));
     // sorted points (x, y, z, q=0)
     const size_t psz = ctx->fp64 ? sizeof(double4) : sizeof(float4);
-    FMM_CUDA_TRY(cudaMallocAsync(&ctx->pts, n * psz, s));
+    FMM_CUDA_TRY(pool_alloc(&ctx->pts, n * psz, s));
     if (ctx->fp64)
         gather_sorted_points<T, double4><<<blocks_for(n, 256), 256, 0, s>>>(xyz, ctx->perm, n, (double4 *)ctx->pts);
     else
         gather_sorted_points<T, float4><<<blocks_for(n, 256), 256, 0, s>>>(xyz, ctx->perm, n, (float4 *)ctx->pts);
     count_launch();
     FMM_CUDA_TRY(cudaGetLastError());
-    // 4. leaves
-    Scratch<int> flags;
-    Scratch<int> dtot;
-    FMM_CUDA_TRY(flags.alloc(n, s));
-    FMM_CUDA_TRY(dtot.alloc(1, s));
-    run_flags<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, n, 0, flags.p); count_launch();
-    FMM_CUDA_TRY(exclusive_scan<int>(flags.p, n, dtot.p, s));
-    int nleaf = 0;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&nleaf, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FMM_CUDA_TRY(cudaStreamSynchronize(s));
-    ctx->nleaf = nleaf;
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->leaf_off, (nleaf + 1) * sizeof(int), s));
-    LevelTables &L = ctx->lev[depth];
-    L.n = nleaf;
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&L.keys, nleaf * sizeof(uint32_t), s));
-    run_compact<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, flags.p, n, 0, ctx->leaf_off, L.keys, nullptr); count_launch();
-    set_last<<<1, 1, 0, s>>>(ctx->leaf_off, nleaf, (int)n); count_launch();
-    FMM_CUDA_TRY(cudaGetLastError());
-    // levels d-1 .. 0: unique parents of the sorted child keys
-    for (int l = depth; l >= 1; --l) {
-        LevelTables &C = ctx->lev[l], &P = ctx->lev[l - 1];
-        Scratch<int> f;
-        FMM_CUDA_TRY(f.alloc(C.n, s));
-        run_flags<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, C.n, 3, f.p); count_launch();
-        FMM_CUDA_TRY(exclusive_scan<int>(f.p, C.n, dtot.p, s));
-        int np = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&np, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        FMM_CUDA_TRY(cudaStreamSynchronize(s));
-        P.n = np;
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&P.keys, np * sizeof(uint32_t), s));
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&C.parent, C.n * sizeof(int), s));
-        run_compact<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, f.p, C.n, 3, nullptr, P.keys, C.parent); count_launch();
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&P.child, (size_t)np * 8 * sizeof(int), s));
-        FMM_CUDA_TRY(cudaMemsetAsync(P.child, 0xff, (size_t)np * 8 * sizeof(int), s));
-        fill_child<<<blocks_for(C.n, 256), 256, 0, s>>>(C.keys, C.parent, C.n, P.child); count_launch();
+    // 4. leaves (runs of equal keys) and the boxes of every level (runs of equal parent keys)
+    {
+        Scratch<int> flags;
+        FMM_CUDA_TRY(flags.alloc(n, s));
+        run_flags<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, n, nullptr, 0, flags.p); count_launch();
+        FMM_CUDA_TRY(exclusive_scan<int>(flags.p, n, cnt + kCntLevel + depth, s));
+        const int64_t bd = bound(depth);
+        FMM_CUDA_TRY(pool_alloc((void **)&ctx->leaf_off, (bd + 1) * sizeof(int), s));
+        FMM_CUDA_TRY(pool_alloc((void **)&ctx->lev[depth].keys, bd * sizeof(uint32_t), s));
+        run_compact<<<blocks_for(n, 256), 256, 0, s>>>(keys.p, flags.p, n, nullptr, 0, ctx->leaf_off,
+                                                         ctx->lev[depth].keys, nullptr); count_launch();
+        set_last<<<1, 1, 0, s>>>(ctx->leaf_off, cnt + kCntLevel + depth, 0, nullptr, (int)n); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
     }
-    // 5. dense tables, row bases
+    for (int l = depth; l >= 1; --l) {
+        LevelTables &C = ctx->lev[l], &P = ctx->lev[l - 1];
+        const int64_t bc = bound(l), bp = bound(l - 1);
+        const int *nc = cnt + kCntLevel + l;
+        Scratch<int> f;
+        FMM_CUDA_TRY(f.alloc(bc, s));
+        run_flags<<<blocks_for(bc, 256), 256, 0, s>>>(C.keys, bc, nc, 3, f.p); count_launch();
+        FMM_CUDA_TRY(exclusive_scan<int>(f.p, bc, cnt + kCntLevel + l - 1, s));
+        FMM_CUDA_TRY(pool_alloc((void **)&P.keys, bp * sizeof(uint32_t), s));
+        FMM_CUDA_TRY(pool_alloc((void **)&C.parent, bc * sizeof(int), s));
+        run_compact<<<blocks_for(bc, 256), 256, 0, s>>>(C.keys, f.p, bc, nc, 3, nullptr, P.keys, C.parent); count_launch();
+        FMM_CUDA_TRY(pool_alloc((void **)&P.child, (size_t)bp * 8 * sizeof(int), s));
+        FMM_CUDA_TRY(cudaMemsetAsync(P.child, 0xff, (size_t)bp * 8 * sizeof(int), s));
+        fill_child<<<blocks_for(bc, 256), 256, 0, s>>>(C.keys, C.parent, bc, nc, P.child); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    // 5. dense tables and the octant histograms
+    for (int l = 0; l <= depth; ++l) {
+        LevelTables &T_ = ctx->lev[l];
+        const int64_t bl = bound(l);
+        size_t sz = (size_t)1 << (3 * l);
+        FMM_CUDA_TRY(pool_alloc((void **)&T_.dense, sz * sizeof(int), s));
+        FMM_CUDA_TRY(cudaMemsetAsync(T_.dense, 0xff, sz * sizeof(int), s));
+        fill_dense<<<blocks_for(bl, 256), 256, 0, s>>>(T_.keys, bl, cnt + kCntLevel + l, T_.dense); count_launch();
+        if (l >= 1) {
+            octant_hist<<<std::min<unsigned>(blocks_for(bl, 256), 256), 256, 0, s>>>(T_.keys, bl, cnt + kCntLevel + l,
+                                                                                       cnt + kCntOct + 8 * l); count_launch();
+        }
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    // 6. U-list sizes and offsets
+    const int64_t bd = bound(depth);
+    FMM_CUDA_TRY(pool_alloc((void **)&ctx->u_off, (bd + 1) * sizeof(int), s));
+    u_count<<<blocks_for(bd, 128), 128, 0, s>>>(ctx->lev[depth].keys, (int)bd, cnt + kCntLevel + depth,
+                                                 ctx->lev[depth].dense, depth, ctx->u_off); count_launch();
+    FMM_CUDA_TRY(cudaGetLastError());
+    FMM_CUDA_TRY(exclusive_scan<int>(ctx->u_off, bd, cnt + kCntU, s));
+    set_last<<<1, 1, 0, s>>>(ctx->u_off, cnt + kCntLevel + depth, 0, cnt + kCntU, 0); count_launch();
+    // the one read-back of the build
+    int *hc = ctx->host_counts;
+    FMM_CUDA_TRY(cudaMemcpyAsync(hc, cnt, kCntSize * sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hc[kCntBad]) return cudaErrorInvalidValue;   // mapped to FMM_EINVAL by the caller
     int64_t rows = 0;
     for (int l = 0; l <= depth; ++l) {
         LevelTables &T_ = ctx->lev[l];
+        T_.n = hc[kCntLevel + l];
         T_.row_base = rows;
         rows += T_.n;
-        size_t sz = (size_t)1 << (3 * l);
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&T_.dense, sz * sizeof(int), s));
-        FMM_CUDA_TRY(cudaMemsetAsync(T_.dense, 0xff, sz * sizeof(int), s));
-        fill_dense<<<blocks_for(T_.n, 256), 256, 0, s>>>(T_.keys, T_.n, T_.dense); count_launch();
-        FMM_CUDA_TRY(cudaGetLastError());
+        T_.cls_off[0] = 0;
+        for (int c = 0; c < 8; ++c) T_.cls_off[c + 1] = T_.cls_off[c] + (l >= 1 ? hc[kCntOct + 8 * l + c] : 0);
     }
     ctx->total_rows = rows;
-    // 6. U lists
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->u_off, (nleaf + 1) * sizeof(int), s));
-    u_count<<<blocks_for(nleaf, 128), 128, 0, s>>>(L.keys, nleaf, L.dense, depth, ctx->u_off); count_launch();
+    const int nleaf = (int)ctx->lev[depth].n;
+    ctx->nleaf = nleaf;
+    ctx->n_u = hc[kCntU];
+    // U lists
+    FMM_CUDA_TRY(pool_alloc((void **)&ctx->u_idx, std::max<int64_t>(ctx->n_u, 1) * sizeof(int), s));
+    u_fill<<<blocks_for(nleaf, 128), 128, 0, s>>>(ctx->lev[depth].keys, nleaf, ctx->lev[depth].dense, depth,
+                                                   ctx->u_off, ctx->u_idx); count_launch();
     FMM_CUDA_TRY(cudaGetLastError());
-    FMM_CUDA_TRY(exclusive_scan<int>(ctx->u_off, nleaf, dtot.p, s));
-    int nu = 0;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&nu, dtot.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FMM_CUDA_TRY(cudaStreamSynchronize(s));
-    ctx->n_u = nu;
-    set_last<<<1, 1, 0, s>>>(ctx->u_off, nleaf, nu); count_launch();
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->u_idx, std::max(nu, 1) * sizeof(int), s));
-    u_fill<<<blocks_for(nleaf, 128), 128, 0, s>>>(L.keys, nleaf, L.dense, depth, ctx->u_off, ctx->u_idx); count_launch();
-    FMM_CUDA_TRY(cudaGetLastError());
-    // P2P schedule (decreasing work) and the total pair count
+    // P2P schedule (decreasing work) and the total pair count (read when asked for)
     {
         Scratch<uint32_t> wk;
-        Scratch<unsigned long long> tot;
         FMM_CUDA_TRY(wk.alloc(nleaf, s));
-        FMM_CUDA_TRY(tot.alloc(1, s));
-        FMM_CUDA_TRY(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->p2p_order, nleaf * sizeof(int), s));
+        FMM_CUDA_TRY(pool_alloc((void **)&ctx->p2p_order, std::max(nleaf, 1) * sizeof(int), s));
         p2p_work<<<blocks_for(nleaf, 256), 256, 0, s>>>(ctx->leaf_off, ctx->u_off, ctx->u_idx, nleaf,
-                                                          wk.p, ctx->p2p_order, tot.p); count_launch();
+                                                          wk.p, ctx->p2p_order, ctx->dev_pairs); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
         FMM_CUDA_TRY(radix_sort(wk.p, ctx->p2p_order, nleaf, 32, s));
-        unsigned long long h = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-        FMM_CUDA_TRY(cudaStreamSynchronize(s));
-        ctx->p2p_pairs = (int64_t)h;
+        ctx->p2p_pairs = -1;
     }
-    // class (octant) order per level >= 1
+    // class (octant) order per level >= 1: stable sort by octant, class offsets from the counts
     for (int l = 1; l <= depth; ++l) {
         LevelTables &T_ = ctx->lev[l];
         Scratch<uint32_t> oct;
         FMM_CUDA_TRY(oct.alloc(T_.n, s));
-        FMM_CUDA_TRY(cudaMallocAsync((void **)&T_.cls_rows, T_.n * sizeof(int), s));
+        FMM_CUDA_TRY(pool_alloc((void **)&T_.cls_rows, std::max<int64_t>(T_.n, 1) * sizeof(int), s));
         octant_keys<<<blocks_for(T_.n, 256), 256, 0, s>>>(T_.keys, T_.n, oct.p, T_.cls_rows); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
         FMM_CUDA_TRY(radix_sort(oct.p, T_.cls_rows, T_.n, 3, s));
-        std::vector<uint32_t> h(T_.n);
-        FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), oct.p, T_.n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        FMM_CUDA_TRY(cudaStreamSynchronize(s));
-        for (int c = 0; c <= 8; ++c)
-            T_.cls_off[c] = (int)(std::lower_bound(h.begin(), h.end(), (uint32_t)c) - h.begin());
     }
-    std::vector<int> slots, deltas;
-    class_slot_table(slots, deltas);
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->class_slots, slots.size() * sizeof(int), s));
-    FMM_CUDA_TRY(cudaMemcpyAsync(ctx->class_slots, slots.data(), slots.size() * sizeof(int),
-                                 cudaMemcpyHostToDevice, s));
-    FMM_CUDA_TRY(cudaMallocAsync((void **)&ctx->class_delta, deltas.size() * sizeof(int), s));
-    FMM_CUDA_TRY(cudaMemcpyAsync(ctx->class_delta, deltas.data(), deltas.size() * sizeof(int),
-                                 cudaMemcpyHostToDevice, s));
-    FMM_CUDA_TRY(cudaStreamSynchronize(s));
     return cudaSuccess;
 }
 
@@ -677,9 +711,17 @@ cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz) {
     return build_tree_t<float>(ctx, (const float *)d_xyz);
 }
 
+// Tile lists of every level, copied to the device from one pinned staging buffer (reused once
+// the copies out of it have completed).
 cudaError_t build_tiles(fmm_ctx *ctx, int tile_m) {
     cudaStream_t s = ctx->stream;
     const int depth = ctx->opt.depth;
+    std::vector<Tile> staged;
+    struct Copy {
+        Tile *dst;
+        int count;
+    };
+    std::vector<Copy> copies;
     for (int l = 0; l <= depth; ++l) {
         for (TileSet *ts : {&ctx->tiles_plain[l], &ctx->tiles_cls[l]}) {
             if (ts->tiles) cudaFreeAsync(ts->tiles, s);
@@ -703,19 +745,38 @@ cudaError_t build_tiles(fmm_ctx *ctx, int tile_m) {
         for (TileSet *ts : {&pl, &cl}) {
             ts->ntiles = (int)ts->host.size();
             if (!ts->ntiles) continue;
-            FMM_CUDA_TRY(cudaMallocAsync((void **)&ts->tiles, ts->ntiles * sizeof(Tile), s));
-            FMM_CUDA_TRY(cudaMemcpyAsync(ts->tiles, ts->host.data(), ts->ntiles * sizeof(Tile),
-                                         cudaMemcpyHostToDevice, s));
-        }
-        if (l >= 2 && cl.ntiles) {
-            FMM_CUDA_TRY(cudaMallocAsync((void **)&cl.masks, (size_t)cl.ntiles * 6 * sizeof(uint32_t), s));
-            tile_masks<<<cl.ntiles, 256, 0, s>>>(cl.tiles, cl.ntiles, T_.cls_rows, T_.keys, T_.dense, l,
-                                                 ctx->class_delta, cl.masks); count_launch();
-            FMM_CUDA_TRY(cudaGetLastError());
+            FMM_CUDA_TRY(pool_alloc((void **)&ts->tiles, ts->ntiles * sizeof(Tile), s));
+            staged.insert(staged.end(), ts->host.begin(), ts->host.end());
+            copies.push_back({ts->tiles, ts->ntiles});
         }
     }
+    if (!ctx->tiles_ev) FMM_CUDA_TRY(cudaEventCreateWithFlags(&ctx->tiles_ev, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventSynchronize(ctx->tiles_ev));   // earlier copies out of the staging buffer
+    if (staged.size() > ctx->host_tiles_cap) {
+        if (ctx->host_tiles) cudaFreeHost(ctx->host_tiles);
+        ctx->host_tiles = nullptr;
+        ctx->host_tiles_cap = 0;
+        FMM_CUDA_TRY(cudaMallocHost((void **)&ctx->host_tiles, staged.size() * 2 * sizeof(Tile)));
+        ctx->host_tiles_cap = staged.size() * 2;
+    }
+    std::copy(staged.begin(), staged.end(), ctx->host_tiles);
+    size_t off = 0;
+    for (const Copy &c : copies) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(c.dst, ctx->host_tiles + off, c.count * sizeof(Tile), cudaMemcpyHostToDevice, s));
+        off += c.count;
+    }
+    FMM_CUDA_TRY(cudaEventRecord(ctx->tiles_ev, s));
+    for (int l = 2; l <= depth; ++l) {
+        LevelTables &T_ = ctx->lev[l];
+        TileSet &cl = ctx->tiles_cls[l];
+        if (!cl.ntiles) continue;
+        FMM_CUDA_TRY(pool_alloc((void **)&cl.masks, (size_t)cl.ntiles * 6 * sizeof(uint32_t), s));
+        tile_masks<<<cl.ntiles, 256, 0, s>>>(cl.tiles, cl.ntiles, T_.cls_rows, T_.keys, T_.dense, l,
+                                             ctx->class_delta, cl.masks); count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
     ctx->tile_m = tile_m;
-    return cudaStreamSynchronize(s);
+    return cudaSuccess;
 }
 
 cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, int32_t *tv,
@@ -838,7 +899,7 @@ extern "C" fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int d
     int *sums = hist + kNoAllocHist;
     const double scale = std::ldexp(1.0, depth) / side;
     morton_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, origin[0], origin[1], origin[2], scale, depth,
-                                                           keys, perm);
+                                                           keys, perm, nullptr);
     count_launch();
     // stable LSD radix sort of (keys, perm), 8-bit digits, ping-ponging with the scratch copies
     const int bits = 3 * depth;
