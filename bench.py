@@ -185,8 +185,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere8m_p6_d7", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="bf16x6",
-                    choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--precision", default="fp16x3",
+                    choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -317,9 +317,9 @@ def main():
         nv = len(lv["v_idx"])
         vpairs += nv
         m2l_flops += 2.0 * kin * ns * nl + 2.0 * kout * kin * nv
-    tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3")
+    tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3", "fp16x3")
     if tensor:
-        mult = {"bf16x3": 3, "bf16x6": 6, "tf32x3": 3}[args.precision]
+        mult = {"bf16x3": 3, "bf16x6": 6, "tf32x3": 3, "fp16x3": 3}[args.precision]
         base = float(peaks["bf16_tflops_sustained"]) * (0.5 if args.precision == "tf32x3" else 1.0)
         m2l = {"bound": "tensor", "achieved": mult * m2l_flops / (m2l_ms * 1e-3) / 1e12,
                "peak": base, "unit": "TFLOP/s",
@@ -353,9 +353,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0:
         line["accuracy"] = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
                                           grad.cpu().numpy().astype(np.float64))
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(w.p)
     if rank == 0:
         print(json.dumps(line), flush=True)

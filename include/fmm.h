@@ -54,7 +54,11 @@ typedef enum {
     FMM_FP64 = 1,          /* FP64 SIMT everywhere; inputs and outputs are double */
     FMM_TF32X3 = 2,        /* contractions on tcgen05 tensor cores, 3 TF32 products (big/small split) */
     FMM_BF16X3 = 3,        /* contractions on tcgen05 tensor cores, 3 BF16 products (hi/lo split) */
-    FMM_BF16X6 = 4         /* contractions on tcgen05 tensor cores, 6 BF16 products (hi/mid/lo split) */
+    FMM_BF16X6 = 4,        /* contractions on tcgen05 tensor cores, 6 BF16 products (hi/mid/lo split) */
+    FMM_FP16X3 = 5         /* as FMM_BF16X6, except the M2L stencil products (the VLI's bulk): FP16
+                              hi/lo splits of power-of-two scaled operands (the compressed vectors
+                              scaled per box and 64-column chunk, the operators per chunk), 3 FP16
+                              products, about 2^-22 relative per term, scales applied in FP32 */
 } fmm_precision;
 
 typedef struct {

@@ -20,7 +20,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libfmm.so")
 
-PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
+PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp16x3": 5}
 STATUS = {0: "FMM_OK", 1: "FMM_EINVAL", 2: "FMM_ENOMEM", 3: "FMM_ECUDA", 4: "FMM_ESTATE",
           5: "FMM_ETIMEOUT", 6: "FMM_EUNSUPPORTED"}
 PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3

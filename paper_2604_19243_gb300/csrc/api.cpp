@@ -91,7 +91,7 @@ void free_async(P *&p, cudaStream_t s) {
 void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
-    free_async(ctx->UtP, s);
+    free_async(ctx->UtP, s), free_async(ctx->Uscale, s);
     free_async(ctx->Yc, s), free_async(ctx->Dq, s), free_async(ctx->Cmean, s);
     free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
     free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
@@ -174,6 +174,12 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         const int np = ctx->opt.precision == FMM_BF16X6 ? 3 : 2;
         const size_t pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
         ctx->utp_plane = (long long)((size_t)rows * kw * pesz + 256) / 256 * 256;
+        if (ctx->opt.precision == FMM_FP16X3 &&
+            pool_alloc((void **)&ctx->Uscale, (size_t)rows * ((kw + 63) / 64) * sizeof(float) + 16, s) != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(ctx);
+            return fail(ctx, FMM_ENOMEM, "workspace allocation failed (plane scales)");
+        }
         if (pool_alloc(&ctx->UtP, (size_t)ctx->utp_plane * np, s) != cudaSuccess) {
             cudaGetLastError();
             free_workspace(ctx);
@@ -318,7 +324,7 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     *out = nullptr;
     if (opt->order_p < 2 || opt->order_p > 10) return FMM_EINVAL;
     if (opt->depth < 0 || opt->depth > kMaxDepth) return FMM_EINVAL;
-    if (opt->precision < FMM_FP32 || opt->precision > FMM_BF16X6) return FMM_EINVAL;
+    if (opt->precision < FMM_FP32 || opt->precision > FMM_FP16X3) return FMM_EINVAL;
     if (!(opt->svd_rtol > 0 && opt->svd_rtol < 1) || !(opt->pinv_rtol > 0 && opt->pinv_rtol < 1))
         return FMM_EINVAL;
     if (opt->has_domain) {
@@ -331,7 +337,8 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     ctx->opt = *opt;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->fp64 = opt->precision == FMM_FP64;
-    ctx->tensor = opt->precision == FMM_TF32X3 || opt->precision == FMM_BF16X3 || opt->precision == FMM_BF16X6;
+    ctx->tensor = opt->precision == FMM_TF32X3 || opt->precision == FMM_BF16X3 || opt->precision == FMM_BF16X6 ||
+                  opt->precision == FMM_FP16X3;
     ctx->ns = 6 * (opt->order_p - 1) * (opt->order_p - 1) + 2;
     ctx->nsp = round_up(ctx->ns, 16);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {

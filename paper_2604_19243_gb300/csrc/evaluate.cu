@@ -140,9 +140,12 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
         c.Y = rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;
         unsigned char *planes = nullptr;
+        const int nchk = (kw + 63) / 64;
+        float *scales = ctx->Uscale ? ctx->Uscale + (size_t)ctx->lev[l].row_base * nchk : nullptr;
         if (ctx->tensor) {
             planes = (unsigned char *)ctx->UtP + (size_t)ctx->lev[l].row_base * kw * pesz;
             c.Yp = planes, c.yp_ld = kw, c.yp_plane = ctx->utp_plane;
+            c.yp_scale = scales, c.scale_ld = nchk;
         }
         FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, ls));
         GemmCall st;
@@ -152,6 +155,7 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
         if (ctx->tensor) {
             st.Xp = planes, st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
+            st.xp_scale = scales, st.scale_ld = nchk;
         }
         FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, ls));
         FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));

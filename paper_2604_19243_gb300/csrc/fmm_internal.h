@@ -61,6 +61,8 @@ struct TcMat {
     int rows = 0, cols = 0;     // padded N x K
     int nplanes = 0;
     size_t bytes = 0;           // one operator
+    float *scale = nullptr;     // FP16 planes: 1 / (power-of-two scale) per operator and K chunk
+    int scale_ld = 0;           // K chunks per operator
 };
 
 struct TcOpSet {
@@ -152,6 +154,7 @@ struct fmm_ctx {
     void *Yc = nullptr;                  // [nleaf x rclp] closing intermediate
     void *Dq = nullptr;                  // [nleaf x nsp] leaf equivalent densities
     void *Cmean = nullptr;               // [total_rows] FP64 constant part of the downward check potentials
+    float *Uscale = nullptr;             // FMM_FP16X3: 1 / scale of UtP per row and 64-column chunk
     void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
     void *far_phi = nullptr, *far_grad = nullptr;
     size_t ws_bytes = 0;
@@ -257,6 +260,8 @@ struct GemmCall {
     // byte (r * ld + k) * esize + p * plane within the buffer (esize 2 for BF16, 4 for TF32).
     const void *Xp = nullptr; int xp_ld = 0; int xp_rows = 0; long long xp_plane = 0;
     void *Yp = nullptr; int yp_ld = 0; long long yp_plane = 0;
+    // FP16 split planes (FMM_FP16X3): 1 / scale per row and 64-column chunk of Xp / Yp
+    const float *xp_scale = nullptr; float *yp_scale = nullptr; int scale_ld = 0;
 };
 template <typename T>
 cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &g, cudaStream_t s);

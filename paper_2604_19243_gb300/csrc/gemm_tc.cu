@@ -27,8 +27,10 @@
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel records an error
 // code in a device flag, stops producing/issuing, still releases its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -62,6 +64,18 @@ struct TcDev {
     unsigned char *yp;              // split-plane output (instead of FP32 Y) if non-null
     long long yp_plane;             // bytes between output planes
     int yp_ld;                      // output row stride in elements
+    // FP16 operands (FMM_FP16X3 stencil): power-of-two scaled hi/lo planes; the partial sum of
+    // every stage item is multiplied by a_scale[src row][chunk] * b_scale[operator][chunk]
+    int f16;
+    const float *a_scale;
+    int a_scale_ld;
+    const float *b_scale;
+    int b_scale_ld;
+    // FP16 output planes: each row scaled by a power of two per 64-column chunk, 1 / scale
+    // written to yp_scale[row][chunk]
+    int yp_f16;
+    float *yp_scale;
+    int yp_scale_ld;
 };
 
 namespace {
@@ -224,16 +238,52 @@ struct SegInfo {
     int nchunks;
 };
 
-__device__ __forceinline__ SegInfo seg_info(const TcDev &p, const Tile &t, int seg, int chunk_elems) {
+// Per-tile tables held in shared memory: the operator index and the transfer vector of every
+// class slot of the tile's octant class (stencil mode), so that moving to the next segment
+// needs no dependent global loads.
+struct TileTables {
+    int slot[kClassSlots];
+    int delta[kClassSlots];
+};
+
+__device__ __forceinline__ long long w_index_fast(const GemmDev &g, const Tile &t, const TileTables &tt, int seg) {
+    return g.mode == GM_STENCIL ? (long long)tt.slot[seg] : gemm_w_index(g, t, seg);
+}
+
+__device__ __forceinline__ SegInfo seg_info(const TcDev &p, const Tile &t, const TileTables &tt, int seg,
+                                            int chunk_elems) {
     SegInfo s;
     const GemmDev &g = p.g;
     const bool second = g.mode == GM_PARENT2 && seg == 1;
     s.X = (const float *)(second ? g.X1 : g.X0);
     s.ldx = second ? g.ldx1 : g.ldx0;
     s.K = second ? g.k1 : g.k0;
-    s.Wt = second ? p.Wt1[t.cls] : p.Wt0 + gemm_w_index(g, t, seg) * p.wt_stride;
+    s.Wt = second ? p.Wt1[t.cls] : p.Wt0 + w_index_fast(g, t, tt, seg) * p.wt_stride;
     s.nchunks = (s.K + chunk_elems - 1) / chunk_elems;
     return s;
+}
+
+// One tile row: its box and, for the stencil, the box's integer coordinates.
+struct RowRef {
+    int box, ax, ay, az;
+};
+
+__device__ __forceinline__ RowRef row_ref(const GemmDev &g, int box) {
+    RowRef r{box, 0, 0, 0};
+    if (box >= 0 && g.mode == GM_STENCIL) demorton3(g.keys[box], r.ax, r.ay, r.az);
+    return r;
+}
+
+// source row of (row, seg), -1 for none (one global load: the dense table or the child/parent table)
+__device__ __forceinline__ int src_fast(const GemmDev &g, const Tile &t, const TileTables &tt, const RowRef &r,
+                                        int seg) {
+    if (r.box < 0) return -1;
+    if (g.mode == GM_STENCIL) {
+        int dx, dy, dz;
+        unpack_delta(tt.delta[seg], dx, dy, dz);
+        return dense_find(g.dense, g.level, r.ax + dx, r.ay + dy, r.az + dz);
+    }
+    return gemm_src_row(g, t, r.box, seg);
 }
 
 
@@ -248,6 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     __shared__ int srcs[2][kTcRows];
     __shared__ uint32_t mask[6];
     __shared__ int abort_flag;
+    __shared__ TileTables tt;
 
     const GemmDev &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -277,12 +328,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     }
     if (tid < 6) mask[tid] = g.mode == GM_STENCIL ? g.masks[(size_t)t.mask * 6 + tid] : 0xffffffffu;
     if (tid < kTcRows) box[tid] = tid < t.nrows ? gemm_row_box(g, t, tid) : -1;
+    if (g.mode == GM_STENCIL)
+        for (int k = tid; k < kClassSlots; k += kTcThreads) {
+            tt.slot[k] = g.class_slots[t.cls * kClassSlots + k];
+            tt.delta[k] = g.class_delta[t.cls * kClassSlots + k];
+        }
     if (warp == 0) tmem_alloc(&tmem_base, p.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = make_idesc(N, TF32 ? 2 : 1);
+    const uint32_t idesc = make_idesc(N, TF32 ? 2 : (p.f16 ? 0 : 1));   // kind::f16: 0 = FP16, 1 = BF16
     const int nseg = gemm_nseg(g);
     auto active = [&](int seg) { return g.mode != GM_STENCIL || ((mask[seg >> 5] >> (seg & 31)) & 1u); };
     // number of stage items (segment chunks) of the tile
@@ -299,13 +355,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         // Thread 0 adds the operator's bulk copy.  Copies of several stages stay in flight.
         // Every producer thread runs the same segment loop and the same named barrier per active
         // segment whatever happens; after a failed (bounded) wait it only skips its copies.
+        // The source row of the next active segment is looked up while the current one is copied.
         int item = 0, sidx = 0;
         bool ok = true;
-        for (int seg = 0; seg < nseg; ++seg) {
-            if (!active(seg)) continue;
-            const SegInfo si = seg_info(p, t, seg, chunk_elems);
-            srcs[sidx][tid] = box[tid] >= 0 ? gemm_src_row(g, t, box[tid], seg) : -1;
+        const RowRef me = row_ref(g, box[tid]);
+        int seg = 0;
+        while (seg < nseg && !active(seg)) ++seg;
+        int src_next = seg < nseg ? src_fast(g, t, tt, me, seg) : -1;
+        for (; seg < nseg;) {
+            int seg2 = seg + 1;
+            while (seg2 < nseg && !active(seg2)) ++seg2;
+            const SegInfo si = seg_info(p, t, tt, seg, chunk_elems);
+            srcs[sidx][tid] = src_next;
             asm volatile("bar.sync 1, 128;" ::: "memory");
+            src_next = seg2 < nseg ? src_fast(g, t, tt, me, seg2) : -1;
             const int *rs = srcs[sidx];
             const int unit = lane & 7;
             for (int c = 0; c < si.nchunks; ++c, ++item) {
@@ -347,6 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 cp_async_arrive(&full_bar[stage]);
             }
             sidx ^= 1;
+            seg = seg2;
         }
         if (!ok) {
             atomicExch(p.err, FMM_ETIMEOUT);
@@ -356,11 +420,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         // ------------------------------------------------------------ producers
         int item = 0;
         bool ok = true;
-        for (int seg = 0; seg < nseg && ok; ++seg) {
-            if (!active(seg)) continue;
-            const SegInfo si = seg_info(p, t, seg, chunk_elems);
-            // source row of this warp's rows (row 32 * warp + lane), shared by shuffles
-            const int my_src = box[tid] >= 0 ? gemm_src_row(g, t, box[tid], seg) : -1;
+        const RowRef me = row_ref(g, box[tid]);
+        int seg0 = 0;
+        while (seg0 < nseg && !active(seg0)) ++seg0;
+        int src_next = seg0 < nseg ? src_fast(g, t, tt, me, seg0) : -1;
+        for (int seg = seg0; seg < nseg && ok;) {
+            int seg2 = seg + 1;
+            while (seg2 < nseg && !active(seg2)) ++seg2;
+            const SegInfo si = seg_info(p, t, tt, seg, chunk_elems);
+            // source row of this warp's rows (row 32 * warp + lane), shared by shuffles; the
+            // next segment's is looked up now
+            const int my_src = src_next;
+            src_next = seg2 < nseg ? src_fast(g, t, tt, me, seg2) : -1;
             for (int c = 0; c < si.nchunks; ++c, ++item) {
                 const int stage = item % p.nstages;
                 if (item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1)) {
@@ -439,6 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full_bar[stage]);
             }
+            seg = seg2;
         }
         if (!ok) {
             atomicExch(p.err, FMM_ETIMEOUT);
@@ -455,7 +527,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
 #pragma unroll
         for (int i = 0; i < kTcMaxN; ++i) acc[i] = 0.f;
         bool ok = true;
+        // Scaled FP16 operands: the factor of every item for this thread's row.  The walk keeps
+        // the source row of the current and the next active segment, so that every load behind
+        // a factor is issued at least one item before the factor is used.
+        const bool scaled = p.a_scale != nullptr;
+        const int my_row = q * 32 + lane;
+        const int my_box = my_row < t.nrows ? box[my_row] : -1;
+        auto next_active = [&](int sg) {
+            ++sg;
+            while (sg < nseg && !active(sg)) ++sg;
+            return sg;
+        };
+        const RowRef me = row_ref(g, scaled ? my_box : -1);
+        auto src_of = [&](int sg) { return sg < nseg ? src_fast(g, t, tt, me, sg) : -1; };
+        auto factor = [&](int src, int sg, int ch) -> float {
+            if (!scaled || sg >= nseg) return 1.f;
+            const float fb = __ldg(p.b_scale + w_index_fast(g, t, tt, sg) * p.b_scale_ld + ch);
+            return src >= 0 ? __ldg(p.a_scale + (size_t)src * p.a_scale_ld + ch) * fb : 0.f;
+        };
+        int d_seg = next_active(-1), d_next = next_active(d_seg), d_chunk = 0;
+        int d_src = scaled ? src_of(d_seg) : -1, d_src_next = scaled ? src_of(d_next) : -1;
+        float f_cur = factor(d_src, d_seg, 0);
+        auto advance = [&]() -> float {   // step to the next item; its factor, loads issued now
+            if (d_seg >= nseg) return 1.f;
+            if (++d_chunk * chunk_elems >= gemm_seg_k(g, d_seg)) {
+                d_chunk = 0;
+                d_seg = d_next;
+                d_next = next_active(d_seg);
+                d_src = d_src_next;
+                d_src_next = scaled ? src_of(d_next) : -1;
+            }
+            return factor(d_src, d_seg, d_chunk);
+        };
         auto drain = [&](int item) -> bool {
+            const float f = f_cur;
+            f_cur = advance();
             const int b = item & 1;
             if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1)) return false;
             tc_fence_after();
@@ -469,7 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                     // N is a multiple of 16: the upper half of the last load may be past N
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        if (n0 + i < kTcMaxN && (i < 16 || n0 + 16 < N)) acc[n0 + i] += __uint_as_float(v[i]);
+                        if (n0 + i < kTcMaxN && (i < 16 || n0 + 16 < N)) acc[n0 + i] = fmaf(f, __uint_as_float(v[i]), acc[n0 + i]);
                 }
             }
             tc_fence_before();
@@ -484,7 +590,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             int seg = 0, chunk = 0;
             while (seg < nseg && !active(seg)) ++seg;
             SegInfo si{};
-            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
+            if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
             for (int item = 0; item < n_items && ok; ++item) {
                 int good = 1;
                 if (lane == 0) {
@@ -517,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                             chunk = 0;
                             ++seg;
                             while (seg < nseg && !active(seg)) ++seg;
-                            if (seg < nseg) si = seg_info(p, t, seg, chunk_elems);
+                            if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
                         }
                     }
                 }
@@ -532,7 +638,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         } else {
             const int row = q * 32 + lane;
             const int b = row < t.nrows ? box[row] : -1;
-            if (b >= 0 && p.yp) {
+            if (b >= 0 && p.yp && p.yp_f16) {
+                // FP16 hi/lo planes of the row scaled by a power of two per 64-column chunk, so
+                // that its largest entry is below 2^14 (no overflow, full FP16 precision)
+                float mx[(kTcMaxN + 63) / 64] = {};
+#pragma unroll
+                for (int n = 0; n < kTcMaxN; ++n)
+                    if (n < N) mx[n / 64] = fmaxf(mx[n / 64], fabsf(g.alpha * acc[n]));
+                float sc[(kTcMaxN + 63) / 64];
+#pragma unroll
+                for (int c = 0; c < (kTcMaxN + 63) / 64; ++c) {
+                    int ex = 0;
+                    frexpf(mx[c], &ex);                        // mx < 2^ex
+                    const int e = min(max(14 - ex, -126), 126);
+                    sc[c] = mx[c] > 0.f ? ldexpf(1.f, e) : 1.f;
+                    if (c * 64 < N)
+                        p.yp_scale[(size_t)b * p.yp_scale_ld + n_lo / 64 + c] = mx[c] > 0.f ? ldexpf(1.f, -e) : 0.f;
+                }
+#pragma unroll
+                for (int n0 = 0; n0 < kTcMaxN; n0 += 8) {
+                    if (n0 < N) {
+                        const size_t e = (size_t)b * p.yp_ld + n_lo + n0;
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int i = 0; i < 8; i += 2) {
+                            uint32_t h[2], l[2];
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                const float x = g.alpha * acc[n0 + i + j] * sc[(n0 + i + j) / 64];
+                                const __half hh = __float2half_rn(x);
+                                h[j] = __half_as_ushort(hh);
+                                l[j] = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+                            }
+                            hw[i / 2] = h[0] | (h[1] << 16);
+                            lw[i / 2] = l[0] | (l[1] << 16);
+                        }
+                        *reinterpret_cast<uint4 *>(p.yp + e * 2) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 2) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+            } else if (b >= 0 && p.yp) {
                 // split planes for a later tensor-core gather (BF16 hi/lo[/third] or TF32 big/small)
 #pragma unroll
                 for (int n0 = 0; n0 < kTcMaxN; n0 += 8) {
@@ -607,7 +752,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
 // ---------------------------------------------------------------------------------------
 namespace {
 
-int planes_of(int prec) { return prec == FMM_BF16X6 ? 3 : 2; }
+// planes of the operands in a precision mode (FMM_FP16X3: of every GEMM but the stencil's)
+int planes_of(int prec) { return (prec == FMM_BF16X6 || prec == FMM_FP16X3) ? 3 : 2; }
 
 uint16_t host_bf16(float x) {   // round to nearest even
     uint32_t u;
@@ -633,15 +779,38 @@ float host_f(uint32_t u) {
     std::memcpy(&f, &u, 4);
     return f;
 }
+uint16_t host_f16(float x) {   // IEEE binary16, round to nearest even (|x| < 65520 here)
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    const uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+    const uint32_t a = u & 0x7fffffffu;
+    if (a >= 0x477ff000u) return sign | 0x7c00u;                 // rounds beyond the largest finite
+    if (a < 0x38800000u) {                                       // below 2^-14: subnormal steps of 2^-24
+        float f;
+        std::memcpy(&f, &a, 4);
+        return sign | (uint16_t)std::nearbyint((double)f * 16777216.0);
+    }
+    uint32_t h = ((((a >> 23) - 112u) << 10) | ((a & 0x7fffffu) >> 13));
+    const uint32_t rem = a & 0x1fffu;
+    if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;     // a carry moves into the exponent
+    return sign | (uint16_t)h;
+}
+double host_f16_val(uint16_t h) {
+    const int e = (h >> 10) & 0x1f, m = h & 0x3ff;
+    const double v = e == 0 ? std::ldexp((double)m, -24) : std::ldexp(1.0 + m / 1024.0, e - 15);
+    return (h & 0x8000u) ? -v : v;
+}
 
 }  // namespace
 
 // rows x cols FP64 (row-major) -> the split planes of the padded rows_p x cols_p operand, in
-// the stage layout [chunk][plane][rows_p x 128 B, SWIZZLE_128B], appended to `out`.
-static void tc_pack(int prec, const double *w, int rows, int cols, int rows_p, int cols_p,
-                    std::vector<unsigned char> &out) {
+// the stage layout [chunk][plane][rows_p x 128 B, SWIZZLE_128B], appended to `out`.  With
+// `f16` the planes are FP16 hi/lo of the operand scaled per chunk by a power of two (largest
+// entry below 2^14); 1 / scale of every chunk is appended to `scales`.
+static void tc_pack(int prec, bool f16, const double *w, int rows, int cols, int rows_p, int cols_p,
+                    std::vector<unsigned char> &out, std::vector<float> &scales) {
     const bool tf32 = prec == FMM_TF32X3;
-    const int np = planes_of(prec);
+    const int np = f16 ? 2 : planes_of(prec);
     const int esz = tf32 ? 4 : 2;
     const int ce = kAtomBytes / esz;
     const int nchunks = (cols_p + ce - 1) / ce;
@@ -649,14 +818,30 @@ static void tc_pack(int prec, const double *w, int rows, int cols, int rows_p, i
     const size_t base = out.size();
     out.resize(base + (size_t)nchunks * np * plane_bytes, 0);
     unsigned char *h = out.data() + base;
+    std::vector<double> sc(nchunks, 1.0);
+    if (f16)
+        for (int k = 0; k < nchunks; ++k) {
+            double mx = 0;
+            for (int r = 0; r < rows; ++r)
+                for (int c = k * ce; c < std::min(cols, (k + 1) * ce); ++c) mx = std::max(mx, std::fabs(w[(size_t)r * cols + c]));
+            int ex = 0;
+            std::frexp(mx, &ex);
+            sc[k] = mx > 0 ? std::ldexp(1.0, 14 - ex) : 1.0;
+            scales.push_back(mx > 0 ? (float)std::ldexp(1.0, ex - 14) : 0.f);
+        }
     for (int r = 0; r < rows; ++r)
         for (int c = 0; c < cols; ++c) {
-            const double x = w[(size_t)r * cols + c];
+            const double x = w[(size_t)r * cols + c] * sc[c / ce];
             const int chunk = c / ce, kin = c % ce;
             const int unit = (kin * esz) >> 4, within = (kin * esz) & 15;
             const size_t off = (size_t)(r >> 3) * 1024 + (r & 7) * 128 + ((unit ^ (r & 7)) << 4) + within;
             unsigned char *dst = h + (size_t)chunk * np * plane_bytes + off;
-            if (tf32) {
+            if (f16) {
+                const uint16_t hi = host_f16((float)x);
+                const uint16_t lo = host_f16((float)(x - host_f16_val(hi)));
+                std::memcpy(dst, &hi, 2);
+                std::memcpy(dst + plane_bytes, &lo, 2);
+            } else if (tf32) {
                 const uint32_t b = host_tf32((float)x);
                 const uint32_t sm = host_tf32((float)(x - (double)host_f(b)));
                 std::memcpy(dst, &b, 4);
@@ -675,10 +860,11 @@ static void tc_pack(int prec, const double *w, int rows, int cols, int rows_p, i
 
 // `count` operators of rows x cols (consecutive in w) packed into one allocation
 static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int rows, int cols,
-                                  int rows_p, int cols_p, TcMat *out) {
+                                  int rows_p, int cols_p, TcMat *out, bool f16 = false) {
     std::vector<unsigned char> h;
+    std::vector<float> scales;
     for (int k = 0; k < count; ++k)
-        tc_pack(ctx->opt.precision, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h);
+        tc_pack(ctx->opt.precision, f16, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h, scales);
     void *d = nullptr;
     FMM_CUDA_TRY(cudaMalloc(&d, h.size()));
     ctx->op_allocs.push_back(d);
@@ -686,8 +872,16 @@ static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int 
     out->planes[0] = d;
     out->rows = rows_p;
     out->cols = cols_p;
-    out->nplanes = planes_of(ctx->opt.precision);
+    out->nplanes = f16 ? 2 : planes_of(ctx->opt.precision);
     out->bytes = h.size() / count;   // bytes of one operator (the stride)
+    if (f16) {
+        void *ds = nullptr;
+        FMM_CUDA_TRY(cudaMalloc(&ds, scales.size() * sizeof(float)));
+        ctx->op_allocs.push_back(ds);
+        FMM_CUDA_TRY(cudaMemcpy(ds, scales.data(), scales.size() * sizeof(float), cudaMemcpyHostToDevice));
+        out->scale = (float *)ds;
+        out->scale_ld = (int)(scales.size() / count);
+    }
     return cudaSuccess;
 }
 
@@ -704,7 +898,7 @@ static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, c
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_decompress : h.decompress).data(), 1, ns, o.kout, nsp,
                                 o.koutp, &t.decompress));
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_stencil : h.stencil).data(), kNumTransfer, o.kout, o.kin,
-                                o.koutp, o.kinp, &t.stencil));
+                                o.koutp, o.kinp, &t.stencil, ctx->opt.precision == FMM_FP16X3));
     return cudaSuccess;
 }
 
@@ -747,8 +941,9 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     }
     const int prec = ctx->opt.precision;
     p.tf32 = prec == FMM_TF32X3;
-    p.nplanes = planes_of(prec);
-    if (prec == FMM_BF16X6) {
+    p.f16 = prec == FMM_FP16X3 && op == OP_STENCIL;
+    p.nplanes = p.f16 ? 2 : planes_of(prec);
+    if (p.nplanes == 3) {
         const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
         p.nprod = 6;
         for (int i = 0; i < 6; ++i) p.prod_a[i] = a[i], p.prod_b[i] = b[i];
@@ -757,11 +952,26 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         p.nprod = 3;
         for (int i = 0; i < 3; ++i) p.prod_a[i] = a[i], p.prod_b[i] = b[i];
     }
+    if (p.f16) {
+        if (!c.Xp || !c.xp_scale || !T.stencil.scale) return cudaErrorInvalidValue;
+        p.a_scale = c.xp_scale;
+        p.a_scale_ld = c.scale_ld;
+        p.b_scale = T.stencil.scale;
+        p.b_scale_ld = T.stencil.scale_ld;
+    }
     if (c.n_out % 16 != 0 || (c.k0 % 16) != 0 || (c.X1 && c.k1 % 16 != 0)) return cudaErrorInvalidValue;
-    const int nsplit = (c.n_out + kTcMaxN - 1) / kTcMaxN;
+    int nsplit = (c.n_out + kTcMaxN - 1) / kTcMaxN;
     p.ncta = round_up((c.n_out + nsplit - 1) / nsplit, 16);
+    if (prec == FMM_FP16X3 && c.Yp && nsplit > 1) {   // FP16 output planes: 64-column aligned CTAs
+        p.ncta = 128;
+        nsplit = (c.n_out + 127) / 128;
+    }
     const int stage_bytes = p.nplanes * (kTcRows + p.ncta) * kAtomBytes;
-    const int budget = 227 * 1024 - 2048;
+    // 227 KB per CTA in all: the stages, 1 KB of alignment slack and the static shared memory
+    auto kern = p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
+    cudaFuncAttributes fa{};
+    FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int budget = 227 * 1024 - 1024 - (int)fa.sharedSizeBytes;
     p.nstages = std::min(4, budget / stage_bytes);
     if (p.nstages < 2) return cudaErrorInvalidValue;
     // two accumulators of ncta columns; the drain reads 32 columns at a time, so the last read
@@ -784,9 +994,15 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         p.yp = (unsigned char *)c.Yp;
         p.yp_plane = c.yp_plane;
         p.yp_ld = c.yp_ld;
+        if (prec == FMM_FP16X3) {
+            // per-chunk scales need every CTA's columns to start on a 64-column chunk
+            if (!c.yp_scale || (nsplit > 1 && p.ncta % 64 != 0)) return cudaErrorInvalidValue;
+            p.yp_f16 = 1;
+            p.yp_scale = c.yp_scale;
+            p.yp_scale_ld = c.scale_ld;
+        }
     }
     const size_t smem = (size_t)p.nstages * stage_bytes + 1024;
-    auto kern = p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
     FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3(ts.ntiles, (c.n_out + p.ncta - 1) / p.ncta), kTcThreads, smem, s>>>(p);
     count_launch();
