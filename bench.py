@@ -57,6 +57,22 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest(seconds, dev, ws):
+    """The largest of every rank's `seconds` (the job's time); `seconds` itself on one rank."""
+    if ws <= 1:
+        return seconds
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([seconds], device=dev, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t)
+
+
+def job_rate(points_per_rank, steps, ws, seconds):
+    """Whole-job throughput: the points of all ranks over the slowest rank's time."""
+    return points_per_rank * steps * ws / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -247,11 +263,8 @@ def main():
     launches = pkg.kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t)
-    value = w.n * args.steps * ws / total_s
+    total_s = slowest(total_s, dev, ws)
+    value = job_rate(w.n, args.steps, ws, total_s)
     ms_per_step = total_s / args.steps * 1e3
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -264,6 +277,8 @@ def main():
         fmm.evaluate_into(qh, ph, gh)
     torch.cuda.synchronize()
     e2e_s = []
+    if ws > 1:
+        torch.distributed.barrier()
     for _ in range(args.steps):
         flush.fill_(3)
         torch.cuda.synchronize()
@@ -271,7 +286,7 @@ def main():
         fmm.build_tree(xh)
         fmm.evaluate_into(qh, ph, gh)     # host outputs: returns after the device-to-host copy
         e2e_s.append(time.perf_counter() - t0)
-    e2e_value = w.n / (sum(e2e_s) / len(e2e_s)) * ws
+    e2e_value = job_rate(w.n, args.steps, ws, slowest(sum(e2e_s), dev, ws))
     es = 8 if fp64 else 4
     h2d = w.n * 3 * es + w.n * es
     d2h = w.n * es + w.n * 3 * es
@@ -293,48 +308,97 @@ def main():
     peaks, peak_src = read_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tf = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    nominal_fp32_tf = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    fp32_scalar_tf, fp32_pair_tf = pkg.measure_fp32_peak()
+    fp32_peak_tf = max(fp32_scalar_tf, fp32_pair_tf)
     near_ms = statistics.median(p["near"] for p in phases)
     m2l_ms = statistics.median(p["m2l"] for p in phases)
     up_ms = statistics.median(p["upward"] for p in phases)
     down_ms = statistics.median(p["downward"] for p in phases)
+    # the near-field kernel alone (same launch, no far field beside it), for its own rate
+    iso = []
+    for _ in range(5):
+        fmm.evaluate_into(q, phi, grad, parts=pkg.PART_NEAR)
+        iso.append(fmm.timings()["near"])
+    near_iso_ms = statistics.median(iso[1:])
+    fmm.evaluate_into(q, phi, grad)
+    torch.cuda.synchronize()
     pairs = info["p2p_pairs"]
-    p2p = {"bound": "alu", "achieved": pairs * FLOPS_PER_PAIR / (near_ms * 1e-3) / 1e12,
+    p2p_flops = pairs * FLOPS_PER_PAIR
+    p2p = {"bound": "alu", "achieved": p2p_flops / (near_ms * 1e-3) / 1e12,
            "peak": fp32_peak_tf, "unit": "TFLOP/s",
-           "kernel": "p2p_kernel (ULI near field)",
-           "peak_basis": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz "
-                         f"(max SM clock, {peak_src} peaks file); {FLOPS_PER_PAIR} flops per pair",
-           "pairs": pairs, "ms": near_ms}
+           "kernel": "p2p_f32_kernel (ULI near field)",
+           "peak_basis": f"measured FP32 FMA throughput on this GPU (fmm_measure_fp32_peak: scalar "
+                         f"{fp32_scalar_tf:.1f}, float2 {fp32_pair_tf:.1f} TFLOP/s); nominal "
+                         f"{sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz = {nominal_fp32_tf:.1f}; "
+                         f"{FLOPS_PER_PAIR} flops per pair",
+           "pairs": pairs, "ms": near_ms,
+           "timing": "CUDA events around the kernel on its own stream inside the timed steps, where "
+                     "it runs at low priority beside the far field and fills the SMs that leave idle",
+           "isolated": {"ms": near_iso_ms, "achieved": p2p_flops / (near_iso_ms * 1e-3) / 1e12,
+                        "frac": p2p_flops / (near_iso_ms * 1e-3) / 1e12 / fp32_peak_tf,
+                        "frac_of_nominal": p2p_flops / (near_iso_ms * 1e-3) / 1e12 / nominal_fp32_tf,
+                        "timing": "the same launch with the near field alone (after the timed steps)"}}
     p2p["frac"] = p2p["achieved"] / p2p["peak"]
-    p2p["traffic"] = recorded_traffic("p2p_kernel", source_digest("p2p.cu"))
-    # M2L algorithmic flops: compress + stencil products over the real V pairs + decompress
+    p2p["traffic"] = recorded_traffic("p2p_f32_kernel", source_digest("p2p.cu"))
+    # M2L algorithmic flops: compress + stencil products over the real V pairs
     kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"]
     vpairs = 0
-    m2l_flops = 0.0
+    compress_flops = stencil_flops = 0.0
     for level in range(2, w.depth + 1):
         nl = info["n_boxes"][level]
         lv = fmm.export_level(level, lists=True)
         nv = len(lv["v_idx"])
         vpairs += nv
-        m2l_flops += 2.0 * kin * ns * nl + 2.0 * kout * kin * nv
+        compress_flops += 2.0 * kin * ns * nl
+        stencil_flops += 2.0 * kout * kin * nv
+    m2l_flops = compress_flops + stencil_flops
     tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3", "fp16x3")
     if tensor:
-        mult = {"bf16x3": 3, "bf16x6": 6, "tf32x3": 3, "fp16x3": 3}[args.precision]
+        six = args.precision in ("bf16x6", "fp16x3")          # compress runs BF16x6 in both
+        m_compress = 6 if six else 3
+        m_stencil = 6 if args.precision == "bf16x6" else 3
+        tc_flops = m_compress * compress_flops + m_stencil * stencil_flops
         base = float(peaks["bf16_tflops_sustained"]) * (0.5 if args.precision == "tf32x3" else 1.0)
-        m2l = {"bound": "tensor", "achieved": mult * m2l_flops / (m2l_ms * 1e-3) / 1e12,
+        m2l = {"bound": "tensor", "achieved": tc_flops / (m2l_ms * 1e-3) / 1e12,
                "peak": base, "unit": "TFLOP/s",
                "peak_basis": f"{peak_src} bf16 sustained" + (" x 1/2 (tf32 nominal ratio)"
-                                                           if args.precision == "tf32x3" else ""),
-               "split_products": mult}
+                                                           if args.precision == "tf32x3" else "")
+                             + "; FP16 and BF16 share the dense tensor rate",
+               "split_products": {"compress": m_compress, "stencil": m_stencil},
+               "tensor_flops": tc_flops}
     else:
         m2l = {"bound": "alu", "achieved": m2l_flops / (m2l_ms * 1e-3) / 1e12,
                "peak": fp32_peak_tf if not fp64 else None, "unit": "TFLOP/s",
-               "peak_basis": "FP32 FMA pipe (SIMT contraction)"}
-    m2l.update({"kernel": "M2L phase: compress + stencil GEMMs, all levels", "ms": m2l_ms,
-                "v_pairs": vpairs, "algorithmic_flops": m2l_flops})
+               "peak_basis": "measured FP32 FMA throughput (SIMT contraction)"}
+    m2l.update({"kernel": "M2L phase: compress + stencil GEMMs of all levels (gemm_tc_kernel)",
+                "ms": m2l_ms, "v_pairs": vpairs, "algorithmic_flops": m2l_flops,
+                "timing": "CUDA events on the far-field stream: end of the upward pass to the start "
+                          "of the leaf level's downward step"})
     m2l["frac"] = (m2l["achieved"] / m2l["peak"]) if m2l["peak"] else None
     m2l["traffic"] = None
-    dominant, other = (p2p, m2l) if near_ms >= m2l_ms else (m2l, p2p)
+    # upward and downward passes in achieved GB/s (algorithmic bytes: every row read once and
+    # written once, the points and outputs of the leaf steps once)
+    es = 8 if fp64 else 4
+    nsp_b = ns * es
+    nb = info["n_boxes"]
+    nleaf = nb[w.depth]
+    up_bytes = 16.0 * w.n + nleaf * nsp_b + sum((nb[l + 1] + nb[l]) * nsp_b for l in range(2, w.depth))
+    down_bytes = sum((nb[l] * 2 + nb[l - 1] if l >= 3 else nb[l] * 2) * nsp_b for l in range(2, w.depth + 1)) \
+        + 2 * nleaf * nsp_b + 16.0 * w.n + 16.0 * w.n
+    passes = {"upward": {"ms": up_ms, "algorithmic_bytes": up_bytes,
+                         "achieved_gbs": up_bytes / (up_ms * 1e-3) / 1e9,
+                         "frac_of_hbm": up_bytes / (up_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},
+              "downward": {"ms": down_ms, "algorithmic_bytes": down_bytes,
+                           "achieved_gbs": down_bytes / (down_ms * 1e-3) / 1e9,
+                           "frac_of_hbm": down_bytes / (down_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])},
+              "basis": "S2U reads the points (16 B each) and writes the leaf rows; U2U reads the child "
+                       "rows and writes the parent rows; the downward step reads the compressed rows, the "
+                       "parent rows and writes each level's rows, then the leaf closing and D2T read the "
+                       "leaf rows and the points and write potential and gradient (16 B per point); rows "
+                       f"of {ns} {'FP64' if fp64 else 'FP32'} values; peak = measured HBM copy "
+                       f"{float(peaks['hbm_gbs']):.0f} GB/s"}
+    dominant, other = p2p, m2l
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -349,7 +413,7 @@ def main():
                           "evaluate_total": statistics.median(p["total"] for p in phases),
                           "build_tree": ms_per_step - statistics.median(p["total"] for p in phases),
                           "adjoint": adjoint_ms},
-            "roofline": dominant, "roofline_other": other,
+            "roofline": dominant, "roofline_other": other, "passes": passes,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk}

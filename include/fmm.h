@@ -207,6 +207,15 @@ fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int depth, const
 /* Number of CUDA kernels this library has launched in the process so far (all contexts). */
 long long fmm_kernel_launches(void);
 
+/* Measurement utility (no counterpart in the paper): the FP32 fused multiply-add throughput of
+ * the current device in TFLOP/s (2 flops per FMA), as scalar FP32 (*tflops_scalar) and in the
+ * two-wide float2 form (*tflops_pair), each from the second of two launches of `iters`
+ * iterations of 8 independent FMA chains per thread on 8 x 256 threads per SM.  It is the
+ * measured denominator of the near-field roofline and depends on the clock at the time.
+ * Synchronous; uses its own stream.  EINVAL for iters <= 0 or a null output; ECUDA on a CUDA
+ * failure. */
+fmm_status fmm_measure_fp32_peak(int iters, double *tflops_scalar, double *tflops_pair);
+
 /* Message for the last failed call on ctx ("" if none).  Never NULL. */
 const char *fmm_last_error(const fmm_ctx *ctx);
 

@@ -29,8 +29,8 @@ PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
 ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
                 "fmm_evaluate", "fmm_evaluate_parts", "fmm_adjoint", "fmm_get_tree_info",
                 "fmm_export_tree", "fmm_export_level", "fmm_export_check", "fmm_last_timings",
-                "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches", "fmm_last_error",
-                "fmm_destroy")
+                "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches",
+                "fmm_measure_fp32_peak", "fmm_last_error", "fmm_destroy")
 
 
 class Options(ctypes.Structure):
@@ -82,6 +82,7 @@ def lib():
             "fmm_last_timings": [vp, vp, i32],
             "fmm_sync": [vp],
             "fmm_sort_points_noalloc": [vp, i64, i32, vp, ctypes.c_double, vp, vp, vp],
+            "fmm_measure_fp32_peak": [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -111,6 +112,15 @@ def _ptr(a):
 def kernel_launches():
     """Kernels launched by libfmm in this process so far."""
     return int(lib().fmm_kernel_launches())
+
+
+def measure_fp32_peak(iters=2048):
+    """FP32 FMA throughput of the current device in TFLOP/s: (scalar, float2 form)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = lib().fmm_measure_fp32_peak(int(iters), ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise FmmError(st, "fmm_measure_fp32_peak failed")
+    return a.value, b.value
 
 
 class FMM:

@@ -12,10 +12,13 @@
 // moves it; A rows are gathered by the producer warps, split and written with st.shared.
 //
 // Warp roles (256 threads, two warps per SM sub-partition so that the accumulator warps can hold
-// 160 FP32 partial sums in registers): warps 0-3 gather A and issue the B copy (warp 0 also owns
-// the tensor memory allocation); warps 4-7 drain the tensor memory accumulators (warp w owns TMEM
-// lanes 32(w-4).. = tile rows) into FP32 registers and write Y; lane 0 of warp 4 issues every
-// tcgen05.mma (item i), after which its warp drains item i - 1 while item i runs.
+// 160 FP32 partial sums in registers): warps 4-7 drain the tensor memory accumulators (warp w
+// owns TMEM lanes 32(w-4).. = tile rows) into FP32 registers and write Y; warp 0 owns the tensor
+// memory allocation.  A rows from FP32 (gathered and split in registers): warps 0-3 produce the
+// stages and lane 0 of warp 4 issues every tcgen05.mma (item i), after which its warp drains item
+// i - 1.  A rows from split planes (copies only): warps 0-2 produce and lane 0 of warp 3 issues,
+// so the tensor pipe keeps running while all four accumulator warps drain (issuing an item's
+// MMAs takes as long as the tensor pipe needs for them).
 //
 // Accumulation.  The tensor core adds an MMA's products into the FP32 accumulator with
 // truncation, so a long chain of MMAs into one accumulator drifts toward zero by about one
@@ -43,6 +46,7 @@ constexpr int kTcRows = 128;
 constexpr int kTcMaxN = 160;               // output columns per CTA (wider N: several CTAs)
 constexpr int kAtomBytes = 128;            // one swizzle atom row
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr int kPlaneProducers = 96;        // plane mode: warps 0-2 copy, warp 3 issues the MMAs
 
 struct TcDev {
     GemmDev g;                      // gather description (W fields unused)
@@ -315,8 +319,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     if (tid == 0) {
         for (int s = 0; s < p.nstages; ++s) {
             // register gather: 4 producer warps + the B copy's expect_tx arrive;
-            // plane copies: 128 cp.async arrivals + the B copy's expect_tx arrive
-            mbar_init(&full_bar[s], p.a_planes ? 128 + 1 : 4 + 1);
+            // plane copies: 96 cp.async arrivals (3 producer warps) + the B copy's expect_tx arrive
+            mbar_init(&full_bar[s], p.a_planes ? kPlaneProducers + 1 : 4 + 1);
             mbar_init(&empty_bar[s], 1);      // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
@@ -333,7 +337,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             tt.slot[k] = g.class_slots[t.cls * kClassSlots + k];
             tt.delta[k] = g.class_delta[t.cls * kClassSlots + k];
         }
+    // Rows and K units that are never copied keep what the stage held before: zero the stages
+    // once so that they hold finite values (their products are then multiplied by zero).
+    const bool scaled_a = p.a_planes && p.a_scale != nullptr;
+    if (scaled_a)
+        for (int i = tid; i < p.nstages * stage_bytes / 16; i += kTcThreads)
+            reinterpret_cast<uint4 *>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (warp == 0) tmem_alloc(&tmem_base, p.tmem_cols);
+    fence_proxy_async();   // the zeroed stages (generic proxy) before any tensor-core read
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -346,29 +357,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     for (int seg = 0; seg < nseg; ++seg)
         if (active(seg)) n_items += (gemm_seg_k(g, seg) + chunk_elems - 1) / chunk_elems;
 
-    if (warp < 4 && p.a_planes) {
+    // One stage item's MMAs into accumulator b, issued by one thread: the split products of the
+    // chunk, then commits that free the stage and mark the accumulator full.
+    auto issue_item = [&](int stage, int b, const SegInfo &si, int chunk) {
+        tc_fence_after();
+        fence_proxy_async();   // cp.async / st.shared writes (generic proxy) -> tcgen05.mma
+        const uint32_t sa = smem_u32(base + (size_t)stage * stage_bytes);
+        const uint32_t sb = sa + p.nplanes * a_plane_bytes;
+        const uint32_t dt = tmem + (uint32_t)(b * p.ncta);
+        const int kval = min(chunk_elems, si.K - chunk * chunk_elems);
+        const int ksteps = min(kAtomBytes / 32, (kval * esz + 31) / 32);
+        uint32_t accum = 0;
+        for (int pr = 0; pr < p.nprod; ++pr) {
+            for (int ks = 0; ks < ksteps; ++ks) {
+                const uint64_t ad = sw128_desc(sa + p.prod_a[pr] * a_plane_bytes + ks * 32);
+                const uint64_t bd = sw128_desc(sb + p.prod_b[pr] * b_plane_bytes + ks * 32);
+                if (TF32) mma_tf32(dt, ad, bd, idesc, accum);
+                else mma_bf16(dt, ad, bd, idesc, accum);
+                accum = 1;
+            }
+        }
+        mma_commit(&empty_bar[stage]);
+        mma_commit(&tfull_bar[b]);
+    };
+
+    if (warp < 3 && p.a_planes) {
         // ------------------------------------------------------------ producers, split planes
         // The source rows are already split into planes in global memory, so the producers only
         // copy: every thread issues 16-byte cp.async copies straight into the swizzled stage
-        // (8 lanes per row, 4 rows per warp instruction, zero fill for missing rows and for K
-        // past the segment), then arrives on the stage barrier when its copies have landed.
+        // (8 lanes per row, 4 rows per warp instruction, zero fill for missing rows), then
+        // arrives on the stage barrier when its copies have landed.
         // Thread 0 adds the operator's bulk copy.  Copies of several stages stay in flight.
         // Every producer thread runs the same segment loop and the same named barrier per active
         // segment whatever happens; after a failed (bounded) wait it only skips its copies.
         // The source row of the next active segment is looked up while the current one is copied.
+        // Three warps (96 threads) cover the 128 rows: thread i looks up rows i and i + 96.
         int item = 0, sidx = 0;
         bool ok = true;
+        const bool two = tid + kPlaneProducers < kTcRows;
         const RowRef me = row_ref(g, box[tid]);
+        const RowRef me2 = row_ref(g, two ? box[tid + kPlaneProducers] : -1);
         int seg = 0;
         while (seg < nseg && !active(seg)) ++seg;
         int src_next = seg < nseg ? src_fast(g, t, tt, me, seg) : -1;
+        int src_next2 = seg < nseg ? src_fast(g, t, tt, me2, seg) : -1;
         for (; seg < nseg;) {
             int seg2 = seg + 1;
             while (seg2 < nseg && !active(seg2)) ++seg2;
             const SegInfo si = seg_info(p, t, tt, seg, chunk_elems);
             srcs[sidx][tid] = src_next;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (two) srcs[sidx][tid + kPlaneProducers] = src_next2;
+            asm volatile("bar.sync 1, 96;" ::: "memory");
             src_next = seg2 < nseg ? src_fast(g, t, tt, me, seg2) : -1;
+            src_next2 = seg2 < nseg ? src_fast(g, t, tt, me2, seg2) : -1;
             const int *rs = srcs[sidx];
             const int unit = lane & 7;
             for (int c = 0; c < si.nchunks; ++c, ++item) {
@@ -384,20 +425,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 if (tid == 0) {
                     mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
                     const size_t plane_full = (size_t)g.n_out * kAtomBytes;
-                    for (int pl = 0; pl < p.nplanes; ++pl)
-                        bulk_g2s(sb + pl * b_plane_bytes,
-                                 si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
-                                 (uint32_t)b_plane_bytes, &full_bar[stage]);
+                    if ((size_t)b_plane_bytes == plane_full)   // the chunk's planes are contiguous: one copy
+                        bulk_g2s(sb, si.Wt + (size_t)c * p.nplanes * plane_full,
+                                 (uint32_t)(p.nplanes * b_plane_bytes), &full_bar[stage]);
+                    else
+                        for (int pl = 0; pl < p.nplanes; ++pl)
+                            bulk_g2s(sb + pl * b_plane_bytes,
+                                     si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
+                                     (uint32_t)b_plane_bytes, &full_bar[stage]);
                 }
                 const int k0 = c * chunk_elems;
                 const int kval = min(chunk_elems, si.K - k0);
                 const int valid_units = (kval * esz + 15) / 16;
                 const bool unit_ok = unit < valid_units;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int r = warp * 32 + j * 4 + (lane >> 3);
+                for (int j = 0; j < (kTcRows + 11) / 12; ++j) {   // 12 rows per pass of 3 warps
+                    const int r = j * 12 + warp * 4 + (lane >> 3);
+                    if (r >= kTcRows) break;
                     const int sr = rs[r];
                     const bool have = unit_ok && sr >= 0;
+                    // with per-row factors (scaled planes) a row without a source is multiplied by
+                    // zero in the drain, so it needs no copy; K units past the segment are never read
+                    if (!have && (scaled_a || !unit_ok)) continue;
                     const size_t elem = (size_t)(have ? sr : 0) * p.xp_ld + k0 + unit * (16 / esz);
                     const int dst_off = r * kAtomBytes + ((unit ^ (r & 7)) << 4);
 #pragma unroll
@@ -415,6 +464,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         if (!ok) {
             atomicExch(p.err, FMM_ETIMEOUT);
             *(volatile int *)&abort_flag = 1;
+        }
+    } else if (warp == 3 && p.a_planes) {
+        // ------------------------------------------------------------ MMA issuer (plane mode)
+        // A warp of its own issues the MMAs, so the tensor pipe runs while the accumulator
+        // warps drain: the issue of an item's MMAs returns only as the tensor pipe takes them.
+        if (lane == 0) {
+            bool ok = true;
+            int seg = 0, chunk = 0;
+            while (seg < nseg && !active(seg)) ++seg;
+            SegInfo si{};
+            if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
+            for (int item = 0; item < n_items; ++item) {
+                const int stage = item % p.nstages, b = item & 1;
+                if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1) ||
+                    (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1)) ||
+                    *(volatile int *)&abort_flag) {
+                    ok = false;
+                    break;
+                }
+                issue_item(stage, b, si, chunk);
+                if (++chunk == si.nchunks) {
+                    chunk = 0;
+                    ++seg;
+                    while (seg < nseg && !active(seg)) ++seg;
+                    if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
+                }
+            }
+            if (!ok) {
+                atomicExch(p.err, FMM_ETIMEOUT);
+                *(volatile int *)&abort_flag = 1;
+            }
         }
     } else if (warp < 4) {
         // ------------------------------------------------------------ producers
@@ -442,13 +522,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 unsigned char *sa = base + (size_t)stage * stage_bytes;
                 unsigned char *sb = sa + p.nplanes * a_plane_bytes;
                 if (tid == 0) {
-                    // rows [n_lo, n_lo + N) of every plane of chunk c: contiguous per plane
+                    // rows [n_lo, n_lo + N) of every plane of chunk c: contiguous per plane, and
+                    // all planes contiguous when the CTA covers every row (one copy then)
                     mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
                     const size_t plane_full = (size_t)g.n_out * kAtomBytes;
-                    for (int pl = 0; pl < p.nplanes; ++pl)
-                        bulk_g2s(sb + pl * b_plane_bytes,
-                                 si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
-                                 (uint32_t)b_plane_bytes, &full_bar[stage]);
+                    if ((size_t)b_plane_bytes == plane_full)
+                        bulk_g2s(sb, si.Wt + (size_t)c * p.nplanes * plane_full,
+                                 (uint32_t)(p.nplanes * b_plane_bytes), &full_bar[stage]);
+                    else
+                        for (int pl = 0; pl < p.nplanes; ++pl)
+                            bulk_g2s(sb + pl * b_plane_bytes,
+                                     si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
+                                     (uint32_t)b_plane_bytes, &full_bar[stage]);
                 }
                 // gather: each warp covers its 32 rows; lanes split a row into 16-byte pieces.
                 // All loads of the warp are issued before any is used (memory-level parallelism).
@@ -522,7 +607,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         // item's partial sums (32 rows each) into FP32 registers, so that no TMEM accumulator
         // takes more than one stage of tensor-core additions.
         const int q = warp - 4;                           // TMEM lane quarter
-        const bool issuer = warp == 4;
+        const bool issuer = warp == 4 && !p.a_planes;   // plane mode: warp 3 issues
         float acc[kTcMaxN];
 #pragma unroll
         for (int i = 0; i < kTcMaxN; ++i) acc[i] = 0.f;
@@ -600,25 +685,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                         *(volatile int *)&abort_flag) {
                         good = 0;
                     } else {
-                        tc_fence_after();
-                        fence_proxy_async();   // cp.async / st.shared writes (generic proxy) -> tcgen05.mma
-                        const uint32_t sa = smem_u32(base + (size_t)stage * stage_bytes);
-                        const uint32_t sb = sa + p.nplanes * a_plane_bytes;
-                        const uint32_t dt = tmem + (uint32_t)(b * p.ncta);
-                        const int kval = min(chunk_elems, si.K - chunk * chunk_elems);
-                        const int ksteps = min(kAtomBytes / 32, (kval * esz + 31) / 32);
-                        uint32_t accum = 0;
-                        for (int pr = 0; pr < p.nprod; ++pr) {
-                            for (int ks = 0; ks < ksteps; ++ks) {
-                                const uint64_t ad = sw128_desc(sa + p.prod_a[pr] * a_plane_bytes + ks * 32);
-                                const uint64_t bd = sw128_desc(sb + p.prod_b[pr] * b_plane_bytes + ks * 32);
-                                if (TF32) mma_tf32(dt, ad, bd, idesc, accum);
-                                else mma_bf16(dt, ad, bd, idesc, accum);
-                                accum = 1;
-                            }
-                        }
-                        mma_commit(&empty_bar[stage]);
-                        mma_commit(&tfull_bar[b]);
+                        issue_item(stage, b, si, chunk);
                         if (++chunk == si.nchunks) {
                             chunk = 0;
                             ++seg;

@@ -82,13 +82,16 @@ CUBE = ((0.0, 0.0, 0.0), 1.0)
 BALL = ((-1.0, -1.0, -1.0), 2.0)
 
 # The five workloads: a small plain case, a 1M cube, the 8M sphere (the headline),
-# the differentiation case and the 33.5M scale case.
+# the differentiation case and the 33.5M scale case; and a 2M sphere at depth 6, the quarter-
+# size stand-in of the headline (the same ~112 points per non-empty leaf) for timed CPU samples
+# and for profiler captures that must stay small.
 WORKLOADS = {
     "cube20k_p4_d3": Workload("cube20k_p4_d3", 20_000, "cube", "u01", 4, 3, *CUBE, False),
     "cube1m_p6_d5": Workload("cube1m_p6_d5", 1_048_576, "cube", "u11", 6, 5, *CUBE, True),
     "sphere8m_p6_d7": Workload("sphere8m_p6_d7", 8_388_608, "sphere", "u01", 6, 7, *BALL, True),
     "cube262k_p6_d4": Workload("cube262k_p6_d4", 262_144, "cube", "normal", 6, 4, *CUBE, True),
     "cube33m_p8_d8": Workload("cube33m_p8_d8", 33_554_432, "cube", "u01", 8, 8, *CUBE, True),
+    "sphere2m_p6_d6": Workload("sphere2m_p6_d6", 2_097_152, "sphere", "u01", 6, 6, *BALL, True),
 }
 
 
