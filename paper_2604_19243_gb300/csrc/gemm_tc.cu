@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     __shared__ uint32_t tmem_base;
     __shared__ int box[kTcRows];
     __shared__ int srcs[2][kTcRows];
+    __shared__ int plist[2][kTcRows + 1];   // rows with a source row ([kTcRows] = their count)
     __shared__ uint32_t mask[6];
     __shared__ int abort_flag;
     __shared__ TileTables tt;
@@ -408,6 +409,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             srcs[sidx][tid] = src_next;
             if (two) srcs[sidx][tid + kPlaneProducers] = src_next2;
             asm volatile("bar.sync 1, 96;" ::: "memory");
+            if (scaled_a && warp == 0) {
+                // rows that have a source, compacted, so that every copy instruction carries full
+                // rows (rows without one are multiplied by zero in the drain and are not copied)
+                int cnt = 0;
+#pragma unroll
+                for (int r0 = 0; r0 < kTcRows; r0 += 32) {
+                    const bool has = srcs[sidx][r0 + lane] >= 0;
+                    const unsigned m = __ballot_sync(0xffffffffu, has);
+                    if (has) plist[sidx][cnt + __popc(m & ((1u << lane) - 1u))] = r0 + lane;
+                    cnt += __popc(m);
+                }
+                if (lane == 0) plist[sidx][kTcRows] = cnt;
+            }
+            if (scaled_a) asm volatile("bar.sync 1, 96;" ::: "memory");
             src_next = seg2 < nseg ? src_fast(g, t, tt, me, seg2) : -1;
             src_next2 = seg2 < nseg ? src_fast(g, t, tt, me2, seg2) : -1;
             const int *rs = srcs[sidx];
@@ -438,6 +453,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 const int kval = min(chunk_elems, si.K - k0);
                 const int valid_units = (kval * esz + 15) / 16;
                 const bool unit_ok = unit < valid_units;
+                if (scaled_a) {
+                    // (present row, valid 16-byte unit) pairs, consecutive over the producers
+                    const int *pl_rows = plist[sidx];
+                    const int total = pl_rows[kTcRows] * valid_units;
+                    for (int e = tid; e < total; e += kPlaneProducers) {
+                        const int r = pl_rows[e / valid_units], u = e % valid_units;
+                        const size_t elem = (size_t)rs[r] * p.xp_ld + k0 + u * (16 / esz);
+                        const int dst_off = r * kAtomBytes + ((u ^ (r & 7)) << 4);
+#pragma unroll
+                        for (int pl = 0; pl < 3; ++pl)
+                            if (pl < p.nplanes)
+                                cp_async16(sa + pl * a_plane_bytes + dst_off, p.xp + pl * p.xp_plane + elem * esz, 16);
+                    }
+                    cp_async_arrive(&full_bar[stage]);
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < (kTcRows + 11) / 12; ++j) {   // 12 rows per pass of 3 warps
                     const int r = j * 12 + warp * 4 + (lane >> 3);
