@@ -403,6 +403,59 @@ leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__r
     }
 }
 
+// FP32 form: one thread per surface point (160 threads cover the 152 points of p = 6 in one
+// pass), the leaf's points staged as pairs and summed with the two-wide FP32 instructions.  An
+// odd count is padded with a copy of the last point carrying zero charge: every source lies in
+// the leaf box and every target on the 2.95 surface outside it, so no distance is zero.
+constexpr int kCheckThreads = 160;
+
+__global__ void __launch_bounds__(kCheckThreads)
+leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
+                      const uint32_t *__restrict__ keys, const float *__restrict__ grid, int ns, int nsp,
+                      double ox, double oy, double oz, double width, double radius, float *__restrict__ out) {
+    __shared__ __align__(16) float4 src[kLeafChunk];   // kLeafChunk sources as pairs
+    float *sf = reinterpret_cast<float *>(src);
+    const int b = blockIdx.x;
+    const int s0 = leaf_off[b], s1 = leaf_off[b + 1];
+    int ax, ay, az;
+    demorton3(keys[b], ax, ay, az);
+    const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
+                 cz = oz + (az + 0.5) * width;
+    for (int i0 = 0; i0 < nsp; i0 += kCheckThreads) {
+        const int i = i0 + threadIdx.x;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (i < ns) {
+            px = (float)(cx + radius * (double)grid[3 * i]);
+            py = (float)(cy + radius * (double)grid[3 * i + 1]);
+            pz = (float)(cz + radius * (double)grid[3 * i + 2]);
+        }
+        const float2 nx = make_float2(-px, -px), ny = make_float2(-py, -py), nz = make_float2(-pz, -pz);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c0 = s0; c0 < s1; c0 += kLeafChunk) {
+            const int c1 = min(s1, c0 + kLeafChunk), n = c1 - c0;
+            __syncthreads();
+            for (int e = threadIdx.x; e < n + (n & 1); e += kCheckThreads) {
+                const float4 v = pts[c0 + min(e, n - 1)];
+                float *o = sf + 8 * (e >> 1) + (e & 1);
+                o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = e < n ? v.w : 0.f;
+            }
+            __syncthreads();
+            if (i < ns)
+                for (int e = 0; e < (n + 1) >> 1; ++e) {
+                    const float4 a = src[2 * e], c = src[2 * e + 1];
+                    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+                    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+                    const float2 dz = __fadd2_rn(make_float2(c.x, c.y), nz);
+                    float2 r2 = __fmul2_rn(dx, dx);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    acc = __ffma2_rn(make_float2(c.z, c.w), make_float2(rsqrtf(r2.x), rsqrtf(r2.y)), acc);
+                }
+        }
+        if (i < nsp) out[(int64_t)b * nsp + i] = i < ns ? (acc.x + acc.y) * inv4pi<float>() : 0.f;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // D2T: potentials (and gradients) at the points of leaf b from densities on its 2.95 surface.
 // ---------------------------------------------------------------------------------------
@@ -431,6 +484,32 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
     }
     __syncthreads();
     const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: the (even) surface count re-staged as pairs, two-wide FP32 arithmetic; the
+        // surface lies outside the leaf box, so no distance is zero
+        float4 *pr = reinterpret_cast<float4 *>(smem_raw) + ns;   // [ns] float4 = ns / 2 pairs
+        float *sf = reinterpret_cast<float *>(pr);
+        for (int j = threadIdx.x; j < ns; j += kLeafThreads) {
+            const float4 v = src[j];
+            float *o = sf + 8 * (j >> 1) + (j & 1);
+            o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
+        }
+        __syncthreads();
+        for (int i = t0 + threadIdx.x; i < t1; i += kLeafThreads) {
+            const float4 x = pts[i];
+            const float2 nx = make_float2(-x.x, -x.x), ny = make_float2(-x.y, -x.y), nz = make_float2(-x.z, -x.z);
+            float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+            for (int e = 0; e < ns / 2; ++e) pair_step<1, false>(pr, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+            const float f = scale * inv4pi<float>();
+            phi[i] = (pot.x + pot.y) * f + (shift ? (float)shift[b] : 0.f);   // the leaf's constant part
+            if (GRAD) {
+                grad[3 * (int64_t)i] = (gx.x + gx.y) * f;
+                grad[3 * (int64_t)i + 1] = (gy.x + gy.y) * f;
+                grad[3 * (int64_t)i + 2] = (gz.x + gz.y) * f;
+            }
+        }
+        return;
+    }
     for (int i = t0 + threadIdx.x; i < t1; i += kLeafThreads) {
         const P x = pts[i];
         T pot = 0, gx = 0, gy = 0, gz = 0;
@@ -523,9 +602,15 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
     const int d = ctx->opt.depth;
     const double width = ctx->side / (double)(1 << d);
     const double radius = 2.95 * 0.5 * width;
-    leaf_check_kernel<T><<<ctx->nleaf, kLeafThreads, 0, s>>>(
-        (const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns,
-        ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out); count_launch();
+    if constexpr (std::is_same<T, float>::value)
+        leaf_check_f32_kernel<<<ctx->nleaf, kCheckThreads, 0, s>>>(
+            (const float4 *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, ctx->nsp,
+            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out);
+    else
+        leaf_check_kernel<T><<<ctx->nleaf, kLeafThreads, 0, s>>>(
+            (const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns,
+            ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -537,7 +622,7 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     const double width = ctx->side / (double)(1 << d);
     const double radius = 2.95 * 0.5 * width;
     using P = typename Vec4<T>::type;
-    size_t smem = sizeof(P) * ctx->ns;
+    size_t smem = sizeof(P) * ctx->ns * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
     if (grad)
         leaf_eval_kernel<T, true><<<ctx->nleaf, kLeafThreads, smem, s>>>(
             (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
