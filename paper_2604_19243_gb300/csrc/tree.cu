@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "devutil.cuh"
@@ -168,6 +169,32 @@ double from_ordered_bits(long long l) {
 
 // anchor a = min(max(floor((x - o) * scale), 0), 2^d - 1), every FP64 operation rounded
 // separately (no fused multiply-add) so that the host oracle reproduces it bit for bit.
+template <typename T>
+__device__ __forceinline__ uint32_t anchor_fp64(T x, double o, double scale, double amax) {
+    double t = __dmul_rn(__dsub_rn((double)x, o), scale);
+    t = floor(t);
+    t = fmin(fmax(t, 0.0), amax);
+    return (uint32_t)t;
+}
+
+// The same anchor from FP32 arithmetic where that is provably the same integer: t32 =
+// (x - o32) * s32 is within 2^-24 (s (|o| + 2 |x - o32|) + |t32|) of the exact (x - o) * s
+// (one rounding each for o32, s32, the difference and the product), and the FP64 value is
+// within 2^-50 of it.  When the fractional part of t32 is farther than four times that bound
+// from 0 and from 1, all three floor to the same integer; otherwise (a point within rounding
+// distance of a box face) the FP64 form decides.  FP64 arithmetic is slow on this part, and
+// this leaves it to a vanishing fraction of the points.
+__device__ __forceinline__ uint32_t anchor_fast(float x, double o, double scale, float o32, float s32, double amax) {
+    const float d = __fsub_rn(x, o32);
+    const float t = __fmul_rn(d, s32);
+    const float bound = 2.4e-7f * (s32 * (fabsf(o32) + 2.f * fabsf(d)) + fabsf(t)) + 1e-6f;   // 4 x 2^-24 x (...)
+    const float fl = floorf(t);
+    const float fr = t - fl;
+    if (fr > bound && 1.f - fr > bound && fabsf(t) < 8388608.f)
+        return (uint32_t)fminf(fmaxf(fl, 0.f), (float)amax);
+    return anchor_fp64<float>(x, o, scale, amax);
+}
+
 // A non-finite coordinate sets *bad (when given).
 template <typename T>
 __global__ void morton_kernel(const T *xyz, int64_t n, double ox, double oy, double oz,
@@ -178,11 +205,13 @@ __global__ void morton_kernel(const T *xyz, int64_t n, double ox, double oy, dou
     const double amax = (double)((1 << depth) - 1);
     uint32_t a[3];
     for (int k = 0; k < 3; ++k) {
-        if (bad && !isfinite((double)xyz[3 * i + k])) *bad = 1;
-        double t = __dmul_rn(__dsub_rn((double)xyz[3 * i + k], o[k]), scale);
-        t = floor(t);
-        t = fmin(fmax(t, 0.0), amax);
-        a[k] = (uint32_t)t;
+        const T x = xyz[3 * i + k];
+        if (bad && !isfinite((double)x)) *bad = 1;
+        if constexpr (std::is_same<T, float>::value)
+            a[k] = isfinite(x) ? anchor_fast(x, o[k], scale, (float)o[k], (float)scale, amax)
+                               : anchor_fp64<float>(x, o[k], scale, amax);
+        else
+            a[k] = anchor_fp64<T>(x, o[k], scale, amax);
     }
     keys[i] = morton3(a[0], a[1], a[2]);
     idx[i] = (int)i;
