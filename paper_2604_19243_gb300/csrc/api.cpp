@@ -92,6 +92,8 @@ void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
     free_async(ctx->UtP, s), free_async(ctx->Uscale, s);
+    free_async(ctx->UpP, s), free_async(ctx->DnP, s), free_async(ctx->CtP, s);
+    free_async(ctx->Ups, s), free_async(ctx->Dns, s), free_async(ctx->Cts, s);
     free_async(ctx->Yc, s), free_async(ctx->Dq, s), free_async(ctx->Cmean, s);
     free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
     free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
@@ -174,11 +176,25 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         const int np = ctx->opt.precision == FMM_BF16X6 ? 3 : 2;
         const size_t pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
         ctx->utp_plane = (long long)((size_t)rows * kw * pesz + 256) / 256 * 256;
-        if (ctx->opt.precision == FMM_FP16X3 &&
-            pool_alloc((void **)&ctx->Uscale, (size_t)rows * ((kw + 63) / 64) * sizeof(float) + 16, s) != cudaSuccess) {
-            cudaGetLastError();
-            free_workspace(ctx);
-            return fail(ctx, FMM_ENOMEM, "workspace allocation failed (plane scales)");
+        if (ctx->opt.precision == FMM_FP16X3) {
+            // every contraction reads FP16 planes: the upward- and downward-side rows, the
+            // compressed vectors (UtP) and the stencil output, each with its row scales
+            ctx->upp_plane = (long long)((size_t)rows * nsp * 2 + 256) / 256 * 256;
+            ctx->ctp_plane = ctx->utp_plane;
+            const size_t ns_chunks = (size_t)rows * ((nsp + 63) / 64) * sizeof(float) + 16;
+            const size_t kw_chunks = (size_t)rows * ((kw + 63) / 64) * sizeof(float) + 16;
+            bool okp = pool_alloc((void **)&ctx->Uscale, kw_chunks, s) == cudaSuccess &&
+                       pool_alloc((void **)&ctx->Cts, kw_chunks, s) == cudaSuccess &&
+                       pool_alloc((void **)&ctx->Ups, ns_chunks, s) == cudaSuccess &&
+                       pool_alloc((void **)&ctx->Dns, ns_chunks, s) == cudaSuccess &&
+                       pool_alloc(&ctx->UpP, (size_t)ctx->upp_plane * 2, s) == cudaSuccess &&
+                       pool_alloc(&ctx->DnP, (size_t)ctx->upp_plane * 2, s) == cudaSuccess &&
+                       pool_alloc(&ctx->CtP, (size_t)ctx->ctp_plane * 2, s) == cudaSuccess;
+            if (!okp) {
+                cudaGetLastError();
+                free_workspace(ctx);
+                return fail(ctx, FMM_ENOMEM, "workspace allocation failed (FP16 planes)");
+            }
         }
         if (pool_alloc(&ctx->UtP, (size_t)ctx->utp_plane * np, s) != cudaSuccess) {
             cudaGetLastError();
@@ -327,6 +343,8 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     if (opt->precision < FMM_FP32 || opt->precision > FMM_FP16X3) return FMM_EINVAL;
     if (!(opt->svd_rtol > 0 && opt->svd_rtol < 1) || !(opt->pinv_rtol > 0 && opt->pinv_rtol < 1))
         return FMM_EINVAL;
+    // the FP16 planes of FMM_FP16X3 carry the downward rows as produced, before a mean is taken off
+    if (opt->mean_free && opt->precision == FMM_FP16X3) return FMM_EUNSUPPORTED;
     if (opt->has_domain) {
         if (!(std::isfinite(opt->side) && opt->side > 0)) return FMM_EINVAL;
         for (int a = 0; a < 3; ++a)

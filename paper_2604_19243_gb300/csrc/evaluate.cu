@@ -97,6 +97,18 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
     const T *grid = (const T *)ctx->grid_dev;
     const double r_leaf = ctx->side / (double)(1 << d) * 0.5;
     const int dir = adjoint ? 1 : 0;
+    // FMM_FP16X3: every contraction reads FP16 planes, which the step producing its input writes
+    // beside (or instead of) the FP32 rows: level l's rows of the upward side (UpP), of the
+    // downward side (DnP), of the compressed vectors (UtP) and of the stencil output (CtP)
+    const bool f16 = ctx->opt.precision == FMM_FP16X3;
+    const int nck_s = (nsp + 63) / 64, nck_k = (kw + 63) / 64;
+    auto base = [&](int l) { return (size_t)ctx->lev[l].row_base; };
+    auto upP = [&](int l) { return (unsigned char *)ctx->UpP + base(l) * nsp * 2; };
+    auto dnP = [&](int l) { return (unsigned char *)ctx->DnP + base(l) * nsp * 2; };
+    auto ctP = [&](int l) { return (unsigned char *)ctx->CtP + base(l) * kw * 2; };
+    auto upS = [&](int l) { return ctx->Ups + base(l) * nck_s; };
+    auto dnS = [&](int l) { return ctx->Dns + base(l) * nck_s; };
+    auto ctS = [&](int l) { return ctx->Cts + base(l) * nck_k; };
 
     // leaf stage
     if (!adjoint) {
@@ -114,6 +126,9 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         c2.Y = rows_at<T>(A, ctx, d, nsp), c2.ldy = nsp;
         FMM_CUDA_TRY(gemm<T>(ctx, c2, OP_CLOSE2 + dir * OP_COUNT, s));
     }
+    if (f16)
+        FMM_CUDA_TRY(launch_rows_to_planes((const float *)rows_at<T>(A, ctx, d, nsp), nsp, ctx->lev[d].n, nsp, upP(d),
+                                           ctx->upp_plane, nsp, upS(d), nck_s, s));
     cudaEventRecord(ctx->ev[2], s);
     // upward sweep
     for (int l = d - 1; l >= 2; --l) {
@@ -122,6 +137,10 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         c.X0 = rows_at<T>(A, ctx, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
         c.W0 = o.up[0], c.w_stride = (int64_t)nsp * nsp;
         c.Y = rows_at<T>(A, ctx, l, nsp), c.ldy = nsp;
+        if (f16) {
+            c.Xp = upP(l + 1), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l + 1), c.xp_scale_ld = nck_s;
+            c.Yp = upP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = upS(l), c.yp_scale_ld = nck_s;
+        }
         FMM_CUDA_TRY(gemm<T>(ctx, c, OP_UP + dir * OP_COUNT, s));
     }
     cudaEventRecord(ctx->ev[3], s);
@@ -138,15 +157,15 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         GemmCall c;
         c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
         c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
-        c.Y = rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;
+        c.Y = ctx->tensor ? nullptr : rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;   // tensor modes: planes only
         unsigned char *planes = nullptr;
-        const int nchk = (kw + 63) / 64;
-        float *scales = ctx->Uscale ? ctx->Uscale + (size_t)ctx->lev[l].row_base * nchk : nullptr;
+        float *scales = ctx->Uscale ? ctx->Uscale + base(l) * nck_k : nullptr;
         if (ctx->tensor) {
-            planes = (unsigned char *)ctx->UtP + (size_t)ctx->lev[l].row_base * kw * pesz;
+            planes = (unsigned char *)ctx->UtP + base(l) * kw * pesz;
             c.Yp = planes, c.yp_ld = kw, c.yp_plane = ctx->utp_plane;
-            c.yp_scale = scales, c.scale_ld = nchk;
+            c.yp_scale = scales, c.yp_scale_ld = nck_k;
         }
+        if (f16) c.Xp = upP(l), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l), c.xp_scale_ld = nck_s;
         FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, ls));
         GemmCall st;
         st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
@@ -155,7 +174,11 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
         if (ctx->tensor) {
             st.Xp = planes, st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
-            st.xp_scale = scales, st.scale_ld = nchk;
+            st.xp_scale = scales, st.xp_scale_ld = nck_k;
+        }
+        if (f16) {   // the decompress reads the stencil output as planes
+            st.Y = nullptr;
+            st.Yp = ctP(l), st.yp_ld = kw, st.yp_plane = ctx->ctp_plane, st.yp_scale = ctS(l), st.yp_scale_ld = nck_k;
         }
         FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, ls));
         FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
@@ -172,6 +195,14 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
             c.W1_by_cls = o.down;
         }
         c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
+        if (f16) {
+            c.Xp = ctP(l), c.xp_ld = kw, c.xp_plane = ctx->ctp_plane, c.xp_scale = ctS(l), c.xp_scale_ld = nck_k;
+            if (l >= 3)
+                c.Xp1 = dnP(l - 1), c.xp1_ld = nsp, c.xp1_plane = ctx->upp_plane, c.xp1_scale = dnS(l - 1),
+                c.xp1_scale_ld = nck_s;
+            if (l < d)   // the leaves' rows have no children to read them as planes
+                c.Yp = dnP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = dnS(l), c.yp_scale_ld = nck_s;
+        }
         FMM_CUDA_TRY(gemm<T>(ctx, c, OP_DECOMPRESS + dir * OP_COUNT, s));
         if (!adjoint && ctx->opt.mean_free) {
             const LevelTables &L = ctx->lev[l];

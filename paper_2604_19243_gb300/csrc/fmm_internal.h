@@ -155,6 +155,11 @@ struct fmm_ctx {
     void *Dq = nullptr;                  // [nleaf x nsp] leaf equivalent densities
     void *Cmean = nullptr;               // [total_rows] FP64 constant part of the downward check potentials
     float *Uscale = nullptr;             // FMM_FP16X3: 1 / scale of UtP per row and 64-column chunk
+    // FMM_FP16X3: FP16 hi/lo planes (and scales) of the upward-side rows of the current direction
+    // (UpP, [rows x nsp]), of its downward-side rows (DnP) and of the stencil output (CtP, [rows x ws_kw])
+    void *UpP = nullptr, *DnP = nullptr, *CtP = nullptr;
+    long long upp_plane = 0, ctp_plane = 0;   // bytes per plane (UpP and DnP share the first)
+    float *Ups = nullptr, *Dns = nullptr, *Cts = nullptr;
     void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
     void *far_phi = nullptr, *far_grad = nullptr;
     size_t ws_bytes = 0;
@@ -261,11 +266,19 @@ struct GemmCall {
     const void *Xp = nullptr; int xp_ld = 0; int xp_rows = 0; long long xp_plane = 0;
     void *Yp = nullptr; int yp_ld = 0; long long yp_plane = 0;
     // FP16 split planes (FMM_FP16X3): 1 / scale per row and 64-column chunk of Xp / Yp
-    const float *xp_scale = nullptr; float *yp_scale = nullptr; int scale_ld = 0;
+    const float *xp_scale = nullptr; int xp_scale_ld = 0;
+    float *yp_scale = nullptr; int yp_scale_ld = 0;
+    // PARENT2 segment 1 from split planes (FMM_FP16X3): the parent rows
+    const void *Xp1 = nullptr; int xp1_ld = 0; long long xp1_plane = 0;
+    const float *xp1_scale = nullptr; int xp1_scale_ld = 0;
 };
 template <typename T>
 cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &g, cudaStream_t s);
 cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &g, int op_id, cudaStream_t s);
+// FP32 rows (nrows x ncols, stride ldx) -> FP16 hi/lo planes (stride ldp, planes plane_bytes
+// apart) and 1 / scale per row and 64-column chunk (stride lds), as FMM_FP16X3 contractions read
+cudaError_t launch_rows_to_planes(const float *x, int ldx, int64_t nrows, int ncols, void *planes,
+                                  long long plane_bytes, int ldp, float *scales, int lds, cudaStream_t s);
 cudaError_t tc_upload_operators(fmm_ctx *ctx);
 void tc_free(fmm_ctx *ctx);
 

@@ -75,6 +75,15 @@ struct TcDev {
     int a_scale_ld;
     const float *b_scale;
     int b_scale_ld;
+    // PARENT2 segment 1 (the parent rows): its own planes, row scales and, per octant class,
+    // operator scales
+    const unsigned char *xp1;
+    long long xp1_plane;
+    int xp1_ld;
+    const float *a_scale1;
+    int a_scale1_ld;
+    const float *b_scale1;
+    int b_scale1_ld;
     // FP16 output planes: each row scaled by a power of two per 64-column chunk, 1 / scale
     // written to yp_scale[row][chunk]
     int yp_f16;
@@ -427,6 +436,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             src_next2 = seg2 < nseg ? src_fast(g, t, tt, me2, seg2) : -1;
             const int *rs = srcs[sidx];
             const int unit = lane & 7;
+            const bool seg_second = g.mode == GM_PARENT2 && seg == 1;   // parent rows
+            const unsigned char *xpb = seg_second ? p.xp1 : p.xp;
+            const long long xpp = seg_second ? p.xp1_plane : p.xp_plane;
+            const int xld = seg_second ? p.xp1_ld : p.xp_ld;
             for (int c = 0; c < si.nchunks; ++c, ++item) {
                 const int stage = item % p.nstages;
                 if (!ok) continue;
@@ -459,12 +472,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                     const int total = pl_rows[kTcRows] * valid_units;
                     for (int e = tid; e < total; e += kPlaneProducers) {
                         const int r = pl_rows[e / valid_units], u = e % valid_units;
-                        const size_t elem = (size_t)rs[r] * p.xp_ld + k0 + u * (16 / esz);
+                        const size_t elem = (size_t)rs[r] * xld + k0 + u * (16 / esz);
                         const int dst_off = r * kAtomBytes + ((u ^ (r & 7)) << 4);
 #pragma unroll
                         for (int pl = 0; pl < 3; ++pl)
                             if (pl < p.nplanes)
-                                cp_async16(sa + pl * a_plane_bytes + dst_off, p.xp + pl * p.xp_plane + elem * esz, 16);
+                                cp_async16(sa + pl * a_plane_bytes + dst_off, xpb + pl * xpp + elem * esz, 16);
                     }
                     cp_async_arrive(&full_bar[stage]);
                     continue;
@@ -478,12 +491,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                     // with per-row factors (scaled planes) a row without a source is multiplied by
                     // zero in the drain, so it needs no copy; K units past the segment are never read
                     if (!have && (scaled_a || !unit_ok)) continue;
-                    const size_t elem = (size_t)(have ? sr : 0) * p.xp_ld + k0 + unit * (16 / esz);
+                    const size_t elem = (size_t)(have ? sr : 0) * xld + k0 + unit * (16 / esz);
                     const int dst_off = r * kAtomBytes + ((unit ^ (r & 7)) << 4);
 #pragma unroll
                     for (int pl = 0; pl < 3; ++pl) {
                         if (pl < p.nplanes)
-                            cp_async16(sa + pl * a_plane_bytes + dst_off, p.xp + pl * p.xp_plane + elem * esz,
+                            cp_async16(sa + pl * a_plane_bytes + dst_off, xpb + pl * xpp + elem * esz,
                                        have ? 16 : 0);
                     }
                 }
@@ -658,6 +671,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         auto src_of = [&](int sg) { return sg < nseg ? src_fast(g, t, tt, me, sg) : -1; };
         auto factor = [&](int src, int sg, int ch) -> float {
             if (!scaled || sg >= nseg) return 1.f;
+            if (g.mode == GM_PARENT2 && sg == 1) {   // parent rows, operator of the tile's class
+                const float fb1 = __ldg(p.b_scale1 + t.cls * p.b_scale1_ld + ch);
+                return src >= 0 ? __ldg(p.a_scale1 + (size_t)src * p.a_scale1_ld + ch) * fb1 : 0.f;
+            }
             const float fb = __ldg(p.b_scale + w_index_fast(g, t, tt, sg) * p.b_scale_ld + ch);
             return src >= 0 ? __ldg(p.a_scale + (size_t)src * p.a_scale_ld + ch) * fb : 0.f;
         };
@@ -736,6 +753,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         } else {
             const int row = q * 32 + lane;
             const int b = row < t.nrows ? box[row] : -1;
+            if (b >= 0 && g.Y) {   // FP32 rows (alone, or beside split planes for a later gather)
+                float *y = (float *)g.Y + (size_t)b * g.ldy + n_lo;
+#pragma unroll
+                for (int n0 = 0; n0 < kTcMaxN; n0 += 4) {
+                    if (n0 < N) {
+                        float4 o = make_float4(g.alpha * acc[n0], g.alpha * acc[n0 + 1], g.alpha * acc[n0 + 2],
+                                               g.alpha * acc[n0 + 3]);
+                        if (g.accumulate) {
+                            const float4 old = *reinterpret_cast<const float4 *>(y + n0);
+                            o.x += old.x, o.y += old.y, o.z += old.z, o.w += old.w;
+                        }
+                        *reinterpret_cast<float4 *>(y + n0) = o;
+                    }
+                }
+            }
             if (b >= 0 && p.yp && p.yp_f16) {
                 // FP16 hi/lo planes of the row scaled by a power of two per 64-column chunk, so
                 // that its largest entry is below 2^14 (no overflow, full FP16 precision)
@@ -820,20 +852,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                         }
                     }
                 }
-            } else if (b >= 0) {
-                float *y = (float *)g.Y + (size_t)b * g.ldy + n_lo;
-#pragma unroll
-                for (int n0 = 0; n0 < kTcMaxN; n0 += 4) {
-                    if (n0 < N) {
-                        float4 o = make_float4(g.alpha * acc[n0], g.alpha * acc[n0 + 1], g.alpha * acc[n0 + 2],
-                                               g.alpha * acc[n0 + 3]);
-                        if (g.accumulate) {
-                            const float4 old = *reinterpret_cast<const float4 *>(y + n0);
-                            o.x += old.x, o.y += old.y, o.z += old.z, o.w += old.w;
-                        }
-                        *reinterpret_cast<float4 *>(y + n0) = o;
-                    }
-                }
             }
         }
     }
@@ -843,6 +861,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         tc_fence_after();
         tmem_dealloc(tmem, p.tmem_cols);
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32 rows -> FP16 hi/lo planes, each row scaled by a power of two per 64-column chunk (its
+// largest entry below 2^14), 1 / scale per (row, chunk): the form the FP16X3 contractions read.
+// One warp per row.
+// ---------------------------------------------------------------------------------------
+namespace {
+__global__ void rows_to_planes_kernel(const float *__restrict__ x, int ldx, int nrows, int ncols,
+                                      unsigned char *__restrict__ planes, long long plane_bytes, int ldp,
+                                      float *__restrict__ scales, int lds) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const float *xr = x + (size_t)row * ldx;
+    uint16_t *hi = reinterpret_cast<uint16_t *>(planes) + (size_t)row * ldp;
+    uint16_t *lo = reinterpret_cast<uint16_t *>(planes + plane_bytes) + (size_t)row * ldp;
+    for (int c0 = 0; c0 < ncols; c0 += 64) {
+        const int i0 = c0 + lane, i1 = c0 + 32 + lane;
+        const float v0 = i0 < ncols ? xr[i0] : 0.f, v1 = i1 < ncols ? xr[i1] : 0.f;
+        float m = fmaxf(fabsf(v0), fabsf(v1));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int ex = 0;
+        frexpf(m, &ex);
+        const int e = min(max(14 - ex, -126), 126);
+        const float sc = m > 0.f ? ldexpf(1.f, e) : 1.f;
+        if (lane == 0) scales[(size_t)row * lds + c0 / 64] = m > 0.f ? ldexpf(1.f, -e) : 0.f;
+        for (int k = 0; k < 2; ++k) {
+            const int i = k ? i1 : i0;
+            if (i >= ncols) continue;
+            const float v = (k ? v1 : v0) * sc;
+            const __half h = __float2half_rn(v);
+            hi[i] = __half_as_ushort(h);
+            lo[i] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_rows_to_planes(const float *x, int ldx, int64_t nrows, int ncols, void *planes,
+                                  long long plane_bytes, int ldp, float *scales, int lds, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    rows_to_planes_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, s>>>(x, ldx, (int)nrows, ncols,
+                                                                      (unsigned char *)planes, plane_bytes, ldp,
+                                                                      scales, lds);
+    count_launch();
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -989,12 +1053,25 @@ static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, c
     const auto &D = adjoint ? h.a_down : h.down;
     std::vector<double> ups;
     for (int c = 0; c < 8; ++c) ups.insert(ups.end(), U[c].begin(), U[c].end());
-    FMM_CUDA_TRY(tc_upload_many(ctx, ups.data(), 8, ns, ns, nsp, nsp, &t.up));
-    for (int c = 0; c < 8; ++c) FMM_CUDA_TRY(tc_upload_many(ctx, D[c].data(), 1, ns, ns, nsp, nsp, &t.down[c]));
+    const bool f16ops = ctx->opt.precision == FMM_FP16X3;   // FP16 planes for every contraction
+    FMM_CUDA_TRY(tc_upload_many(ctx, ups.data(), 8, ns, ns, nsp, nsp, &t.up, f16ops));
+    // the 8 D2D operators in one allocation (contiguous operators and scales), one view each
+    {
+        const bool f16 = ctx->opt.precision == FMM_FP16X3;
+        std::vector<double> downs;
+        for (int c = 0; c < 8; ++c) downs.insert(downs.end(), D[c].begin(), D[c].end());
+        TcMat all;
+        FMM_CUDA_TRY(tc_upload_many(ctx, downs.data(), 8, ns, ns, nsp, nsp, &all, f16));
+        for (int c = 0; c < 8; ++c) {
+            t.down[c] = all;
+            t.down[c].planes[0] = (unsigned char *)all.planes[0] + (size_t)c * all.bytes;
+            if (all.scale) t.down[c].scale = all.scale + (size_t)c * all.scale_ld;
+        }
+    }
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_compress : h.compress).data(), 1, o.kin, ns, o.kinp, nsp,
-                                &t.compress));
+                                &t.compress, f16ops));
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_decompress : h.decompress).data(), 1, ns, o.kout, nsp,
-                                o.koutp, &t.decompress));
+                                o.koutp, &t.decompress, f16ops));
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_stencil : h.stencil).data(), kNumTransfer, o.kout, o.kin,
                                 o.koutp, o.kinp, &t.stencil, ctx->opt.precision == FMM_FP16X3));
     return cudaSuccess;
@@ -1039,7 +1116,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     }
     const int prec = ctx->opt.precision;
     p.tf32 = prec == FMM_TF32X3;
-    p.f16 = prec == FMM_FP16X3 && op == OP_STENCIL;
+    p.f16 = prec == FMM_FP16X3;   // FP16 split planes with scales for every contraction
     p.nplanes = p.f16 ? 2 : planes_of(prec);
     if (p.nplanes == 3) {
         const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
@@ -1051,11 +1128,24 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         for (int i = 0; i < 3; ++i) p.prod_a[i] = a[i], p.prod_b[i] = b[i];
     }
     if (p.f16) {
-        if (!c.Xp || !c.xp_scale || !T.stencil.scale) return cudaErrorInvalidValue;
+        const TcMat &W = op == OP_UP ? T.up : op == OP_COMPRESS ? T.compress : op == OP_STENCIL ? T.stencil : T.decompress;
+        if (!c.Xp || !c.xp_scale || !W.scale) return cudaErrorInvalidValue;
         p.a_scale = c.xp_scale;
-        p.a_scale_ld = c.scale_ld;
-        p.b_scale = T.stencil.scale;
-        p.b_scale_ld = T.stencil.scale_ld;
+        p.a_scale_ld = c.xp_scale_ld;
+        p.b_scale = W.scale;
+        p.b_scale_ld = W.scale_ld;
+        if (c.mode == GM_PARENT2 && c.X1) {
+            if (!c.Xp1 || !c.xp1_scale || !T.down[0].scale || ((uintptr_t)c.Xp1 & 15) || ((c.xp1_ld * 2) & 15) ||
+                (c.xp1_plane & 15))
+                return cudaErrorInvalidValue;
+            p.xp1 = (const unsigned char *)c.Xp1;
+            p.xp1_plane = c.xp1_plane;
+            p.xp1_ld = c.xp1_ld;
+            p.a_scale1 = c.xp1_scale;
+            p.a_scale1_ld = c.xp1_scale_ld;
+            p.b_scale1 = T.down[0].scale;   // the 8 class operators' scales, contiguous
+            p.b_scale1_ld = T.down[0].scale_ld;
+        }
     }
     if (c.n_out % 16 != 0 || (c.k0 % 16) != 0 || (c.X1 && c.k1 % 16 != 0)) return cudaErrorInvalidValue;
     int nsplit = (c.n_out + kTcMaxN - 1) / kTcMaxN;
@@ -1080,7 +1170,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     p.err = ctx->dev_flag;
     if (c.Xp) {
         // A rows from split planes: K of the segment must be the planes' width
-        if (c.mode != GM_STENCIL && c.mode != GM_IDENTITY) return cudaErrorInvalidValue;
+        if (c.mode == GM_PARENT2 && c.X1 && !c.Xp1) return cudaErrorInvalidValue;
         if (((uintptr_t)c.Xp & 15) || ((c.xp_ld * (p.tf32 ? 4 : 2)) & 15) || (c.xp_plane & 15))
             return cudaErrorInvalidValue;
         p.a_planes = 1;
@@ -1097,7 +1187,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
             if (!c.yp_scale || (nsplit > 1 && p.ncta % 64 != 0)) return cudaErrorInvalidValue;
             p.yp_f16 = 1;
             p.yp_scale = c.yp_scale;
-            p.yp_scale_ld = c.scale_ld;
+            p.yp_scale_ld = c.yp_scale_ld;
         }
     }
     const size_t smem = (size_t)p.nstages * stage_bytes + 1024;

@@ -414,20 +414,25 @@ leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ le
                       const uint32_t *__restrict__ keys, const float *__restrict__ grid, int ns, int nsp,
                       double ox, double oy, double oz, double width, double radius, float *__restrict__ out) {
     __shared__ __align__(16) float4 src[kLeafChunk];   // kLeafChunk sources as pairs
+    __shared__ float cen[3];
     float *sf = reinterpret_cast<float *>(src);
     const int b = blockIdx.x;
     const int s0 = leaf_off[b], s1 = leaf_off[b + 1];
-    int ax, ay, az;
-    demorton3(keys[b], ax, ay, az);
-    const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
-                 cz = oz + (az + 0.5) * width;
+    if (threadIdx.x == 0) {   // the box centre in FP64 once, rounded to FP32
+        int ax, ay, az;
+        demorton3(keys[b], ax, ay, az);
+        cen[0] = (float)(ox + (ax + 0.5) * width), cen[1] = (float)(oy + (ay + 0.5) * width);
+        cen[2] = (float)(oz + (az + 0.5) * width);
+    }
+    __syncthreads();
+    const float r32 = (float)radius;
     for (int i0 = 0; i0 < nsp; i0 += kCheckThreads) {
         const int i = i0 + threadIdx.x;
         float px = 0.f, py = 0.f, pz = 0.f;
-        if (i < ns) {
-            px = (float)(cx + radius * (double)grid[3 * i]);
-            py = (float)(cy + radius * (double)grid[3 * i + 1]);
-            pz = (float)(cz + radius * (double)grid[3 * i + 2]);
+        if (i < ns) {   // centre + radius * grid point: two FP32 roundings, no FP64 per thread
+            px = fmaf(r32, grid[3 * i], cen[0]);
+            py = fmaf(r32, grid[3 * i + 1], cen[1]);
+            pz = fmaf(r32, grid[3 * i + 2], cen[2]);
         }
         const float2 nx = make_float2(-px, -px), ny = make_float2(-py, -py), nz = make_float2(-pz, -pz);
         float2 acc = make_float2(0.f, 0.f);
@@ -469,16 +474,28 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
     using P = typename Vec4<T>::type;
     extern __shared__ unsigned char smem_raw[];
     P *src = reinterpret_cast<P *>(smem_raw);    // [ns]
+    __shared__ double cen[3];
+    __shared__ float cenf[3];
     const int b = blockIdx.x;
-    int ax, ay, az;
-    demorton3(keys[b], ax, ay, az);
-    const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
-                 cz = oz + (az + 0.5) * width;
+    if (threadIdx.x == 0) {   // the box centre once per leaf
+        int ax, ay, az;
+        demorton3(keys[b], ax, ay, az);
+        cen[0] = ox + (ax + 0.5) * width, cen[1] = oy + (ay + 0.5) * width, cen[2] = oz + (az + 0.5) * width;
+        cenf[0] = (float)cen[0], cenf[1] = (float)cen[1], cenf[2] = (float)cen[2];
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < ns; j += kLeafThreads) {
         P p;
-        p.x = (T)(cx + radius * (double)grid[3 * j]);
-        p.y = (T)(cy + radius * (double)grid[3 * j + 1]);
-        p.z = (T)(cz + radius * (double)grid[3 * j + 2]);
+        if constexpr (std::is_same<T, float>::value) {   // FP32: no FP64 arithmetic per surface point
+            const float r32 = (float)radius;
+            p.x = fmaf(r32, grid[3 * j], cenf[0]);
+            p.y = fmaf(r32, grid[3 * j + 1], cenf[1]);
+            p.z = fmaf(r32, grid[3 * j + 2], cenf[2]);
+        } else {
+            p.x = (T)(cen[0] + radius * (double)grid[3 * j]);
+            p.y = (T)(cen[1] + radius * (double)grid[3 * j + 1]);
+            p.z = (T)(cen[2] + radius * (double)grid[3 * j + 2]);
+        }
         p.w = dens[(int64_t)b * ldd + j];
         src[j] = p;
     }

@@ -184,31 +184,36 @@ __device__ __forceinline__ uint32_t anchor_fp64(T x, double o, double scale, dou
 // from 0 and from 1, all three floor to the same integer; otherwise (a point within rounding
 // distance of a box face) the FP64 form decides.  FP64 arithmetic is slow on this part, and
 // this leaves it to a vanishing fraction of the points.
-__device__ __forceinline__ uint32_t anchor_fast(float x, double o, double scale, float o32, float s32, double amax) {
+__device__ __forceinline__ uint32_t anchor_fast(float x, double o, double scale, float o32, float s32, float amax32,
+                                                double amax) {
     const float d = __fsub_rn(x, o32);
     const float t = __fmul_rn(d, s32);
     const float bound = 2.4e-7f * (s32 * (fabsf(o32) + 2.f * fabsf(d)) + fabsf(t)) + 1e-6f;   // 4 x 2^-24 x (...)
     const float fl = floorf(t);
     const float fr = t - fl;
-    if (fr > bound && 1.f - fr > bound && fabsf(t) < 8388608.f)
-        return (uint32_t)fminf(fmaxf(fl, 0.f), (float)amax);
+    if (fr > bound && 1.f - fr > bound && fabsf(t) < 8388608.f) return (uint32_t)fminf(fmaxf(fl, 0.f), amax32);
     return anchor_fp64<float>(x, o, scale, amax);
 }
 
 // A non-finite coordinate sets *bad (when given).
+// (The FP32 copies of the origin and scale come from the host: conversions from FP64 would
+// run on the FP64 pipe for every point.)
 template <typename T>
 __global__ void morton_kernel(const T *xyz, int64_t n, double ox, double oy, double oz,
-                              double scale, int depth, uint32_t *keys, int *idx, int *bad) {
+                              double scale, int depth, uint32_t *keys, int *idx, int *bad,
+                              float ox32, float oy32, float oz32, float s32) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double o[3] = {ox, oy, oz};
+    const float o32[3] = {ox32, oy32, oz32};
     const double amax = (double)((1 << depth) - 1);
+    const float amax32 = (float)((1 << depth) - 1);
     uint32_t a[3];
     for (int k = 0; k < 3; ++k) {
         const T x = xyz[3 * i + k];
-        if (bad && !isfinite((double)x)) *bad = 1;
+        if (bad && !isfinite(x)) *bad = 1;
         if constexpr (std::is_same<T, float>::value)
-            a[k] = isfinite(x) ? anchor_fast(x, o[k], scale, (float)o[k], (float)scale, amax)
+            a[k] = isfinite(x) ? anchor_fast(x, o[k], scale, o32[k], s32, amax32, amax)
                                : anchor_fp64<float>(x, o[k], scale, amax);
         else
             a[k] = anchor_fp64<T>(x, o[k], scale, amax);
@@ -624,7 +629,9 @@ static cudaError_t build_tree_t(fmm_ctx *ctx, const T *xyz) {
     FMM_CUDA_TRY(keys.alloc(n, s));
     FMM_CUDA_TRY(pool_alloc((void **)&ctx->perm, n * sizeof(int), s));
     morton_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ctx->origin[0], ctx->origin[1], ctx->origin[2],
-                                                          scale, depth, keys.p, ctx->perm, cnt + kCntBad); count_launch();
+                                                          scale, depth, keys.p, ctx->perm, cnt + kCntBad,
+                                                          (float)ctx->origin[0], (float)ctx->origin[1],
+                                                          (float)ctx->origin[2], (float)scale); count_launch();
     FMM_CUDA_TRY(cudaGetLastError());
     FMM_CUDA_TRY(radix_sort(keys.p, ctx->perm, n, 3 * depth, s));
     // sorted points (x, y, z, q=0)
@@ -928,7 +935,8 @@ extern "C" fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int d
     int *sums = hist + kNoAllocHist;
     const double scale = std::ldexp(1.0, depth) / side;
     morton_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, origin[0], origin[1], origin[2], scale, depth,
-                                                           keys, perm, nullptr);
+                                                           keys, perm, nullptr, (float)origin[0], (float)origin[1],
+                                                           (float)origin[2], (float)scale);
     count_launch();
     // stable LSD radix sort of (keys, perm), 8-bit digits, ping-ponging with the scratch copies
     const int bits = 3 * depth;
