@@ -197,7 +197,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere8m_p6_d7", choices=sorted(WORKLOADS))
@@ -376,7 +376,8 @@ def main():
                 "timing": "CUDA events on the far-field stream: end of the upward pass to the start "
                           "of the leaf level's downward step"})
     m2l["frac"] = (m2l["achieved"] / m2l["peak"]) if m2l["peak"] else None
-    m2l["traffic"] = None
+    m2l["traffic"] = None   # several launches per phase; the level-7 stencil's own figure follows
+    m2l["traffic_level7_stencil"] = recorded_traffic("gemm_tc_kernel_stencil_level7", source_digest("gemm_tc.cu"))
     # upward and downward passes in achieved GB/s (algorithmic bytes: every row read once and
     # written once, the points and outputs of the leaf steps once)
     es = 8 if fp64 else 4
