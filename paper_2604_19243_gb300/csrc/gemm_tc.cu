@@ -47,6 +47,7 @@ constexpr int kTcMaxN = 160;               // output columns per CTA (wider N: s
 constexpr int kAtomBytes = 128;            // one swizzle atom row
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr int kPlaneProducers = 96;        // plane mode: warps 0-2 copy, warp 3 issues the MMAs
+constexpr int kPlaneStages = 2;            // plane mode: stages in shared memory
 
 struct TcDev {
     GemmDev g;                      // gather description (W fields unused)
@@ -302,8 +303,16 @@ __device__ __forceinline__ int src_fast(const GemmDev &g, const Tile &t, const T
 
 }  // namespace
 
-template <bool TF32>
-__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_constant__ TcDev p) {
+// The kernel body.  PL (plane layout, A rows from split planes): 384 threads, warps 0-2
+// produce, warp 3 issues, warps 4-11 drain, two per TMEM lane quarter, each holding half of the
+// row's columns (80), so that a CTA needs about half the registers of the 256-thread layout and
+// near-field CTAs can share its SM.  Otherwise: 256 threads, warps 0-3 gather and split A in
+// registers, warps 4-7 drain whole rows (warp 4 also issues).
+template <bool TF32, bool PL>
+__device__ __forceinline__ void tc_body(const TcDev &p) {
+    constexpr int NT = PL ? 384 : kTcThreads;        // threads
+    constexpr int DC = PL ? kTcMaxN / 2 : kTcMaxN;   // columns a drain thread holds
+    constexpr int NDRAIN = PL ? 8 : 4;               // drain warps
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t full_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t tmem_base;
@@ -313,6 +322,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     __shared__ uint32_t mask[6];
     __shared__ int abort_flag;
     __shared__ TileTables tt;
+    __shared__ float pmax[2][(kTcMaxN + 63) / 64][kTcRows];   // PL: the halves' chunk maxima of each row
 
     const GemmDev &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull_bar[b], 1);      // tcgen05.commit
-            mbar_init(&tempty_bar[b], 4);     // the 4 accumulator warps
+            mbar_init(&tempty_bar[b], NDRAIN);   // the accumulator warps
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     if (tid < 6) mask[tid] = g.mode == GM_STENCIL ? g.masks[(size_t)t.mask * 6 + tid] : 0xffffffffu;
     if (tid < kTcRows) box[tid] = tid < t.nrows ? gemm_row_box(g, t, tid) : -1;
     if (g.mode == GM_STENCIL)
-        for (int k = tid; k < kClassSlots; k += kTcThreads) {
+        for (int k = tid; k < kClassSlots; k += NT) {
             tt.slot[k] = g.class_slots[t.cls * kClassSlots + k];
             tt.delta[k] = g.class_delta[t.cls * kClassSlots + k];
         }
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     // once so that they hold finite values (their products are then multiplied by zero).
     const bool scaled_a = p.a_planes && p.a_scale != nullptr;
     if (scaled_a)
-        for (int i = tid; i < p.nstages * stage_bytes / 16; i += kTcThreads)
+        for (int i = tid; i < p.nstages * stage_bytes / 16; i += NT)
             reinterpret_cast<uint4 *>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (warp == 0) tmem_alloc(&tmem_base, p.tmem_cols);
     fence_proxy_async();   // the zeroed stages (generic proxy) before any tensor-core read
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 *(volatile int *)&abort_flag = 1;
             }
         }
-    } else if (warp < 4) {
+    } else if (!PL && warp < 4) {
         // ------------------------------------------------------------ producers
         int item = 0;
         bool ok = true;
@@ -650,11 +660,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         // Each stage item's products land in one of two TMEM accumulators; these warps add the
         // item's partial sums (32 rows each) into FP32 registers, so that no TMEM accumulator
         // takes more than one stage of tensor-core additions.
-        const int q = warp - 4;                           // TMEM lane quarter
-        const bool issuer = warp == 4 && !p.a_planes;   // plane mode: warp 3 issues
-        float acc[kTcMaxN];
+        const int q = (warp - 4) & 3;                     // TMEM lane quarter
+        const int hf = PL ? (warp - 4) >> 2 : 0;          // column half (PL)
+        const int c0 = hf * DC;                           // first column this thread holds
+        const bool issuer = !PL && warp == 4;             // PL: warp 3 issues
+        float acc[DC];
 #pragma unroll
-        for (int i = 0; i < kTcMaxN; ++i) acc[i] = 0.f;
+        for (int i = 0; i < DC; ++i) acc[i] = 0.f;
         bool ok = true;
         // Scaled FP16 operands: the factor of every item for this thread's row.  The walk keeps
         // the source row of the current and the next active segment, so that every load behind
@@ -699,16 +711,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1)) return false;
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.ncta);
+            if constexpr (PL) {
 #pragma unroll
-            for (int n0 = 0; n0 < kTcMaxN; n0 += 32) {
-                if (n0 < N) {
-                    uint32_t v[32];
-                    tmem_ld32(ta + (uint32_t)n0, v);
-                    tmem_wait_ld();
-                    // N is a multiple of 16: the upper half of the last load may be past N
+                for (int n0 = 0; n0 < DC; n0 += 16) {
+                    if (c0 + n0 < N) {   // N is a multiple of 16
+                        float v[16];
+                        tmem_ld16(ta + (uint32_t)(c0 + n0), v);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (n0 + i < kTcMaxN && (i < 16 || n0 + 16 < N)) acc[n0 + i] = fmaf(f, __uint_as_float(v[i]), acc[n0 + i]);
+                        for (int i = 0; i < 16; ++i) acc[n0 + i] = fmaf(f, v[i], acc[n0 + i]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int n0 = 0; n0 < kTcMaxN; n0 += 32) {
+                    if (n0 < N) {
+                        uint32_t v[32];
+                        tmem_ld32(ta + (uint32_t)n0, v);
+                        tmem_wait_ld();
+                        // N is a multiple of 16: the upper half of the last load may be past N
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (n0 + i < kTcMaxN && (i < 16 || n0 + 16 < N))
+                                acc[n0 + i] = fmaf(f, __uint_as_float(v[i]), acc[n0 + i]);
+                    }
                 }
             }
             tc_fence_before();
@@ -747,109 +772,134 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             }
             if (ok && n_items >= 1) ok = drain(n_items - 1);
         }
+        // epilogue: this thread's row (q * 32 + lane) and columns [c0, c0 + DC)
+        const int row = q * 32 + lane;
+        const int b = row < t.nrows ? box[row] : -1;
+        const bool f16p = p.yp && p.yp_f16;            // uniform over the launch
+        float pm0 = 0.f, pm1 = 0.f, pm2 = 0.f;         // |value| maxima of the 64-column chunks
         if (!ok) {
             atomicExch(p.err, FMM_ETIMEOUT);
             *(volatile int *)&abort_flag = 1;
         } else {
-            const int row = q * 32 + lane;
-            const int b = row < t.nrows ? box[row] : -1;
             if (b >= 0 && g.Y) {   // FP32 rows (alone, or beside split planes for a later gather)
                 float *y = (float *)g.Y + (size_t)b * g.ldy + n_lo;
 #pragma unroll
-                for (int n0 = 0; n0 < kTcMaxN; n0 += 4) {
-                    if (n0 < N) {
+                for (int n0 = 0; n0 < DC; n0 += 4) {
+                    const int col = c0 + n0;
+                    if (col < N) {
                         float4 o = make_float4(g.alpha * acc[n0], g.alpha * acc[n0 + 1], g.alpha * acc[n0 + 2],
                                                g.alpha * acc[n0 + 3]);
                         if (g.accumulate) {
-                            const float4 old = *reinterpret_cast<const float4 *>(y + n0);
+                            const float4 old = *reinterpret_cast<const float4 *>(y + col);
                             o.x += old.x, o.y += old.y, o.z += old.z, o.w += old.w;
                         }
-                        *reinterpret_cast<float4 *>(y + n0) = o;
+                        *reinterpret_cast<float4 *>(y + col) = o;
                     }
                 }
             }
-            if (b >= 0 && p.yp && p.yp_f16) {
-                // FP16 hi/lo planes of the row scaled by a power of two per 64-column chunk, so
-                // that its largest entry is below 2^14 (no overflow, full FP16 precision)
-                float mx[(kTcMaxN + 63) / 64] = {};
+            if (f16p) {
 #pragma unroll
-                for (int n = 0; n < kTcMaxN; ++n)
-                    if (n < N) mx[n / 64] = fmaxf(mx[n / 64], fabsf(g.alpha * acc[n]));
-                float sc[(kTcMaxN + 63) / 64];
-#pragma unroll
-                for (int c = 0; c < (kTcMaxN + 63) / 64; ++c) {
-                    int ex = 0;
-                    frexpf(mx[c], &ex);                        // mx < 2^ex
-                    const int e = min(max(14 - ex, -126), 126);
-                    sc[c] = mx[c] > 0.f ? ldexpf(1.f, e) : 1.f;
-                    if (c * 64 < N)
-                        p.yp_scale[(size_t)b * p.yp_scale_ld + n_lo / 64 + c] = mx[c] > 0.f ? ldexpf(1.f, -e) : 0.f;
+                for (int n = 0; n < DC; ++n) {
+                    const int col = c0 + n, ch = col >> 6;
+                    const float m = col < N ? fabsf(g.alpha * acc[n]) : 0.f;
+                    pm0 = ch == 0 ? fmaxf(pm0, m) : pm0;
+                    pm1 = ch == 1 ? fmaxf(pm1, m) : pm1;
+                    pm2 = ch == 2 ? fmaxf(pm2, m) : pm2;
                 }
+            }
+        }
+        if (PL && f16p) {
+            // a chunk can straddle the two halves of a row: exchange the maxima.  Every drain warp
+            // passes this barrier, also after a failed wait, so none is left waiting.
+            pmax[hf][0][row] = pm0, pmax[hf][1][row] = pm1, pmax[hf][2][row] = pm2;
+            asm volatile("bar.sync 2, 256;" ::: "memory");
+            pm0 = fmaxf(pmax[0][0][row], pmax[1][0][row]);
+            pm1 = fmaxf(pmax[0][1][row], pmax[1][1][row]);
+            pm2 = fmaxf(pmax[0][2][row], pmax[1][2][row]);
+        }
+        if (ok && b >= 0 && f16p) {
+            // FP16 hi/lo planes of the row scaled by a power of two per 64-column chunk, so that
+            // its largest entry is below 2^14 (no overflow, full FP16 precision)
+            float sc[3];
+            const float mxs[3] = {pm0, pm1, pm2};
 #pragma unroll
-                for (int n0 = 0; n0 < kTcMaxN; n0 += 8) {
-                    if (n0 < N) {
-                        const size_t e = (size_t)b * p.yp_ld + n_lo + n0;
-                        uint32_t hw[4], lw[4];
+            for (int c = 0; c < 3; ++c) {
+                int ex = 0;
+                frexpf(mxs[c], &ex);                       // mx < 2^ex
+                const int e = min(max(14 - ex, -126), 126);
+                sc[c] = mxs[c] > 0.f ? ldexpf(1.f, e) : 1.f;
+                // the scale entry is written by the thread holding the chunk's first column
+                if (c * 64 < N && c * 64 >= c0 && c * 64 < c0 + DC)
+                    p.yp_scale[(size_t)b * p.yp_scale_ld + n_lo / 64 + c] = mxs[c] > 0.f ? ldexpf(1.f, -e) : 0.f;
+            }
+#pragma unroll
+            for (int n0 = 0; n0 < DC; n0 += 8) {
+                const int col = c0 + n0;   // 8 columns never straddle a 64-column chunk
+                if (col < N) {
+                    const int ch = col >> 6;
+                    const float s8 = ch == 0 ? sc[0] : ch == 1 ? sc[1] : sc[2];
+                    const size_t e = (size_t)b * p.yp_ld + n_lo + col;
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int i = 0; i < 8; i += 2) {
+                        uint32_t h[2], l[2];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const float x = g.alpha * acc[n0 + i + j] * s8;
+                            const __half hh = __float2half_rn(x);
+                            h[j] = __half_as_ushort(hh);
+                            l[j] = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+                        }
+                        hw[i / 2] = h[0] | (h[1] << 16);
+                        lw[i / 2] = l[0] | (l[1] << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(p.yp + e * 2) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 2) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            }
+        } else if (ok && b >= 0 && p.yp) {
+            // split planes for a later tensor-core gather (BF16 hi/lo[/third] or TF32 big/small)
+#pragma unroll
+            for (int n0 = 0; n0 < DC; n0 += 8) {
+                const int col = c0 + n0;
+                if (col < N) {
+                    const size_t e = (size_t)b * p.yp_ld + n_lo + col;
+                    if (!TF32) {
+                        uint32_t w[3][4];
 #pragma unroll
                         for (int i = 0; i < 8; i += 2) {
-                            uint32_t h[2], l[2];
+                            uint32_t h[2], l[2], m[2];
 #pragma unroll
                             for (int j = 0; j < 2; ++j) {
-                                const float x = g.alpha * acc[n0 + i + j] * sc[(n0 + i + j) / 64];
-                                const __half hh = __float2half_rn(x);
-                                h[j] = __half_as_ushort(hh);
-                                l[j] = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+                                const float x = g.alpha * acc[n0 + i + j];
+                                h[j] = bf16_bits(x);
+                                const float r1 = x - bf16_val(h[j]);
+                                l[j] = bf16_bits(r1);
+                                m[j] = bf16_bits(r1 - bf16_val(l[j]));
                             }
-                            hw[i / 2] = h[0] | (h[1] << 16);
-                            lw[i / 2] = l[0] | (l[1] << 16);
+                            w[0][i / 2] = h[0] | (h[1] << 16);
+                            w[1][i / 2] = l[0] | (l[1] << 16);
+                            w[2][i / 2] = m[0] | (m[1] << 16);
                         }
-                        *reinterpret_cast<uint4 *>(p.yp + e * 2) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 2) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    }
-                }
-            } else if (b >= 0 && p.yp) {
-                // split planes for a later tensor-core gather (BF16 hi/lo[/third] or TF32 big/small)
 #pragma unroll
-                for (int n0 = 0; n0 < kTcMaxN; n0 += 8) {
-                    if (n0 < N) {
-                        const size_t e = (size_t)b * p.yp_ld + n_lo + n0;
-                        if (!TF32) {
-                            uint32_t w[3][4];
+                        for (int pl = 0; pl < 3; ++pl)
+                            if (pl < p.nplanes)
+                                *reinterpret_cast<uint4 *>(p.yp + pl * p.yp_plane + e * 2) =
+                                    make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+                    } else {
+                        uint32_t bb[8], ss[8];
 #pragma unroll
-                            for (int i = 0; i < 8; i += 2) {
-                                uint32_t h[2], l[2], m[2];
-#pragma unroll
-                                for (int j = 0; j < 2; ++j) {
-                                    const float x = g.alpha * acc[n0 + i + j];
-                                    h[j] = bf16_bits(x);
-                                    const float r1 = x - bf16_val(h[j]);
-                                    l[j] = bf16_bits(r1);
-                                    m[j] = bf16_bits(r1 - bf16_val(l[j]));
-                                }
-                                w[0][i / 2] = h[0] | (h[1] << 16);
-                                w[1][i / 2] = l[0] | (l[1] << 16);
-                                w[2][i / 2] = m[0] | (m[1] << 16);
-                            }
-#pragma unroll
-                            for (int pl = 0; pl < 3; ++pl)
-                                if (pl < p.nplanes)
-                                    *reinterpret_cast<uint4 *>(p.yp + pl * p.yp_plane + e * 2) =
-                                        make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
-                        } else {
-                            uint32_t bb[8], ss[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float x = g.alpha * acc[n0 + i];
-                                bb[i] = tf32_round(x);
-                                ss[i] = tf32_round(x - __uint_as_float(bb[i]));
-                            }
-                            uint4 *d0 = reinterpret_cast<uint4 *>(p.yp + e * 4);
-                            uint4 *d1 = reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 4);
-                            d0[0] = make_uint4(bb[0], bb[1], bb[2], bb[3]);
-                            d0[1] = make_uint4(bb[4], bb[5], bb[6], bb[7]);
-                            d1[0] = make_uint4(ss[0], ss[1], ss[2], ss[3]);
-                            d1[1] = make_uint4(ss[4], ss[5], ss[6], ss[7]);
+                        for (int i = 0; i < 8; ++i) {
+                            const float x = g.alpha * acc[n0 + i];
+                            bb[i] = tf32_round(x);
+                            ss[i] = tf32_round(x - __uint_as_float(bb[i]));
                         }
+                        uint4 *d0 = reinterpret_cast<uint4 *>(p.yp + e * 4);
+                        uint4 *d1 = reinterpret_cast<uint4 *>(p.yp + p.yp_plane + e * 4);
+                        d0[0] = make_uint4(bb[0], bb[1], bb[2], bb[3]);
+                        d0[1] = make_uint4(bb[4], bb[5], bb[6], bb[7]);
+                        d1[0] = make_uint4(ss[0], ss[1], ss[2], ss[3]);
+                        d1[1] = make_uint4(ss[4], ss[5], ss[6], ss[7]);
                     }
                 }
             }
@@ -861,6 +911,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         tc_fence_after();
         tmem_dealloc(tmem, p.tmem_cols);
     }
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_constant__ TcDev p) {
+    tc_body<TF32, false>(p);
+}
+
+// Plane layout: capped at 120 registers a thread (46K for the CTA), so that near-field CTAs fit
+// beside it on an SM.
+template <bool TF32>
+__global__ void __maxnreg__(120) gemm_tc_plane_kernel(const __grid_constant__ TcDev p) {
+    tc_body<TF32, true>(p);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1155,12 +1217,16 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         nsplit = (c.n_out + 127) / 128;
     }
     const int stage_bytes = p.nplanes * (kTcRows + p.ncta) * kAtomBytes;
-    // 227 KB per CTA in all: the stages, 1 KB of alignment slack and the static shared memory
-    auto kern = p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
+    // 227 KB per CTA in all: the stages, 1 KB of alignment slack and the static shared memory.
+    // The plane layout keeps two stages, which leaves room on the SM for near-field CTAs.
+    const bool plane = c.Xp != nullptr;
+    auto kern = plane ? (p.tf32 ? gemm_tc_plane_kernel<true> : gemm_tc_plane_kernel<false>)
+                      : (p.tf32 ? gemm_tc_kernel<true> : gemm_tc_kernel<false>);
+    const int threads = plane ? 384 : kTcThreads;
     cudaFuncAttributes fa{};
     FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
     const int budget = 227 * 1024 - 1024 - (int)fa.sharedSizeBytes;
-    p.nstages = std::min(4, budget / stage_bytes);
+    p.nstages = std::min(plane ? kPlaneStages : 4, budget / stage_bytes);
     if (p.nstages < 2) return cudaErrorInvalidValue;
     // two accumulators of ncta columns; the drain reads 32 columns at a time, so the last read
     // of the second accumulator may extend 16 columns past it: keep that inside the allocation
@@ -1192,7 +1258,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     }
     const size_t smem = (size_t)p.nstages * stage_bytes + 1024;
     FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<dim3(ts.ntiles, (c.n_out + p.ncta - 1) / p.ncta), kTcThreads, smem, s>>>(p);
+    kern<<<dim3(ts.ntiles, (c.n_out + p.ncta - 1) / p.ncta), threads, smem, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }
