@@ -3,10 +3,12 @@
  *
  * One routine: for every target group g, for every target i of that group and every source j
  * in the group's source ranges, add K(x_i, y_j) s_j to f_i, where K is the 3D Laplace kernel
- * 1/(4 pi |x - y|) (Eq. 2, normalised by 4 pi), i.e. Eq. 1 restricted to the given pairs.
- * Pairs with |x_i - y_j| == 0 exactly are skipped: that excludes self-interaction and
+ * 1/(4 pi |x - y|) (Eq. 2, normalised by 4 pi) or, with kappa > 0, the modified Helmholtz
+ * (Yukawa) kernel exp(-kappa |x - y|) / (4 pi |x - y|), i.e. Eq. 1 restricted to the given
+ * pairs.  Pairs with |x_i - y_j| == 0 exactly are skipped: that excludes self-interaction and
  * coincident points.  With `grad` non-NULL the gradient with respect to the target position,
- * -sum_j s_j (x_i - y_j) / (4 pi |x_i - y_j|^3), is accumulated as well.
+ * -sum_j s_j (1 + kappa r) exp(-kappa r) (x_i - y_j) / (4 pi r^3), r = |x_i - y_j|, is
+ * accumulated as well.
  *
  * This is a plain double loop with no blocking; OpenMP only splits the groups between threads.
  */
@@ -23,7 +25,8 @@ void oracle_grouped_sum(int64_t n_groups,
                         const double *sx,          /* [n_sources*3] source coordinates */
                         const double *sq,          /* [n_sources] source densities */
                         double *pot,               /* [n_targets], accumulated */
-                        double *grad)              /* [n_targets*3] or NULL, accumulated */
+                        double *grad,              /* [n_targets*3] or NULL, accumulated */
+                        double kappa)              /* 0: Laplace; > 0: Yukawa decay rate */
 {
     int64_t g;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -39,10 +42,12 @@ void oracle_grouped_sum(int64_t n_groups,
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 == 0.0) continue;
                     const double rinv = 1.0 / sqrt(r2);
-                    const double w = sq[j] * rinv;
+                    const double r = r2 * rinv;
+                    const double e = kappa > 0.0 ? exp(-kappa * r) : 1.0;
+                    const double w = sq[j] * rinv * e;
                     f += w;
                     if (grad) {
-                        const double w3 = w * rinv * rinv;
+                        const double w3 = w * (1.0 + kappa * r) * rinv * rinv;
                         gx -= w3 * dx;
                         gy -= w3 * dy;
                         gz -= w3 * dz;

@@ -1,6 +1,8 @@
 """FP64 direct evaluation of the field sum (Eq. 1) with the 3D Laplace kernel (Eq. 2).
 
-The kernel is normalised as K(x, y) = 1 / (4 pi |x - y|).  The paper writes 1/|x - y|; the
+The kernel is normalised as K(x, y) = 1 / (4 pi |x - y|); with `kappa` > 0 it is the modified
+Helmholtz (Yukawa) kernel exp(-kappa |x - y|) / (4 pi |x - y|), the second kernel the
+kernel-independent method is run with.  The paper writes 1/|x - y|; the
 factor only scales every result, so relative errors are unaffected.  Pairs at distance exactly
 zero are skipped (self-interaction and coincident points).
 
@@ -26,7 +28,7 @@ def _native():
     if _lib is None:
         lib = ctypes.CDLL(_build.build())
         p = ctypes.c_void_p
-        lib.oracle_grouped_sum.argtypes = [ctypes.c_int64, p, p, p, p, p, p, p, p]
+        lib.oracle_grouped_sum.argtypes = [ctypes.c_int64, p, p, p, p, p, p, p, p, ctypes.c_double]
         lib.oracle_grouped_sum.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -42,7 +44,7 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 
 
-def direct_numpy(targets, sources, charges, gradient=True, chunk=2048):
+def direct_numpy(targets, sources, charges, gradient=True, chunk=2048, kappa=0.0):
     """phi_i = sum_j K(x_i, y_j) s_j and its gradient, by dense broadcasting (FP64)."""
     x = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
     y = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
@@ -54,15 +56,16 @@ def direct_numpy(targets, sources, charges, gradient=True, chunk=2048):
         r2 = np.einsum("ijk,ijk->ij", d, d)
         with np.errstate(divide="ignore"):
             rinv = np.where(r2 > 0.0, 1.0 / np.sqrt(np.where(r2 > 0.0, r2, 1.0)), 0.0)
-        w = rinv * s[None, :]
+        r = r2 * rinv
+        w = rinv * np.exp(-kappa * r) * s[None, :]
         pot[a:a + chunk] = w.sum(axis=1) * INV4PI
         if gradient:
-            w3 = w * rinv * rinv
+            w3 = w * (1.0 + kappa * r) * rinv * rinv
             grad[a:a + chunk] = -np.einsum("ij,ijk->ik", w3, d) * INV4PI
     return pot, grad
 
 
-def grouped_sum(t_off, tx, r_off, ranges, sx, sq, gradient=True, pot=None, grad=None):
+def grouped_sum(t_off, tx, r_off, ranges, sx, sq, gradient=True, pot=None, grad=None, kappa=0.0):
     """Accumulate kernel sums over (target group, source ranges) with the C helper (FP64).
 
     t_off[g]:t_off[g+1] are the targets of group g; ranges[r_off[g]:r_off[g+1]] are its
@@ -84,19 +87,20 @@ def grouped_sum(t_off, tx, r_off, ranges, sx, sq, gradient=True, pot=None, grad=
     if gradient:
         assert grad.dtype == np.float64 and grad.flags.c_contiguous
     _native().oracle_grouped_sum(n_groups, _ptr(t_off), _ptr(tx), _ptr(r_off), _ptr(ranges),
-                                 _ptr(sx), _ptr(sq), _ptr(pot), _ptr(grad) if gradient else None)
+                                 _ptr(sx), _ptr(sq), _ptr(pot), _ptr(grad) if gradient else None,
+                                 float(kappa))
     return pot, (grad if gradient else None)
 
 
-def direct_c(targets, sources, charges, gradient=True):
+def direct_c(targets, sources, charges, gradient=True, kappa=0.0):
     """Eq. 1 at the given targets from all sources, with the C helper (FP64)."""
     tx = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
     n_s = len(np.asarray(sources).reshape(-1, 3))
-    return grouped_sum([0, len(tx)], tx, [0, 1], [[0, n_s]], sources, charges, gradient)
+    return grouped_sum([0, len(tx)], tx, [0, 1], [[0, n_s]], sources, charges, gradient, kappa=kappa)
 
 
-def direct_self(points, charges, gradient=True, sample=None):
+def direct_self(points, charges, gradient=True, sample=None, kappa=0.0):
     """Field at the points themselves (targets = sources), optionally only at `sample` indices."""
     x = np.asarray(points, dtype=np.float64).reshape(-1, 3)
     t = x if sample is None else x[np.asarray(sample)]
-    return direct_c(t, x, charges, gradient)
+    return direct_c(t, x, charges, gradient, kappa=kappa)

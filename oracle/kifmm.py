@@ -26,6 +26,11 @@ transfer vector share one operator (Section 2.2); `m2l="pairwise"` instead build
 pair's matrix from the two boxes' own coordinates (slow; used to pin the grouped form).
 The M2L is not compressed here, so the GPU path's SVD truncation error is inside the budget.
 
+With `kappa` > 0 every K above is the modified Helmholtz (Yukawa) kernel
+exp(-kappa r) / (4 pi r), a real kernel admitted by Eq. 1; the steps are unchanged, which is what
+makes the method kernel-independent (Section 2.1).  That kernel is not homogeneous, so its
+operators of different levels are not rescalings of one another.
+
 The pseudo-inverse truncates singular values below rtol * sigma_max (the paper is silent on
 regularisation).
 """
@@ -61,14 +66,15 @@ def surface(p, centre, halfwidth, alpha):
     return np.asarray(centre, dtype=np.float64).reshape(1, 3) + alpha * halfwidth * surface_grid(p)
 
 
-def kernel_matrix(x, y):
-    """K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised), zero where |x_i - y_j| = 0."""
+def kernel_matrix(x, y, kappa=0.0):
+    """K(x_i, y_j) = exp(-kappa r) / (4 pi r), r = |x_i - y_j| (kappa = 0: Eq. 2 normalised;
+    kappa > 0: the modified Helmholtz kernel), zero where r = 0."""
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     y = np.asarray(y, dtype=np.float64).reshape(-1, 3)
     d = x[:, None, :] - y[None, :, :]
     r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
     with np.errstate(divide="ignore"):
-        return np.where(r > 0.0, INV4PI / np.where(r > 0.0, r, 1.0), 0.0)
+        return np.where(r > 0.0, INV4PI * np.exp(-kappa * r) / np.where(r > 0.0, r, 1.0), 0.0)
 
 
 def pinv(a, rtol):
@@ -88,6 +94,7 @@ class Operators:
     m2m: dict         # (parent level, octant) -> K(uc_P, ue_child)
     l2l: dict         # (child level, octant) -> K(dc_child, de_P)
     m2l: dict         # (level, t) -> K(dc_b, ue_{b + t})
+    kappa: float = 0.0  # kernel: 0 Laplace, > 0 modified Helmholtz exp(-kappa r) / (4 pi r)
 
 
 def child_offset(c):
@@ -95,29 +102,30 @@ def child_offset(c):
     return np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1], dtype=np.float64)
 
 
-def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None):
+def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None, kappa=0.0):
     tv = otree.transfer_vectors()
-    ops = Operators(p, {}, {}, {}, {}, {})
+    ops = Operators(p, {}, {}, {}, {}, {}, kappa)
+    km = lambda a, b: kernel_matrix(a, b, kappa)
     zero = np.zeros(3)
     for level in range(0, depth + 1):
         r = side / 2.0 ** (level + 1)
-        ops.uc2e[level] = pinv(kernel_matrix(surface(p, zero, r, ALPHA_OUTER),
+        ops.uc2e[level] = pinv(km(surface(p, zero, r, ALPHA_OUTER),
                                              surface(p, zero, r, ALPHA_INNER)), rtol)
-        ops.dc2e[level] = pinv(kernel_matrix(surface(p, zero, r, ALPHA_INNER),
+        ops.dc2e[level] = pinv(km(surface(p, zero, r, ALPHA_INNER),
                                              surface(p, zero, r, ALPHA_OUTER)), rtol)
     for level in range(0, depth):
         r_p, r_c = side / 2.0 ** (level + 1), side / 2.0 ** (level + 2)
         for c in range(8):
             cc = (2.0 * child_offset(c) - 1.0) * r_c          # child centre relative to parent
-            ops.m2m[(level, c)] = kernel_matrix(surface(p, zero, r_p, ALPHA_OUTER),
+            ops.m2m[(level, c)] = km(surface(p, zero, r_p, ALPHA_OUTER),
                                                 surface(p, cc, r_c, ALPHA_INNER))
-            ops.l2l[(level + 1, c)] = kernel_matrix(surface(p, cc, r_c, ALPHA_INNER),
+            ops.l2l[(level + 1, c)] = km(surface(p, cc, r_c, ALPHA_INNER),
                                                     surface(p, zero, r_p, ALPHA_OUTER))
     for level in (range(2, depth + 1) if m2l_levels is None else m2l_levels):
         r = side / 2.0 ** (level + 1)
         tgt = surface(p, zero, r, ALPHA_INNER)
         for t, delta in enumerate(tv):
-            ops.m2l[(level, t)] = kernel_matrix(tgt, surface(p, 2.0 * r * delta, r, ALPHA_INNER))
+            ops.m2l[(level, t)] = km(tgt, surface(p, 2.0 * r * delta, r, ALPHA_INNER))
     return ops
 
 
@@ -150,7 +158,7 @@ def upward(tr, xs, qs, ops, chunk=65536):
         t_off = np.arange(len(leaves) + 1, dtype=np.int64) * ns
         ranges = np.stack([tr.leaf_offsets[leaves], tr.leaf_offsets[leaves + 1]], axis=1)
         q_uc, _ = direct.grouped_sum(t_off, chk, np.arange(len(leaves) + 1), ranges, xs, qs,
-                                     gradient=False)
+                                     gradient=False, kappa=ops.kappa)
         u[d][leaves] = q_uc.reshape(len(leaves), ns) @ ops.uc2e[d].T
     for level in range(d - 1, 1, -1):
         ch = tr.children(level)
@@ -192,7 +200,7 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
             for k in range(len(idx)):
                 b, a = boxes[rows[k]], idx[k]
                 kmat = kernel_matrix(surface(p, ctr[b], r, ALPHA_INNER),
-                                     surface(p, ctr[a], r, ALPHA_INNER))
+                                     surface(p, ctr[a], r, ALPHA_INNER), ops.kappa)
                 q_dc[rows[k]] += kmat @ u[level][a]
         if level >= 3:
             par = tr.parent(level)[boxes]
@@ -208,7 +216,7 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
 
 def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
              pinv_rtol=DEFAULT_PINV_RTOL, sample=None, parts=("near", "far"), m2l="grouped",
-             ops=None):
+             ops=None, kappa=0.0):
     """FP64 kiFMM field at every point (or at the `sample` indices, input order).
 
     Returns a Result whose phi/grad follow the input order of the points (or of `sample`).
@@ -229,7 +237,8 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
     leaf_of = np.searchsorted(tr.leaf_offsets, tpos, side="right") - 1
     leaves = np.unique(leaf_of)
     if ops is None:
-        ops = build_operators(p, tr.side, depth, pinv_rtol)
+        ops = build_operators(p, tr.side, depth, pinv_rtol, kappa=kappa)
+    kappa = ops.kappa
     phi_s = np.zeros(n)
     grad_s = np.zeros((n, 3)) if gradient else None
     u, dvec, need = {}, {}, {}
@@ -250,11 +259,11 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
         ns = n_surface(p)
         ranges = np.stack([np.arange(len(leaves)) * ns, np.arange(1, len(leaves) + 1) * ns], 1)
         direct.grouped_sum(grp_off, tx, np.arange(len(leaves) + 1), ranges, de, dens,
-                           gradient, pot, grd)
+                           gradient, pot, grd, kappa=kappa)
     if "near" in parts:
         uoff, uidx = otree.u_lists(tr, leaves)
         ranges = np.stack([tr.leaf_offsets[uidx], tr.leaf_offsets[uidx + 1]], axis=1)
-        direct.grouped_sum(grp_off, tx, uoff, ranges, xs, qs, gradient, pot, grd)
+        direct.grouped_sum(grp_off, tx, uoff, ranges, xs, qs, gradient, pot, grd, kappa=kappa)
     phi_s[tsort] = pot
     if gradient:
         grad_s[tsort] = grd
@@ -272,7 +281,7 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
 
 
 def adjoint(points, g, p, depth, origin=None, side=None, pinv_rtol=DEFAULT_PINV_RTOL,
-            parts=("near", "far"), ops=None):
+            parts=("near", "far"), ops=None, kappa=0.0):
     """psi = A^T g for the FP64 kiFMM map A (charges -> potentials), input order.
 
     The transposed steps run in reverse order of Algorithm 1: D2T^T, the closing pinv^T,
@@ -286,7 +295,8 @@ def adjoint(points, g, p, depth, origin=None, side=None, pinv_rtol=DEFAULT_PINV_
     gs = g_in[tr.perm]
     n = len(xs)
     if ops is None:
-        ops = build_operators(p, tr.side, depth, pinv_rtol)
+        ops = build_operators(p, tr.side, depth, pinv_rtol, kappa=kappa)
+    kappa = ops.kappa
     ns = n_surface(p)
     nl = len(tr.leaf_keys)
     psi = np.zeros(n)
@@ -296,7 +306,7 @@ def adjoint(points, g, p, depth, origin=None, side=None, pinv_rtol=DEFAULT_PINV_
         de = _leaf_surface_points(tr, p, leaves, ALPHA_OUTER)
         ranges = np.stack([tr.leaf_offsets[:-1], tr.leaf_offsets[1:]], axis=1)
         dbar, _ = direct.grouped_sum(np.arange(nl + 1) * ns, de, np.arange(nl + 1), ranges,
-                                     xs, gs, gradient=False)
+                                     xs, gs, gradient=False, kappa=kappa)
         dbar = {depth: dbar.reshape(nl, ns)}
         ubar = {lvl: np.zeros((len(tr.level_keys[lvl]), ns)) for lvl in range(2, depth + 1)}
         for level in range(depth, 1, -1):
@@ -324,11 +334,11 @@ def adjoint(points, g, p, depth, origin=None, side=None, pinv_rtol=DEFAULT_PINV_
         uc = _leaf_surface_points(tr, p, leaves, ALPHA_OUTER)
         ranges = np.stack([np.arange(nl) * ns, np.arange(1, nl + 1) * ns], axis=1)
         direct.grouped_sum(tr.leaf_offsets, xs, np.arange(nl + 1), ranges, uc,
-                           ebar.reshape(-1), False, psi, None)
+                           ebar.reshape(-1), False, psi, None, kappa=kappa)
     if "near" in parts:
         uoff, uidx = otree.u_lists(tr, leaves)
         ranges = np.stack([tr.leaf_offsets[uidx], tr.leaf_offsets[uidx + 1]], axis=1)
-        direct.grouped_sum(tr.leaf_offsets, xs, uoff, ranges, xs, gs, False, psi, None)
+        direct.grouped_sum(tr.leaf_offsets, xs, uoff, ranges, xs, gs, False, psi, None, kappa=kappa)
     out = np.empty(n)
     out[tr.perm] = psi
     return out
