@@ -1,7 +1,9 @@
 /*
  * fmm.h - C ABI of libfmm: a kernel-independent fast multipole method (kiFMM) for the 3D
  * Laplace kernel K(x, y) = 1 / (4 pi |x - y|) over a Morton-keyed uniform octree, evaluated on
- * one NVIDIA GB300 (sm_103a).
+ * one NVIDIA GB300 (sm_103a).  The same steps also run with the modified Helmholtz (Yukawa)
+ * kernel K(x, y) = exp(-kappa |x - y|) / (4 pi |x - y|) (option `kernel`), a second real kernel
+ * of Eq. 1 that the kernel-independent method of Section 2.1 takes without change.
  *
  * What is computed (the paper's problem statement, Section 1, Eq. 1 with the kernel of Eq. 2
  * normalised by 4 pi): for N points x_i that are both sources and targets, given in arbitrary
@@ -61,6 +63,12 @@ typedef enum {
                               products, about 2^-22 relative per term, scales applied in FP32 */
 } fmm_precision;
 
+/* Kernel of Eq. 1 (option `kernel`). */
+typedef enum {
+    FMM_LAPLACE = 0,       /* 1 / (4 pi r) (Eq. 2, normalised by 4 pi) */
+    FMM_YUKAWA = 1         /* exp(-kappa r) / (4 pi r), kappa > 0; gradient -(1 + kappa r) exp(-kappa r) d / (4 pi r^3) */
+} fmm_kernel;
+
 typedef struct {
     int order_p;           /* expansion order p >= 2; each box vector has 6(p-1)^2+2 entries
                               (Section 4, global portion).  Supported: 2..10. */
@@ -81,6 +89,13 @@ typedef struct {
                               constant, where the textbook operators reproduce it only up to their
                               fit error, so results differ from the textbook kiFMM by about that
                               error (1e-7 relative at p >= 6, 1e-4 at p = 4).  Default 0. */
+    int kernel;            /* an fmm_kernel value.  Default FMM_LAPLACE.  FMM_YUKAWA needs has_domain:
+                              the kernel is not homogeneous, so its operators depend on the physical
+                              box sizes and are built per level by fmm_precompute from `side`
+                              (fmm_create returns FMM_EUNSUPPORTED without a domain, and with
+                              mean_free, whose constant-potential argument holds for Laplace only). */
+    double kappa;          /* FMM_YUKAWA: screening constant, finite and > 0, in inverse units of the
+                              coordinates.  Ignored for FMM_LAPLACE. */
 } fmm_options;
 
 /* Part selectors for fmm_evaluate_parts (Section 1, Eq. 3: near field + far field). */

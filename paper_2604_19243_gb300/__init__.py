@@ -1,4 +1,5 @@
-"""Python binding of libfmm, a GB300 (sm_103a) kernel-independent FMM for the 3D Laplace kernel.
+"""Python binding of libfmm, a GB300 (sm_103a) kernel-independent FMM for the 3D Laplace kernel
+(and the modified Helmholtz kernel exp(-kappa r) / (4 pi r), `kernel="yukawa"`).
 
 Argument marshalling only: every step of the FMM runs in the CUDA library behind the C ABI of
 include/fmm.h.  Importing this package does not build anything; call
@@ -24,6 +25,7 @@ PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp16
 STATUS = {0: "FMM_OK", 1: "FMM_EINVAL", 2: "FMM_ENOMEM", 3: "FMM_ECUDA", 4: "FMM_ESTATE",
           5: "FMM_ETIMEOUT", 6: "FMM_EUNSUPPORTED"}
 PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
+KERNELS = {"laplace": 0, "yukawa": 1}
 
 # C entry points declared in include/fmm.h (checked by the export test)
 ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
@@ -38,7 +40,7 @@ class Options(ctypes.Structure):
                 ("svd_rtol", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("with_gradient", ctypes.c_int), ("has_domain", ctypes.c_int),
                 ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
-                ("mean_free", ctypes.c_int)]
+                ("mean_free", ctypes.c_int), ("kernel", ctypes.c_int), ("kappa", ctypes.c_double)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -127,7 +129,8 @@ class FMM:
     """One FMM context: a tree over a point set and the operators of one expansion order."""
 
     def __init__(self, p=6, depth=4, precision="fp32", svd_rtol=1e-6, pinv_rtol=1e-7,
-                 with_gradient=True, domain=None, stream=None, mean_free=False):
+                 with_gradient=True, domain=None, stream=None, mean_free=False, kernel="laplace",
+                 kappa=0.0):
         L = lib()
         opt = Options()
         L.fmm_default_options(ctypes.byref(opt))
@@ -136,6 +139,8 @@ class FMM:
         opt.svd_rtol, opt.pinv_rtol = svd_rtol, pinv_rtol
         opt.with_gradient = int(with_gradient)
         opt.mean_free = int(mean_free)
+        opt.kernel = KERNELS[kernel]
+        opt.kappa = float(kappa)
         if domain is not None:
             opt.has_domain = 1
             for a in range(3):
@@ -152,6 +157,7 @@ class FMM:
         if st != 0:
             raise FmmError(st, "fmm_create rejected the options")
         self.p, self.depth, self.precision = p, depth, precision
+        self.kernel, self.kappa = kernel, float(kappa)
         self.dtype = np.float64 if precision == "fp64" else np.float32
         self.n = 0
 

@@ -2,6 +2,7 @@
 // order of the evaluation steps.  No C++ exception crosses this boundary.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -131,8 +132,11 @@ void free_ops(fmm_ctx *ctx) {
     for (void *p : ctx->op_allocs) cudaFree(p);
     ctx->op_allocs.clear();
     tc_free(ctx);
-    ctx->fwd = OpSet{};
-    ctx->adj = OpSet{};
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        ctx->fwd[l] = OpSet{};
+        ctx->adj[l] = OpSet{};
+        ctx->host_ops[l] = nullptr;
+    }
     ctx->grid_dev = nullptr;
     ctx->have_ops = false;
 }
@@ -155,7 +159,8 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     const size_t es = elem_size(ctx);
     const int nsp = ctx->nsp;
-    const int kw = std::max(std::max(ctx->fwd.kinp, ctx->fwd.koutp), 16);
+    const OpSet &o = ctx->fwd[ctx->opt.depth];   // every level has the same shapes
+    const int kw = std::max(std::max(o.kinp, o.koutp), 16);
     ctx->ws_kw = kw;
     const int64_t rows = need_rows, nl = need_nl, n = need_n;
     struct A {
@@ -166,7 +171,7 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         // tensor-core modes hand the compressed vectors over as split planes (UtP) instead
         {&ctx->Ut, ctx->tensor ? (size_t)16 : (size_t)rows * kw * es},
         {&ctx->Ct, (size_t)rows * kw * es},
-        {&ctx->Yc, (size_t)nl * ctx->fwd.rclp * es},
+        {&ctx->Yc, (size_t)nl * o.rclp * es},
         {&ctx->Dq, (size_t)nl * nsp * es},     {&ctx->Cmean, (size_t)rows * sizeof(double)},
         {&ctx->near_phi, (size_t)n * es},
         {&ctx->near_grad, (size_t)n * 3 * es}, {&ctx->far_phi, (size_t)n * es},
@@ -345,6 +350,13 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
         return FMM_EINVAL;
     // the FP16 planes of FMM_FP16X3 carry the downward rows as produced, before a mean is taken off
     if (opt->mean_free && opt->precision == FMM_FP16X3) return FMM_EUNSUPPORTED;
+    if (opt->kernel != FMM_LAPLACE && opt->kernel != FMM_YUKAWA) return FMM_EINVAL;
+    if (opt->kernel == FMM_YUKAWA) {
+        if (!(std::isfinite(opt->kappa) && opt->kappa > 0)) return FMM_EINVAL;
+        // the operators depend on the physical box sizes (no homogeneity), and the means that
+        // mean_free carries down the tree are exact for Laplace only
+        if (!opt->has_domain || opt->mean_free) return FMM_EUNSUPPORTED;
+    }
     if (opt->has_domain) {
         if (!(std::isfinite(opt->side) && opt->side > 0)) return FMM_EINVAL;
         for (int a = 0; a < 3; ++a)
@@ -427,16 +439,27 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     if (ctx->have_ops) return FMM_OK;
     std::string err;
-    const HostOps *h = nullptr;
+    // Laplace: one set for every level.  Modified Helmholtz: one per level that a step uses
+    // (2..d, or d alone for d < 2: U2U, VLI and D2D run on levels >= 2, the closing on d), with
+    // kappa in units of that level's half-width side / 2^(l+1); the other levels alias the
+    // coarsest built one and are never read.
+    const int d = ctx->opt.depth;
+    const int lo = ctx->opt.kernel == FMM_YUKAWA ? (d < 2 ? d : 2) : 0;
+    std::vector<double> ku;
+    for (int l = lo; l <= d; ++l)
+        ku.push_back(ctx->opt.kernel == FMM_YUKAWA ? ctx->opt.kappa * std::ldexp(ctx->opt.side, -(l + 1)) : 0.0);
+    if (ctx->opt.kernel == FMM_LAPLACE) ku.resize(1);
+    std::vector<const HostOps *> hs;
     try {
-        h = host_operators(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, &err);
+        hs = host_operator_levels(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, ku, &err);
     } catch (const std::bad_alloc &) {
         return fail(ctx, FMM_ENOMEM, "host memory exhausted in precompute");
     } catch (...) {
         return fail(ctx, FMM_EINVAL, "precompute failed");
     }
-    if (!h) return fail(ctx, FMM_EINVAL, "precompute failed: " + err);
-    ctx->host_ops = const_cast<HostOps *>(h);
+    if (hs.size() != ku.size()) return fail(ctx, FMM_EINVAL, "precompute failed: " + err);
+    for (int l = 0; l <= kMaxDepth; ++l)
+        ctx->host_ops[l] = ctx->opt.kernel == FMM_LAPLACE ? hs[0] : hs[std::min(std::max(l, lo), d) - lo];
     cudaError_t e;
     if (!ctx->dev_flag) {
         if (cudaMalloc((void **)&ctx->dev_flag, sizeof(int)) != cudaSuccess) {
@@ -507,8 +530,8 @@ fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
     info->n_points = ctx->n;
     info->depth = ctx->opt.depth;
     info->n_surface = ctx->ns;
-    info->m2l_rank_in = ctx->have_ops ? ctx->fwd.kin : 0;
-    info->m2l_rank_out = ctx->have_ops ? ctx->fwd.kout : 0;
+    info->m2l_rank_in = ctx->have_ops ? ctx->fwd[ctx->opt.depth].kin : 0;
+    info->m2l_rank_out = ctx->have_ops ? ctx->fwd[ctx->opt.depth].kout : 0;
     for (int l = 0; l <= ctx->opt.depth; ++l) info->n_boxes[l] = ctx->lev[l].n;
     info->n_u_entries = ctx->n_u;
     info->p2p_pairs = ctx->p2p_pairs;

@@ -88,8 +88,10 @@ T *rows_at(void *base, const fmm_ctx *ctx, int level, int ld) {
 
 template <typename T>
 cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
-    const OpSet &o = adjoint ? ctx->adj : ctx->fwd;
     const int d = ctx->opt.depth;
+    // operators of level l (one set for Laplace; per level for the modified Helmholtz kernel)
+    auto O = [&](int l) -> const OpSet & { return adjoint ? ctx->adj[l] : ctx->fwd[l]; };
+    const OpSet &o = O(d);   // shapes, and the leaf closing
     const int nsp = ctx->nsp;
     const int kw = ctx->ws_kw;   // row stride of Ut / Ct
     void *A = adjoint ? ctx->Dc : ctx->Uc;   // upward-side array of this direction
@@ -135,7 +137,7 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         GemmCall c;
         c.mode = GM_CHILDREN, c.level = l, c.n_out = nsp;
         c.X0 = rows_at<T>(A, ctx, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
-        c.W0 = o.up[0], c.w_stride = (int64_t)nsp * nsp;
+        c.W0 = O(l).up[0], c.w_stride = (int64_t)nsp * nsp;
         c.Y = rows_at<T>(A, ctx, l, nsp), c.ldy = nsp;
         if (f16) {
             c.Xp = upP(l + 1), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l + 1), c.xp_scale_ld = nck_s;
@@ -156,7 +158,7 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
         GemmCall c;
         c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
-        c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
+        c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = O(l).compress;
         c.Y = ctx->tensor ? nullptr : rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;   // tensor modes: planes only
         unsigned char *planes = nullptr;
         float *scales = ctx->Uscale ? ctx->Uscale + base(l) * nck_k : nullptr;
@@ -170,7 +172,7 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         GemmCall st;
         st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
         st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
-        st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
+        st.W0 = O(l).stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
         st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
         if (ctx->tensor) {
             st.Xp = planes, st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
@@ -189,10 +191,10 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         if (l == d) cudaEventRecord(ctx->ev[4], s);
         GemmCall c;
         c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
-        c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = o.decompress;
-        if (l >= 3) {
+        c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = O(l).decompress;
+        if (l >= 3) {   // D2D from the parent level: that level's operators
             c.X1 = rows_at<T>(B, ctx, l - 1, nsp), c.ldx1 = nsp, c.k1 = nsp;
-            c.W1_by_cls = o.down;
+            c.W1_by_cls = O(l - 1).down;
         }
         c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
         if (f16) {
@@ -290,13 +292,24 @@ cudaError_t upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, OpSet &o) {
 }  // namespace
 
 cudaError_t upload_operators(fmm_ctx *ctx) {
-    const HostOps &h = *ctx->host_ops;
-    if (ctx->fp64) {
-        FMM_CUDA_TRY(upload_set<double>(ctx, h, false, ctx->fwd));
-        FMM_CUDA_TRY(upload_set<double>(ctx, h, true, ctx->adj));
-    } else {
-        FMM_CUDA_TRY(upload_set<float>(ctx, h, false, ctx->fwd));
-        FMM_CUDA_TRY(upload_set<float>(ctx, h, true, ctx->adj));
+    // every distinct host set once; levels sharing a set share its device copy
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        int first = -1;
+        for (int k = 0; k < l && first < 0; ++k)
+            if (ctx->host_ops[k] == ctx->host_ops[l]) first = k;
+        if (first >= 0) {
+            ctx->fwd[l] = ctx->fwd[first];
+            ctx->adj[l] = ctx->adj[first];
+            continue;
+        }
+        const HostOps &h = *ctx->host_ops[l];
+        if (ctx->fp64) {
+            FMM_CUDA_TRY(upload_set<double>(ctx, h, false, ctx->fwd[l]));
+            FMM_CUDA_TRY(upload_set<double>(ctx, h, true, ctx->adj[l]));
+        } else {
+            FMM_CUDA_TRY(upload_set<float>(ctx, h, false, ctx->fwd[l]));
+            FMM_CUDA_TRY(upload_set<float>(ctx, h, true, ctx->adj[l]));
+        }
     }
     if (ctx->tensor) FMM_CUDA_TRY(tc_upload_operators(ctx));
     // unit surface grid in the storage type

@@ -10,8 +10,10 @@
 //   VLI  D_b += sum_{a in V(b)} T_t U_a,  T_t = K(dc_b, ue_a) pinv(K(uc_a, ue_a)) ~ Uo C_t Vi^T
 //   D2D  D_c += B_c D_P,              B_c = K(dc_c, de_P) pinv(K(dc_P, de_P))
 //   D2T  d_b  = pinv(K(dc_b, de_b)) D_b  (factored: (V S^-1)(U^T D_b)), f += K(x, de_b) d_b
-// All of these are level-invariant in units of the box half-width (K is homogeneous of degree
-// -1); only the leaf closing carries the factor r_leaf.
+// For Laplace all of these are level-invariant in units of the box half-width (K is homogeneous
+// of degree -1); only the leaf closing carries the factor r_leaf.  The modified Helmholtz kernel
+// at half-width r is (1/r) times the unit-box kernel with kappa r, so it has one operator set per
+// level (kappa r_l), with the same M2L ranks on every level, and the same r_leaf closing factor.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -170,9 +172,12 @@ struct fmm_ctx {
 
     // operators
     bool have_ops = false;
-    fmm::HostOps *host_ops = nullptr;
-    fmm::OpSet fwd, adj;
-    fmm::TcOpSet *tc_fwd = nullptr, *tc_adj = nullptr;
+    // one set per level (Laplace: every entry the same set; levels that no step uses alias a
+    // used one); uniform shapes across levels
+    const fmm::HostOps *host_ops[fmm::kMaxDepth + 1] = {};
+    fmm::OpSet fwd[fmm::kMaxDepth + 1], adj[fmm::kMaxDepth + 1];
+    fmm::TcOpSet *tc_fwd[fmm::kMaxDepth + 1] = {}, *tc_adj[fmm::kMaxDepth + 1] = {};
+    std::vector<fmm::TcOpSet *> tc_owned;
     std::vector<void *> op_allocs;
 
     bool last_adjoint = false;  // what the last evaluation left in the workspaces
@@ -198,6 +203,7 @@ long long launches();
 // ---- precompute.cpp ----
 struct HostOps {
     int p = 0, ns = 0;
+    double kappa_u = 0;                               // kernel's kappa in units of the half-width
     int kin = 0, kout = 0, rcl = 0;
     std::vector<double> surf_inner, surf_outer;       // [ns x 3] unit grids scaled by alpha
     std::vector<double> up[8], down[8];               // [ns x ns]
@@ -211,6 +217,10 @@ struct HostOps {
 };
 // Build (or fetch from the process-wide cache) the FP64 operators for (p, pinv_rtol, svd_rtol).
 const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err);
+// One operator set per entry of kappa_u (the kernel's kappa times a level's half-width; 0 =
+// Laplace), all with the M2L ranks of the entry that needs the largest; cached per argument list.
+std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol,
+                                                  const std::vector<double> &kappa_u, std::string *err);
 // Unit surface grid of order p (lexicographic), [n x 3] in [-1,1]^3.
 std::vector<double> surface_grid(int p);
 

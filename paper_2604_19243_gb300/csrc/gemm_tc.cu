@@ -1140,17 +1140,27 @@ static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, c
 }
 
 cudaError_t tc_upload_operators(fmm_ctx *ctx) {
-    ctx->tc_fwd = new TcOpSet();
-    ctx->tc_adj = new TcOpSet();
-    FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops, false, ctx->fwd, *ctx->tc_fwd));
-    FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops, true, ctx->adj, *ctx->tc_adj));
+    for (int l = 0; l <= kMaxDepth; ++l) {   // each distinct host set once, as the SIMT copies
+        int first = -1;
+        for (int k = 0; k < l && first < 0; ++k)
+            if (ctx->host_ops[k] == ctx->host_ops[l]) first = k;
+        if (first >= 0) {
+            ctx->tc_fwd[l] = ctx->tc_fwd[first];
+            ctx->tc_adj[l] = ctx->tc_adj[first];
+            continue;
+        }
+        ctx->tc_owned.push_back(ctx->tc_fwd[l] = new TcOpSet());
+        ctx->tc_owned.push_back(ctx->tc_adj[l] = new TcOpSet());
+        FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops[l], false, ctx->fwd[l], *ctx->tc_fwd[l]));
+        FMM_CUDA_TRY(tc_upload_set(ctx, *ctx->host_ops[l], true, ctx->adj[l], *ctx->tc_adj[l]));
+    }
     return cudaSuccess;
 }
 
 void tc_free(fmm_ctx *ctx) {
-    delete ctx->tc_fwd;
-    delete ctx->tc_adj;
-    ctx->tc_fwd = ctx->tc_adj = nullptr;
+    for (TcOpSet *t : ctx->tc_owned) delete t;
+    ctx->tc_owned.clear();
+    for (int l = 0; l <= kMaxDepth; ++l) ctx->tc_fwd[l] = ctx->tc_adj[l] = nullptr;
 }
 
 GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c);
@@ -1158,7 +1168,10 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c);
 cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream_t s) {
     const bool adj = op_id >= OP_COUNT;
     const int op = op_id % OP_COUNT;
-    const TcOpSet &T = adj ? *ctx->tc_adj : *ctx->tc_fwd;
+    // the output level's operators; PARENT2's D2D segment those of the parent level
+    const TcOpSet &T = adj ? *ctx->tc_adj[c.level] : *ctx->tc_fwd[c.level];
+    const int lp = c.level > 0 ? c.level - 1 : 0;
+    const TcOpSet &T1 = adj ? *ctx->tc_adj[lp] : *ctx->tc_fwd[lp];
     TcDev p{};
     p.g = make_gemm_dev(ctx, c);
     const TileSet &ts = (c.mode == GM_STENCIL || c.mode == GM_PARENT2) ? ctx->tiles_cls[c.level]
@@ -1172,7 +1185,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         case OP_STENCIL: p.Wt0 = (const unsigned char *)T.stencil.planes[0]; p.wt_stride = (long long)T.stencil.bytes; break;
         case OP_DECOMPRESS:
             p.Wt0 = (const unsigned char *)T.decompress.planes[0];
-            for (int k = 0; k < 8; ++k) p.Wt1[k] = (const unsigned char *)T.down[k].planes[0];
+            for (int k = 0; k < 8; ++k) p.Wt1[k] = (const unsigned char *)T1.down[k].planes[0];
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -1197,7 +1210,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
         p.b_scale = W.scale;
         p.b_scale_ld = W.scale_ld;
         if (c.mode == GM_PARENT2 && c.X1) {
-            if (!c.Xp1 || !c.xp1_scale || !T.down[0].scale || ((uintptr_t)c.Xp1 & 15) || ((c.xp1_ld * 2) & 15) ||
+            if (!c.Xp1 || !c.xp1_scale || !T1.down[0].scale || ((uintptr_t)c.Xp1 & 15) || ((c.xp1_ld * 2) & 15) ||
                 (c.xp1_plane & 15))
                 return cudaErrorInvalidValue;
             p.xp1 = (const unsigned char *)c.Xp1;
@@ -1205,8 +1218,8 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
             p.xp1_ld = c.xp1_ld;
             p.a_scale1 = c.xp1_scale;
             p.a_scale1_ld = c.xp1_scale_ld;
-            p.b_scale1 = T.down[0].scale;   // the 8 class operators' scales, contiguous
-            p.b_scale1_ld = T.down[0].scale_ld;
+            p.b_scale1 = T1.down[0].scale;   // the 8 class operators' scales, contiguous
+            p.b_scale1_ld = T1.down[0].scale_ld;
         }
     }
     if (c.n_out % 16 != 0 || (c.k0 % 16) != 0 || (c.X1 && c.k1 % 16 != 0)) return cudaErrorInvalidValue;

@@ -3,8 +3,11 @@
 // leaves' far field (step 3b).  Points live in Morton order as (x, y, z, q) vectors.
 //
 // Kernel: K(x, y) = 1/(4 pi |x - y|) (Eq. 2 normalised by 4 pi); the gradient with respect to
-// the target is (y - x) q / (4 pi |x - y|^3).  Pairs at distance zero are skipped (the self
-// interaction and coincident points, which share a leaf).
+// the target is (y - x) q / (4 pi |x - y|^3).  With YUK the modified Helmholtz kernel
+// exp(-kappa r) / (4 pi r), r = |x - y|, whose gradient is (y - x) q (1 + kappa r) exp(-kappa r)
+// / (4 pi r^3); the screening factor is exp2(-kappa log2(e) r) (FP32) or exp(-kappa r) (FP64).
+// Pairs at distance zero are skipped (the self interaction and coincident points, which share a
+// leaf).
 #include <algorithm>
 #include <type_traits>
 
@@ -23,6 +26,11 @@ template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); 
 template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
 
 template <typename T> __host__ __device__ constexpr T inv4pi() { return (T)0.079577471545947667884441881686257181; }
+constexpr double kLog2E = 1.44269504088896340736;   // log2(e)
+
+// screening factor exp(-kappa r) of the modified Helmholtz kernel
+__device__ __forceinline__ float screen(float r, float kappa) { return exp2f(-(kappa * (float)kLog2E) * r); }
+__device__ __forceinline__ double screen(double r, double kappa) { return exp(-kappa * r); }
 
 // ---------------------------------------------------------------------------------------
 // ULI: one CTA (4 warps) per target leaf.  The leaf's targets are cut into chunks of 32 (one
@@ -35,16 +43,21 @@ constexpr int kP2PThreads = 128;
 constexpr int kP2PChunk = 1024;     // sources staged per pass (16 KB as float4)
 
 // one (target, source) interaction; `checked` skips pairs at distance zero
-template <typename T, bool checked>
+template <typename T, bool checked, bool YUK = false>
 __device__ __forceinline__ void interact(const typename Vec4<T>::type &sp, T xi, T yi, T zi,
-                                         T &pot, T &gx, T &gy, T &gz) {
+                                         T &pot, T &gx, T &gy, T &gz, T kappa = (T)0) {
     const T dx = sp.x - xi, dy = sp.y - yi, dz = sp.z - zi;
     const T r2 = dx * dx + dy * dy + dz * dz;
     T rinv = rsqrt_t<T>(r2);
     if (checked) rinv = r2 > (T)0 ? rinv : (T)0;
-    const T qr = sp.w * rinv;
+    T qr = sp.w * rinv;
+    T qr3 = qr * rinv * rinv;
+    if (YUK) {
+        const T r = r2 * rinv;
+        qr *= screen(r, kappa);
+        qr3 = qr * rinv * rinv * (kappa * r + (T)1);
+    }
     pot += qr;
-    const T qr3 = qr * rinv * rinv;
     gx += qr3 * dx;
     gy += qr3 * dy;
     gz += qr3 * dz;
@@ -57,11 +70,11 @@ struct P2PRanges {
 
 // One round: chunks [cbase, cbase + nch) of the leaf with R chunks per warp group and S source
 // slices (4 / S groups of S warps).
-template <typename T, int R, bool GRAD>
+template <typename T, int R, bool GRAD, bool YUK>
 __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restrict__ pts,
                                           typename Vec4<T>::type *src, T *red, const P2PRanges &rg,
                                           int t0, int t1, int cbase, int nch, int S, T *__restrict__ phi,
-                                          T *__restrict__ grad) {
+                                          T *__restrict__ grad, T kappa) {
     using P = typename Vec4<T>::type;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp / S, slice = warp % S;
@@ -90,7 +103,7 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
         for (int e = s0; e < chk_end; ++e) {
             const P sp = src[e];
 #pragma unroll
-            for (int r = 0; r < R; ++r) interact<T, true>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+            for (int r = 0; r < R; ++r) interact<T, true, YUK>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r], kappa);
         }
         int e = chk_end;
         for (; e + 4 <= s1; e += 4) {
@@ -98,13 +111,13 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
             for (int u = 0; u < 4; ++u) {
                 const P sp = src[e + u];
 #pragma unroll
-                for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+                for (int r = 0; r < R; ++r) interact<T, false, YUK>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r], kappa);
             }
         }
         for (; e < s1; ++e) {
             const P sp = src[e];
 #pragma unroll
-            for (int r = 0; r < R; ++r) interact<T, false>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r]);
+            for (int r = 0; r < R; ++r) interact<T, false, YUK>(sp, xi[r], yi[r], zi[r], pot[r], gx[r], gy[r], gz[r], kappa);
         }
     }
     if (S > 1) {   // reduce the S slices of every group
@@ -149,9 +162,10 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
 // [x_j x_k y_j y_k] [z_j z_k q_j q_k], padded with zero charges to an even number of pairs.
 // Targets are held negated so that one add forms y - x.
 // ---------------------------------------------------------------------------------------
-template <bool checked>
+template <bool checked, bool YUK = false>
 __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, float2 nx, float2 ny,
-                                          float2 nz, float2 &pot, float2 &gx, float2 &gy, float2 &gz) {
+                                          float2 nz, float2 &pot, float2 &gx, float2 &gy, float2 &gz,
+                                          float kappa = 0.f) {
     const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
     const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
     const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
@@ -163,21 +177,30 @@ __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, floa
         ri.x = r2.x > 0.f ? ri.x : 0.f;
         ri.y = r2.y > 0.f ? ri.y : 0.f;
     }
-    const float2 qr = __fmul2_rn(make_float2(b.z, b.w), ri);
+    float2 qr = __fmul2_rn(make_float2(b.z, b.w), ri);
+    float2 qr3;
+    if (YUK) {   // r = r2 / r (0 for a skipped pair), q exp(-kappa r) / r, times (1 + kappa r) / r^2
+        const float2 r = __fmul2_rn(r2, ri);
+        qr = __fmul2_rn(qr, make_float2(screen(r.x, kappa), screen(r.y, kappa)));
+        const float2 f = __ffma2_rn(make_float2(kappa, kappa), r, make_float2(1.f, 1.f));
+        qr3 = __fmul2_rn(__fmul2_rn(__fmul2_rn(qr, ri), ri), f);
+    } else {
+        qr3 = __fmul2_rn(__fmul2_rn(qr, ri), ri);
+    }
     pot = __fadd2_rn(pot, qr);
-    const float2 qr3 = __fmul2_rn(__fmul2_rn(qr, ri), ri);
     gx = __ffma2_rn(qr3, dx, gx);
     gy = __ffma2_rn(qr3, dy, gy);
     gz = __ffma2_rn(qr3, dz, gz);
 }
 
-template <int R, bool checked>
+template <int R, bool checked, bool YUK = false>
 __device__ __forceinline__ void pair_step(const float4 *__restrict__ sp, int e, const float2 *nx,
                                           const float2 *ny, const float2 *nz, float2 *pot, float2 *gx,
-                                          float2 *gy, float2 *gz) {
+                                          float2 *gy, float2 *gz, float kappa = 0.f) {
     const float4 a = sp[2 * e], b = sp[2 * e + 1];
 #pragma unroll
-    for (int r = 0; r < R; ++r) interact2<checked>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r]);
+    for (int r = 0; r < R; ++r)
+        interact2<checked, YUK>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r], kappa);
 }
 
 // FP32 ULI kernel.  Targets go to half-warps 16 at a time (the padding of a leaf's last group
@@ -212,11 +235,11 @@ __device__ __forceinline__ void build_ranges(P2PRanges &rg, int b, const int *__
     rg.self_len = nt;
 }
 
-template <bool GRAD>
+template <bool GRAD, bool YUK>
 __global__ void __launch_bounds__(kP2PThreads)
 p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                const int *__restrict__ u_off, const int *__restrict__ u_idx,
-               const int *__restrict__ order, float *__restrict__ phi, float *__restrict__ grad) {
+               const int *__restrict__ order, float *__restrict__ phi, float *__restrict__ grad, float kappa) {
     __shared__ __align__(16) float4 src[kP2PChunk];       // sources, pair layout
     __shared__ __align__(16) float4 tgt[kRoundT];
     __shared__ __align__(16) float4 acc[kRoundT];         // (pot, gx, gy, gz) per target
@@ -279,14 +302,15 @@ p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                 // checked: pairs that may hold a target (the leaf's own points lead the list)
                 // or a padding charge at the origin; the bounds are the same for both halves
                 const int ce = min(e1, max(e0, self_pairs)), ue = max(ce, min(e1, u == npair ? pad_split : pad_pair));
-                for (int e = e0; e < ce; ++e) pair_step<1, true>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                for (int e = e0; e < ce; ++e) pair_step<1, true, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 int e = ce;
                 for (; e + 4 <= ue; e += 4) {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) pair_step<1, false>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                    for (int v = 0; v < 4; ++v)
+                        pair_step<1, false, YUK>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 }
-                for (; e < ue; ++e) pair_step<1, false>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
-                for (e = ue; e < e1; ++e) pair_step<1, true>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+                for (; e < ue; ++e) pair_step<1, false, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                for (e = ue; e < e1; ++e) pair_step<1, true, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 part[(u + warp) * 32 + lane] =
                     make_float4(pot.x + pot.y, gx.x + gx.y, gy.x + gy.y, gz.x + gz.y);
                 at += e1 - e0;
@@ -326,11 +350,11 @@ p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
     }
 }
 
-template <typename T, bool GRAD>
+template <typename T, bool GRAD, bool YUK>
 __global__ void __launch_bounds__(kP2PThreads)
 p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
            const int *__restrict__ u_off, const int *__restrict__ u_idx,
-           const int *__restrict__ order, T *__restrict__ phi, T *__restrict__ grad) {
+           const int *__restrict__ order, T *__restrict__ phi, T *__restrict__ grad, T kappa) {
     using P = typename Vec4<T>::type;
     __shared__ __align__(16) unsigned char smem_raw[kP2PChunk * sizeof(P)];
     __shared__ P2PRanges rg;
@@ -350,10 +374,10 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
         else if (nch <= 8) R = (nch + 1) / 2, S = 2;
         else R = (nch + 3) / 4, S = 1;
         switch (R) {
-            case 1: p2p_round<T, 1, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 2: p2p_round<T, 2, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            case 3: p2p_round<T, 3, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
-            default: p2p_round<T, 4, GRAD>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad); break;
+            case 1: p2p_round<T, 1, GRAD, YUK>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad, kappa); break;
+            case 2: p2p_round<T, 2, GRAD, YUK>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad, kappa); break;
+            case 3: p2p_round<T, 3, GRAD, YUK>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad, kappa); break;
+            default: p2p_round<T, 4, GRAD, YUK>(pts, src, red, rg, t0, t1, cbase, nch, S, phi, grad, kappa); break;
         }
     }
 }
@@ -364,12 +388,12 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
 constexpr int kLeafThreads = 128;
 constexpr int kLeafChunk = 1024;
 
-template <typename T>
+template <typename T, bool YUK>
 __global__ void __launch_bounds__(kLeafThreads)
 leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
                   const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns, int nsp,
                   double ox, double oy, double oz, double width, double radius,
-                  T *__restrict__ out) {
+                  T *__restrict__ out, T kappa) {
     using P = typename Vec4<T>::type;
     __shared__ P src[kLeafChunk];
     const int b = blockIdx.x;
@@ -396,7 +420,8 @@ leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__r
                 for (int e = 0; e < c1 - c0; ++e) {
                     const P sp = src[e];
                     const T dx = sp.x - px, dy = sp.y - py, dz = sp.z - pz;
-                    acc += sp.w * rsqrt_t<T>(dx * dx + dy * dy + dz * dz);
+                    const T r2 = dx * dx + dy * dy + dz * dz, ri = rsqrt_t<T>(r2);
+                    acc += YUK ? sp.w * ri * screen(r2 * ri, kappa) : sp.w * ri;
                 }
         }
         if (i < nsp) out[(int64_t)b * nsp + i] = i < ns ? acc * inv4pi<T>() : (T)0;
@@ -409,10 +434,12 @@ leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__r
 // the leaf box and every target on the 2.95 surface outside it, so no distance is zero.
 constexpr int kCheckThreads = 160;
 
+template <bool YUK>
 __global__ void __launch_bounds__(kCheckThreads)
 leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                       const uint32_t *__restrict__ keys, const float *__restrict__ grid, int ns, int nsp,
-                      double ox, double oy, double oz, double width, double radius, float *__restrict__ out) {
+                      double ox, double oy, double oz, double width, double radius, float *__restrict__ out,
+                      float kappa) {
     __shared__ __align__(16) float4 src[kLeafChunk];   // kLeafChunk sources as pairs
     __shared__ float cen[3];
     float *sf = reinterpret_cast<float *>(src);
@@ -454,7 +481,12 @@ leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ le
                     float2 r2 = __fmul2_rn(dx, dx);
                     r2 = __ffma2_rn(dy, dy, r2);
                     r2 = __ffma2_rn(dz, dz, r2);
-                    acc = __ffma2_rn(make_float2(c.z, c.w), make_float2(rsqrtf(r2.x), rsqrtf(r2.y)), acc);
+                    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                    if (YUK) {
+                        const float2 r = __fmul2_rn(r2, ri);
+                        ri = __fmul2_rn(ri, make_float2(screen(r.x, kappa), screen(r.y, kappa)));
+                    }
+                    acc = __ffma2_rn(make_float2(c.z, c.w), ri, acc);
                 }
         }
         if (i < nsp) out[(int64_t)b * nsp + i] = i < ns ? (acc.x + acc.y) * inv4pi<float>() : 0.f;
@@ -464,13 +496,13 @@ leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ le
 // ---------------------------------------------------------------------------------------
 // D2T: potentials (and gradients) at the points of leaf b from densities on its 2.95 surface.
 // ---------------------------------------------------------------------------------------
-template <typename T, bool GRAD>
+template <typename T, bool GRAD, bool YUK>
 __global__ void __launch_bounds__(kLeafThreads)
 leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
                  const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns,
                  const T *__restrict__ dens, int ldd, T scale, double ox, double oy, double oz,
                  double width, double radius, T *__restrict__ phi, T *__restrict__ grad,
-                 const double *__restrict__ shift) {
+                 const double *__restrict__ shift, T kappa) {
     using P = typename Vec4<T>::type;
     extern __shared__ unsigned char smem_raw[];
     P *src = reinterpret_cast<P *>(smem_raw);    // [ns]
@@ -516,7 +548,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
             const float4 x = pts[i];
             const float2 nx = make_float2(-x.x, -x.x), ny = make_float2(-x.y, -x.y), nz = make_float2(-x.z, -x.z);
             float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
-            for (int e = 0; e < ns / 2; ++e) pair_step<1, false>(pr, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz);
+            for (int e = 0; e < ns / 2; ++e) pair_step<1, false, YUK>(pr, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
             const float f = scale * inv4pi<float>();
             phi[i] = (pot.x + pot.y) * f + (shift ? (float)shift[b] : 0.f);   // the leaf's constant part
             if (GRAD) {
@@ -530,7 +562,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
     for (int i = t0 + threadIdx.x; i < t1; i += kLeafThreads) {
         const P x = pts[i];
         T pot = 0, gx = 0, gy = 0, gz = 0;
-        for (int e = 0; e < ns; ++e) interact<T, false>(src[e], x.x, x.y, x.z, pot, gx, gy, gz);
+        for (int e = 0; e < ns; ++e) interact<T, false, YUK>(src[e], x.x, x.y, x.z, pot, gx, gy, gz, kappa);
         const T f = scale * inv4pi<T>();
         phi[i] = pot * f + (shift ? (T)shift[b] : (T)0);   // the leaf's constant potential part
         if (GRAD) {
@@ -595,19 +627,18 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     if (ctx->nleaf == 0) return cudaSuccess;
     using P = typename Vec4<T>::type;
     const P *pts = (const P *)ctx->pts;
+    const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
+    const T kappa = (T)ctx->opt.kappa;
+    auto go = [&](auto kern, T *g) {
+        kern<<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx, ctx->p2p_order, phi, g,
+                                                 kappa);
+    };
     if constexpr (std::is_same<T, float>::value) {
-        if (grad)
-            p2p_f32_kernel<true><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                                    ctx->p2p_order, phi, grad);
-        else
-            p2p_f32_kernel<false><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                                     ctx->p2p_order, phi, nullptr);
-    } else if (grad) {
-        p2p_kernel<T, true><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                                ctx->p2p_order, phi, grad);
+        if (grad) yuk ? go(p2p_f32_kernel<true, true>, grad) : go(p2p_f32_kernel<true, false>, grad);
+        else yuk ? go(p2p_f32_kernel<false, true>, nullptr) : go(p2p_f32_kernel<false, false>, nullptr);
     } else {
-        p2p_kernel<T, false><<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, ctx->leaf_off, ctx->u_off, ctx->u_idx,
-                                                                 ctx->p2p_order, phi, nullptr);
+        if (grad) yuk ? go(p2p_kernel<T, true, true>, grad) : go(p2p_kernel<T, true, false>, grad);
+        else yuk ? go(p2p_kernel<T, false, true>, nullptr) : go(p2p_kernel<T, false, false>, nullptr);
     }
     count_launch();
     return cudaGetLastError();
@@ -619,14 +650,17 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
     const int d = ctx->opt.depth;
     const double width = ctx->side / (double)(1 << d);
     const double radius = 2.95 * 0.5 * width;
+    const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
+    const T kappa = (T)ctx->opt.kappa;
+    auto go = [&](auto kern, int threads) {
+        kern<<<ctx->nleaf, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys,
+                                            grid, ctx->ns, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2],
+                                            width, radius, out, kappa);
+    };
     if constexpr (std::is_same<T, float>::value)
-        leaf_check_f32_kernel<<<ctx->nleaf, kCheckThreads, 0, s>>>(
-            (const float4 *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, ctx->nsp,
-            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out);
+        yuk ? go(leaf_check_f32_kernel<true>, kCheckThreads) : go(leaf_check_f32_kernel<false>, kCheckThreads);
     else
-        leaf_check_kernel<T><<<ctx->nleaf, kLeafThreads, 0, s>>>(
-            (const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns,
-            ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, out);
+        yuk ? go(leaf_check_kernel<T, true>, kLeafThreads) : go(leaf_check_kernel<T, false>, kLeafThreads);
     count_launch();
     return cudaGetLastError();
 }
@@ -640,14 +674,15 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     const double radius = 2.95 * 0.5 * width;
     using P = typename Vec4<T>::type;
     size_t smem = sizeof(P) * ctx->ns * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
-    if (grad)
-        leaf_eval_kernel<T, true><<<ctx->nleaf, kLeafThreads, smem, s>>>(
-            (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
-            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, grad, shift);
-    else
-        leaf_eval_kernel<T, false><<<ctx->nleaf, kLeafThreads, smem, s>>>(
-            (const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid, ctx->ns, dens, ldd, scale,
-            ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius, phi, nullptr, shift);
+    const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
+    const T kappa = (T)ctx->opt.kappa;
+    auto go = [&](auto kern, T *g) {
+        kern<<<ctx->nleaf, kLeafThreads, smem, s>>>((const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid,
+                                                    ctx->ns, dens, ldd, scale, ctx->origin[0], ctx->origin[1],
+                                                    ctx->origin[2], width, radius, phi, g, shift, kappa);
+    };
+    if (grad) yuk ? go(leaf_eval_kernel<T, true, true>, grad) : go(leaf_eval_kernel<T, true, false>, grad);
+    else yuk ? go(leaf_eval_kernel<T, false, true>, nullptr) : go(leaf_eval_kernel<T, false, false>, nullptr);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,11 +1,12 @@
 // Host FP64 precompute of the kiFMM operators (the one place FP64 is used on the fast path's
-// behalf).  Everything is built once per (p, pinv_rtol, svd_rtol) in units of the box
-// half-width and cached for the life of the process.
+// behalf).  Everything is built once per (p, pinv_rtol, svd_rtol, kappa_u) in units of the box
+// half-width and cached for the life of the process; kappa_u = 0 is the Laplace kernel, whose
+// one set serves every level, and kappa_u = kappa r_l gives level l's modified Helmholtz set.
 //
 // Operators (Table 1 of the paper, algebraic kiFMM of Section 2.1), with the box data held as
 // check potentials (see fmm_internal.h):
 //   UC2E = pinv(K(uc, ue)), DC2E = pinv(K(dc, de)) on the unit box (truncated SVD);
-//   A_c  = K(uc_P, ue_c) * (1/2) UC2E       U2U, child half-width 1/2
+//   A_c  = K(uc_P, ue_c) * pinv(K(uc_c, ue_c))  U2U, child half-width 1/2 ((1/2) UC2E for Laplace)
 //   B_c  = K(dc_c, de_P) * DC2E             D2D
 //   T_t  = K(dc_0, ue_{2 t}) * UC2E         VLI for transfer vector t (316 of them; the
 //                                           translational symmetry of Section 2.2)
@@ -87,8 +88,9 @@ Mat scaled_surface(const std::vector<double> &grid, double cx, double cy, double
     return s;
 }
 
-// K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised); 0 where the points coincide.
-Mat kernel_matrix(const Mat &x, const Mat &y) {
+// K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised), or with kappa > 0 the modified
+// Helmholtz kernel exp(-kappa |x_i - y_j|) / (4 pi |x_i - y_j|); 0 where the points coincide.
+Mat kernel_matrix(const Mat &x, const Mat &y, double kappa) {
     int m = (int)x.size() / 3, n = (int)y.size() / 3;
     Mat k((size_t)m * n);
     for (int i = 0; i < m; ++i)
@@ -96,7 +98,7 @@ Mat kernel_matrix(const Mat &x, const Mat &y) {
             double dx = x[3 * i] - y[3 * j], dy = x[3 * i + 1] - y[3 * j + 1],
                    dz = x[3 * i + 2] - y[3 * j + 2];
             double r = std::sqrt(dx * dx + dy * dy + dz * dz);
-            k[(size_t)i * n + j] = r > 0.0 ? kInv4Pi / r : 0.0;
+            k[(size_t)i * n + j] = r > 0.0 ? kInv4Pi * (kappa > 0.0 ? std::exp(-kappa * r) : 1.0) / r : 0.0;
         }
     return k;
 }
@@ -256,9 +258,24 @@ int transfer_index_of(int dx, int dy, int dz) {
     return -1;
 }
 
-std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::string *err) {
-    auto h = std::make_unique<HostOps>();
+// Operators of one level, up to the choice of the M2L ranks: everything in units of the level's
+// box half-width r, where the kernel of a level is (1/r) times the unit-box kernel with
+// kappa_u = kappa r (the factor 1/r cancels in every "evaluation o pseudo-inverse" product and
+// is applied to the leaf closing by the caller).  For Laplace kappa_u = 0 and one set serves all
+// levels.
+struct LevelBuild {
+    std::unique_ptr<HostOps> h;
+    std::vector<Mat> T;                 // the 316 M2L operators
+    Mat ql, qr;                         // eigenvectors of the two Gram matrices (descending)
+    std::vector<double> ll, lr;         // their eigenvalues
+};
+
+LevelBuild build_level(int p, double pinv_rtol, double kappa_u) {
+    LevelBuild b;
+    b.h = std::make_unique<HostOps>();
+    HostOps *h = b.h.get();
     h->p = p;
+    h->kappa_u = kappa_u;
     std::vector<double> grid = surface_grid(p);
     const int ns = (int)grid.size() / 3;
     h->ns = ns;
@@ -272,13 +289,25 @@ std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::st
     // check-to-equivalent pseudo-inverses on the unit box
     Mat uc_vs, uc_ut, dc_vs, dc_ut;
     int r_uc = 0, r_dc = 0;
-    pinv_factors(kernel_matrix(uc, ue), ns, pinv_rtol, uc_vs, uc_ut, r_uc);
-    pinv_factors(kernel_matrix(dc, de), ns, pinv_rtol, dc_vs, dc_ut, r_dc);
+    pinv_factors(kernel_matrix(uc, ue, kappa_u), ns, pinv_rtol, uc_vs, uc_ut, r_uc);
+    pinv_factors(kernel_matrix(dc, de, kappa_u), ns, pinv_rtol, dc_vs, dc_ut, r_dc);
     Mat uc2e = matmul(uc_vs, uc_ut, ns, r_uc, ns);
     Mat dc2e = matmul(dc_vs, dc_ut, ns, r_dc, ns);
     h->rcl = r_dc;
     h->close1 = dc_ut;   // [r_dc x ns]
     h->close2 = dc_vs;   // [ns x r_dc]
+
+    // A child box of half-width 1/2 sees the kernel K_{kappa_u}(x/2, y/2) = 2 K_{kappa_u/2}(x, y)
+    // of its own unit box, so its pseudo-inverse is (1/2) pinv(K_{kappa_u/2}(uc, ue)); for
+    // Laplace that is (1/2) UC2E.
+    Mat child_uc2e = uc2e;
+    if (kappa_u > 0.0) {
+        Mat vs, ut;
+        int rk = 0;
+        pinv_factors(kernel_matrix(uc, ue, 0.5 * kappa_u), ns, pinv_rtol, vs, ut, rk);
+        child_uc2e = matmul(vs, ut, ns, rk, ns);
+    }
+    for (auto &x : child_uc2e) x *= 0.5;
 
     // U2U and D2D per octant (child half-width 1/2, centre offset +-1/2 per axis, x bit first)
     for (int c = 0; c < 8; ++c) {
@@ -286,27 +315,24 @@ std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::st
                cz = (c & 1) ? 0.5 : -0.5;
         Mat child_ue = scaled_surface(grid, cx, cy, cz, 0.5, kAlphaInner);
         Mat child_dc = child_ue;
-        Mat kk = kernel_matrix(uc, child_ue);
-        Mat half_uc2e = uc2e;
-        for (auto &x : half_uc2e) x *= 0.5;      // pinv at half-width 1/2 = (1/2) pinv at 1
-        h->up[c] = matmul(kk, half_uc2e, ns, ns, ns);
-        h->down[c] = matmul(kernel_matrix(child_dc, de), dc2e, ns, ns, ns);
+        h->up[c] = matmul(kernel_matrix(uc, child_ue, kappa_u), child_uc2e, ns, ns, ns);
+        h->down[c] = matmul(kernel_matrix(child_dc, de, kappa_u), dc2e, ns, ns, ns);
     }
 
-    // M2L operators T_t = K(dc_0, ue_{2t}) UC2E and their SVD compression
-    std::vector<Mat> T(kNumTransfer);
+    // M2L operators T_t = K(dc_0, ue_{2t}) UC2E
+    b.T.resize(kNumTransfer);
     parallel_for(kNumTransfer, [&](int t) {
         int dx, dy, dz;
         transfer_vector(t, dx, dy, dz);
         Mat src = scaled_surface(grid, 2.0 * dx, 2.0 * dy, 2.0 * dz, 1.0, kAlphaInner);
-        T[t] = matmul(kernel_matrix(dc, src), uc2e, ns, ns, ns);
+        b.T[t] = matmul(kernel_matrix(dc, src, kappa_u), uc2e, ns, ns, ns);
     });
     // Gram matrices of the fat [T_1 .. T_316] (left) and tall [T_1; ..; T_316] (right) stacks
     int nt = hw_threads();
     std::vector<Mat> gl(nt, Mat((size_t)ns * ns, 0.0)), gr(nt, Mat((size_t)ns * ns, 0.0));
     parallel_for(nt, [&](int w) {
         for (int t = w; t < kNumTransfer; t += nt) {
-            const Mat &a = T[t];
+            const Mat &a = b.T[t];
             Mat at = transpose(a, ns, ns);
             Mat l = matmul(a, at, ns, ns, ns), r = matmul(at, a, ns, ns, ns);
             for (size_t i = 0; i < l.size(); ++i) {
@@ -320,33 +346,40 @@ std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::st
             gl[0][i] += gl[w][i];
             gr[0][i] += gr[w][i];
         }
-    Mat ql, qr;
-    std::vector<double> ll, lr;
-    jacobi_eig(gl[0], ns, ql, ll);
-    jacobi_eig(gr[0], ns, qr, lr);
-    // sigma_i >= svd_rtol * sigma_1  <=>  lambda_i >= svd_rtol^2 * lambda_1
-    auto rank_of = [&](const std::vector<double> &l) {
-        int k = 0;
-        while (k < ns && l[k] > 0 && l[k] >= svd_rtol * svd_rtol * l[0]) ++k;
-        return std::max(k, 1);
-    };
-    int kout = rank_of(ll), kin = rank_of(lr);
+    jacobi_eig(gl[0], ns, b.ql, b.ll);
+    jacobi_eig(gr[0], ns, b.qr, b.lr);
+    return b;
+}
+
+// sigma_i >= svd_rtol * sigma_1  <=>  lambda_i >= svd_rtol^2 * lambda_1
+int rank_of(const std::vector<double> &l, double svd_rtol) {
+    const int n = (int)l.size();
+    int k = 0;
+    while (k < n && l[k] > 0 && l[k] >= svd_rtol * svd_rtol * l[0]) ++k;
+    return std::max(k, 1);
+}
+
+// The compressed M2L at ranks (kin, kout) and the adjoint operators.
+std::unique_ptr<HostOps> finish_level(LevelBuild &b, int kin, int kout) {
+    HostOps *h = b.h.get();
+    const int ns = h->ns;
     h->kout = kout;
     h->kin = kin;
     Mat uo((size_t)ns * kout), vi((size_t)ns * kin);
     for (int i = 0; i < ns; ++i) {
-        for (int j = 0; j < kout; ++j) uo[(size_t)i * kout + j] = ql[(size_t)i * ns + j];
-        for (int j = 0; j < kin; ++j) vi[(size_t)i * kin + j] = qr[(size_t)i * ns + j];
+        for (int j = 0; j < kout; ++j) uo[(size_t)i * kout + j] = b.ql[(size_t)i * ns + j];
+        for (int j = 0; j < kin; ++j) vi[(size_t)i * kin + j] = b.qr[(size_t)i * ns + j];
     }
     h->decompress = uo;                       // [ns x kout]
     h->compress = transpose(vi, ns, kin);     // [kin x ns]
     Mat uot = transpose(uo, ns, kout);
     h->stencil.assign((size_t)kNumTransfer * kout * kin, 0.0);
     parallel_for(kNumTransfer, [&](int t) {
-        Mat tv = matmul(T[t], vi, ns, ns, kin);            // ns x kin
+        Mat tv = matmul(b.T[t], vi, ns, ns, kin);          // ns x kin
         Mat c = matmul(uot, tv, kout, ns, kin);            // kout x kin
         std::copy(c.begin(), c.end(), h->stencil.begin() + (size_t)t * kout * kin);
     });
+    b.T.clear();
 
     // adjoint operators: transposes, with the stencil re-indexed by the opposite vector
     for (int c = 0; c < 8; ++c) {
@@ -365,10 +398,9 @@ std::unique_ptr<HostOps> build(int p, double pinv_rtol, double svd_rtol, std::st
         for (int i = 0; i < kout; ++i)
             for (int j = 0; j < kin; ++j) o[(size_t)j * kout + i] = c[(size_t)i * kin + j];
     }
-    h->a_close1 = transpose(dc_vs, ns, r_dc);         // [r_dc x ns] = (V S^-1)^T
-    h->a_close2 = transpose(dc_ut, r_dc, ns);         // [ns x r_dc] = U
-    (void)err;
-    return h;
+    h->a_close1 = transpose(h->close2, ns, h->rcl);   // [r_dc x ns] = (V S^-1)^T
+    h->a_close2 = transpose(h->close1, h->rcl, ns);   // [ns x r_dc] = U
+    return std::move(b.h);
 }
 
 }  // namespace
@@ -387,18 +419,50 @@ std::vector<double> surface_grid(int p) {
     return g;
 }
 
-const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err) {
+std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol,
+                                                  const std::vector<double> &kappa_u, std::string *err) {
     static std::mutex mu;
-    static std::map<std::tuple<int, double, double>, std::unique_ptr<HostOps>> cache;
+    static std::map<std::tuple<int, double, double, std::vector<double>>, std::vector<std::unique_ptr<HostOps>>>
+        cache;
     std::lock_guard<std::mutex> lock(mu);
-    auto key = std::make_tuple(p, pinv_rtol, svd_rtol);
+    std::vector<double> key_k = kappa_u;
+    for (auto &k : key_k) k = std::max(k, 0.0);
+    auto key = std::make_tuple(p, pinv_rtol, svd_rtol, key_k);
     auto it = cache.find(key);
-    if (it != cache.end()) return it->second.get();
-    auto h = build(p, pinv_rtol, svd_rtol, err);
-    if (!h) return nullptr;
-    const HostOps *ptr = h.get();
-    cache.emplace(key, std::move(h));
-    return ptr;
+    if (it == cache.end()) {
+        // distinct kappa_u values only; the M2L ranks are the largest any of them needs, so that
+        // every level's contractions have one shape
+        std::vector<double> uniq = key_k;
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        std::vector<LevelBuild> lb;
+        int kin = 1, kout = 1;
+        for (double k : uniq) {
+            lb.push_back(build_level(p, pinv_rtol, k));
+            kin = std::max(kin, rank_of(lb.back().lr, svd_rtol));
+            kout = std::max(kout, rank_of(lb.back().ll, svd_rtol));
+        }
+        std::vector<std::unique_ptr<HostOps>> built;
+        for (auto &b : lb) built.push_back(finish_level(b, kin, kout));
+        it = cache.emplace(key, std::move(built)).first;
+    }
+    std::vector<const HostOps *> out;
+    for (double k : key_k)
+        for (const auto &h : it->second)
+            if (h->kappa_u == k) {
+                out.push_back(h.get());
+                break;
+            }
+    if (out.size() != key_k.size()) {
+        if (err) *err = "operator cache lookup failed";
+        return {};
+    }
+    return out;
+}
+
+const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err) {
+    auto v = host_operator_levels(p, pinv_rtol, svd_rtol, {0.0}, err);
+    return v.empty() ? nullptr : v[0];
 }
 
 }  // namespace fmm

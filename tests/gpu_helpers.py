@@ -13,11 +13,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def make_fmm(x, p, depth, precision="fp32", domain=None, with_gradient=True, mean_free=False):
+def make_fmm(x, p, depth, precision="fp32", domain=None, with_gradient=True, mean_free=False, **kw):
     import torch
     dt = torch.float64 if precision == "fp64" else torch.float32
     f = pkg.FMM(p=p, depth=depth, precision=precision, domain=domain, pinv_rtol=PINV_RTOL,
-                svd_rtol=SVD_RTOL, with_gradient=with_gradient, mean_free=mean_free)
+                svd_rtol=SVD_RTOL, with_gradient=with_gradient, mean_free=mean_free, **kw)
     f.build_tree(torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt))
     f.precompute()
     return f

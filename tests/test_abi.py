@@ -65,6 +65,16 @@ def test_default_options_and_validation_without_gpu(libpath):
     lib.fmm_default_options(ctypes.byref(o))
     o.has_domain, o.side = 1, -1.0
     assert lib.fmm_create(ctypes.byref(o), None, ctypes.byref(ctx)) == 1
+    # the modified Helmholtz kernel: kappa finite and > 0, a domain, no mean_free
+    for kernel, kappa, has_domain, mean_free, want in ((2, 1.0, 1, 0, 1), (1, 0.0, 1, 0, 1),
+                                                       (1, -1.0, 1, 0, 1), (1, float("nan"), 1, 0, 1),
+                                                       (1, float("inf"), 1, 0, 1), (1, 1.0, 0, 0, 6),
+                                                       (1, 1.0, 1, 1, 6)):
+        o = pkg.Options()
+        lib.fmm_default_options(ctypes.byref(o))
+        assert o.kernel == 0 and o.kappa == 0.0
+        o.kernel, o.kappa, o.has_domain, o.side, o.mean_free = kernel, kappa, has_domain, 1.0, mean_free
+        assert lib.fmm_create(ctypes.byref(o), None, ctypes.byref(ctx)) == want, (kernel, kappa, has_domain)
     assert lib.fmm_last_error(None) == b"null context"
     lib.fmm_destroy(None)
 
