@@ -14,6 +14,8 @@ Default: 1 GPU, 3 warm-up steps, 10 timed steps, then the FP64 CPU oracle on a b
 (the cpu_baseline leg).  `--impl reference` times only that oracle (the reference arm).
 Under torchrun with N > 1 every rank runs an independent replica (the path has no exchange
 step on one GPU per process); value = all ranks' points / the slowest rank's time.
+`--kernel yukawa --kappa K` runs the same workload and step with the modified Helmholtz kernel
+exp(-K r) / (4 pi r) (operators per level, built once before timing).
 """
 from __future__ import annotations
 
@@ -37,6 +39,9 @@ from synth import WORKLOADS, SEED_SAMPLE, sample_indices, sphere_points, charges
 METRIC = "kiFMM points/sec (potential+gradient) at N=8M, p=6, rel err ≤1e-5 vs FP64"
 UNIT = "points/s"
 FLOPS_PER_PAIR = 20          # conventional count for a potential+gradient Laplace interaction
+# modified Helmholtz: + r = r2 / r, the exponent's argument, exp (one flop, like rsqrt), the
+# screening product, 1 + kappa r (two) and the gradient factor's product
+FLOPS_PER_PAIR_YUKAWA = FLOPS_PER_PAIR + 7
 SAMPLE_N = 2_097_152         # CPU sample: same sphere distribution, depth 6 -> ~112 points/leaf
 SAMPLE_DEPTH = 6
 
@@ -142,28 +147,29 @@ def recorded_traffic(kernel, digest):
     return rec.get("bytes_per_launch_full")
 
 
-def cpu_baseline_sample(p):
+def cpu_baseline_sample(p, kappa=0.0):
     """The FP64 oracle kiFMM on a bounded sample of the same workload family."""
     from oracle import direct, kifmm
     x = sphere_points(SAMPLE_N)
     q = charges(SAMPLE_N, "u01")
     t0 = time.perf_counter()
     kifmm.evaluate(x.astype(np.float64), q.astype(np.float64), p, SAMPLE_DEPTH, (-1, -1, -1), 2.0,
-                   pinv_rtol=1e-7, gradient=True)
+                   pinv_rtol=1e-7, gradient=True, kappa=kappa)
     dt = time.perf_counter() - t0
+    kern = f"modified Helmholtz kappa={kappa:g}, " if kappa > 0 else ""
     return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": direct.num_threads(),
             "host_cpus": os.cpu_count(), "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"FP64 oracle kiFMM (p={p}, potentials+gradients, tree and operators "
+            "sample": f"FP64 oracle kiFMM ({kern}p={p}, potentials+gradients, tree and operators "
                       f"included) on {SAMPLE_N:,} points of the same unit-sphere distribution at "
                       f"depth {SAMPLE_DEPTH} (~112 points per leaf, as in the full workload)"}
 
 
-def accuracy_check(w, x, q, phi, grad, m=256):
+def accuracy_check(w, x, q, phi, grad, m=256, kappa=0.0):
     """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum."""
     from oracle import direct
     idx = sample_indices(w.n, m, SEED_SAMPLE)
     x64 = x.astype(np.float64)
-    p_ref, g_ref = direct.direct_self(x64, q.astype(np.float64), sample=idx)
+    p_ref, g_ref = direct.direct_self(x64, q.astype(np.float64), sample=idx, kappa=kappa)
     e_p = float(np.linalg.norm(phi[idx] - p_ref) / np.linalg.norm(p_ref))
     e_g = float(np.linalg.norm(grad[idx] - g_ref) / np.linalg.norm(g_ref))
     return {"phi": e_p, "grad": e_g, "targets": int(m),
@@ -177,7 +183,7 @@ def run_reference(args, w):
     times = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline_sample(w.p)
+        info = cpu_baseline_sample(w.p, args.kappa)
         if i >= args.warmup:
             times.append(info["seconds"])
     mean_s = sum(times) / len(times)
@@ -186,7 +192,8 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "n": w.n, "p": w.p,
-                                            "depth": w.depth, "dist": w.dist},
+                                            "depth": w.depth, "dist": w.dist, "kernel": args.kernel,
+                                            **({"kappa": args.kappa} if args.kernel == "yukawa" else {})},
             "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -204,9 +211,22 @@ def main():
     ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="laplace", choices=["laplace", "yukawa"],
+                    help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r)")
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="yukawa screening constant (default 3, i.e. kappa r = 0.023 at the leaves "
+                         "and 0.75 at level 2 of the default workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if args.kernel == "laplace":
+        if args.kappa not in (None, 0.0):
+            ap.error("--kappa applies to --kernel yukawa")
+        args.kappa = 0.0
+    elif args.kappa is None:
+        args.kappa = 3.0
+    elif not args.kappa > 0:
+        ap.error("--kappa must be > 0")
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
@@ -229,7 +249,7 @@ def main():
     phi = torch.empty(w.n, device=dev, dtype=tdt)
     grad = torch.empty(w.n, 3, device=dev, dtype=tdt)
     fmm = pkg.FMM(p=w.p, depth=w.depth, precision=args.precision, domain=(w.origin, w.side),
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, kernel=args.kernel, kappa=args.kappa)
     fmm.precompute()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -324,14 +344,15 @@ def main():
     fmm.evaluate_into(q, phi, grad)
     torch.cuda.synchronize()
     pairs = info["p2p_pairs"]
-    p2p_flops = pairs * FLOPS_PER_PAIR
+    fpp = FLOPS_PER_PAIR_YUKAWA if args.kernel == "yukawa" else FLOPS_PER_PAIR
+    p2p_flops = pairs * fpp
     p2p = {"bound": "alu", "achieved": p2p_flops / (near_ms * 1e-3) / 1e12,
            "peak": fp32_peak_tf, "unit": "TFLOP/s",
            "kernel": "p2p_f32_kernel (ULI near field)",
            "peak_basis": f"measured FP32 FMA throughput on this GPU (fmm_measure_fp32_peak: scalar "
                          f"{fp32_scalar_tf:.1f}, float2 {fp32_pair_tf:.1f} TFLOP/s); nominal "
                          f"{sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz = {nominal_fp32_tf:.1f}; "
-                         f"{FLOPS_PER_PAIR} flops per pair",
+                         f"{fpp} flops per pair",
            "pairs": pairs, "ms": near_ms,
            "timing": "CUDA events around the kernel on its own stream inside the timed steps, where "
                      "it runs at low priority beside the far field and fills the SMs that leave idle",
@@ -406,7 +427,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
-                       "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                       "precision": args.precision, "kernel": args.kernel,
+                       **({"kappa": args.kappa} if args.kernel == "yukawa" else {}),
+                       "l2": "flushed (256 MB write) between steps",
                        "step": "build_tree + evaluate(potential+gradient)",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": {"near_p2p": near_ms, "upward": up_ms, "m2l": m2l_ms,
@@ -420,9 +443,9 @@ def main():
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         line["accuracy"] = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
-                                          grad.cpu().numpy().astype(np.float64))
+                                          grad.cpu().numpy().astype(np.float64), kappa=args.kappa)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(w.p)
+        line["cpu_baseline"] = cpu_baseline_sample(w.p, args.kappa)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fmm.close()
