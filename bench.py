@@ -165,12 +165,13 @@ def cpu_baseline_sample(p, kappa=0.0):
 
 
 def accuracy_check(w, x, q, phi, grad, m=256, kappa=0.0):
-    """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum."""
+    """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum
+    (phi None: gradient only)."""
     from oracle import direct
     idx = sample_indices(w.n, m, SEED_SAMPLE)
     x64 = x.astype(np.float64)
     p_ref, g_ref = direct.direct_self(x64, q.astype(np.float64), sample=idx, kappa=kappa)
-    e_p = float(np.linalg.norm(phi[idx] - p_ref) / np.linalg.norm(p_ref))
+    e_p = None if phi is None else float(np.linalg.norm(phi[idx] - p_ref) / np.linalg.norm(p_ref))
     e_g = float(np.linalg.norm(grad[idx] - g_ref) / np.linalg.norm(g_ref))
     return {"phi": e_p, "grad": e_g, "targets": int(m),
             "reference": "FP64 direct sum (Eq. 1) at seeded sampled targets"}
@@ -213,6 +214,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="laplace", choices=["laplace", "yukawa"],
                     help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r)")
+    ap.add_argument("--outputs", default="potential+gradient", choices=["potential+gradient", "gradient"],
+                    help="gradient: the gradient-only (force) evaluation, phi = NULL")
     ap.add_argument("--kappa", type=float, default=None,
                     help="yukawa screening constant (default 3, i.e. kappa r = 0.023 at the leaves "
                          "and 0.75 at level 2 of the default workload)")
@@ -253,9 +256,12 @@ def main():
     fmm.precompute()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    grad_only = args.outputs == "gradient"
+    phi_out = None if grad_only else phi
+
     def step():
         fmm.build_tree(x)
-        fmm.evaluate_into(q, phi, grad)
+        fmm.evaluate_into(q, phi_out, grad)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -292,9 +298,10 @@ def main():
     qh = torch.from_numpy(q_np).to(tdt).pin_memory()
     ph = torch.empty(w.n, dtype=tdt).pin_memory()
     gh = torch.empty(w.n, 3, dtype=tdt).pin_memory()
+    ph_out = None if grad_only else ph
     for _ in range(2):
         fmm.build_tree(xh)
-        fmm.evaluate_into(qh, ph, gh)
+        fmm.evaluate_into(qh, ph_out, gh)
     torch.cuda.synchronize()
     e2e_s = []
     if ws > 1:
@@ -304,12 +311,12 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fmm.build_tree(xh)
-        fmm.evaluate_into(qh, ph, gh)     # host outputs: returns after the device-to-host copy
+        fmm.evaluate_into(qh, ph_out, gh)     # host outputs: returns after the device-to-host copy
         e2e_s.append(time.perf_counter() - t0)
     e2e_value = job_rate(w.n, args.steps, ws, slowest(sum(e2e_s), dev, ws))
     es = 8 if fp64 else 4
     h2d = w.n * 3 * es + w.n * es
-    d2h = w.n * es + w.n * 3 * es
+    d2h = (0 if grad_only else w.n * es) + w.n * 3 * es
 
     # adjoint timing (reported beside the metric, not part of the step)
     fmm.build_tree(x)
@@ -338,13 +345,13 @@ def main():
     # the near-field kernel alone (same launch, no far field beside it), for its own rate
     iso = []
     for _ in range(5):
-        fmm.evaluate_into(q, phi, grad, parts=pkg.PART_NEAR)
+        fmm.evaluate_into(q, phi_out, grad, parts=pkg.PART_NEAR)
         iso.append(fmm.timings()["near"])
     near_iso_ms = statistics.median(iso[1:])
     fmm.evaluate_into(q, phi, grad)
     torch.cuda.synchronize()
     pairs = info["p2p_pairs"]
-    fpp = FLOPS_PER_PAIR_YUKAWA if args.kernel == "yukawa" else FLOPS_PER_PAIR
+    fpp = (FLOPS_PER_PAIR_YUKAWA if args.kernel == "yukawa" else FLOPS_PER_PAIR) - (1 if grad_only else 0)
     p2p_flops = pairs * fpp
     p2p = {"bound": "alu", "achieved": p2p_flops / (near_ms * 1e-3) / 1e12,
            "peak": fp32_peak_tf, "unit": "TFLOP/s",
@@ -422,7 +429,8 @@ def main():
                        f"{float(peaks['hbm_gbs']):.0f} GB/s"}
     dominant, other = p2p, m2l
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    metric = METRIC if not grad_only else METRIC.replace("(potential+gradient)", "(gradient only)")
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
@@ -430,7 +438,7 @@ def main():
                        "precision": args.precision, "kernel": args.kernel,
                        **({"kappa": args.kappa} if args.kernel == "yukawa" else {}),
                        "l2": "flushed (256 MB write) between steps",
-                       "step": "build_tree + evaluate(potential+gradient)",
+                       "step": f"build_tree + evaluate({args.outputs})", "outputs": args.outputs,
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": {"near_p2p": near_ms, "upward": up_ms, "m2l": m2l_ms,
                           "downward": down_ms,
@@ -442,7 +450,10 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:
-        line["accuracy"] = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
+        if grad_only:   # the timed steps left no potentials: check the gradient-only result
+            fmm.evaluate_into(q, None, grad)
+            torch.cuda.synchronize()
+        line["accuracy"] = accuracy_check(w, x_np, q_np, None if grad_only else phi.cpu().numpy().astype(np.float64),
                                           grad.cpu().numpy().astype(np.float64), kappa=args.kappa)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(w.p, args.kappa)

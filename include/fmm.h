@@ -138,7 +138,11 @@ fmm_status fmm_precompute(fmm_ctx *ctx);
 
 /* phi = A q (Algorithm 1), and grad phi if `grad` is non-NULL (requires with_gradient).
  * q: n densities; phi: n outputs; grad: n x 3 outputs; all in the input order of the points.
- * Errors: ESTATE before fmm_build_tree and fmm_precompute; EINVAL for null q/phi. */
+ * phi may be NULL when grad is not: the gradient-only ("force") evaluation of N-body codes, which
+ * skips the potential sums of the near field and the potential outputs; its gradients are those
+ * of the full evaluation bit for bit.
+ * Errors: ESTATE before fmm_build_tree and fmm_precompute; EINVAL for null q, for phi and grad
+ * both NULL, and for grad with with_gradient = 0. */
 fmm_status fmm_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad);
 
 /* As fmm_evaluate, restricted to the parts in `parts` (FMM_PART_NEAR | FMM_PART_FAR). */

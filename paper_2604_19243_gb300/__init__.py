@@ -201,15 +201,17 @@ class FMM:
         self._check(lib().fmm_precompute(self._ctx))
         return self
 
-    def evaluate(self, q, gradient=True, parts=PART_ALL):
+    def evaluate(self, q, gradient=True, parts=PART_ALL, potential=True):
+        """(phi, grad); potential=False gives the gradient-only evaluation (phi is None)."""
         q = self._as_input(q)
-        phi = self._like(q, (self.n,))
+        phi = self._like(q, (self.n,)) if potential else None
         grad = self._like(q, (self.n, 3)) if gradient else None
         self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
         return phi, grad
 
     def evaluate_into(self, q, phi, grad=None, parts=PART_ALL):
-        """fmm_evaluate_parts on caller-owned arrays (host or device, contiguous)."""
+        """fmm_evaluate_parts on caller-owned arrays (host or device, contiguous); phi may be
+        None when grad is given (gradient only)."""
         self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
 
     def adjoint(self, g, gradient=False):

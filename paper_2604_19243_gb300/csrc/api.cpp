@@ -265,7 +265,7 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     Staged sq, sphi, sgrad;
     fmm_status st;
     if ((st = stage(ctx, q, n * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
-    if ((st = stage(ctx, phi, n * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
+    if (phi && (st = stage(ctx, phi, n * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
     if (grad && (st = stage(ctx, grad, 3 * n * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
     cudaError_t e;
     cudaEventRecord(ctx->ev[0], s);
@@ -281,7 +281,7 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     cudaStreamWaitEvent(ns, ctx->ev[7], 0);
     cudaStreamWaitEvent(fs, ctx->ev[7], 0);
     if (far) {
-        e = run_far<T>(ctx, adjoint, (T *)ctx->far_phi, fg, fs);
+        e = run_far<T>(ctx, adjoint, phi ? (T *)ctx->far_phi : nullptr, fg, fs);
         if (e == cudaErrorNotSupported)
             return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "far field");
@@ -289,22 +289,22 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
         cudaEventRecord(ctx->ev[2], fs), cudaEventRecord(ctx->ev[3], fs), cudaEventRecord(ctx->ev[4], fs);
     }
     cudaEventRecord(ctx->ev[5], fs);
-    if (near && (e = launch_p2p<T>(ctx, (T *)ctx->near_phi, ng, ns)) != cudaSuccess)
+    if (near && (e = launch_p2p<T>(ctx, phi ? (T *)ctx->near_phi : nullptr, ng, ns)) != cudaSuccess)
         return cuda_fail(ctx, e, "near field");
     cudaEventRecord(ctx->ev[1], ns);
     cudaStreamWaitEvent(s, ctx->ev[5], 0);   // join the far field
     cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
-    e = launch_scatter<T>(near ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
-                          far ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
+    e = launch_scatter<T>(near && phi ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
+                          far && phi ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
                           (T *)sphi.dev, (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter");
     cudaEventRecord(ctx->ev[6], s);
-    if (sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if (phi && sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "device-to-host copy");
     if (grad && !adjoint && sgrad.host &&
         (e = cudaMemcpyAsync(grad, sgrad.dev, 3 * n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "device-to-host copy");
-    if (sq.host || sphi.host || (grad && sgrad.host)) {
+    if (sq.host || (phi && sphi.host) || (grad && sgrad.host)) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
     }
     ctx->last_adjoint = adjoint;
@@ -312,11 +312,13 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     return FMM_OK;
 }
 
-fmm_status check_ready(fmm_ctx *ctx, const void *q, const void *phi) {
+// `out`: the output that must be present (the potentials, or for a gradient-only evaluation the
+// gradients)
+fmm_status check_ready(fmm_ctx *ctx, const void *q, const void *out) {
     if (!ctx) return FMM_EINVAL;
     if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
     if (!ctx->have_ops) return fail(ctx, FMM_ESTATE, "fmm_precompute has not been called");
-    if (!q || !phi) return fail(ctx, FMM_EINVAL, "null density or output pointer");
+    if (!q || !out) return fail(ctx, FMM_EINVAL, "null density or output pointer");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     return ensure_workspace(ctx);
 }
@@ -488,7 +490,8 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
 }
 
 fmm_status fmm_evaluate_parts(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts) {
-    fmm_status st = check_ready(ctx, q, phi);
+    // phi == NULL with grad: the gradient-only ("force") evaluation
+    fmm_status st = check_ready(ctx, q, phi ? phi : grad);
     if (st != FMM_OK) return st;
     if (grad && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
     if (parts < 1 || parts > FMM_PART_ALL) return fail(ctx, FMM_EINVAL, "parts must be a nonempty subset of near|far");

@@ -240,7 +240,7 @@ template <typename T>
 cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_phi,
                            const T *far_grad, const int *perm, T *phi, T *grad, int64_t n,
                            cudaStream_t s);
-// ULI near field in sorted order (phi written, grad written if non-null)
+// ULI near field in sorted order (phi and grad each written if non-null, one of them non-null)
 template <typename T>
 cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
 // check potentials on the 2.95 surface of every leaf from its own points -> rows [nleaf x nsp]

@@ -142,7 +142,7 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
             const int ch = grp * R + r;
             const int i = t0 + (cbase + ch) * 32 + lane;
             if (ch < nch && i < t1) {
-                phi[i] = pot[r] * inv4pi<T>();
+                if (phi) phi[i] = pot[r] * inv4pi<T>();
                 if (GRAD) {
                     grad[3 * (int64_t)i] = gx[r] * inv4pi<T>();
                     grad[3 * (int64_t)i + 1] = gy[r] * inv4pi<T>();
@@ -162,7 +162,7 @@ __device__ __forceinline__ void p2p_round(const typename Vec4<T>::type *__restri
 // [x_j x_k y_j y_k] [z_j z_k q_j q_k], padded with zero charges to an even number of pairs.
 // Targets are held negated so that one add forms y - x.
 // ---------------------------------------------------------------------------------------
-template <bool checked, bool YUK = false>
+template <bool checked, bool YUK = false, bool POT = true>
 __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, float2 nx, float2 ny,
                                           float2 nz, float2 &pot, float2 &gx, float2 &gy, float2 &gz,
                                           float kappa = 0.f) {
@@ -187,20 +187,20 @@ __device__ __forceinline__ void interact2(const float4 &a, const float4 &b, floa
     } else {
         qr3 = __fmul2_rn(__fmul2_rn(qr, ri), ri);
     }
-    pot = __fadd2_rn(pot, qr);
+    if (POT) pot = __fadd2_rn(pot, qr);
     gx = __ffma2_rn(qr3, dx, gx);
     gy = __ffma2_rn(qr3, dy, gy);
     gz = __ffma2_rn(qr3, dz, gz);
 }
 
-template <int R, bool checked, bool YUK = false>
+template <int R, bool checked, bool YUK = false, bool POT = true>
 __device__ __forceinline__ void pair_step(const float4 *__restrict__ sp, int e, const float2 *nx,
                                           const float2 *ny, const float2 *nz, float2 *pot, float2 *gx,
                                           float2 *gy, float2 *gz, float kappa = 0.f) {
     const float4 a = sp[2 * e], b = sp[2 * e + 1];
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        interact2<checked, YUK>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r], kappa);
+        interact2<checked, YUK, POT>(a, b, nx[r], ny[r], nz[r], pot[r], gx[r], gy[r], gz[r], kappa);
 }
 
 // FP32 ULI kernel.  Targets go to half-warps 16 at a time (the padding of a leaf's last group
@@ -235,7 +235,10 @@ __device__ __forceinline__ void build_ranges(P2PRanges &rg, int b, const int *__
     rg.self_len = nt;
 }
 
-template <bool GRAD, bool YUK>
+// OUT: bit 0 potentials, bit 1 gradients (gradient only: the "force" evaluation of N-body codes)
+constexpr int kOutPhi = 1, kOutGrad = 2;
+
+template <int OUT, bool YUK>
 __global__ void __launch_bounds__(kP2PThreads)
 p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                const int *__restrict__ u_off, const int *__restrict__ u_idx,
@@ -302,15 +305,17 @@ p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                 // checked: pairs that may hold a target (the leaf's own points lead the list)
                 // or a padding charge at the origin; the bounds are the same for both halves
                 const int ce = min(e1, max(e0, self_pairs)), ue = max(ce, min(e1, u == npair ? pad_split : pad_pair));
-                for (int e = e0; e < ce; ++e) pair_step<1, true, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                constexpr bool POT = OUT & kOutPhi;
+                for (int e = e0; e < ce; ++e)
+                    pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 int e = ce;
                 for (; e + 4 <= ue; e += 4) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
-                        pair_step<1, false, YUK>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                        pair_step<1, false, YUK, POT>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 }
-                for (; e < ue; ++e) pair_step<1, false, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
-                for (e = ue; e < e1; ++e) pair_step<1, true, YUK>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                for (; e < ue; ++e) pair_step<1, false, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                for (e = ue; e < e1; ++e) pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
                 part[(u + warp) * 32 + lane] =
                     make_float4(pot.x + pot.y, gx.x + gx.y, gy.x + gy.y, gz.x + gz.y);
                 at += e1 - e0;
@@ -339,8 +344,8 @@ p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
             const int i = tb + j;
             if (i < t1) {
                 const float4 s = acc[j];
-                phi[i] = s.x * inv4pi<float>();
-                if (GRAD) {
+                if (OUT & kOutPhi) phi[i] = s.x * inv4pi<float>();
+                if (OUT & kOutGrad) {
                     grad[3 * (int64_t)i] = s.y * inv4pi<float>();
                     grad[3 * (int64_t)i + 1] = s.z * inv4pi<float>();
                     grad[3 * (int64_t)i + 2] = s.w * inv4pi<float>();
@@ -550,7 +555,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
             float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
             for (int e = 0; e < ns / 2; ++e) pair_step<1, false, YUK>(pr, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
             const float f = scale * inv4pi<float>();
-            phi[i] = (pot.x + pot.y) * f + (shift ? (float)shift[b] : 0.f);   // the leaf's constant part
+            if (phi) phi[i] = (pot.x + pot.y) * f + (shift ? (float)shift[b] : 0.f);   // the leaf's constant part
             if (GRAD) {
                 grad[3 * (int64_t)i] = (gx.x + gx.y) * f;
                 grad[3 * (int64_t)i + 1] = (gy.x + gy.y) * f;
@@ -564,7 +569,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
         T pot = 0, gx = 0, gy = 0, gz = 0;
         for (int e = 0; e < ns; ++e) interact<T, false, YUK>(src[e], x.x, x.y, x.z, pot, gx, gy, gz, kappa);
         const T f = scale * inv4pi<T>();
-        phi[i] = pot * f + (shift ? (T)shift[b] : (T)0);   // the leaf's constant potential part
+        if (phi) phi[i] = pot * f + (shift ? (T)shift[b] : (T)0);   // the leaf's constant potential part
         if (GRAD) {
             grad[3 * (int64_t)i] = gx * f;
             grad[3 * (int64_t)i + 1] = gy * f;
@@ -588,10 +593,12 @@ __global__ void scatter_kernel(const T *__restrict__ near_phi, const T *__restri
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = perm[i];
-    T v = 0;
-    if (near_phi) v += near_phi[i];
-    if (far_phi) v += far_phi[i];
-    phi[o] = v;
+    if (phi) {
+        T v = 0;
+        if (near_phi) v += near_phi[i];
+        if (far_phi) v += far_phi[i];
+        phi[o] = v;
+    }
     if (grad) {
         for (int a = 0; a < 3; ++a) {
             T g = 0;
@@ -634,8 +641,9 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
                                                  kappa);
     };
     if constexpr (std::is_same<T, float>::value) {
-        if (grad) yuk ? go(p2p_f32_kernel<true, true>, grad) : go(p2p_f32_kernel<true, false>, grad);
-        else yuk ? go(p2p_f32_kernel<false, true>, nullptr) : go(p2p_f32_kernel<false, false>, nullptr);
+        if (grad && phi) yuk ? go(p2p_f32_kernel<3, true>, grad) : go(p2p_f32_kernel<3, false>, grad);
+        else if (grad) yuk ? go(p2p_f32_kernel<kOutGrad, true>, grad) : go(p2p_f32_kernel<kOutGrad, false>, grad);
+        else yuk ? go(p2p_f32_kernel<kOutPhi, true>, nullptr) : go(p2p_f32_kernel<kOutPhi, false>, nullptr);
     } else {
         if (grad) yuk ? go(p2p_kernel<T, true, true>, grad) : go(p2p_kernel<T, true, false>, grad);
         else yuk ? go(p2p_kernel<T, false, true>, nullptr) : go(p2p_kernel<T, false, false>, nullptr);
