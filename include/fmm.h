@@ -156,6 +156,71 @@ fmm_status fmm_evaluate_parts(fmm_ctx *ctx, const void *q, void *phi, void *grad
  * Same argument rules and errors as fmm_evaluate. */
 fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi);
 
+/* ---- Partitioned evaluation on virtual ranks (Section 3: Box comm-setup, Box comm-runtime) ----
+ *
+ * The tree is split at depth d_global: its level-d_global boxes are the local roots, each the
+ * root of a local tree.  n_ranks virtual ranks on this GPU each own a contiguous Morton run of
+ * local roots (the layout, balanced by point counts) and hold their own buffers: their points,
+ * the rows of their local trees, and receive rows for the ghost boxes of their local essential
+ * tree (Eq. 3).  Setup forms each rank's U and V query packets from the layout, the owners'
+ * existence answers, the neighbourhoods and the ghost points' coordinates.  An evaluation runs
+ * the local upward stage of every rank, the exchanges (U: ghost densities; V: the ghosts'
+ * compressed upward rows), the gather of the local roots' upward rows into a nominated global
+ * context, the global upward and downward passes over levels 2..d_global there, the scatter of
+ * the local roots' downward rows, and the local downward stage with the ULI.  Every output is
+ * computed by the same kernels from the same values in the same order as by fmm_evaluate, so the
+ * two agree bit for bit.  Exchanges are device copies between the ranks' buffers.
+ */
+typedef enum {
+    FMM_PARTITION_OWN = 0,           /* keys of the rank's own boxes at `level` (d_global..depth) */
+    FMM_PARTITION_GHOST_V = 1,       /* keys of its V-list ghost boxes at `level` (d_global+1..depth) */
+    FMM_PARTITION_GHOST_U = 2,       /* keys of its U-list ghost leaves (level ignored) */
+    FMM_PARTITION_NEIGHBOURS_U = 3,  /* ranks its U query packets address, ascending (level ignored) */
+    FMM_PARTITION_NEIGHBOURS_V = 4,  /* ranks its V query packets address, ascending (level ignored) */
+    FMM_PARTITION_LAYOUT = 5         /* per local root in Morton order: key | (owner rank << 32)
+                                        (rank and level ignored) */
+} fmm_partition_export_kind;
+
+typedef struct {
+    int32_t rank, n_ranks, d_global;
+    int32_t n_local_roots;         /* local roots owned */
+    int64_t first_root;            /* index of its first local root among the level-d_global boxes */
+    int64_t first_point;           /* its points are sorted positions first_point .. + n_points - 1 */
+    int64_t n_points;
+    int64_t n_boxes[11];           /* own boxes per level (levels d_global..depth; 0 above) */
+    int64_t n_ghost_v[11];         /* V-list ghost boxes per level (levels d_global+1..depth) */
+    int64_t n_ghost_u;             /* U-list ghost leaves */
+    int64_t n_ghost_points;        /* their points */
+    int64_t n_query_u, n_query_v;  /* keys in its U and V query packets (before the existence answers) */
+    int32_t n_neighbours_u, n_neighbours_v;   /* ranks its U and V packets address */
+    int64_t bytes_u;               /* received per evaluation: densities of the ghost points */
+    int64_t bytes_v;               /* received per evaluation: the V ghosts' compressed upward rows */
+    int64_t bytes_gather;          /* sent per evaluation: its local roots' upward rows */
+    int64_t bytes_scatter;         /* received per evaluation: its local roots' downward rows */
+} fmm_rank_info;
+
+/* Build the partition: 2 <= d_global < depth, 1 <= n_ranks <= the number of local roots.
+ * Needs fmm_build_tree and fmm_precompute; a new fmm_build_tree drops the partition.
+ * Errors: ESTATE, EINVAL (ranges), EUNSUPPORTED (mean_free), ENOMEM, ECUDA. */
+fmm_status fmm_partition_setup(fmm_ctx *ctx, int d_global, int n_ranks);
+
+/* fmm_evaluate through the partition (same arguments and output rules; phi may be NULL when grad
+ * is not).  ESTATE before fmm_partition_setup. */
+fmm_status fmm_partition_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad);
+
+/* Sizes, neighbourhoods and exchange volumes of one rank.  ESTATE before fmm_partition_setup;
+ * EINVAL for a rank out of range. */
+fmm_status fmm_partition_info(fmm_ctx *ctx, int rank, fmm_rank_info *info);
+
+/* Export one list of a rank (an fmm_partition_export_kind) into out[*count]; with out == NULL
+ * only *count is set.  EINVAL for a bad rank, level or kind. */
+fmm_status fmm_partition_export(fmm_ctx *ctx, int rank, int level, int kind, uint64_t *out, int64_t *count);
+
+/* Device times (ms) of the last partitioned evaluation, up to n of: densities and U exchange,
+ * local upward stage, V exchange, gather, global stage, scatter, local downward stage, ULI,
+ * output, total.  Waits for that evaluation. */
+fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n);
+
 /* Sizes of the built tree and operators.  ESTATE before fmm_build_tree. */
 fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info);
 

@@ -32,7 +32,9 @@ ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_prec
                 "fmm_evaluate", "fmm_evaluate_parts", "fmm_adjoint", "fmm_get_tree_info",
                 "fmm_export_tree", "fmm_export_level", "fmm_export_check", "fmm_last_timings",
                 "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches",
-                "fmm_measure_fp32_peak", "fmm_last_error", "fmm_destroy")
+                "fmm_measure_fp32_peak", "fmm_partition_setup", "fmm_partition_evaluate",
+                "fmm_partition_info", "fmm_partition_export", "fmm_partition_timings",
+                "fmm_last_error", "fmm_destroy")
 
 
 class Options(ctypes.Structure):
@@ -49,6 +51,25 @@ class TreeInfo(ctypes.Structure):
                 ("m2l_rank_out", ctypes.c_int32), ("n_boxes", ctypes.c_int64 * 11),
                 ("n_u_entries", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
                 ("origin", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+class RankInfo(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("n_ranks", ctypes.c_int32), ("d_global", ctypes.c_int32),
+                ("n_local_roots", ctypes.c_int32), ("first_root", ctypes.c_int64),
+                ("first_point", ctypes.c_int64), ("n_points", ctypes.c_int64),
+                ("n_boxes", ctypes.c_int64 * 11), ("n_ghost_v", ctypes.c_int64 * 11),
+                ("n_ghost_u", ctypes.c_int64), ("n_ghost_points", ctypes.c_int64),
+                ("n_query_u", ctypes.c_int64), ("n_query_v", ctypes.c_int64),
+                ("n_neighbours_u", ctypes.c_int32), ("n_neighbours_v", ctypes.c_int32),
+                ("bytes_u", ctypes.c_int64), ("bytes_v", ctypes.c_int64),
+                ("bytes_gather", ctypes.c_int64), ("bytes_scatter", ctypes.c_int64)]
+
+
+# fmm_partition_export kinds
+PARTITION_OWN, PARTITION_GHOST_V, PARTITION_GHOST_U = 0, 1, 2
+PARTITION_NEIGHBOURS_U, PARTITION_NEIGHBOURS_V, PARTITION_LAYOUT = 3, 4, 5
+PARTITION_PHASES = ("densities_u_exchange", "local_upward", "v_exchange", "gather", "global",
+                    "scatter", "local_downward", "uli", "output", "total")
 
 
 class FmmError(RuntimeError):
@@ -85,6 +106,11 @@ def lib():
             "fmm_sync": [vp],
             "fmm_sort_points_noalloc": [vp, i64, i32, vp, ctypes.c_double, vp, vp, vp],
             "fmm_measure_fp32_peak": [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+            "fmm_partition_setup": [vp, i32, i32],
+            "fmm_partition_evaluate": [vp, vp, vp, vp],
+            "fmm_partition_info": [vp, i32, ctypes.POINTER(RankInfo)],
+            "fmm_partition_export": [vp, i32, i32, i32, vp, vp],
+            "fmm_partition_timings": [vp, vp, i32],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -270,6 +296,50 @@ class FMM:
     def sync(self):
         """Wait for the context's stream; raises if a kernel reported a device-side failure."""
         self._check(lib().fmm_sync(self._ctx))
+
+    # -- partitioned evaluation on virtual ranks -------------------------------------------
+    def partition_setup(self, d_global, n_ranks):
+        """Split the built tree at d_global over n_ranks virtual ranks (needs precompute)."""
+        self._check(lib().fmm_partition_setup(self._ctx, int(d_global), int(n_ranks)))
+
+    def partition_evaluate(self, q, gradient=True, potential=True):
+        """As evaluate, through the partition: (phi, grad)."""
+        q = self._as_input(q)
+        phi = self._like(q, (self.n,)) if potential else None
+        grad = self._like(q, (self.n, 3)) if gradient else None
+        self._check(lib().fmm_partition_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad)))
+        return phi, grad
+
+    def partition_evaluate_into(self, q, phi, grad=None):
+        self._check(lib().fmm_partition_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad)))
+
+    def partition_info(self, rank):
+        ri = RankInfo()
+        self._check(lib().fmm_partition_info(self._ctx, int(rank), ctypes.byref(ri)))
+        out = {}
+        for name, _ in RankInfo._fields_:
+            v = getattr(ri, name)
+            out[name] = list(v) if name in ("n_boxes", "n_ghost_v") else v
+        return out
+
+    def partition_export(self, rank, level, kind):
+        cnt = ctypes.c_int64()
+        self._check(lib().fmm_partition_export(self._ctx, int(rank), int(level), int(kind), None,
+                                               ctypes.addressof(cnt)))
+        out = np.empty(cnt.value, np.uint64)
+        self._check(lib().fmm_partition_export(self._ctx, int(rank), int(level), int(kind), _ptr(out),
+                                               ctypes.addressof(cnt)))
+        return out
+
+    def partition_layout(self):
+        """(local root keys in Morton order, owner rank of each)."""
+        v = self.partition_export(0, 0, PARTITION_LAYOUT)
+        return (v & np.uint64(0xffffffff)).astype(np.int64), (v >> np.uint64(32)).astype(np.int64)
+
+    def partition_timings(self):
+        ms = np.zeros(len(PARTITION_PHASES), np.float64)
+        self._check(lib().fmm_partition_timings(self._ctx, _ptr(ms), len(ms)))
+        return dict(zip(PARTITION_PHASES, ms.tolist()))
 
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""

@@ -89,6 +89,10 @@ void free_async(P *&p, cudaStream_t s) {
     p = nullptr;
 }
 
+}  // namespace
+
+namespace fmm {
+
 void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
@@ -232,6 +236,10 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     return FMM_OK;
 }
 
+}  // namespace fmm
+
+namespace {
+
 // device view of a caller array: either the pointer itself or a staging buffer
 struct Staged {
     void *dev = nullptr;
@@ -314,6 +322,29 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
 
 // `out`: the output that must be present (the potentials, or for a gradient-only evaluation the
 // gradients)
+template <typename T>
+fmm_status run_partition(fmm_ctx *ctx, const void *q, void *phi, void *grad) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n;
+    Staged sq, sphi, sgrad;
+    fmm_status st;
+    if ((st = stage(ctx, q, n * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
+    if (phi && (st = stage(ctx, phi, n * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
+    if (grad && (st = stage(ctx, grad, 3 * n * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
+    st = split_run<T>(ctx, (const T *)sq.dev, (T *)sphi.dev, (T *)sgrad.dev);
+    if (st != FMM_OK) return st;
+    cudaError_t e;
+    if (phi && sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if (grad && sgrad.host &&
+        (e = cudaMemcpyAsync(grad, sgrad.dev, 3 * n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "device-to-host copy");
+    if (sq.host || (phi && sphi.host) || (grad && sgrad.host)) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    }
+    return FMM_OK;
+}
+
 fmm_status check_ready(fmm_ctx *ctx, const void *q, const void *out) {
     if (!ctx) return FMM_EINVAL;
     if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
@@ -406,6 +437,7 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n) {
     if (!xyz) return fail(ctx, FMM_EINVAL, "null coordinate pointer");
     if (n <= 0 || n > 2147483647LL) return fail(ctx, FMM_EINVAL, "n must be in [1, 2^31 - 1]");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    split_free(ctx);   // a partition belongs to the tree it was built on
     free_tree(ctx);
     ctx->n = n;
     const size_t bytes = (size_t)n * 3 * elem_size(ctx);
@@ -524,6 +556,41 @@ fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
     cudaFreeAsync(tmp, ctx->stream);
     if (st == FMM_OK) ctx->last_adjoint = true;
     return st;
+}
+
+fmm_status fmm_partition_setup(fmm_ctx *ctx, int d_global, int n_ranks) {
+    if (!ctx) return FMM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    try {
+        return split_setup(ctx, d_global, n_ranks);
+    } catch (const std::bad_alloc &) {
+        split_free(ctx);
+        return fail(ctx, FMM_ENOMEM, "host memory exhausted in the partition setup");
+    }
+}
+
+fmm_status fmm_partition_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad) {
+    if (!ctx) return FMM_EINVAL;
+    if (!ctx->split) return fail(ctx, FMM_ESTATE, "fmm_partition_setup has not been called");
+    if (!q || (!phi && !grad)) return fail(ctx, FMM_EINVAL, "null density or output pointer");
+    if (grad && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    return ctx->fp64 ? run_partition<double>(ctx, q, phi, grad) : run_partition<float>(ctx, q, phi, grad);
+}
+
+fmm_status fmm_partition_info(fmm_ctx *ctx, int rank, fmm_rank_info *info) {
+    if (!ctx || !info) return FMM_EINVAL;
+    return split_info(ctx, rank, info);
+}
+
+fmm_status fmm_partition_export(fmm_ctx *ctx, int rank, int level, int kind, uint64_t *out, int64_t *count) {
+    if (!ctx) return FMM_EINVAL;
+    return split_export(ctx, rank, level, kind, out, count);
+}
+
+fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n) {
+    if (!ctx || !ms || n < 0) return FMM_EINVAL;
+    return split_timings(ctx, ms, n);
 }
 
 fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
@@ -670,6 +737,7 @@ void fmm_destroy(fmm_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    split_free(ctx);
     free_tree(ctx);
     free_workspace(ctx);
     free_ops(ctx);

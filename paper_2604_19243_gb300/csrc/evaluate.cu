@@ -87,32 +87,43 @@ T *rows_at(void *base, const fmm_ctx *ctx, int level, int ld) {
 }  // namespace
 
 template <typename T>
-cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
-    const int d = ctx->opt.depth;
-    // operators of level l (one set for Laplace; per level for the modified Helmholtz kernel)
-    auto O = [&](int l) -> const OpSet & { return adjoint ? ctx->adj[l] : ctx->fwd[l]; };
-    const OpSet &o = O(d);   // shapes, and the leaf closing
-    const int nsp = ctx->nsp;
-    const int kw = ctx->ws_kw;   // row stride of Ut / Ct
-    void *A = adjoint ? ctx->Dc : ctx->Uc;   // upward-side array of this direction
-    void *B = adjoint ? ctx->Uc : ctx->Dc;   // downward-side array
+FarSteps<T>::FarSteps(fmm_ctx *c, bool adj) : ctx(c), adjoint(adj) {
+    d = ctx->opt.depth;
+    nsp = ctx->nsp;
+    kw = ctx->ws_kw;
+    A = adjoint ? ctx->Dc : ctx->Uc;
+    B = adjoint ? ctx->Uc : ctx->Dc;
+    f16 = ctx->opt.precision == FMM_FP16X3;
+    nck_s = (nsp + 63) / 64, nck_k = (kw + 63) / 64;
+}
+
+// FMM_FP16X3: every contraction reads FP16 planes, which the step producing its input writes
+// beside (or instead of) the FP32 rows: level l's rows of the upward side (UpP), of the
+// downward side (DnP), of the compressed vectors (UtP) and of the stencil output (CtP)
+template <typename T> unsigned char *FarSteps<T>::upP(int l) const {
+    return (unsigned char *)ctx->UpP + base(l) * nsp * 2;
+}
+template <typename T> unsigned char *FarSteps<T>::dnP(int l) const {
+    return (unsigned char *)ctx->DnP + base(l) * nsp * 2;
+}
+template <typename T> unsigned char *FarSteps<T>::ctP(int l) const {
+    return (unsigned char *)ctx->CtP + base(l) * kw * 2;
+}
+template <typename T> float *FarSteps<T>::upS(int l) const { return ctx->Ups + base(l) * nck_s; }
+template <typename T> float *FarSteps<T>::dnS(int l) const { return ctx->Dns + base(l) * nck_s; }
+template <typename T> float *FarSteps<T>::ctS(int l) const { return ctx->Cts + base(l) * nck_k; }
+
+// operators of level l (one set for Laplace; per level for the modified Helmholtz kernel)
+template <typename T> const OpSet &FarSteps<T>::O(int l) const { return adjoint ? ctx->adj[l] : ctx->fwd[l]; }
+
+// S2U (forward) or D2T^T and the transposed closing (adjoint) on the leaves, and the leaf
+// rows' planes
+template <typename T>
+cudaError_t FarSteps<T>::leaf_in(cudaStream_t s) {
+    const OpSet &o = O(d);
     const T *grid = (const T *)ctx->grid_dev;
     const double r_leaf = ctx->side / (double)(1 << d) * 0.5;
     const int dir = adjoint ? 1 : 0;
-    // FMM_FP16X3: every contraction reads FP16 planes, which the step producing its input writes
-    // beside (or instead of) the FP32 rows: level l's rows of the upward side (UpP), of the
-    // downward side (DnP), of the compressed vectors (UtP) and of the stencil output (CtP)
-    const bool f16 = ctx->opt.precision == FMM_FP16X3;
-    const int nck_s = (nsp + 63) / 64, nck_k = (kw + 63) / 64;
-    auto base = [&](int l) { return (size_t)ctx->lev[l].row_base; };
-    auto upP = [&](int l) { return (unsigned char *)ctx->UpP + base(l) * nsp * 2; };
-    auto dnP = [&](int l) { return (unsigned char *)ctx->DnP + base(l) * nsp * 2; };
-    auto ctP = [&](int l) { return (unsigned char *)ctx->CtP + base(l) * kw * 2; };
-    auto upS = [&](int l) { return ctx->Ups + base(l) * nck_s; };
-    auto dnS = [&](int l) { return ctx->Dns + base(l) * nck_s; };
-    auto ctS = [&](int l) { return ctx->Cts + base(l) * nck_k; };
-
-    // leaf stage
     if (!adjoint) {
         FMM_CUDA_TRY(launch_leaf_check<T>(ctx, grid, rows_at<T>(A, ctx, d, nsp), s));
     } else {
@@ -131,92 +142,106 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
     if (f16)
         FMM_CUDA_TRY(launch_rows_to_planes((const float *)rows_at<T>(A, ctx, d, nsp), nsp, ctx->lev[d].n, nsp, upP(d),
                                            ctx->upp_plane, nsp, upS(d), nck_s, s));
-    cudaEventRecord(ctx->ev[2], s);
-    // upward sweep
-    for (int l = d - 1; l >= 2; --l) {
-        GemmCall c;
-        c.mode = GM_CHILDREN, c.level = l, c.n_out = nsp;
-        c.X0 = rows_at<T>(A, ctx, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
-        c.W0 = O(l).up[0], c.w_stride = (int64_t)nsp * nsp;
-        c.Y = rows_at<T>(A, ctx, l, nsp), c.ldy = nsp;
-        if (f16) {
-            c.Xp = upP(l + 1), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l + 1), c.xp_scale_ld = nck_s;
-            c.Yp = upP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = upS(l), c.yp_scale_ld = nck_s;
-        }
-        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_UP + dir * OP_COUNT, s));
+    return cudaSuccess;
+}
+
+// U2U: level l's upward-side rows from level l + 1's
+template <typename T>
+cudaError_t FarSteps<T>::up(int l, cudaStream_t s) {
+    GemmCall c;
+    c.mode = GM_CHILDREN, c.level = l, c.n_out = nsp;
+    c.X0 = rows_at<T>(A, ctx, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
+    c.W0 = O(l).up[0], c.w_stride = (int64_t)nsp * nsp;
+    c.Y = rows_at<T>(A, ctx, l, nsp), c.ldy = nsp;
+    if (f16) {
+        c.Xp = upP(l + 1), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l + 1), c.xp_scale_ld = nck_s;
+        c.Yp = upP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = upS(l), c.yp_scale_ld = nck_s;
     }
-    cudaEventRecord(ctx->ev[3], s);
-    // VLI
-    // VLI of every level on its own stream (levels are independent once the upward pass is
-    // done); the downward sweep below waits for each level's VLI just before using it.
-    // Tensor-core modes pass the compressed vectors between the two GEMMs as split planes, so
-    // that the stencil copies its source rows instead of converting them itself.
+    return gemm<T>(ctx, c, OP_UP + (adjoint ? OP_COUNT : 0), s);
+}
+
+// VLI compress: Ut_l = Vi^T U_l.  Tensor-core modes pass the compressed vectors to the stencil
+// as split planes, so that it copies its source rows instead of converting them itself.
+template <typename T>
+cudaError_t FarSteps<T>::compress(int l, cudaStream_t s) {
+    const OpSet &o = O(l);
+    GemmCall c;
+    c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
+    c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
+    c.Y = ctx->tensor ? nullptr : rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;   // tensor modes: planes only
+    if (ctx->tensor) {
+        c.Yp = utP(l), c.yp_ld = kw, c.yp_plane = ctx->utp_plane;
+        c.yp_scale = utS(l), c.yp_scale_ld = nck_k;
+    }
+    if (f16) c.Xp = upP(l), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l), c.xp_scale_ld = nck_s;
+    return gemm<T>(ctx, c, OP_COMPRESS + (adjoint ? OP_COUNT : 0), s);
+}
+
+template <typename T> unsigned char *FarSteps<T>::utP(int l) const {
     const int pesz = ctx->opt.precision == FMM_TF32X3 ? 4 : 2;
-    FMM_CUDA_TRY(cudaEventRecord(ctx->fork_ev[0], s));
-    for (int l = 2; l <= d; ++l) {
-        cudaStream_t ls = ctx->aux[l];
-        FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
-        GemmCall c;
-        c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
-        c.X0 = rows_at<T>(A, ctx, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = O(l).compress;
-        c.Y = ctx->tensor ? nullptr : rows_at<T>(ctx->Ut, ctx, l, kw), c.ldy = kw;   // tensor modes: planes only
-        unsigned char *planes = nullptr;
-        float *scales = ctx->Uscale ? ctx->Uscale + base(l) * nck_k : nullptr;
-        if (ctx->tensor) {
-            planes = (unsigned char *)ctx->UtP + base(l) * kw * pesz;
-            c.Yp = planes, c.yp_ld = kw, c.yp_plane = ctx->utp_plane;
-            c.yp_scale = scales, c.yp_scale_ld = nck_k;
-        }
-        if (f16) c.Xp = upP(l), c.xp_ld = nsp, c.xp_plane = ctx->upp_plane, c.xp_scale = upS(l), c.xp_scale_ld = nck_s;
-        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_COMPRESS + dir * OP_COUNT, ls));
-        GemmCall st;
-        st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
-        st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
-        st.W0 = O(l).stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
-        st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
-        if (ctx->tensor) {
-            st.Xp = planes, st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
-            st.xp_scale = scales, st.xp_scale_ld = nck_k;
-        }
-        if (f16) {   // the decompress reads the stencil output as planes
-            st.Y = nullptr;
-            st.Yp = ctP(l), st.yp_ld = kw, st.yp_plane = ctx->ctp_plane, st.yp_scale = ctS(l), st.yp_scale_ld = nck_k;
-        }
-        FMM_CUDA_TRY(gemm<T>(ctx, st, OP_STENCIL + dir * OP_COUNT, ls));
-        FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
+    return (unsigned char *)ctx->UtP + base(l) * kw * pesz;
+}
+template <typename T> float *FarSteps<T>::utS(int l) const { return ctx->Uscale ? ctx->Uscale + base(l) * nck_k : nullptr; }
+
+// VLI stencil: Ct_l[b] = sum_t C_t Ut_l[b + t]
+template <typename T>
+cudaError_t FarSteps<T>::stencil(int l, cudaStream_t s) {
+    const OpSet &o = O(l);
+    GemmCall st;
+    st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
+    st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
+    st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
+    st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
+    if (ctx->tensor) {
+        st.Xp = utP(l), st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
+        st.xp_scale = utS(l), st.xp_scale_ld = nck_k;
     }
-    // downward sweep: decompress fused with the parent's contribution
-    for (int l = 2; l <= d; ++l) {
-        FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
-        if (l == d) cudaEventRecord(ctx->ev[4], s);
-        GemmCall c;
-        c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
-        c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = O(l).decompress;
-        if (l >= 3) {   // D2D from the parent level: that level's operators
-            c.X1 = rows_at<T>(B, ctx, l - 1, nsp), c.ldx1 = nsp, c.k1 = nsp;
-            c.W1_by_cls = O(l - 1).down;
-        }
-        c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
-        if (f16) {
-            c.Xp = ctP(l), c.xp_ld = kw, c.xp_plane = ctx->ctp_plane, c.xp_scale = ctS(l), c.xp_scale_ld = nck_k;
-            if (l >= 3)
-                c.Xp1 = dnP(l - 1), c.xp1_ld = nsp, c.xp1_plane = ctx->upp_plane, c.xp1_scale = dnS(l - 1),
-                c.xp1_scale_ld = nck_s;
-            if (l < d)   // the leaves' rows have no children to read them as planes
-                c.Yp = dnP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = dnS(l), c.yp_scale_ld = nck_s;
-        }
-        FMM_CUDA_TRY(gemm<T>(ctx, c, OP_DECOMPRESS + dir * OP_COUNT, s));
-        if (!adjoint && ctx->opt.mean_free) {
-            const LevelTables &L = ctx->lev[l];
-            double *cm = (double *)ctx->Cmean;
-            remove_mean_kernel<T><<<(unsigned)((L.n + 7) / 8), 256, 0, s>>>(
-                rows_at<T>(B, ctx, l, nsp), (int)L.n, ctx->ns, nsp, L.parent,
-                l >= 3 ? cm + ctx->lev[l - 1].row_base : nullptr, cm + L.row_base);
-            count_launch();
-            FMM_CUDA_TRY(cudaGetLastError());
-        }
+    if (f16) {   // the decompress reads the stencil output as planes
+        st.Y = nullptr;
+        st.Yp = ctP(l), st.yp_ld = kw, st.yp_plane = ctx->ctp_plane, st.yp_scale = ctS(l), st.yp_scale_ld = nck_k;
     }
-    // leaf output
+    return gemm<T>(ctx, st, OP_STENCIL + (adjoint ? OP_COUNT : 0), s);
+}
+
+// downward step of level l: decompress fused with the parent's D2D contribution (l >= 3)
+template <typename T>
+cudaError_t FarSteps<T>::down(int l, cudaStream_t s) {
+    const OpSet &o = O(d);
+    GemmCall c;
+    c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
+    c.X0 = rows_at<T>(ctx->Ct, ctx, l, kw), c.ldx0 = kw, c.k0 = o.koutp, c.W0 = O(l).decompress;
+    if (l >= 3) {   // D2D from the parent level: that level's operators
+        c.X1 = rows_at<T>(B, ctx, l - 1, nsp), c.ldx1 = nsp, c.k1 = nsp;
+        c.W1_by_cls = O(l - 1).down;
+    }
+    c.Y = rows_at<T>(B, ctx, l, nsp), c.ldy = nsp;
+    if (f16) {
+        c.Xp = ctP(l), c.xp_ld = kw, c.xp_plane = ctx->ctp_plane, c.xp_scale = ctS(l), c.xp_scale_ld = nck_k;
+        if (l >= 3)
+            c.Xp1 = dnP(l - 1), c.xp1_ld = nsp, c.xp1_plane = ctx->upp_plane, c.xp1_scale = dnS(l - 1),
+            c.xp1_scale_ld = nck_s;
+        if (l < d)   // the leaves' rows have no children to read them as planes
+            c.Yp = dnP(l), c.yp_ld = nsp, c.yp_plane = ctx->upp_plane, c.yp_scale = dnS(l), c.yp_scale_ld = nck_s;
+    }
+    FMM_CUDA_TRY(gemm<T>(ctx, c, OP_DECOMPRESS + (adjoint ? OP_COUNT : 0), s));
+    if (!adjoint && ctx->opt.mean_free) {
+        const LevelTables &L = ctx->lev[l];
+        double *cm = (double *)ctx->Cmean;
+        remove_mean_kernel<T><<<(unsigned)((L.n + 7) / 8), 256, 0, s>>>(
+            rows_at<T>(B, ctx, l, nsp), (int)L.n, ctx->ns, nsp, L.parent,
+            l >= 3 ? cm + ctx->lev[l - 1].row_base : nullptr, cm + L.row_base);
+        count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+// leaf output: closing pseudo-inverse and D2T (forward), or the S2U^T evaluation (adjoint)
+template <typename T>
+cudaError_t FarSteps<T>::leaf_out(T *far_phi, T *far_grad, cudaStream_t s) {
+    const OpSet &o = O(d);
+    const T *grid = (const T *)ctx->grid_dev;
+    const double r_leaf = ctx->side / (double)(1 << d) * 0.5;
     if (!adjoint) {
         GemmCall c1;
         c1.mode = GM_IDENTITY, c1.level = d, c1.n_out = o.rclp;
@@ -228,16 +253,40 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         c2.X0 = ctx->Yc, c2.ldx0 = o.rclp, c2.k0 = o.rclp, c2.W0 = o.close2;
         c2.Y = ctx->Dq, c2.ldy = nsp;
         FMM_CUDA_TRY(gemm<T>(ctx, c2, OP_CLOSE2, s));
-        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, (const T *)ctx->Dq, nsp, (T)1, far_phi, far_grad, s,
-                                         ctx->opt.mean_free ? (const double *)ctx->Cmean + ctx->lev[d].row_base
-                                                            : nullptr));
-    } else {
-        FMM_CUDA_TRY(launch_leaf_eval<T>(ctx, grid, rows_at<T>(B, ctx, d, nsp), nsp, (T)1, far_phi,
-                                         nullptr, s, nullptr));
+        return launch_leaf_eval<T>(ctx, grid, (const T *)ctx->Dq, nsp, (T)1, far_phi, far_grad, s,
+                                   ctx->opt.mean_free ? (const double *)ctx->Cmean + ctx->lev[d].row_base : nullptr);
     }
-    return cudaSuccess;
+    return launch_leaf_eval<T>(ctx, grid, rows_at<T>(B, ctx, d, nsp), nsp, (T)1, far_phi, nullptr, s, nullptr);
 }
 
+template <typename T>
+cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
+    FarSteps<T> f(ctx, adjoint);
+    const int d = f.d;
+    FMM_CUDA_TRY(f.leaf_in(s));
+    cudaEventRecord(ctx->ev[2], s);
+    for (int l = d - 1; l >= 2; --l) FMM_CUDA_TRY(f.up(l, s));
+    cudaEventRecord(ctx->ev[3], s);
+    // VLI of every level on its own stream (levels are independent once the upward pass is
+    // done); the downward sweep below waits for each level's VLI just before using it
+    FMM_CUDA_TRY(cudaEventRecord(ctx->fork_ev[0], s));
+    for (int l = 2; l <= d; ++l) {
+        cudaStream_t ls = ctx->aux[l];
+        FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
+        FMM_CUDA_TRY(f.compress(l, ls));
+        FMM_CUDA_TRY(f.stencil(l, ls));
+        FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
+    }
+    for (int l = 2; l <= d; ++l) {
+        FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
+        if (l == d) cudaEventRecord(ctx->ev[4], s);
+        FMM_CUDA_TRY(f.down(l, s));
+    }
+    return f.leaf_out(far_phi, far_grad, s);
+}
+
+template struct FarSteps<float>;
+template struct FarSteps<double>;
 template cudaError_t run_far<float>(fmm_ctx *, bool, float *, float *, cudaStream_t);
 template cudaError_t run_far<double>(fmm_ctx *, bool, double *, double *, cudaStream_t);
 

@@ -74,6 +74,7 @@ struct TcOpSet {
 };
 
 struct HostOps;  // FP64 host operators (precompute.cpp)
+struct SplitState;  // virtual-rank partition (split.cu)
 
 // Tile of output rows for the GEMM kernels: rows [row0, row0+nrows) of a level's row list,
 // all of one child octant class `cls` (or -1 when not class-ordered); `mask` indexes the
@@ -180,6 +181,8 @@ struct fmm_ctx {
     std::vector<fmm::TcOpSet *> tc_owned;
     std::vector<void *> op_allocs;
 
+    fmm::SplitState *split = nullptr;   // partitioned evaluation on virtual ranks (split.cu)
+
     bool last_adjoint = false;  // what the last evaluation left in the workspaces
     bool last_far = false;
 
@@ -224,8 +227,26 @@ std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, doubl
 // Unit surface grid of order p (lexicographic), [n x 3] in [-1,1]^3.
 std::vector<double> surface_grid(int p);
 
+// ---- api.cpp ----
+// Workspaces of a context for its tree (allocated once, reused while they fit; tiles rebuilt).
+fmm_status ensure_workspace(fmm_ctx *ctx);
+void free_workspace(fmm_ctx *ctx);
+
+// ---- split.cu ----
+// Partitioned evaluation on virtual ranks; the message of a failure goes to ctx->err.
+fmm_status split_setup(fmm_ctx *ctx, int d_global, int n_ranks);
+template <typename T>
+fmm_status split_run(fmm_ctx *ctx, const T *q, T *phi, T *grad);
+void split_free(fmm_ctx *ctx);
+fmm_status split_info(fmm_ctx *ctx, int rank, fmm_rank_info *out);
+fmm_status split_export(fmm_ctx *ctx, int rank, int level, int kind, uint64_t *out, int64_t *count);
+fmm_status split_timings(fmm_ctx *ctx, double *ms, int n);
+
 // ---- tree.cu ----
 cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz);
+// Class slot table: for child octant c, the 189 transfer indices (and packed deltas) of the
+// V-list sources whose parent is adjacent to the target's parent.
+void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas);
 cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, int32_t *tv,
                            int64_t *count);
 cudaError_t build_tiles(fmm_ctx *ctx, int tile_m);
@@ -296,5 +317,32 @@ void tc_free(fmm_ctx *ctx);
 cudaError_t upload_operators(fmm_ctx *ctx);
 template <typename T>
 cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s);
+// The far-field steps of one context, each on the given stream (run_far orders them for a whole
+// tree; the partitioned evaluation orders them across rank contexts).
+template <typename T>
+struct FarSteps {
+    fmm_ctx *ctx;
+    bool adjoint;
+    int d = 0, nsp = 0, kw = 0, nck_s = 0, nck_k = 0;
+    bool f16 = false;
+    void *A = nullptr, *B = nullptr;   // upward- and downward-side rows of this direction
+    FarSteps(fmm_ctx *c, bool adj);
+    cudaError_t leaf_in(cudaStream_t s);                 // S2U (+ leaf planes)
+    cudaError_t up(int l, cudaStream_t s);               // U2U into level l
+    cudaError_t compress(int l, cudaStream_t s);         // VLI compress of level l
+    cudaError_t stencil(int l, cudaStream_t s);          // VLI stencil of level l
+    cudaError_t down(int l, cudaStream_t s);             // decompress + D2D into level l
+    cudaError_t leaf_out(T *far_phi, T *far_grad, cudaStream_t s);   // closing + D2T
+    size_t base(int l) const { return (size_t)ctx->lev[l].row_base; }
+    const OpSet &O(int l) const;
+    unsigned char *upP(int l) const;
+    unsigned char *dnP(int l) const;
+    unsigned char *ctP(int l) const;
+    unsigned char *utP(int l) const;
+    float *upS(int l) const;
+    float *dnS(int l) const;
+    float *ctS(int l) const;
+    float *utS(int l) const;
+};
 
 }  // namespace fmm

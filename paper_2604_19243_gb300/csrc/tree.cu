@@ -457,6 +457,8 @@ __global__ void octant_keys(const uint32_t *keys, int64_t n, uint32_t *oct, int 
     idx[i] = (int)i;
 }
 
+}  // namespace
+
 // Class slot table: for child octant c, the 189 transfer indices t (ascending) whose source
 // box has a parent adjacent to (or equal to) the target's parent.
 void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas) {
@@ -484,6 +486,8 @@ void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas) {
                 }
     }
 }
+
+namespace {
 
 // Per tile: bit s of masks[tile*6 + s/32] is set when some row of the tile has a non-empty
 // source box for class slot s.
