@@ -202,6 +202,82 @@ def run_reference(args, w):
     return 0
 
 
+def run_partition_bench(args, w, fmm, x, q, phi, grad, flush, stream, ws, rank):
+    """Partitioned evaluation (Section 3) on the workload's tree, one entry per rank count.
+
+    The step is one evaluation (potential + gradient) with the tree and the partition built
+    beforehand (the paper's setup is a one-time cost, reported here as `setup_s`); the
+    unpartitioned evaluation on the same tree is timed the same way beside it."""
+    import torch
+    dg_s, ps = args.partition.split(":")
+    dg = int(dg_s)
+    ranks = [int(v) for v in ps.split(",")]
+    fmm.build_tree(x)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    base_ms = timed(lambda: fmm.evaluate_into(q, phi, grad))
+    ref_phi, ref_grad = phi.clone(), grad.clone()
+    info = fmm.info()
+    runs = []
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0")
+    clocks.start()
+    for P in ranks:
+        t0 = time.perf_counter()
+        fmm.partition_setup(dg, P)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        ms = timed(lambda: fmm.partition_evaluate_into(q, phi, grad))
+        phases = fmm.partition_timings()
+        same = bool(torch.equal(phi, ref_phi) and torch.equal(grad, ref_grad))
+        per = [fmm.partition_info(r) for r in range(P)]
+
+        def agg(key):
+            vals = [sum(p[key]) if isinstance(p[key], list) else p[key] for p in per]
+            return {"max": max(vals), "mean": sum(vals) / P}
+        runs.append({"ranks": P, "ms": ms, "points_per_s": w.n / (ms * 1e-3), "setup_s": round(setup_s, 3),
+                     "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+                     "bit_identical_to_unpartitioned": same,
+                     "local_roots": agg("n_local_roots"), "points": agg("n_points"),
+                     "ghost_u_leaves": agg("n_ghost_u"), "ghost_points": agg("n_ghost_points"),
+                     "ghost_v_boxes": agg("n_ghost_v"),
+                     "neighbours_u": agg("n_neighbours_u"), "neighbours_v": agg("n_neighbours_v"),
+                     "bytes_u": agg("bytes_u"), "bytes_v": agg("bytes_v"),
+                     "bytes_gather": agg("bytes_gather"), "bytes_scatter": agg("bytes_scatter")})
+    clk = clocks.stop()
+    last = runs[-1]
+    line = {"metric": METRIC.replace("at N=8M", "at N=8M, partitioned over virtual ranks"),
+            "value": last["points_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": last["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
+                       "precision": args.precision, "kernel": args.kernel, "d_global": dg,
+                       "local_roots": info["n_boxes"][dg], "ranks": ranks,
+                       "step": "evaluate (potential+gradient) on a built tree and partition",
+                       "l2": "flushed (256 MB write) between steps"},
+            "unpartitioned_ms": base_ms, "partition": runs, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fmm.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +292,9 @@ def main():
                     help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r)")
     ap.add_argument("--outputs", default="potential+gradient", choices=["potential+gradient", "gradient"],
                     help="gradient: the gradient-only (force) evaluation, phi = NULL")
+    ap.add_argument("--partition", default=None, metavar="DG:P1,P2,...",
+                    help="time the partitioned evaluation on virtual ranks (tree split at depth DG, "
+                         "P ranks) beside the unpartitioned one, for every P listed")
     ap.add_argument("--kappa", type=float, default=None,
                     help="yukawa screening constant (default 3, i.e. kappa r = 0.023 at the leaves "
                          "and 0.75 at level 2 of the default workload)")
@@ -255,6 +334,8 @@ def main():
                   stream=stream.cuda_stream, kernel=args.kernel, kappa=args.kappa)
     fmm.precompute()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if args.partition:
+        return run_partition_bench(args, w, fmm, x, q, phi, grad, flush, stream, ws, rank)
 
     grad_only = args.outputs == "gradient"
     phi_out = None if grad_only else phi

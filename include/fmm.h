@@ -217,8 +217,14 @@ fmm_status fmm_partition_info(fmm_ctx *ctx, int rank, fmm_rank_info *info);
 fmm_status fmm_partition_export(fmm_ctx *ctx, int rank, int level, int kind, uint64_t *out, int64_t *count);
 
 /* Device times (ms) of the last partitioned evaluation, up to n of: densities and U exchange,
- * local upward stage, V exchange, gather, global stage, scatter, local downward stage, ULI,
- * output, total.  Waits for that evaluation. */
+ * local upward stage, V exchange, gather, global stage, scatter, local downward stage, the part
+ * of the ULI still running after it (the ULI runs beside all the stages from the local upward
+ * one on), output, total.  Waits for that evaluation.
+ *
+ * Concurrency: the ranks' chains of launches run on a pool of far-field streams and their ULI
+ * on near-field streams of lower priority; each output mode's evaluation is captured once as a
+ * CUDA graph (densities read from, and outputs written to, buffers of the partition, with one
+ * device copy in and out per call) and replayed. */
 fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n);
 
 /* Sizes of the built tree and operators.  ESTATE before fmm_build_tree. */

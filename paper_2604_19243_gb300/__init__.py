@@ -69,7 +69,7 @@ class RankInfo(ctypes.Structure):
 PARTITION_OWN, PARTITION_GHOST_V, PARTITION_GHOST_U = 0, 1, 2
 PARTITION_NEIGHBOURS_U, PARTITION_NEIGHBOURS_V, PARTITION_LAYOUT = 3, 4, 5
 PARTITION_PHASES = ("densities_u_exchange", "local_upward", "v_exchange", "gather", "global",
-                    "scatter", "local_downward", "uli", "output", "total")
+                    "scatter", "local_downward", "uli_tail", "output", "total")
 
 
 class FmmError(RuntimeError):

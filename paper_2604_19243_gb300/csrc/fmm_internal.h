@@ -202,6 +202,7 @@ namespace fmm {
 // Process-wide count of kernels launched by the library (every launch site calls it).
 void count_launch();
 long long launches();
+void count_launches(long long n);   // the kernels of a replayed CUDA graph
 
 // ---- precompute.cpp ----
 struct HostOps {

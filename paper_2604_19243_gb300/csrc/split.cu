@@ -67,6 +67,12 @@ __global__ void copy_rows_kernel(const RowCopy *__restrict__ e, int n, unsigned 
     for (int i = lane; i < words; i += 32) dst[i] = src[i];
 }
 
+// Dense key -> row table of one level of a rank's local essential tree (set to -1 before).
+__global__ void let_dense_kernel(const uint32_t *__restrict__ keys, int n, int *__restrict__ dense) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dense[keys[i]] = i;
+}
+
 // One block per ghost leaf: whole points (setup) or densities only (every evaluation).
 template <typename P4>
 __global__ void copy_pts_kernel(const PtsCopy *__restrict__ e, P4 *const *__restrict__ base, int whole) {
@@ -125,6 +131,16 @@ struct SplitState {
     std::vector<void *> allocs;        // the tables above
     cudaEvent_t ev[10] = {};
     bool timed = false;
+    // Concurrency: the ranks' chains of launches run on a pool of far-field streams (highest
+    // priority) and their ULI on near-field streams (lowest), forked from and joined into a
+    // capture stream; the whole evaluation is captured once per output mode as a CUDA graph
+    // that reads the densities from q_in and writes phi_out / grad_out.
+    static constexpr int kFar = 16, kNear = 4;
+    cudaStream_t cap = nullptr, far_s[kFar] = {}, near_s[kNear] = {};
+    cudaEvent_t fork = nullptr, ev_far[kFar] = {}, ev_near[kNear] = {}, ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec[4] = {};      // by output mode: 1 potentials, 2 gradients, 3 both
+    long long graph_launches[4] = {};  // kernels in each graph
+    void *q_in = nullptr, *phi_out = nullptr, *grad_out = nullptr;
 };
 
 namespace {
@@ -205,6 +221,19 @@ void split_free(fmm_ctx *ctx) {
     for (void *p : S->allocs) cudaFreeAsync(p, ctx->stream);
     for (auto &e : S->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &g : S->exec)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaStream_t st : S->far_s)
+        if (st) cudaStreamDestroy(st);
+    for (cudaStream_t st : S->near_s)
+        if (st) cudaStreamDestroy(st);
+    if (S->cap) cudaStreamDestroy(S->cap);
+    for (cudaEvent_t ev : S->ev_far)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : S->ev_near)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {S->fork, S->ev_in, S->ev_out})
+        if (ev) cudaEventDestroy(ev);
     cudaStreamSynchronize(ctx->stream);
     delete S;
     ctx->split = nullptr;
@@ -359,7 +388,7 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
     // local essential trees of the ranks: host tables
     struct LetHost {
         std::vector<uint32_t> keys[kMaxDepth + 1];
-        std::vector<int> dense[kMaxDepth + 1], parent[kMaxDepth + 1], child[kMaxDepth + 1], cls[kMaxDepth + 1];
+        std::vector<int> parent[kMaxDepth + 1], child[kMaxDepth + 1], cls[kMaxDepth + 1];
         int cls_off[kMaxDepth + 1][9] = {};
         int64_t row_base[kMaxDepth + 1] = {};
         int64_t rows = 0;
@@ -385,8 +414,6 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
             K.assign(keys[l].begin() + lo, keys[l].begin() + hi);
             K.insert(K.end(), gh.begin(), gh.end());
             const int64_t n_let = (int64_t)K.size();
-            H.dense[l].assign((size_t)1 << (3 * l), -1);
-            for (int64_t i = 0; i < n_let; ++i) H.dense[l][K[i]] = (int)i;
             H.parent[l].assign(n_let, -1);
             if (l > dg)
                 for (int64_t i = 0; i < n_own; ++i) H.parent[l][i] = (int)(par[l][lo + i] - S->lo[r][l - 1]);
@@ -479,7 +506,18 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
             L.row_base = H.row_base[l];
             std::memcpy(L.cls_off, H.cls_off[l], sizeof(L.cls_off));
             e = upload(H.keys[l], &L.keys, own, s);
-            if (e == cudaSuccess) e = upload(H.dense[l], &L.dense, own, s);
+            if (e == cudaSuccess) {   // the dense table is filled on the device (8^l entries)
+                const size_t nd = (size_t)1 << (3 * l);
+                e = pool_alloc((void **)&L.dense, nd * sizeof(int), s);
+                if (e == cudaSuccess) own.push_back(L.dense);
+                if (e == cudaSuccess) e = cudaMemsetAsync(L.dense, 0xff, nd * sizeof(int), s);
+                const int n_let = (int)H.keys[l].size();
+                if (e == cudaSuccess && n_let) {
+                    let_dense_kernel<<<(n_let + 255) / 256, 256, 0, s>>>(L.keys, n_let, L.dense);
+                    count_launch();
+                    e = cudaGetLastError();
+                }
+            }
             if (e == cudaSuccess) e = upload(H.parent[l], &L.parent, own, s);
             if (e == cudaSuccess && l < d) e = upload(H.child[l], &L.child, own, s);
             if (e == cudaSuccess) e = upload(H.cls[l], &L.cls_rows, own, s);
@@ -606,6 +644,28 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
     }
     for (auto &ev : S->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    {   // streams and events of the concurrent schedule; fixed input and output buffers
+        int lo_p = 0, hi_p = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&S->cap, cudaStreamNonBlocking, hi_p);
+        for (int k = 0; k < SplitState::kFar && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithPriority(&S->far_s[k], cudaStreamNonBlocking, hi_p);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_far[k], cudaEventDisableTiming);
+        }
+        for (int k = 0; k < SplitState::kNear && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithPriority(&S->near_s[k], cudaStreamNonBlocking, lo_p);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_near[k], cudaEventDisableTiming);
+        }
+        for (cudaEvent_t *ev : {&S->fork, &S->ev_in, &S->ev_out})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        const size_t es_b = ctx->fp64 ? 8 : 4;
+        const size_t n = (size_t)ctx->n;
+        for (auto pr : {std::make_pair(&S->q_in, n), std::make_pair(&S->phi_out, n), std::make_pair(&S->grad_out, 3 * n)})
+            if (e == cudaSuccess) {
+                e = pool_alloc(pr.first, std::max<size_t>(pr.second * es_b, 16), s);
+                if (e == cudaSuccess) S->allocs.push_back(*pr.first);
+            }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables above are released next
     if (e != cudaSuccess) {
         split_free(ctx);
@@ -629,76 +689,145 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
     return FMM_OK;
 }
 
+namespace {
+
+// The evaluation of one output mode, enqueued on the capture stream (it is captured, not run).
+template <typename T>
+cudaError_t split_enqueue(fmm_ctx *ctx, SplitState &S, bool want_phi, bool want_grad) {
+    cudaStream_t s = S.cap;
+    const int P = S.P, dg = S.dg, d = ctx->opt.depth;
+    const int K = std::min(P, SplitState::kFar), Kn = std::min(P, SplitState::kNear);
+    using P4 = typename std::conditional<sizeof(T) == 8, double4, float4>::type;
+    T *phi_o = want_phi ? (T *)S.phi_out : nullptr, *grad_o = want_grad ? (T *)S.grad_out : nullptr;
+    auto fork = [&](cudaStream_t *to, int n) -> cudaError_t {
+        FMM_CUDA_TRY(cudaEventRecord(S.fork, s));
+        for (int k = 0; k < n; ++k) FMM_CUDA_TRY(cudaStreamWaitEvent(to[k], S.fork, 0));
+        return cudaSuccess;
+    };
+    // phase boundaries: events the graph records when it runs (external event record nodes)
+    auto mark = [&](cudaEvent_t ev) { return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal); };
+    auto join = [&](cudaStream_t *from, cudaEvent_t *evs, int n) -> cudaError_t {
+        for (int k = 0; k < n; ++k) {
+            FMM_CUDA_TRY(cudaEventRecord(evs[k], from[k]));
+            FMM_CUDA_TRY(cudaStreamWaitEvent(s, evs[k], 0));
+        }
+        return cudaSuccess;
+    };
+    FMM_CUDA_TRY(mark(S.ev[0]));
+    // densities: every rank's own points, then its U ghosts' (U exchange)
+    FMM_CUDA_TRY(fork(S.far_s, K));
+    for (int r = 0; r < P; ++r)
+        FMM_CUDA_TRY(launch_gather_points<T>((const T *)S.q_in, ctx->perm + S.pt_lo[r], S.views[r]->pts,
+                                             S.views[r]->n, S.far_s[r % K]));
+    FMM_CUDA_TRY(join(S.far_s, S.ev_far, K));
+    if (S.n_uex) {
+        copy_pts_kernel<P4><<<S.n_uex, 128, 0, s>>>(S.uex, (P4 *const *)S.pts_base, 0);
+        count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    FMM_CUDA_TRY(mark(S.ev[1]));
+    // the ULI of every rank on the near-field streams, beside everything that follows
+    FMM_CUDA_TRY(fork(S.near_s, Kn));
+    for (int r = 0; r < P; ++r) {
+        fmm_ctx *v = S.views[r];
+        FMM_CUDA_TRY(launch_p2p<T>(v, want_phi ? (T *)v->near_phi : nullptr, want_grad ? (T *)v->near_grad : nullptr,
+                                   S.near_s[r % Kn]));
+    }
+    // local stage: S2U, U2U up to the local roots, VLI compress below d_global
+    FMM_CUDA_TRY(fork(S.far_s, K));
+    for (int r = 0; r < P; ++r) {
+        FarSteps<T> f(S.views[r], false);
+        cudaStream_t fs = S.far_s[r % K];
+        FMM_CUDA_TRY(f.leaf_in(fs));
+        for (int l = d - 1; l >= dg; --l) FMM_CUDA_TRY(f.up(l, fs));
+        for (int l = dg + 1; l <= d; ++l) FMM_CUDA_TRY(f.compress(l, fs));
+    }
+    FMM_CUDA_TRY(join(S.far_s, S.ev_far, K));
+    FMM_CUDA_TRY(mark(S.ev[2]));
+    for (const RowArray &a : S.arr_v) FMM_CUDA_TRY(copy_rows(S.vex, S.n_vex, a, s));   // V exchange
+    FMM_CUDA_TRY(mark(S.ev[3]));
+    for (const RowArray &a : S.arr_up) FMM_CUDA_TRY(copy_rows(S.gat, S.n_gat, a, s));  // gather
+    FMM_CUDA_TRY(mark(S.ev[4]));
+    {   // global stage on the nominated context
+        FarSteps<T> g(S.views[P], false);
+        for (int l = dg - 1; l >= 2; --l) FMM_CUDA_TRY(g.up(l, s));
+        for (int l = 2; l <= dg; ++l) {
+            FMM_CUDA_TRY(g.compress(l, s));
+            FMM_CUDA_TRY(g.stencil(l, s));
+        }
+        for (int l = 2; l <= dg; ++l) FMM_CUDA_TRY(g.down(l, s));
+    }
+    FMM_CUDA_TRY(mark(S.ev[5]));
+    for (const RowArray &a : S.arr_dn) FMM_CUDA_TRY(copy_rows(S.sca, S.n_gat, a, s));  // scatter
+    FMM_CUDA_TRY(mark(S.ev[6]));
+    // local downward stage
+    FMM_CUDA_TRY(fork(S.far_s, K));
+    for (int r = 0; r < P; ++r) {
+        fmm_ctx *v = S.views[r];
+        FarSteps<T> f(v, false);
+        cudaStream_t fs = S.far_s[r % K];
+        for (int l = dg + 1; l <= d; ++l) FMM_CUDA_TRY(f.stencil(l, fs));
+        for (int l = dg + 1; l <= d; ++l) FMM_CUDA_TRY(f.down(l, fs));
+        FMM_CUDA_TRY(f.leaf_out(want_phi ? (T *)v->far_phi : nullptr, want_grad ? (T *)v->far_grad : nullptr, fs));
+    }
+    FMM_CUDA_TRY(join(S.far_s, S.ev_far, K));
+    FMM_CUDA_TRY(mark(S.ev[7]));
+    FMM_CUDA_TRY(join(S.near_s, S.ev_near, Kn));   // what is left of the ULI
+    FMM_CUDA_TRY(mark(S.ev[8]));
+    FMM_CUDA_TRY(fork(S.far_s, K));
+    for (int r = 0; r < P; ++r) {   // outputs in input order
+        fmm_ctx *v = S.views[r];
+        FMM_CUDA_TRY(launch_scatter<T>(want_phi ? (const T *)v->near_phi : nullptr,
+                                       want_grad ? (const T *)v->near_grad : nullptr,
+                                       want_phi ? (const T *)v->far_phi : nullptr,
+                                       want_grad ? (const T *)v->far_grad : nullptr, ctx->perm + S.pt_lo[r], phi_o,
+                                       grad_o, v->n, S.far_s[r % K]));
+    }
+    FMM_CUDA_TRY(join(S.far_s, S.ev_far, K));
+    FMM_CUDA_TRY(mark(S.ev[9]));
+    return cudaSuccess;
+}
+
+}  // namespace
+
 template <typename T>
 fmm_status split_run(fmm_ctx *ctx, const T *q, T *phi, T *grad) {
     SplitState &S = *ctx->split;
     cudaStream_t s = ctx->stream;
-    const int P = S.P, dg = S.dg, d = ctx->opt.depth;
-    using P4 = typename std::conditional<sizeof(T) == 8, double4, float4>::type;
-    cudaError_t e = cudaSuccess;
-#define SPLIT_TRY(x)                                                                           \
-    do {                                                                                       \
-        if ((e = (x)) != cudaSuccess) {                                                        \
-            ctx->err = std::string("partitioned evaluation: ") + cudaGetErrorString(e);         \
-            return FMM_ECUDA;                                                                  \
-        }                                                                                      \
-    } while (0)
-    SPLIT_TRY(cudaEventRecord(S.ev[0], s));
-    // densities: every rank's own points, then its U ghosts' (U exchange)
-    for (int r = 0; r < P; ++r)
-        SPLIT_TRY(launch_gather_points<T>(q, ctx->perm + S.pt_lo[r], S.views[r]->pts, S.views[r]->n, s));
-    if (S.n_uex) {
-        copy_pts_kernel<P4><<<S.n_uex, 128, 0, s>>>(S.uex, (P4 *const *)S.pts_base, 0);
-        count_launch();
-        SPLIT_TRY(cudaGetLastError());
-    }
-    SPLIT_TRY(cudaEventRecord(S.ev[1], s));
-    // local stage: S2U, U2U up to the local roots, VLI compress below d_global
-    for (int r = 0; r < P; ++r) {
-        FarSteps<T> f(S.views[r], false);
-        SPLIT_TRY(f.leaf_in(s));
-        for (int l = d - 1; l >= dg; --l) SPLIT_TRY(f.up(l, s));
-        for (int l = dg + 1; l <= d; ++l) SPLIT_TRY(f.compress(l, s));
-    }
-    SPLIT_TRY(cudaEventRecord(S.ev[2], s));
-    for (const RowArray &a : S.arr_v) SPLIT_TRY(copy_rows(S.vex, S.n_vex, a, s));   // V exchange
-    SPLIT_TRY(cudaEventRecord(S.ev[3], s));
-    for (const RowArray &a : S.arr_up) SPLIT_TRY(copy_rows(S.gat, S.n_gat, a, s));  // gather
-    SPLIT_TRY(cudaEventRecord(S.ev[4], s));
-    {   // global stage on the nominated context
-        FarSteps<T> g(S.views[P], false);
-        for (int l = dg - 1; l >= 2; --l) SPLIT_TRY(g.up(l, s));
-        for (int l = 2; l <= dg; ++l) {
-            SPLIT_TRY(g.compress(l, s));
-            SPLIT_TRY(g.stencil(l, s));
+    const int mode = (phi ? 1 : 0) | (grad ? 2 : 0);
+    const size_t n = (size_t)ctx->n;
+    auto bad = [&](cudaError_t e) {
+        ctx->err = std::string("partitioned evaluation: ") + cudaGetErrorString(e);
+        return FMM_ECUDA;
+    };
+    cudaError_t e;
+    if (!S.exec[mode]) {   // capture this output mode once
+        const long long before = launches();
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return bad(e);
+        cudaError_t ee = split_enqueue<T>(ctx, S, phi != nullptr, grad != nullptr);
+        e = cudaStreamEndCapture(S.cap, &graph);
+        if (ee != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return bad(ee != cudaSuccess ? ee : e);
         }
-        for (int l = 2; l <= dg; ++l) SPLIT_TRY(g.down(l, s));
+        e = cudaGraphInstantiate(&S.exec[mode], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            S.exec[mode] = nullptr;
+            return bad(e);
+        }
+        S.graph_launches[mode] = launches() - before;
+        count_launches(-S.graph_launches[mode]);   // captured, not run: counted at every replay
     }
-    SPLIT_TRY(cudaEventRecord(S.ev[5], s));
-    for (const RowArray &a : S.arr_dn) SPLIT_TRY(copy_rows(S.sca, S.n_gat, a, s));  // scatter
-    SPLIT_TRY(cudaEventRecord(S.ev[6], s));
-    // local downward stage
-    for (int r = 0; r < P; ++r) {
-        fmm_ctx *v = S.views[r];
-        FarSteps<T> f(v, false);
-        for (int l = dg + 1; l <= d; ++l) SPLIT_TRY(f.stencil(l, s));
-        for (int l = dg + 1; l <= d; ++l) SPLIT_TRY(f.down(l, s));
-        SPLIT_TRY(f.leaf_out(phi ? (T *)v->far_phi : nullptr, grad ? (T *)v->far_grad : nullptr, s));
-    }
-    SPLIT_TRY(cudaEventRecord(S.ev[7], s));
-    for (int r = 0; r < P; ++r) {   // ULI with the ghost points
-        fmm_ctx *v = S.views[r];
-        SPLIT_TRY(launch_p2p<T>(v, phi ? (T *)v->near_phi : nullptr, grad ? (T *)v->near_grad : nullptr, s));
-    }
-    SPLIT_TRY(cudaEventRecord(S.ev[8], s));
-    for (int r = 0; r < P; ++r) {   // outputs in input order
-        fmm_ctx *v = S.views[r];
-        SPLIT_TRY(launch_scatter<T>(phi ? (const T *)v->near_phi : nullptr, grad ? (const T *)v->near_grad : nullptr,
-                                    phi ? (const T *)v->far_phi : nullptr, grad ? (const T *)v->far_grad : nullptr,
-                                    ctx->perm + S.pt_lo[r], phi, grad, v->n, s));
-    }
-    SPLIT_TRY(cudaEventRecord(S.ev[9], s));
-#undef SPLIT_TRY
+    if ((e = cudaMemcpyAsync(S.q_in, q, n * sizeof(T), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return bad(e);
+    if ((e = cudaGraphLaunch(S.exec[mode], s)) != cudaSuccess) return bad(e);
+    count_launches(S.graph_launches[mode]);
+    if (phi && (e = cudaMemcpyAsync(phi, S.phi_out, n * sizeof(T), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return bad(e);
+    if (grad && (e = cudaMemcpyAsync(grad, S.grad_out, 3 * n * sizeof(T), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return bad(e);
     S.timed = true;
     return FMM_OK;
 }
@@ -788,12 +917,12 @@ fmm_status split_timings(fmm_ctx *ctx, double *ms, int n) {
     SplitState *S = ctx->split;
     if (!S) return sfail(ctx, FMM_ESTATE, "fmm_partition_setup has not been called");
     if (!S->timed) return sfail(ctx, FMM_ESTATE, "no partitioned evaluation yet");
-    if (cudaEventSynchronize(S->ev[9]) != cudaSuccess) return sfail(ctx, FMM_ECUDA, "event synchronize");
-    for (int i = 0; i < n && i < 10; ++i) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return sfail(ctx, FMM_ECUDA, "synchronize");
+    for (int i = 0; i < n && i < 10; ++i) {   // -1 where the driver gives no time
         float t = 0;
-        cudaEventElapsedTime(&t, S->ev[i == 9 ? 0 : i], S->ev[i == 9 ? 9 : i + 1]);
-        ms[i] = t;
+        ms[i] = cudaEventElapsedTime(&t, S->ev[i == 9 ? 0 : i], S->ev[i == 9 ? 9 : i + 1]) == cudaSuccess ? t : -1.0;
     }
+    cudaGetLastError();
     return FMM_OK;
 }
 
