@@ -64,6 +64,57 @@ void oracle_grouped_sum(int64_t n_groups,
     }
 }
 
+/*
+ * The same sums with the Helmholtz kernel exp(i k |x - y|) / (4 pi |x - y|) and complex densities.
+ * Complex arrays are interleaved (re, im): sq[2 * n_sources], pot[2 * n_targets] and, with grad
+ * non-NULL, grad[6 * n_targets] = (d/dx re, d/dx im, d/dy re, d/dy im, d/dz re, d/dz im) per target.
+ * Per pair, w = s_j exp(i k r) / r and the gradient term is w (i k r - 1) (x_i - y_j) / r^2.
+ */
+void oracle_grouped_sum_helm(int64_t n_groups, const int64_t *t_off, const double *tx, const int64_t *r_off,
+                             const int64_t *ranges, const double *sx, const double *sq, double *pot, double *grad,
+                             double k)
+{
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (g = 0; g < n_groups; ++g) {
+        for (int64_t i = t_off[g]; i < t_off[g + 1]; ++i) {
+            const double xi = tx[3 * i], yi = tx[3 * i + 1], zi = tx[3 * i + 2];
+            double fr = 0.0, fi = 0.0;
+            double gr[3] = {0.0, 0.0, 0.0}, gi[3] = {0.0, 0.0, 0.0};
+            for (int64_t r = r_off[g]; r < r_off[g + 1]; ++r) {
+                for (int64_t j = ranges[2 * r]; j < ranges[2 * r + 1]; ++j) {
+                    const double d[3] = {xi - sx[3 * j], yi - sx[3 * j + 1], zi - sx[3 * j + 2]};
+                    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 == 0.0) continue;
+                    const double rinv = 1.0 / sqrt(r2);
+                    const double rr = r2 * rinv;
+                    const double c = cos(k * rr), s = sin(k * rr);
+                    const double qr = sq[2 * j], qi = sq[2 * j + 1];
+                    const double wr = (qr * c - qi * s) * rinv, wi = (qr * s + qi * c) * rinv;
+                    fr += wr;
+                    fi += wi;
+                    if (grad) {
+                        /* w (i k r - 1) / r^2 */
+                        const double zr = (-wr - k * rr * wi) * rinv * rinv;
+                        const double zi = (-wi + k * rr * wr) * rinv * rinv;
+                        for (int a = 0; a < 3; ++a) {
+                            gr[a] += zr * d[a];
+                            gi[a] += zi * d[a];
+                        }
+                    }
+                }
+            }
+            pot[2 * i] += fr * INV4PI;
+            pot[2 * i + 1] += fi * INV4PI;
+            if (grad)
+                for (int a = 0; a < 3; ++a) {
+                    grad[6 * i + 2 * a] += gr[a] * INV4PI;
+                    grad[6 * i + 2 * a + 1] += gi[a] * INV4PI;
+                }
+        }
+    }
+}
+
 /* Number of threads OpenMP would use (1 when built without OpenMP). */
 int oracle_num_threads(void)
 {

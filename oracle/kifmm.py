@@ -29,7 +29,10 @@ The M2L is not compressed here, so the GPU path's SVD truncation error is inside
 With `kappa` > 0 every K above is the modified Helmholtz (Yukawa) kernel
 exp(-kappa r) / (4 pi r), a real kernel admitted by Eq. 1; the steps are unchanged, which is what
 makes the method kernel-independent (Section 2.1).  That kernel is not homogeneous, so its
-operators of different levels are not rescalings of one another.
+operators of different levels are not rescalings of one another.  With `wavenumber` k > 0 every
+K is the Helmholtz kernel exp(i k r) / (4 pi r) (Eq. 1 with F = C): operators, densities and
+fields are complex and the pseudo-inverse uses the conjugate transpose; the adjoint is for real
+kernels only.
 
 The pseudo-inverse truncates singular values below rtol * sigma_max (the paper is silent on
 regularisation).
@@ -66,22 +69,25 @@ def surface(p, centre, halfwidth, alpha):
     return np.asarray(centre, dtype=np.float64).reshape(1, 3) + alpha * halfwidth * surface_grid(p)
 
 
-def kernel_matrix(x, y, kappa=0.0):
+def kernel_matrix(x, y, kappa=0.0, wavenumber=0.0):
     """K(x_i, y_j) = exp(-kappa r) / (4 pi r), r = |x_i - y_j| (kappa = 0: Eq. 2 normalised;
-    kappa > 0: the modified Helmholtz kernel), zero where r = 0."""
+    kappa > 0: the modified Helmholtz kernel), or exp(i k r) / (4 pi r) for wavenumber k > 0 (the
+    Helmholtz kernel, complex), zero where r = 0."""
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     y = np.asarray(y, dtype=np.float64).reshape(-1, 3)
     d = x[:, None, :] - y[None, :, :]
     r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
-    with np.errstate(divide="ignore"):
-        return np.where(r > 0.0, INV4PI * np.exp(-kappa * r) / np.where(r > 0.0, r, 1.0), 0.0)
+    rs = np.where(r > 0.0, r, 1.0)
+    if wavenumber > 0.0:
+        return np.where(r > 0.0, INV4PI * np.exp(1j * wavenumber * r) / rs, 0.0)
+    return np.where(r > 0.0, INV4PI * np.exp(-kappa * r) / rs, 0.0)
 
 
 def pinv(a, rtol):
     """Truncated-SVD pseudo-inverse: singular values below rtol * sigma_max are dropped."""
     u, s, vt = np.linalg.svd(a)
     keep = s >= rtol * s[0]
-    return (vt[keep].T / s[keep]) @ u[:, keep].T
+    return (vt[keep].conj().T / s[keep]) @ u[:, keep].conj().T
 
 
 @dataclasses.dataclass
@@ -95,6 +101,11 @@ class Operators:
     l2l: dict         # (child level, octant) -> K(dc_child, de_P)
     m2l: dict         # (level, t) -> K(dc_b, ue_{b + t})
     kappa: float = 0.0  # kernel: 0 Laplace, > 0 modified Helmholtz exp(-kappa r) / (4 pi r)
+    wavenumber: float = 0.0   # > 0: Helmholtz exp(i k r) / (4 pi r), complex operators and data
+
+    @property
+    def dtype(self):
+        return np.complex128 if self.wavenumber > 0.0 else np.float64
 
 
 def child_offset(c):
@@ -102,10 +113,10 @@ def child_offset(c):
     return np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1], dtype=np.float64)
 
 
-def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None, kappa=0.0):
+def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None, kappa=0.0, wavenumber=0.0):
     tv = otree.transfer_vectors()
-    ops = Operators(p, {}, {}, {}, {}, {}, kappa)
-    km = lambda a, b: kernel_matrix(a, b, kappa)
+    ops = Operators(p, {}, {}, {}, {}, {}, kappa, wavenumber)
+    km = lambda a, b: kernel_matrix(a, b, kappa, wavenumber)
     zero = np.zeros(3)
     for level in range(0, depth + 1):
         r = side / 2.0 ** (level + 1)
@@ -151,18 +162,18 @@ def upward(tr, xs, qs, ops, chunk=65536):
     ns = n_surface(p)
     d = tr.depth
     nl = len(tr.leaf_keys)
-    u = {d: np.zeros((nl, ns))}
+    u = {d: np.zeros((nl, ns), ops.dtype)}
     for a in range(0, nl, chunk):
         leaves = np.arange(a, min(a + chunk, nl))
         chk = _leaf_surface_points(tr, p, leaves, ALPHA_OUTER)
         t_off = np.arange(len(leaves) + 1, dtype=np.int64) * ns
         ranges = np.stack([tr.leaf_offsets[leaves], tr.leaf_offsets[leaves + 1]], axis=1)
         q_uc, _ = direct.grouped_sum(t_off, chk, np.arange(len(leaves) + 1), ranges, xs, qs,
-                                     gradient=False, kappa=ops.kappa)
+                                     gradient=False, kappa=ops.kappa, wavenumber=ops.wavenumber)
         u[d][leaves] = q_uc.reshape(len(leaves), ns) @ ops.uc2e[d].T
     for level in range(d - 1, 1, -1):
         ch = tr.children(level)
-        q_uc = np.zeros((len(tr.level_keys[level]), ns))
+        q_uc = np.zeros((len(tr.level_keys[level]), ns), ops.dtype)
         for c in range(8):
             has = ch[:, c] >= 0
             q_uc[has] += u[level + 1][ch[has, c]] @ ops.m2m[(level, c)].T
@@ -187,7 +198,7 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
     dvec = {}
     for level in range(2, tr.depth + 1):
         boxes = need[level]
-        q_dc = np.zeros((len(boxes), ns))
+        q_dc = np.zeros((len(boxes), ns), ops.dtype)
         off, idx, tvec = otree.v_lists(tr, level, boxes)
         rows = np.repeat(np.arange(len(boxes)), np.diff(off))
         if m2l == "grouped":
@@ -200,7 +211,7 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
             for k in range(len(idx)):
                 b, a = boxes[rows[k]], idx[k]
                 kmat = kernel_matrix(surface(p, ctr[b], r, ALPHA_INNER),
-                                     surface(p, ctr[a], r, ALPHA_INNER), ops.kappa)
+                                     surface(p, ctr[a], r, ALPHA_INNER), ops.kappa, ops.wavenumber)
                 q_dc[rows[k]] += kmat @ u[level][a]
         if level >= 3:
             par = tr.parent(level)[boxes]
@@ -216,15 +227,19 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
 
 def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
              pinv_rtol=DEFAULT_PINV_RTOL, sample=None, parts=("near", "far"), m2l="grouped",
-             ops=None, kappa=0.0):
-    """FP64 kiFMM field at every point (or at the `sample` indices, input order).
+             ops=None, kappa=0.0, wavenumber=0.0):
+    """FP64 kiFMM field at every point (or at the `sample` indices, input order).  With
+    wavenumber > 0 (Helmholtz) the charges, potentials and gradients are complex.
 
     Returns a Result whose phi/grad follow the input order of the points (or of `sample`).
     `parts` selects the near field (ULI), the far field (VLI/D2D/D2T) or both.
     """
     xs_in = np.asarray(points, dtype=np.float64).reshape(-1, 3)
-    q_in = np.asarray(charges, dtype=np.float64).reshape(-1)
     tr = otree.build_tree(xs_in, depth, origin, side)
+    if ops is None:
+        ops = build_operators(p, tr.side, depth, pinv_rtol, kappa=kappa, wavenumber=wavenumber)
+    kappa, wavenumber, dt = ops.kappa, ops.wavenumber, ops.dtype
+    q_in = np.asarray(charges, dtype=dt).reshape(-1)
     xs = xs_in[tr.perm]
     qs = q_in[tr.perm]
     n = len(xs)
@@ -236,11 +251,8 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
         tpos = inv[np.asarray(sample, dtype=np.int64)]              # sorted positions
     leaf_of = np.searchsorted(tr.leaf_offsets, tpos, side="right") - 1
     leaves = np.unique(leaf_of)
-    if ops is None:
-        ops = build_operators(p, tr.side, depth, pinv_rtol, kappa=kappa)
-    kappa = ops.kappa
-    phi_s = np.zeros(n)
-    grad_s = np.zeros((n, 3)) if gradient else None
+    phi_s = np.zeros(n, dt)
+    grad_s = np.zeros((n, 3), dt) if gradient else None
     u, dvec, need = {}, {}, {}
     # Target groups: the sampled targets of each leaf, as contiguous sorted positions.
     tsort = np.sort(tpos)
@@ -248,8 +260,8 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
     grp_off = np.searchsorted(t_leaf, leaves, side="left")
     grp_off = np.append(grp_off, len(tsort)).astype(np.int64)
     tx = xs[tsort]
-    pot = np.zeros(len(tsort))
-    grd = np.zeros((len(tsort), 3)) if gradient else None
+    pot = np.zeros(len(tsort), dt)
+    grd = np.zeros((len(tsort), 3), dt) if gradient else None
     if "far" in parts and depth >= 2:
         u = upward(tr, xs, qs, ops)
         need, dvec = downward(tr, u, ops, leaves, m2l)
@@ -259,20 +271,21 @@ def evaluate(points, charges, p, depth, origin=None, side=None, gradient=True,
         ns = n_surface(p)
         ranges = np.stack([np.arange(len(leaves)) * ns, np.arange(1, len(leaves) + 1) * ns], 1)
         direct.grouped_sum(grp_off, tx, np.arange(len(leaves) + 1), ranges, de, dens,
-                           gradient, pot, grd, kappa=kappa)
+                           gradient, pot, grd, kappa=kappa, wavenumber=wavenumber)
     if "near" in parts:
         uoff, uidx = otree.u_lists(tr, leaves)
         ranges = np.stack([tr.leaf_offsets[uidx], tr.leaf_offsets[uidx + 1]], axis=1)
-        direct.grouped_sum(grp_off, tx, uoff, ranges, xs, qs, gradient, pot, grd, kappa=kappa)
+        direct.grouped_sum(grp_off, tx, uoff, ranges, xs, qs, gradient, pot, grd, kappa=kappa,
+                           wavenumber=wavenumber)
     phi_s[tsort] = pot
     if gradient:
         grad_s[tsort] = grd
     if sample is None:
-        phi = np.empty(n)
+        phi = np.empty(n, dt)
         phi[tr.perm] = phi_s
         grad = None
         if gradient:
-            grad = np.empty((n, 3))
+            grad = np.empty((n, 3), dt)
             grad[tr.perm] = grad_s
     else:
         phi = phi_s[tpos]
