@@ -66,7 +66,12 @@ typedef enum {
 /* Kernel of Eq. 1 (option `kernel`). */
 typedef enum {
     FMM_LAPLACE = 0,       /* 1 / (4 pi r) (Eq. 2, normalised by 4 pi) */
-    FMM_YUKAWA = 1         /* exp(-kappa r) / (4 pi r), kappa > 0; gradient -(1 + kappa r) exp(-kappa r) d / (4 pi r^3) */
+    FMM_YUKAWA = 1,        /* exp(-kappa r) / (4 pi r), kappa > 0; gradient -(1 + kappa r) exp(-kappa r) d / (4 pi r^3) */
+    FMM_HELMHOLTZ = 2      /* exp(i k r) / (4 pi r), wavenumber k = `kappa` > 0 (Eq. 1 with F = C); gradient
+                              (i k r - 1) exp(i k r) d / (4 pi r^3).  Densities and outputs are complex,
+                              stored interleaved (re, im): q and phi hold 2n values, grad 6n
+                              (d/dx re, d/dx im, d/dy re, ... per point).  Box vectors hold the real
+                              and imaginary parts of the surface values (2 (6(p-1)^2+2) entries). */
 } fmm_kernel;
 
 typedef struct {
@@ -89,13 +94,15 @@ typedef struct {
                               constant, where the textbook operators reproduce it only up to their
                               fit error, so results differ from the textbook kiFMM by about that
                               error (1e-7 relative at p >= 6, 1e-4 at p = 4).  Default 0. */
-    int kernel;            /* an fmm_kernel value.  Default FMM_LAPLACE.  FMM_YUKAWA needs has_domain:
-                              the kernel is not homogeneous, so its operators depend on the physical
-                              box sizes and are built per level by fmm_precompute from `side`
-                              (fmm_create returns FMM_EUNSUPPORTED without a domain, and with
-                              mean_free, whose constant-potential argument holds for Laplace only). */
-    double kappa;          /* FMM_YUKAWA: screening constant, finite and > 0, in inverse units of the
-                              coordinates.  Ignored for FMM_LAPLACE. */
+    int kernel;            /* an fmm_kernel value.  Default FMM_LAPLACE.  FMM_YUKAWA and FMM_HELMHOLTZ need
+                              has_domain: these kernels are not homogeneous, so their operators depend
+                              on the physical box sizes and are built per level by fmm_precompute from
+                              `side` (fmm_create returns FMM_EUNSUPPORTED without a domain, and with
+                              mean_free, whose constant-potential argument holds for Laplace only).
+                              FMM_HELMHOLTZ has no fmm_adjoint and no partitioned evaluation
+                              (FMM_EUNSUPPORTED). */
+    double kappa;          /* FMM_YUKAWA: screening constant; FMM_HELMHOLTZ: wavenumber; finite and > 0,
+                              in inverse units of the coordinates.  Ignored for FMM_LAPLACE. */
 } fmm_options;
 
 /* Part selectors for fmm_evaluate_parts (Section 1, Eq. 3: near field + far field). */

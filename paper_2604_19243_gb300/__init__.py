@@ -25,7 +25,7 @@ PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp16
 STATUS = {0: "FMM_OK", 1: "FMM_EINVAL", 2: "FMM_ENOMEM", 3: "FMM_ECUDA", 4: "FMM_ESTATE",
           5: "FMM_ETIMEOUT", 6: "FMM_EUNSUPPORTED"}
 PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
-KERNELS = {"laplace": 0, "yukawa": 1}
+KERNELS = {"laplace": 0, "yukawa": 1, "helmholtz": 2}
 
 # C entry points declared in include/fmm.h (checked by the export test)
 ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_precompute",
@@ -185,6 +185,9 @@ class FMM:
         self.p, self.depth, self.precision = p, depth, precision
         self.kernel, self.kappa = kernel, float(kappa)
         self.dtype = np.float64 if precision == "fp64" else np.float32
+        # densities and outputs: complex for the Helmholtz kernel (interleaved re, im)
+        self.vdtype = ((np.complex128 if precision == "fp64" else np.complex64) if kernel == "helmholtz"
+                       else self.dtype)
         self.n = 0
 
     def _check(self, st):
@@ -204,16 +207,20 @@ class FMM:
 
     # -- marshalling helpers ------------------------------------------------------------
     def _like(self, ref, shape):
+        """An output array of values (densities' dtype) beside `ref`."""
         if isinstance(ref, np.ndarray):
-            return np.empty(shape, dtype=self.dtype)
+            return np.empty(shape, dtype=self.vdtype)
         import torch
         return torch.empty(shape, dtype=ref.dtype, device=ref.device)
 
-    def _as_input(self, a):
+    def _as_input(self, a, values=False):
+        """Coordinates (values=False) or densities (values=True) in the context's types."""
+        dt = self.vdtype if values else self.dtype
         if isinstance(a, np.ndarray):
-            return np.ascontiguousarray(a, dtype=self.dtype)
+            return np.ascontiguousarray(a, dtype=dt)
         import torch
-        want = torch.float64 if self.dtype == np.float64 else torch.float32
+        want = {np.float64: torch.float64, np.float32: torch.float32, np.complex64: torch.complex64,
+                np.complex128: torch.complex128}[dt]
         return a.detach().to(want).contiguous()
 
     # -- C entry points -----------------------------------------------------------------
@@ -229,7 +236,7 @@ class FMM:
 
     def evaluate(self, q, gradient=True, parts=PART_ALL, potential=True):
         """(phi, grad); potential=False gives the gradient-only evaluation (phi is None)."""
-        q = self._as_input(q)
+        q = self._as_input(q, values=True)
         phi = self._like(q, (self.n,)) if potential else None
         grad = self._like(q, (self.n, 3)) if gradient else None
         self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
@@ -241,7 +248,7 @@ class FMM:
         self._check(lib().fmm_evaluate_parts(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
 
     def adjoint(self, g, gradient=False):
-        g = self._as_input(g)
+        g = self._as_input(g, values=True)
         psi = self._like(g, (self.n,))
         grad = self._like(g, (self.n, 3)) if gradient else None
         self._check(lib().fmm_adjoint(self._ctx, _ptr(g), _ptr(psi), _ptr(grad)))
@@ -304,7 +311,7 @@ class FMM:
 
     def partition_evaluate(self, q, gradient=True, potential=True):
         """As evaluate, through the partition: (phi, grad)."""
-        q = self._as_input(q)
+        q = self._as_input(q, values=True)
         phi = self._like(q, (self.n,)) if potential else None
         grad = self._like(q, (self.n, 3)) if gradient else None
         self._check(lib().fmm_partition_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad)))

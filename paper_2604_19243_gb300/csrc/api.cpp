@@ -102,7 +102,7 @@ void free_workspace(fmm_ctx *ctx) {
     free_async(ctx->Ups, s), free_async(ctx->Dns, s), free_async(ctx->Cts, s);
     free_async(ctx->Yc, s), free_async(ctx->Dq, s), free_async(ctx->Cmean, s);
     free_async(ctx->near_phi, s), free_async(ctx->near_grad, s);
-    free_async(ctx->far_phi, s), free_async(ctx->far_grad, s);
+    free_async(ctx->far_phi, s), free_async(ctx->far_grad, s), free_async(ctx->pts_qi, s);
     free_async(ctx->stage_in, s), free_async(ctx->stage_out, s), free_async(ctx->stage_grad, s);
     for (int l = 0; l <= kMaxDepth; ++l)
         for (TileSet *ts : {&ctx->tiles_plain[l], &ctx->tiles_cls[l]}) {
@@ -168,6 +168,7 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
     const int kw = std::max(std::max(o.kinp, o.koutp), 16);
     ctx->ws_kw = kw;
     const int64_t rows = need_rows, nl = need_nl, n = need_n;
+    const int vc = ctx->cplx ? 2 : 1;   // values per point (complex outputs)
     struct A {
         void **p;
         size_t bytes;
@@ -178,9 +179,9 @@ fmm_status ensure_workspace(fmm_ctx *ctx) {
         {&ctx->Ct, (size_t)rows * kw * es},
         {&ctx->Yc, (size_t)nl * o.rclp * es},
         {&ctx->Dq, (size_t)nl * nsp * es},     {&ctx->Cmean, (size_t)rows * sizeof(double)},
-        {&ctx->near_phi, (size_t)n * es},
-        {&ctx->near_grad, (size_t)n * 3 * es}, {&ctx->far_phi, (size_t)n * es},
-        {&ctx->far_grad, (size_t)n * 3 * es},
+        {&ctx->near_phi, (size_t)n * vc * es},
+        {&ctx->near_grad, (size_t)n * 3 * vc * es}, {&ctx->far_phi, (size_t)n * vc * es},
+        {&ctx->far_grad, (size_t)n * 3 * vc * es}, {&ctx->pts_qi, ctx->cplx ? (size_t)n * es : (size_t)16},
     };
     if (ctx->tensor) {
         const int np = ctx->opt.precision == FMM_BF16X6 ? 3 : 2;
@@ -271,15 +272,17 @@ template <typename T>
 fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts, bool adjoint) {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n;
+    const int64_t vn = ctx->cplx ? 2 * n : n;   // values of a density or potential array
     Staged sq, sphi, sgrad;
     fmm_status st;
-    if ((st = stage(ctx, q, n * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
-    if (phi && (st = stage(ctx, phi, n * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
-    if (grad && (st = stage(ctx, grad, 3 * n * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
+    if ((st = stage(ctx, q, vn * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
+    if (phi && (st = stage(ctx, phi, vn * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
+    if (grad && (st = stage(ctx, grad, 3 * vn * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
     cudaError_t e;
     cudaEventRecord(ctx->ev[0], s);
-    if ((e = launch_gather_points<T>((const T *)sq.dev, ctx->perm, ctx->pts, n, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "gather");
+    e = ctx->cplx ? launch_gather_points_c<T>((const T *)sq.dev, ctx->perm, ctx->pts, (T *)ctx->pts_qi, n, s)
+                  : launch_gather_points<T>((const T *)sq.dev, ctx->perm, ctx->pts, n, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather");
     cudaEventRecord(ctx->ev[7], s);
     const bool near = parts & FMM_PART_NEAR;
     const bool far = (parts & FMM_PART_FAR) && ctx->opt.depth >= 2;
@@ -303,15 +306,16 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     cudaEventRecord(ctx->ev[1], ns);
     cudaStreamWaitEvent(s, ctx->ev[5], 0);   // join the far field
     cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
-    e = launch_scatter<T>(near && phi ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
-                          far && phi ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm,
-                          (T *)sphi.dev, (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
+    e = (ctx->cplx ? launch_scatter_c<T> : launch_scatter<T>)(
+        near && phi ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
+        far && phi ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm, (T *)sphi.dev,
+        (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter");
     cudaEventRecord(ctx->ev[6], s);
-    if (phi && sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if (phi && sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, vn * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "device-to-host copy");
     if (grad && !adjoint && sgrad.host &&
-        (e = cudaMemcpyAsync(grad, sgrad.dev, 3 * n * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        (e = cudaMemcpyAsync(grad, sgrad.dev, 3 * vn * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "device-to-host copy");
     if (sq.host || (phi && sphi.host) || (grad && sgrad.host)) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
@@ -384,8 +388,8 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
         return FMM_EINVAL;
     // the FP16 planes of FMM_FP16X3 carry the downward rows as produced, before a mean is taken off
     if (opt->mean_free && opt->precision == FMM_FP16X3) return FMM_EUNSUPPORTED;
-    if (opt->kernel != FMM_LAPLACE && opt->kernel != FMM_YUKAWA) return FMM_EINVAL;
-    if (opt->kernel == FMM_YUKAWA) {
+    if (opt->kernel != FMM_LAPLACE && opt->kernel != FMM_YUKAWA && opt->kernel != FMM_HELMHOLTZ) return FMM_EINVAL;
+    if (opt->kernel != FMM_LAPLACE) {
         if (!(std::isfinite(opt->kappa) && opt->kappa > 0)) return FMM_EINVAL;
         // the operators depend on the physical box sizes (no homogeneity), and the means that
         // mean_free carries down the tree are exact for Laplace only
@@ -403,7 +407,9 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     ctx->fp64 = opt->precision == FMM_FP64;
     ctx->tensor = opt->precision == FMM_TF32X3 || opt->precision == FMM_BF16X3 || opt->precision == FMM_BF16X6 ||
                   opt->precision == FMM_FP16X3;
-    ctx->ns = 6 * (opt->order_p - 1) * (opt->order_p - 1) + 2;
+    ctx->npts = 6 * (opt->order_p - 1) * (opt->order_p - 1) + 2;
+    ctx->cplx = opt->kernel == FMM_HELMHOLTZ;
+    ctx->ns = ctx->cplx ? 2 * ctx->npts : ctx->npts;   // real and imaginary parts of complex values
     ctx->nsp = round_up(ctx->ns, 16);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         cudaGetLastError();
@@ -479,14 +485,14 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     // kappa in units of that level's half-width side / 2^(l+1); the other levels alias the
     // coarsest built one and are never read.
     const int d = ctx->opt.depth;
-    const int lo = ctx->opt.kernel == FMM_YUKAWA ? (d < 2 ? d : 2) : 0;
+    const bool lap = ctx->opt.kernel == FMM_LAPLACE;
+    const int lo = !lap ? (d < 2 ? d : 2) : 0;
     std::vector<double> ku;
-    for (int l = lo; l <= d; ++l)
-        ku.push_back(ctx->opt.kernel == FMM_YUKAWA ? ctx->opt.kappa * std::ldexp(ctx->opt.side, -(l + 1)) : 0.0);
-    if (ctx->opt.kernel == FMM_LAPLACE) ku.resize(1);
+    for (int l = lo; l <= d; ++l) ku.push_back(!lap ? ctx->opt.kappa * std::ldexp(ctx->opt.side, -(l + 1)) : 0.0);
+    if (lap) ku.resize(1);
     std::vector<const HostOps *> hs;
     try {
-        hs = host_operator_levels(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, ku, &err);
+        hs = host_operator_levels(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, ctx->opt.kernel, ku, &err);
     } catch (const std::bad_alloc &) {
         return fail(ctx, FMM_ENOMEM, "host memory exhausted in precompute");
     } catch (...) {
@@ -494,7 +500,7 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     }
     if (hs.size() != ku.size()) return fail(ctx, FMM_EINVAL, "precompute failed: " + err);
     for (int l = 0; l <= kMaxDepth; ++l)
-        ctx->host_ops[l] = ctx->opt.kernel == FMM_LAPLACE ? hs[0] : hs[std::min(std::max(l, lo), d) - lo];
+        ctx->host_ops[l] = lap ? hs[0] : hs[std::min(std::max(l, lo), d) - lo];
     cudaError_t e;
     if (!ctx->dev_flag) {
         if (cudaMalloc((void **)&ctx->dev_flag, sizeof(int)) != cudaSuccess) {
@@ -539,6 +545,7 @@ fmm_status fmm_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad) {
 fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
     fmm_status st = check_ready(ctx, g, psi);
     if (st != FMM_OK) return st;
+    if (ctx->cplx) return fail(ctx, FMM_EUNSUPPORTED, "no adjoint for the Helmholtz kernel");
     if (grad_psi && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
     st = ctx->fp64 ? run_evaluate<double>(ctx, g, psi, nullptr, FMM_PART_ALL, true)
                    : run_evaluate<float>(ctx, g, psi, nullptr, FMM_PART_ALL, true);
@@ -561,6 +568,7 @@ fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
 
 fmm_status fmm_partition_setup(fmm_ctx *ctx, int d_global, int n_ranks) {
     if (!ctx) return FMM_EINVAL;
+    if (ctx->cplx) return fail(ctx, FMM_EUNSUPPORTED, "no partitioned evaluation for the Helmholtz kernel");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     try {
         return split_setup(ctx, d_global, n_ranks);
@@ -600,7 +608,7 @@ fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
     std::memset(info, 0, sizeof(*info));
     info->n_points = ctx->n;
     info->depth = ctx->opt.depth;
-    info->n_surface = ctx->ns;
+    info->n_surface = ctx->npts;
     info->m2l_rank_in = ctx->have_ops ? ctx->fwd[ctx->opt.depth].kin : 0;
     info->m2l_rank_out = ctx->have_ops ? ctx->fwd[ctx->opt.depth].kout : 0;
     for (int l = 0; l <= ctx->opt.depth; ++l) info->n_boxes[l] = ctx->lev[l].n;

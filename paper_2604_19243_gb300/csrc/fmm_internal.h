@@ -115,7 +115,9 @@ struct fmm_ctx {
     std::string err;
     bool fp64 = false;
     bool tensor = false;        // tcgen05 contractions
-    int ns = 0, nsp = 0;
+    bool cplx = false;          // complex densities and outputs (FMM_HELMHOLTZ)
+    int npts = 0;               // surface points, 6(p-1)^2+2
+    int ns = 0, nsp = 0;        // box vector length (npts, or 2 npts: real then imaginary parts), padded
 
     // tree
     bool have_tree = false;
@@ -163,7 +165,8 @@ struct fmm_ctx {
     void *UpP = nullptr, *DnP = nullptr, *CtP = nullptr;
     long long upp_plane = 0, ctp_plane = 0;   // bytes per plane (UpP and DnP share the first)
     float *Ups = nullptr, *Dns = nullptr, *Cts = nullptr;
-    void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3]
+    void *pts_qi = nullptr;              // FMM_HELMHOLTZ: imaginary parts of the sorted densities [n]
+    void *near_phi = nullptr, *near_grad = nullptr;  // sorted-order outputs [n], [n x 3] (complex: x2)
     void *far_phi = nullptr, *far_grad = nullptr;
     size_t ws_bytes = 0;
     int ws_kw = 0;
@@ -206,8 +209,11 @@ void count_launches(long long n);   // the kernels of a replayed CUDA graph
 
 // ---- precompute.cpp ----
 struct HostOps {
-    int p = 0, ns = 0;
-    double kappa_u = 0;                               // kernel's kappa in units of the half-width
+    int p = 0;
+    int ns = 0;                                       // box vector length (npts, or 2 npts if complex)
+    int npts = 0;                                     // surface points
+    int kernel = FMM_LAPLACE;
+    double kappa_u = 0;                               // kernel's kappa (or wavenumber) x the half-width
     int kin = 0, kout = 0, rcl = 0;
     std::vector<double> surf_inner, surf_outer;       // [ns x 3] unit grids scaled by alpha
     std::vector<double> up[8], down[8];               // [ns x ns]
@@ -223,7 +229,7 @@ struct HostOps {
 const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err);
 // One operator set per entry of kappa_u (the kernel's kappa times a level's half-width; 0 =
 // Laplace), all with the M2L ranks of the entry that needs the largest; cached per argument list.
-std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol,
+std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol, int kernel,
                                                   const std::vector<double> &kappa_u, std::string *err);
 // Unit surface grid of order p (lexicographic), [n x 3] in [-1,1]^3.
 std::vector<double> surface_grid(int p);
@@ -273,6 +279,20 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
 template <typename T>
 cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
                              T *phi, T *grad, cudaStream_t s, const double *shift);
+
+// Helmholtz point kernels (helm.cu): complex densities (Re in pts, Im in pts_qi), complex outputs
+// interleaved (re, im); the S2U rows hold [Re | Im] of the surface values, as do the D2T densities.
+template <typename T>
+cudaError_t launch_gather_points_c(const T *q, const int *perm, void *pts, T *qi, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_c(const T *np, const T *ng, const T *fp, const T *fg, const int *perm, T *phi, T *grad,
+                             int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t helm_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
+template <typename T>
+cudaError_t helm_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s);
+template <typename T>
+cudaError_t helm_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T *phi, T *grad, cudaStream_t s);
 
 // Generic gathered GEMM (gemm_simt.cu / gemm_tc.cu): Y[rows] (+)= alpha sum_seg W_seg X[src(row,seg)].
 enum GatherMode { GM_IDENTITY = 0, GM_CHILDREN = 1, GM_PARENT2 = 2, GM_STENCIL = 3 };

@@ -631,6 +631,7 @@ cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_p
 
 template <typename T>
 cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
+    if (ctx->cplx) return helm_p2p<T>(ctx, phi, grad, s);
     if (ctx->nleaf == 0) return cudaSuccess;
     using P = typename Vec4<T>::type;
     const P *pts = (const P *)ctx->pts;
@@ -654,6 +655,7 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s) {
+    if (ctx->cplx) return helm_leaf_check<T>(ctx, grid, out, s);
     if (ctx->nleaf == 0) return cudaSuccess;
     const int d = ctx->opt.depth;
     const double width = ctx->side / (double)(1 << d);
@@ -662,7 +664,7 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
     const T kappa = (T)ctx->opt.kappa;
     auto go = [&](auto kern, int threads) {
         kern<<<ctx->nleaf, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys,
-                                            grid, ctx->ns, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2],
+                                            grid, ctx->npts, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2],
                                             width, radius, out, kappa);
     };
     if constexpr (std::is_same<T, float>::value)
@@ -676,17 +678,18 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
 template <typename T>
 cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, int ldd, T scale,
                              T *phi, T *grad, cudaStream_t s, const double *shift) {
+    if (ctx->cplx) return helm_leaf_eval<T>(ctx, grid, dens, ldd, phi, grad, s);   // scale 1, no shift
     if (ctx->nleaf == 0) return cudaSuccess;
     const int d = ctx->opt.depth;
     const double width = ctx->side / (double)(1 << d);
     const double radius = 2.95 * 0.5 * width;
     using P = typename Vec4<T>::type;
-    size_t smem = sizeof(P) * ctx->ns * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
+    size_t smem = sizeof(P) * ctx->npts * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
     const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
     const T kappa = (T)ctx->opt.kappa;
     auto go = [&](auto kern, T *g) {
         kern<<<ctx->nleaf, kLeafThreads, smem, s>>>((const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid,
-                                                    ctx->ns, dens, ldd, scale, ctx->origin[0], ctx->origin[1],
+                                                    ctx->npts, dens, ldd, scale, ctx->origin[0], ctx->origin[1],
                                                     ctx->origin[2], width, radius, phi, g, shift, kappa);
     };
     if (grad) yuk ? go(leaf_eval_kernel<T, true, true>, grad) : go(leaf_eval_kernel<T, true, false>, grad);

@@ -88,17 +88,32 @@ Mat scaled_surface(const std::vector<double> &grid, double cx, double cy, double
     return s;
 }
 
-// K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised), or with kappa > 0 the modified
-// Helmholtz kernel exp(-kappa |x_i - y_j|) / (4 pi |x_i - y_j|); 0 where the points coincide.
-Mat kernel_matrix(const Mat &x, const Mat &y, double kappa) {
-    int m = (int)x.size() / 3, n = (int)y.size() / 3;
-    Mat k((size_t)m * n);
+// K(x_i, y_j) = 1/(4 pi |x_i - y_j|) (Eq. 2 normalised), with kernel FMM_YUKAWA the modified
+// Helmholtz kernel exp(-param |x_i - y_j|) / (4 pi |x_i - y_j|), 0 where the points coincide; an
+// m x n matrix.  With FMM_HELMHOLTZ the kernel exp(i param |x_i - y_j|) / (4 pi |x_i - y_j|) is
+// complex and the result is its real form [[Re K, -Im K], [Im K, Re K]] (2m x 2n), which maps the
+// real vector [Re v; Im v] to [Re Kv; Im Kv].  Products, transposes and pseudo-inverses of real
+// forms are the real forms of the complex ones, so every operator below is built unchanged.
+Mat kernel_matrix(const Mat &x, const Mat &y, int kernel, double param) {
+    const int m = (int)x.size() / 3, n = (int)y.size() / 3;
+    const bool cplx = kernel == FMM_HELMHOLTZ;
+    const int ld = cplx ? 2 * n : n;
+    Mat k((size_t)(cplx ? 2 * m : m) * ld, 0.0);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < n; ++j) {
             double dx = x[3 * i] - y[3 * j], dy = x[3 * i + 1] - y[3 * j + 1],
                    dz = x[3 * i + 2] - y[3 * j + 2];
             double r = std::sqrt(dx * dx + dy * dy + dz * dz);
-            k[(size_t)i * n + j] = r > 0.0 ? kInv4Pi * (kappa > 0.0 ? std::exp(-kappa * r) : 1.0) / r : 0.0;
+            if (!(r > 0.0)) continue;
+            if (!cplx) {
+                k[(size_t)i * n + j] = kInv4Pi * (kernel == FMM_YUKAWA ? std::exp(-param * r) : 1.0) / r;
+                continue;
+            }
+            const double re = kInv4Pi * std::cos(param * r) / r, im = kInv4Pi * std::sin(param * r) / r;
+            k[(size_t)i * ld + j] = re;
+            k[(size_t)i * ld + n + j] = -im;
+            k[(size_t)(m + i) * ld + j] = im;
+            k[(size_t)(m + i) * ld + n + j] = re;
         }
     return k;
 }
@@ -270,15 +285,21 @@ struct LevelBuild {
     std::vector<double> ll, lr;         // their eigenvalues
 };
 
-LevelBuild build_level(int p, double pinv_rtol, double kappa_u) {
+LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     LevelBuild b;
     b.h = std::make_unique<HostOps>();
     HostOps *h = b.h.get();
     h->p = p;
+    h->kernel = kernel;
     h->kappa_u = kappa_u;
     std::vector<double> grid = surface_grid(p);
-    const int ns = (int)grid.size() / 3;
+    h->npts = (int)grid.size() / 3;
+    // ns: the length of a box vector (the surface points, twice that for complex values)
+    const int ns = kernel == FMM_HELMHOLTZ ? 2 * h->npts : h->npts;
     h->ns = ns;
+    auto kernel_matrix = [&](const Mat &x, const Mat &y, double param) {
+        return fmm::kernel_matrix(x, y, kernel, param);
+    };
     Mat ue = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaInner);   // upward equivalent
     Mat uc = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaOuter);   // upward check
     Mat dc = ue;                                                // downward check (1.05)
@@ -298,8 +319,8 @@ LevelBuild build_level(int p, double pinv_rtol, double kappa_u) {
     h->close2 = dc_vs;   // [ns x r_dc]
 
     // A child box of half-width 1/2 sees the kernel K_{kappa_u}(x/2, y/2) = 2 K_{kappa_u/2}(x, y)
-    // of its own unit box, so its pseudo-inverse is (1/2) pinv(K_{kappa_u/2}(uc, ue)); for
-    // Laplace that is (1/2) UC2E.
+    // of its own unit box (for the Helmholtz kernel with the wavenumber in place of kappa), so
+    // its pseudo-inverse is (1/2) pinv(K_{kappa_u/2}(uc, ue)); for Laplace that is (1/2) UC2E.
     Mat child_uc2e = uc2e;
     if (kappa_u > 0.0) {
         Mat vs, ut;
@@ -419,15 +440,15 @@ std::vector<double> surface_grid(int p) {
     return g;
 }
 
-std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol,
+std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol, int kernel,
                                                   const std::vector<double> &kappa_u, std::string *err) {
     static std::mutex mu;
-    static std::map<std::tuple<int, double, double, std::vector<double>>, std::vector<std::unique_ptr<HostOps>>>
+    static std::map<std::tuple<int, double, double, int, std::vector<double>>, std::vector<std::unique_ptr<HostOps>>>
         cache;
     std::lock_guard<std::mutex> lock(mu);
     std::vector<double> key_k = kappa_u;
-    for (auto &k : key_k) k = std::max(k, 0.0);
-    auto key = std::make_tuple(p, pinv_rtol, svd_rtol, key_k);
+    for (auto &k : key_k) k = kernel == FMM_LAPLACE ? 0.0 : std::max(k, 0.0);
+    auto key = std::make_tuple(p, pinv_rtol, svd_rtol, kernel, key_k);
     auto it = cache.find(key);
     if (it == cache.end()) {
         // distinct kappa_u values only; the M2L ranks are the largest any of them needs, so that
@@ -438,7 +459,7 @@ std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, doubl
         std::vector<LevelBuild> lb;
         int kin = 1, kout = 1;
         for (double k : uniq) {
-            lb.push_back(build_level(p, pinv_rtol, k));
+            lb.push_back(build_level(p, pinv_rtol, kernel, k));
             kin = std::max(kin, rank_of(lb.back().lr, svd_rtol));
             kout = std::max(kout, rank_of(lb.back().ll, svd_rtol));
         }
@@ -461,7 +482,7 @@ std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, doubl
 }
 
 const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err) {
-    auto v = host_operator_levels(p, pinv_rtol, svd_rtol, {0.0}, err);
+    auto v = host_operator_levels(p, pinv_rtol, svd_rtol, FMM_LAPLACE, {0.0}, err);
     return v.empty() ? nullptr : v[0];
 }
 

@@ -158,7 +158,8 @@ fmm_ctx *new_view(const fmm_ctx *ctx) {
     v->device = ctx->device;
     v->fp64 = ctx->fp64;
     v->tensor = ctx->tensor;
-    v->ns = ctx->ns, v->nsp = ctx->nsp;
+    v->ns = ctx->ns, v->nsp = ctx->nsp, v->npts = ctx->npts;
+    v->cplx = ctx->cplx;
     for (int a = 0; a < 3; ++a) v->origin[a] = ctx->origin[a];
     v->side = ctx->side;
     v->grid_dev = ctx->grid_dev;

@@ -8,8 +8,11 @@ SVD_RTOL = 1e-6
 
 
 def rel(a, b):
-    a = np.asarray(a, dtype=np.float64).ravel()
-    b = np.asarray(b, dtype=np.float64).ravel()
+    """Relative L2 error of a against b (complex values keep their imaginary parts)."""
+    cplx = np.iscomplexobj(a) or np.iscomplexobj(b)
+    dt = np.complex128 if cplx else np.float64
+    a = np.asarray(a, dtype=dt).ravel()
+    b = np.asarray(b, dtype=dt).ravel()
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 

@@ -66,7 +66,8 @@ def test_default_options_and_validation_without_gpu(libpath):
     o.has_domain, o.side = 1, -1.0
     assert lib.fmm_create(ctypes.byref(o), None, ctypes.byref(ctx)) == 1
     # the modified Helmholtz kernel: kappa finite and > 0, a domain, no mean_free
-    for kernel, kappa, has_domain, mean_free, want in ((2, 1.0, 1, 0, 1), (1, 0.0, 1, 0, 1),
+    for kernel, kappa, has_domain, mean_free, want in ((3, 1.0, 1, 0, 1), (1, 0.0, 1, 0, 1),
+                                                       (2, 0.0, 1, 0, 1), (2, 1.0, 0, 0, 6), (2, 1.0, 1, 1, 6),
                                                        (1, -1.0, 1, 0, 1), (1, float("nan"), 1, 0, 1),
                                                        (1, float("inf"), 1, 0, 1), (1, 1.0, 0, 0, 6),
                                                        (1, 1.0, 1, 1, 6)):
