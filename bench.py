@@ -42,6 +42,10 @@ FLOPS_PER_PAIR = 20          # conventional count for a potential+gradient Lapla
 # modified Helmholtz: + r = r2 / r, the exponent's argument, exp (one flop, like rsqrt), the
 # screening product, 1 + kappa r (two) and the gradient factor's product
 FLOPS_PER_PAIR_YUKAWA = FLOPS_PER_PAIR + 7
+# Helmholtz (complex charges, potential and gradient): d (3), r^2 (5), rsqrt, r, k r, sin and cos
+# (one flop each), the complex product w = q e^{ikr} / r (8), the potential (2), the gradient
+# factor w (ikr - 1) / r^2 (7) and the six gradient components (12)
+FLOPS_PER_PAIR_HELMHOLTZ = 42
 SAMPLE_N = 2_097_152         # CPU sample: same sphere distribution, depth 6 -> ~112 points/leaf
 SAMPLE_DEPTH = 6
 
@@ -147,16 +151,22 @@ def recorded_traffic(kernel, digest):
     return rec.get("bytes_per_launch_full")
 
 
-def cpu_baseline_sample(p, kappa=0.0):
+def complex_charges(n, seed=1):
+    """Complex densities of the Helmholtz runs: U[0,1) real and imaginary parts (seeds 1 and 101)."""
+    return charges(n, "u01", seed=seed) + 1j * charges(n, "u01", seed=seed + 100)
+
+
+def cpu_baseline_sample(p, kappa=0.0, wavenumber=0.0):
     """The FP64 oracle kiFMM on a bounded sample of the same workload family."""
     from oracle import direct, kifmm
     x = sphere_points(SAMPLE_N)
-    q = charges(SAMPLE_N, "u01")
+    q = complex_charges(SAMPLE_N) if wavenumber > 0 else charges(SAMPLE_N, "u01").astype(np.float64)
     t0 = time.perf_counter()
-    kifmm.evaluate(x.astype(np.float64), q.astype(np.float64), p, SAMPLE_DEPTH, (-1, -1, -1), 2.0,
-                   pinv_rtol=1e-7, gradient=True, kappa=kappa)
+    kifmm.evaluate(x.astype(np.float64), q, p, SAMPLE_DEPTH, (-1, -1, -1), 2.0,
+                   pinv_rtol=1e-7, gradient=True, kappa=kappa, wavenumber=wavenumber)
     dt = time.perf_counter() - t0
-    kern = f"modified Helmholtz kappa={kappa:g}, " if kappa > 0 else ""
+    kern = (f"modified Helmholtz kappa={kappa:g}, " if kappa > 0 else
+            f"Helmholtz k={wavenumber:g}, complex densities, " if wavenumber > 0 else "")
     return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": direct.num_threads(),
             "host_cpus": os.cpu_count(), "kind": "oracle", "seconds": round(dt, 2),
             "sample": f"FP64 oracle kiFMM ({kern}p={p}, potentials+gradients, tree and operators "
@@ -164,13 +174,14 @@ def cpu_baseline_sample(p, kappa=0.0):
                       f"depth {SAMPLE_DEPTH} (~112 points per leaf, as in the full workload)"}
 
 
-def accuracy_check(w, x, q, phi, grad, m=256, kappa=0.0):
+def accuracy_check(w, x, q, phi, grad, m=256, kappa=0.0, wavenumber=0.0):
     """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum
     (phi None: gradient only)."""
     from oracle import direct
     idx = sample_indices(w.n, m, SEED_SAMPLE)
     x64 = x.astype(np.float64)
-    p_ref, g_ref = direct.direct_self(x64, q.astype(np.float64), sample=idx, kappa=kappa)
+    q = q.astype(np.complex128 if wavenumber > 0 else np.float64)
+    p_ref, g_ref = direct.direct_self(x64, q, sample=idx, kappa=kappa, wavenumber=wavenumber)
     e_p = None if phi is None else float(np.linalg.norm(phi[idx] - p_ref) / np.linalg.norm(p_ref))
     e_g = float(np.linalg.norm(grad[idx] - g_ref) / np.linalg.norm(g_ref))
     return {"phi": e_p, "grad": e_g, "targets": int(m),
@@ -184,7 +195,7 @@ def run_reference(args, w):
     times = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline_sample(w.p, args.kappa)
+        info = cpu_baseline_sample(w.p, *kernel_params(args))
         if i >= args.warmup:
             times.append(info["seconds"])
     mean_s = sum(times) / len(times)
@@ -194,7 +205,7 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "n": w.n, "p": w.p,
                                             "depth": w.depth, "dist": w.dist, "kernel": args.kernel,
-                                            **({"kappa": args.kappa} if args.kernel == "yukawa" else {})},
+                                            **kernel_config(args)},
             "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,6 +289,16 @@ def run_partition_bench(args, w, fmm, x, q, phi, grad, flush, stream, ws, rank):
     return 0
 
 
+def kernel_params(args):
+    """(kappa, wavenumber) of the oracle for the chosen kernel."""
+    return (args.kappa if args.kernel == "yukawa" else 0.0, args.kappa if args.kernel == "helmholtz" else 0.0)
+
+
+def kernel_config(args):
+    return ({"kappa": args.kappa} if args.kernel == "yukawa" else
+            {"wavenumber": args.kappa, "values": "complex"} if args.kernel == "helmholtz" else {})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,16 +309,19 @@ def main():
     ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default="laplace", choices=["laplace", "yukawa"],
-                    help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r)")
+    ap.add_argument("--kernel", default="laplace", choices=["laplace", "yukawa", "helmholtz"],
+                    help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r); helmholtz: "
+                         "exp(i kappa r)/(4 pi r) with complex densities")
     ap.add_argument("--outputs", default="potential+gradient", choices=["potential+gradient", "gradient"],
                     help="gradient: the gradient-only (force) evaluation, phi = NULL")
     ap.add_argument("--partition", default=None, metavar="DG:P1,P2,...",
                     help="time the partitioned evaluation on virtual ranks (tree split at depth DG, "
                          "P ranks) beside the unpartitioned one, for every P listed")
     ap.add_argument("--kappa", type=float, default=None,
-                    help="yukawa screening constant (default 3, i.e. kappa r = 0.023 at the leaves "
-                         "and 0.75 at level 2 of the default workload)")
+                    help="yukawa screening constant or helmholtz wavenumber (default 3 for yukawa, "
+                         "i.e. kappa r = 0.023 at the leaves and 0.75 at level 2 of the default "
+                         "workload; 2 for helmholtz: 0.64 wavelengths across the sphere, where p = 6 "
+                         "meets 1e-5)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -306,7 +330,7 @@ def main():
             ap.error("--kappa applies to --kernel yukawa")
         args.kappa = 0.0
     elif args.kappa is None:
-        args.kappa = 3.0
+        args.kappa = 3.0 if args.kernel == "yukawa" else 2.0
     elif not args.kappa > 0:
         ap.error("--kappa must be > 0")
     w = WORKLOADS[args.workload]
@@ -325,11 +349,14 @@ def main():
     stream = torch.cuda.current_stream()
     fp64 = args.precision == "fp64"
     tdt = torch.float64 if fp64 else torch.float32
-    x_np, q_np = w.points(), w.charges()
+    helm = args.kernel == "helmholtz"
+    vdt = (torch.complex128 if fp64 else torch.complex64) if helm else tdt   # densities and outputs
+    x_np = w.points()
+    q_np = complex_charges(w.n) if helm else w.charges()
     x = torch.from_numpy(x_np).to(dev, tdt)
-    q = torch.from_numpy(q_np).to(dev, tdt)
-    phi = torch.empty(w.n, device=dev, dtype=tdt)
-    grad = torch.empty(w.n, 3, device=dev, dtype=tdt)
+    q = torch.from_numpy(q_np).to(dev, vdt)
+    phi = torch.empty(w.n, device=dev, dtype=vdt)
+    grad = torch.empty(w.n, 3, device=dev, dtype=vdt)
     fmm = pkg.FMM(p=w.p, depth=w.depth, precision=args.precision, domain=(w.origin, w.side),
                   stream=stream.cuda_stream, kernel=args.kernel, kappa=args.kappa)
     fmm.precompute()
@@ -376,9 +403,9 @@ def main():
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     xh = torch.from_numpy(x_np).to(tdt).pin_memory()
-    qh = torch.from_numpy(q_np).to(tdt).pin_memory()
-    ph = torch.empty(w.n, dtype=tdt).pin_memory()
-    gh = torch.empty(w.n, 3, dtype=tdt).pin_memory()
+    qh = torch.from_numpy(q_np).to(vdt).pin_memory()
+    ph = torch.empty(w.n, dtype=vdt).pin_memory()
+    gh = torch.empty(w.n, 3, dtype=vdt).pin_memory()
     ph_out = None if grad_only else ph
     for _ in range(2):
         fmm.build_tree(xh)
@@ -396,19 +423,22 @@ def main():
         e2e_s.append(time.perf_counter() - t0)
     e2e_value = job_rate(w.n, args.steps, ws, slowest(sum(e2e_s), dev, ws))
     es = 8 if fp64 else 4
-    h2d = w.n * 3 * es + w.n * es
-    d2h = (0 if grad_only else w.n * es) + w.n * 3 * es
+    vs = 2 * es if helm else es    # one density or output value
+    h2d = w.n * 3 * es + w.n * vs
+    d2h = (0 if grad_only else w.n * vs) + w.n * 3 * vs
 
     # adjoint timing (reported beside the metric, not part of the step)
     fmm.build_tree(x)
     g_adj = torch.empty_like(phi)
     torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    psi, _ = fmm.adjoint(q)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    adjoint_ms = a0.elapsed_time(a1)
+    adjoint_ms = None   # the Helmholtz kernel has no adjoint
+    if not helm:
+        a0.record(stream)
+        psi, _ = fmm.adjoint(q)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        adjoint_ms = a0.elapsed_time(a1)
     fmm.evaluate_into(q, phi, grad)
     torch.cuda.synchronize()
 
@@ -432,11 +462,12 @@ def main():
     fmm.evaluate_into(q, phi, grad)
     torch.cuda.synchronize()
     pairs = info["p2p_pairs"]
-    fpp = (FLOPS_PER_PAIR_YUKAWA if args.kernel == "yukawa" else FLOPS_PER_PAIR) - (1 if grad_only else 0)
+    fpp = ({"yukawa": FLOPS_PER_PAIR_YUKAWA, "helmholtz": FLOPS_PER_PAIR_HELMHOLTZ}.get(args.kernel, FLOPS_PER_PAIR)
+           - (1 if grad_only else 0))
     p2p_flops = pairs * fpp
     p2p = {"bound": "alu", "achieved": p2p_flops / (near_ms * 1e-3) / 1e12,
            "peak": fp32_peak_tf, "unit": "TFLOP/s",
-           "kernel": "p2p_f32_kernel (ULI near field)",
+           "kernel": "helm_p2p_kernel (ULI near field)" if helm else "p2p_f32_kernel (ULI near field)",
            "peak_basis": f"measured FP32 FMA throughput on this GPU (fmm_measure_fp32_peak: scalar "
                          f"{fp32_scalar_tf:.1f}, float2 {fp32_pair_tf:.1f} TFLOP/s); nominal "
                          f"{sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz = {nominal_fp32_tf:.1f}; "
@@ -449,7 +480,7 @@ def main():
                         "frac_of_nominal": p2p_flops / (near_iso_ms * 1e-3) / 1e12 / nominal_fp32_tf,
                         "timing": "the same launch with the near field alone (after the timed steps)"}}
     p2p["frac"] = p2p["achieved"] / p2p["peak"]
-    p2p["traffic"] = recorded_traffic("p2p_f32_kernel", source_digest("p2p.cu"))
+    p2p["traffic"] = None if helm else recorded_traffic("p2p_f32_kernel", source_digest("p2p.cu"))
     # M2L algorithmic flops: compress + stencil products over the real V pairs
     kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"]
     vpairs = 0
@@ -516,8 +547,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
-                       "precision": args.precision, "kernel": args.kernel,
-                       **({"kappa": args.kappa} if args.kernel == "yukawa" else {}),
+                       "precision": args.precision, "kernel": args.kernel, **kernel_config(args),
                        "l2": "flushed (256 MB write) between steps",
                        "step": f"build_tree + evaluate({args.outputs})", "outputs": args.outputs,
                        "parallelism": f"replicas x{ws}"},
@@ -534,10 +564,12 @@ def main():
         if grad_only:   # the timed steps left no potentials: check the gradient-only result
             fmm.evaluate_into(q, None, grad)
             torch.cuda.synchronize()
-        line["accuracy"] = accuracy_check(w, x_np, q_np, None if grad_only else phi.cpu().numpy().astype(np.float64),
-                                          grad.cpu().numpy().astype(np.float64), kappa=args.kappa)
+        odt = np.complex128 if helm else np.float64
+        line["accuracy"] = accuracy_check(w, x_np, q_np, None if grad_only else phi.cpu().numpy().astype(odt),
+                                          grad.cpu().numpy().astype(odt), kappa=kernel_params(args)[0],
+                                          wavenumber=kernel_params(args)[1])
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(w.p, args.kappa)
+        line["cpu_baseline"] = cpu_baseline_sample(w.p, *kernel_params(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     fmm.close()

@@ -6,8 +6,8 @@
 // Per (target x, source y) pair, r = |x - y| and d = x - y:
 //   w = s exp(i k r) / r,  phi += w / (4 pi),  grad phi += w (i k r - 1) d / (4 pi r^2).
 // Pairs at distance zero are skipped.  The densities' imaginary parts live beside the points
-// (pts holds (x, y, z, Re s)); potentials and gradients are interleaved (re, im).  sincos is the
-// accurate form: in shallow trees k r exceeds pi.
+// (pts holds (x, y, z, Re s)); potentials and gradients are interleaved (re, im).  In shallow
+// trees k r exceeds pi, so the FP32 sine and cosine reduce the argument first.
 #include <algorithm>
 #include <type_traits>
 
@@ -25,7 +25,15 @@ template <typename T> __host__ __device__ constexpr T k_inv4pi() { return (T)0.0
 
 __device__ __forceinline__ float rsqrt_c(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_c(double x) { return rsqrt(x); }
-__device__ __forceinline__ void sincos_c(float x, float *s, float *c) { sincosf(x, s, c); }
+// FP32: Cody-Waite reduction of x by multiples of 2 pi (2 pi split into its FP32 rounding and the
+// remainder), then the hardware sin/cos approximation, whose absolute error is about 2^-21 on
+// [-pi, pi]; the reduction keeps that error for |k r| up to about 10^5.
+__device__ __forceinline__ void sincos_c(float x, float *s, float *c) {
+    const float t = rintf(x * 0.15915494309189535f);     // x / (2 pi), rounded
+    float r = fmaf(-t, 6.2831854820251465f, x);          // 2 pi rounded to FP32
+    r = fmaf(-t, -1.7484555314695172e-07f, r);           // 2 pi minus its FP32 rounding
+    __sincosf(r, s, c);
+}
 __device__ __forceinline__ void sincos_c(double x, double *s, double *c) { sincos(x, s, c); }
 
 // one pair: accumulate the potential (pr, pi) and, with GRAD, the gradient g[6]

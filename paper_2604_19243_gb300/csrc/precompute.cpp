@@ -307,11 +307,17 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     h->surf_inner = ue;
     h->surf_outer = uc;
 
-    // check-to-equivalent pseudo-inverses on the unit box
-    Mat uc_vs, uc_ut, dc_vs, dc_ut;
-    int r_uc = 0, r_dc = 0;
-    pinv_factors(kernel_matrix(uc, ue, kappa_u), ns, pinv_rtol, uc_vs, uc_ut, r_uc);
-    pinv_factors(kernel_matrix(dc, de, kappa_u), ns, pinv_rtol, dc_vs, dc_ut, r_dc);
+    // check-to-equivalent pseudo-inverses on the unit box, and the child's (below); the three
+    // factorisations are independent and run on threads of their own
+    Mat uc_vs, uc_ut, dc_vs, dc_ut, ch_vs, ch_ut;
+    int r_uc = 0, r_dc = 0, r_ch = 0;
+    {
+        std::thread t1([&] { pinv_factors(kernel_matrix(uc, ue, kappa_u), ns, pinv_rtol, uc_vs, uc_ut, r_uc); });
+        std::thread t2([&] { pinv_factors(kernel_matrix(dc, de, kappa_u), ns, pinv_rtol, dc_vs, dc_ut, r_dc); });
+        if (kappa_u > 0.0) pinv_factors(kernel_matrix(uc, ue, 0.5 * kappa_u), ns, pinv_rtol, ch_vs, ch_ut, r_ch);
+        t1.join();
+        t2.join();
+    }
     Mat uc2e = matmul(uc_vs, uc_ut, ns, r_uc, ns);
     Mat dc2e = matmul(dc_vs, dc_ut, ns, r_dc, ns);
     h->rcl = r_dc;
@@ -321,13 +327,7 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     // A child box of half-width 1/2 sees the kernel K_{kappa_u}(x/2, y/2) = 2 K_{kappa_u/2}(x, y)
     // of its own unit box (for the Helmholtz kernel with the wavenumber in place of kappa), so
     // its pseudo-inverse is (1/2) pinv(K_{kappa_u/2}(uc, ue)); for Laplace that is (1/2) UC2E.
-    Mat child_uc2e = uc2e;
-    if (kappa_u > 0.0) {
-        Mat vs, ut;
-        int rk = 0;
-        pinv_factors(kernel_matrix(uc, ue, 0.5 * kappa_u), ns, pinv_rtol, vs, ut, rk);
-        child_uc2e = matmul(vs, ut, ns, rk, ns);
-    }
+    Mat child_uc2e = kappa_u > 0.0 ? matmul(ch_vs, ch_ut, ns, r_ch, ns) : uc2e;
     for (auto &x : child_uc2e) x *= 0.5;
 
     // U2U and D2D per octant (child half-width 1/2, centre offset +-1/2 per axis, x bit first)
@@ -367,8 +367,9 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
             gl[0][i] += gl[w][i];
             gr[0][i] += gr[w][i];
         }
-    jacobi_eig(gl[0], ns, b.ql, b.ll);
+    std::thread te([&] { jacobi_eig(gl[0], ns, b.ql, b.ll); });
     jacobi_eig(gr[0], ns, b.qr, b.lr);
+    te.join();
     return b;
 }
 
