@@ -97,6 +97,93 @@ helm_p2p_kernel(const typename V4<T>::type *__restrict__ pts, const T *__restric
     }
 }
 
+// FP32 ULI on pairs of sources: the two-wide FP32 instructions (add, mul, fma on float2) do the
+// arithmetic of two (target, source) pairs per issue slot.  A chunk's sources are staged as pairs
+// (j, k): A = [-x_j -x_k -y_j -y_k], B = [-z_j -z_k Re s_j Re s_k], C = [Im s_j Im s_k], padded with
+// a zero density to an even count, so that one add forms x - y.  The reciprocal square root, the
+// argument reduction and the hardware sine and cosine stay per lane.
+template <bool POT, bool GRAD>
+__global__ void __launch_bounds__(kThreads)
+helm_p2p_f32_kernel(const float4 *__restrict__ pts, const float *__restrict__ qi, const int *__restrict__ leaf_off,
+                    const int *__restrict__ u_off, const int *__restrict__ u_idx, const int *__restrict__ order, float k,
+                    float *__restrict__ phi, float *__restrict__ grad) {
+    constexpr int kPairs = kChunk / 2;
+    __shared__ __align__(16) float4 sa[kPairs], sb[kPairs];
+    __shared__ __align__(16) float2 sc[kPairs];
+    const int b = order[blockIdx.x];
+    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    const float2 k2 = make_float2(k, k);
+    for (int tb = t0; tb < t1; tb += kThreads) {
+        const int i = tb + threadIdx.x;
+        // a warp without targets in this pass only helps stage the sources
+        const bool busy = tb + (int)(threadIdx.x & ~31u) < t1;
+        const float4 x = pts[min(i, t1 - 1)];
+        const float2 x2 = make_float2(x.x, x.x), y2 = make_float2(x.y, x.y), z2 = make_float2(x.z, x.z);
+        float2 pr = make_float2(0.f, 0.f), pim = pr, gxr = pr, gxi = pr, gyr = pr, gyi = pr, gzr = pr, gzi = pr;
+        for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
+            const int a = u_idx[e];
+            const int s0 = leaf_off[a], s1 = leaf_off[a + 1];
+            for (int c0 = s0; c0 < s1; c0 += kChunk) {
+                const int n = min(kChunk, s1 - c0), L = (n + 1) >> 1;
+                __syncthreads();
+                for (int j = threadIdx.x; j < 2 * L; j += kThreads) {
+                    const bool real = j < n;
+                    const float4 v = pts[c0 + min(j, n - 1)];
+                    const float q_i = real ? qi[c0 + j] : 0.f;
+                    float *A = reinterpret_cast<float *>(sa + (j >> 1)), *B = reinterpret_cast<float *>(sb + (j >> 1));
+                    float *C = reinterpret_cast<float *>(sc + (j >> 1));
+                    const int h = j & 1;
+                    A[h] = -v.x, A[2 + h] = -v.y, B[h] = -v.z, B[2 + h] = real ? v.w : 0.f, C[h] = q_i;
+                }
+                __syncthreads();
+                for (int e2 = 0; e2 < (busy ? L : 0); ++e2) {
+                    const float4 A = sa[e2], B = sb[e2];
+                    const float2 qim = sc[e2], qre = make_float2(B.z, B.w);
+                    const float2 dx = __fadd2_rn(make_float2(A.x, A.y), x2);    // x - y
+                    const float2 dy = __fadd2_rn(make_float2(A.z, A.w), y2);
+                    const float2 dz = __fadd2_rn(make_float2(B.x, B.y), z2);
+                    float2 r2 = __fmul2_rn(dx, dx);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+                    const float2 kr = __fmul2_rn(k2, __fmul2_rn(r2, ri));
+                    float2 sn, cs;
+                    sincos_c(kr.x, &sn.x, &cs.x);
+                    sincos_c(kr.y, &sn.y, &cs.y);
+                    // w = s e^{ikr} / r
+                    const float2 nqi = __fmul2_rn(qim, make_float2(-1.f, -1.f));
+                    const float2 wr = __fmul2_rn(__ffma2_rn(qre, cs, __fmul2_rn(nqi, sn)), ri);
+                    const float2 wi = __fmul2_rn(__ffma2_rn(qre, sn, __fmul2_rn(qim, cs)), ri);
+                    if (POT) {
+                        pr = __fadd2_rn(pr, wr);
+                        pim = __fadd2_rn(pim, wi);
+                    }
+                    if (GRAD) {
+                        // z = w (i k r - 1) / r^2 = -(w + ... ): zr = -(wr + kr wi) ri^2, zi = -(wi - kr wr) ri^2
+                        const float2 nri2 = __fmul2_rn(ri, __fmul2_rn(ri, make_float2(-1.f, -1.f)));
+                        const float2 nkr = __fmul2_rn(kr, make_float2(-1.f, -1.f));
+                        const float2 zr = __fmul2_rn(__ffma2_rn(kr, wi, wr), nri2);
+                        const float2 zi = __fmul2_rn(__ffma2_rn(nkr, wr, wi), nri2);
+                        gxr = __ffma2_rn(zr, dx, gxr), gxi = __ffma2_rn(zi, dx, gxi);
+                        gyr = __ffma2_rn(zr, dy, gyr), gyi = __ffma2_rn(zi, dy, gyi);
+                        gzr = __ffma2_rn(zr, dz, gzr), gzi = __ffma2_rn(zi, dz, gzi);
+                    }
+                }
+            }
+        }
+        if (i < t1) {
+            const float f = k_inv4pi<float>();
+            if (POT) phi[2 * (int64_t)i] = (pr.x + pr.y) * f, phi[2 * (int64_t)i + 1] = (pim.x + pim.y) * f;
+            if (GRAD) {
+                float *g = grad + 6 * (int64_t)i;
+                g[0] = (gxr.x + gxr.y) * f, g[1] = (gxi.x + gxi.y) * f;
+                g[2] = (gyr.x + gyr.y) * f, g[3] = (gyi.x + gyi.y) * f;
+                g[4] = (gzr.x + gzr.y) * f, g[5] = (gzi.x + gzi.y) * f;
+            }
+        }
+    }
+}
+
 // S2U: the complex check values on the 2.95 surface of every leaf, row = [Re (npts) | Im (npts) | 0]
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -235,9 +322,15 @@ cudaError_t helm_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
         kern<<<ctx->nleaf, kThreads, 0, s>>>((const P *)ctx->pts, (const T *)ctx->pts_qi, ctx->leaf_off, ctx->u_off,
                                               ctx->u_idx, ctx->p2p_order, k, phi, grad);
     };
-    if (phi && grad) go(helm_p2p_kernel<T, true, true>);
-    else if (grad) go(helm_p2p_kernel<T, false, true>);
-    else go(helm_p2p_kernel<T, true, false>);
+    if constexpr (std::is_same<T, float>::value) {
+        if (phi && grad) go(helm_p2p_f32_kernel<true, true>);
+        else if (grad) go(helm_p2p_f32_kernel<false, true>);
+        else go(helm_p2p_f32_kernel<true, false>);
+    } else {
+        if (phi && grad) go(helm_p2p_kernel<T, true, true>);
+        else if (grad) go(helm_p2p_kernel<T, false, true>);
+        else go(helm_p2p_kernel<T, true, false>);
+    }
     count_launch();
     return cudaGetLastError();
 }
