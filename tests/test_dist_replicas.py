@@ -33,7 +33,7 @@ def _worker(rank, ws, port, out):
 
 def test_slowest_rank_and_job_rate_gloo():
     ws, port = 2, _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
     for r in range(ws):
         t, rate = out[r]
