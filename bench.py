@@ -495,9 +495,9 @@ def main():
     m2l_flops = compress_flops + stencil_flops
     tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3", "fp16x3")
     if tensor:
-        six = args.precision in ("bf16x6", "fp16x3")          # compress runs BF16x6 in both
-        m_compress = 6 if six else 3
-        m_stencil = 6 if args.precision == "bf16x6" else 3
+        # products per contraction: BF16x6 six, the other split modes three (FP16X3 runs every
+        # contraction, the compress included, on hi/lo FP16 planes)
+        m_compress = m_stencil = 6 if args.precision == "bf16x6" else 3
         tc_flops = m_compress * compress_flops + m_stencil * stencil_flops
         base = float(peaks["bf16_tflops_sustained"]) * (0.5 if args.precision == "tf32x3" else 1.0)
         m2l = {"bound": "tensor", "achieved": tc_flops / (m2l_ms * 1e-3) / 1e12,
