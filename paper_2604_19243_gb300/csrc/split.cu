@@ -135,7 +135,7 @@ struct SplitState {
     // priority) and their ULI on near-field streams (lowest), forked from and joined into a
     // capture stream; the whole evaluation is captured once per output mode as a CUDA graph
     // that reads the densities from q_in and writes phi_out / grad_out.
-    static constexpr int kFar = 16, kNear = 4;
+    static constexpr int kFar = 48, kNear = 8;
     cudaStream_t cap = nullptr, far_s[kFar] = {}, near_s[kNear] = {};
     cudaEvent_t fork = nullptr, ev_far[kFar] = {}, ev_near[kNear] = {}, ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t exec[4] = {};      // by output mode: 1 potentials, 2 gradients, 3 both
