@@ -140,11 +140,14 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n);
 
 /* Host FP64 precompute of every operator (check-to-equivalent pseudo-inverses, U2U, D2D,
  * the 316 M2L operators and their SVD compression) and upload in the context's precision.
- * Independent of the points; may be called before or after fmm_build_tree. */
+ * Independent of the points; may be called before or after fmm_build_tree.  Laplace: one set for
+ * every level (homogeneity); FMM_YUKAWA and FMM_HELMHOLTZ: one set per level from the domain's box
+ * sizes, all with the M2L ranks of the level that needs the largest.  Cached per process. */
 fmm_status fmm_precompute(fmm_ctx *ctx);
 
 /* phi = A q (Algorithm 1), and grad phi if `grad` is non-NULL (requires with_gradient).
- * q: n densities; phi: n outputs; grad: n x 3 outputs; all in the input order of the points.
+ * q: n densities; phi: n outputs; grad: n x 3 outputs; all in the input order of the points
+ * (FMM_HELMHOLTZ: complex values, interleaved re, im: 2n, 2n and 6n numbers).
  * phi may be NULL when grad is not: the gradient-only ("force") evaluation of N-body codes, which
  * skips the potential sums of the near field and the potential outputs; its gradients are those
  * of the full evaluation bit for bit.

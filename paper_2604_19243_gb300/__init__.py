@@ -1,15 +1,19 @@
-"""Python binding of libfmm, a GB300 (sm_103a) kernel-independent FMM for the 3D Laplace kernel
-(and the modified Helmholtz kernel exp(-kappa r) / (4 pi r), `kernel="yukawa"`).
+"""Python binding of libfmm, a GB300 (sm_103a) kernel-independent FMM for the 3D Laplace kernel,
+the modified Helmholtz kernel exp(-kappa r) / (4 pi r) (`kernel="yukawa"`) and the Helmholtz
+kernel exp(i kappa r) / (4 pi r) with complex densities (`kernel="helmholtz"`).
 
 Argument marshalling only: every step of the FMM runs in the CUDA library behind the C ABI of
 include/fmm.h.  Importing this package does not build anything; call
 `paper_2604_19243_gb300.build.build()` first.  If the library is missing, every call raises.
 
-    fmm = FMM(p=6, depth=5, precision="fp32", domain=((0, 0, 0), 1.0))
+    fmm = FMM(p=6, depth=5, precision="fp16x3", domain=((0, 0, 0), 1.0))
     fmm.build_tree(x)            # x: (N, 3) float32 torch tensor (CUDA or CPU) or NumPy array
     fmm.precompute()
     phi, grad = fmm.evaluate(q)  # same device and dtype as q
-    psi = fmm.adjoint(g)         # the transpose of q -> phi
+    _, grad = fmm.evaluate(q, potential=False)   # gradient only
+    psi, _ = fmm.adjoint(g)      # the transpose of q -> phi
+    fmm.partition_setup(3, 64)   # the distributed scheme on 64 virtual ranks of this GPU
+    phi, grad = fmm.partition_evaluate(q)        # equal to evaluate(q) bit for bit
 """
 from __future__ import annotations
 
