@@ -72,7 +72,7 @@ def test_autograd_energy_gradients():
     dx = xt.grad.cpu().numpy().astype(np.float64)
     q64 = qn.astype(np.float64)
     phi_d, grad_d = direct.direct_self(x.astype(np.float64), q64)
-    assert abs(float(e) - 0.5 * q64 @ phi_d) / abs(0.5 * q64 @ phi_d) < 1e-5
+    assert abs(float(e.detach()) - 0.5 * q64 @ phi_d) / abs(0.5 * q64 @ phi_d) < 1e-5
     assert rel(dq, phi_d) < 1e-5                      # the symmetric direct-sum derivative
     assert rel(dx, q64[:, None] * grad_d) < 1e-4
     # central differences of the FP64 direct-sum energy (Richardson): moving x_k changes only
