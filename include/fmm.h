@@ -45,7 +45,7 @@ typedef enum {
     FMM_ECUDA = 3,         /* a CUDA call or kernel failed; the context should be destroyed */
     FMM_ESTATE = 4,        /* call out of order (e.g. evaluate before build_tree/precompute) */
     FMM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
-    FMM_EUNSUPPORTED = 6   /* option combination not available in this build */
+    FMM_EUNSUPPORTED = 6   /* option combination not available in this library */
 } fmm_status;
 
 /* Arithmetic of the surface contractions (U2U, VLI, D2D and the check-to-equivalent steps).

@@ -295,7 +295,7 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     if (far) {
         e = run_far<T>(ctx, adjoint, phi ? (T *)ctx->far_phi : nullptr, fg, fs);
         if (e == cudaErrorNotSupported)
-            return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
+            return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this library");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "far field");
     } else {
         cudaEventRecord(ctx->ev[2], fs), cudaEventRecord(ctx->ev[3], fs), cudaEventRecord(ctx->ev[4], fs);
@@ -517,7 +517,7 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     }
     if (e == cudaErrorNotSupported) {
         free_ops(ctx);
-        return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this build");
+        return fail(ctx, FMM_EUNSUPPORTED, "tensor-core contractions are not available in this library");
     }
     if (e != cudaSuccess) {
         free_ops(ctx);
