@@ -98,7 +98,9 @@ helm_p2p_kernel(const typename V4<T>::type *__restrict__ pts, const T *__restric
 }
 
 // FP32 ULI on pairs of sources: the two-wide FP32 instructions (add, mul, fma on float2) do the
-// arithmetic of two (target, source) pairs per issue slot.  A chunk's sources are staged as pairs
+// arithmetic of two (target, source) pairs per issue slot.  The U list's leaves form one sequence of
+// sources, staged kChunk at a time across leaf boundaries (fewer barriers than one leaf per stage),
+// and a chunk's sources are staged as pairs
 // (j, k): A = [-x_j -x_k -y_j -y_k], B = [-z_j -z_k Re s_j Re s_k], C = [Im s_j Im s_k], padded with
 // a zero density to an even count, so that one add forms x - y.  The reciprocal square root, the
 // argument reduction and the hardware sine and cosine stay per lane.
@@ -110,8 +112,21 @@ helm_p2p_f32_kernel(const float4 *__restrict__ pts, const float *__restrict__ qi
     constexpr int kPairs = kChunk / 2;
     __shared__ __align__(16) float4 sa[kPairs], sb[kPairs];
     __shared__ __align__(16) float2 sc[kPairs];
+    __shared__ int rbeg[27], rlen[27];
+    __shared__ int nr, total;
     const int b = order[blockIdx.x];
     const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    if (threadIdx.x == 0) {   // the U list's point ranges, one sequence of sources (at most 27 leaves)
+        int n = 0, tot = 0;
+        for (int e = u_off[b]; e < u_off[b + 1] && n < 27; ++e) {
+            const int a = u_idx[e];
+            rbeg[n] = leaf_off[a];
+            rlen[n] = leaf_off[a + 1] - leaf_off[a];
+            tot += rlen[n++];
+        }
+        nr = n, total = tot;
+    }
+    __syncthreads();
     const float2 k2 = make_float2(k, k);
     for (int tb = t0; tb < t1; tb += kThreads) {
         const int i = tb + threadIdx.x;
@@ -120,54 +135,54 @@ helm_p2p_f32_kernel(const float4 *__restrict__ pts, const float *__restrict__ qi
         const float4 x = pts[min(i, t1 - 1)];
         const float2 x2 = make_float2(x.x, x.x), y2 = make_float2(x.y, x.y), z2 = make_float2(x.z, x.z);
         float2 pr = make_float2(0.f, 0.f), pim = pr, gxr = pr, gxi = pr, gyr = pr, gyi = pr, gzr = pr, gzi = pr;
-        for (int e = u_off[b]; e < u_off[b + 1]; ++e) {
-            const int a = u_idx[e];
-            const int s0 = leaf_off[a], s1 = leaf_off[a + 1];
-            for (int c0 = s0; c0 < s1; c0 += kChunk) {
-                const int n = min(kChunk, s1 - c0), L = (n + 1) >> 1;
-                __syncthreads();
-                for (int j = threadIdx.x; j < 2 * L; j += kThreads) {
-                    const bool real = j < n;
-                    const float4 v = pts[c0 + min(j, n - 1)];
-                    const float q_i = real ? qi[c0 + j] : 0.f;
-                    float *A = reinterpret_cast<float *>(sa + (j >> 1)), *B = reinterpret_cast<float *>(sb + (j >> 1));
-                    float *C = reinterpret_cast<float *>(sc + (j >> 1));
-                    const int h = j & 1;
-                    A[h] = -v.x, A[2 + h] = -v.y, B[h] = -v.z, B[2 + h] = real ? v.w : 0.f, C[h] = q_i;
+        // the sources in chunks of kChunk across leaf boundaries: two barriers per chunk
+        for (int c0 = 0; c0 < total; c0 += kChunk) {
+            const int n = min(kChunk, total - c0), L = (n + 1) >> 1;
+            __syncthreads();
+            for (int j = threadIdx.x; j < 2 * L; j += kThreads) {
+                const bool real = j < n;
+                int g = c0 + min(j, n - 1), r = 0;   // source j of the chunk: range r, point g
+                while (g >= rlen[r]) g -= rlen[r++];
+                const int src = rbeg[r] + g;
+                const float4 v = pts[src];
+                const float q_i = real ? qi[src] : 0.f;
+                float *A = reinterpret_cast<float *>(sa + (j >> 1)), *B = reinterpret_cast<float *>(sb + (j >> 1));
+                float *C = reinterpret_cast<float *>(sc + (j >> 1));
+                const int h = j & 1;
+                A[h] = -v.x, A[2 + h] = -v.y, B[h] = -v.z, B[2 + h] = real ? v.w : 0.f, C[h] = q_i;
+            }
+            __syncthreads();
+            for (int e2 = 0; e2 < (busy ? L : 0); ++e2) {
+                const float4 A = sa[e2], B = sb[e2];
+                const float2 qim = sc[e2], qre = make_float2(B.z, B.w);
+                const float2 dx = __fadd2_rn(make_float2(A.x, A.y), x2);    // x - y
+                const float2 dy = __fadd2_rn(make_float2(A.z, A.w), y2);
+                const float2 dz = __fadd2_rn(make_float2(B.x, B.y), z2);
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+                const float2 kr = __fmul2_rn(k2, __fmul2_rn(r2, ri));
+                float2 sn, cs;
+                sincos_c(kr.x, &sn.x, &cs.x);
+                sincos_c(kr.y, &sn.y, &cs.y);
+                // w = s e^{ikr} / r
+                const float2 nqi = __fmul2_rn(qim, make_float2(-1.f, -1.f));
+                const float2 wr = __fmul2_rn(__ffma2_rn(qre, cs, __fmul2_rn(nqi, sn)), ri);
+                const float2 wi = __fmul2_rn(__ffma2_rn(qre, sn, __fmul2_rn(qim, cs)), ri);
+                if (POT) {
+                    pr = __fadd2_rn(pr, wr);
+                    pim = __fadd2_rn(pim, wi);
                 }
-                __syncthreads();
-                for (int e2 = 0; e2 < (busy ? L : 0); ++e2) {
-                    const float4 A = sa[e2], B = sb[e2];
-                    const float2 qim = sc[e2], qre = make_float2(B.z, B.w);
-                    const float2 dx = __fadd2_rn(make_float2(A.x, A.y), x2);    // x - y
-                    const float2 dy = __fadd2_rn(make_float2(A.z, A.w), y2);
-                    const float2 dz = __fadd2_rn(make_float2(B.x, B.y), z2);
-                    float2 r2 = __fmul2_rn(dx, dx);
-                    r2 = __ffma2_rn(dy, dy, r2);
-                    r2 = __ffma2_rn(dz, dz, r2);
-                    const float2 ri = make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
-                    const float2 kr = __fmul2_rn(k2, __fmul2_rn(r2, ri));
-                    float2 sn, cs;
-                    sincos_c(kr.x, &sn.x, &cs.x);
-                    sincos_c(kr.y, &sn.y, &cs.y);
-                    // w = s e^{ikr} / r
-                    const float2 nqi = __fmul2_rn(qim, make_float2(-1.f, -1.f));
-                    const float2 wr = __fmul2_rn(__ffma2_rn(qre, cs, __fmul2_rn(nqi, sn)), ri);
-                    const float2 wi = __fmul2_rn(__ffma2_rn(qre, sn, __fmul2_rn(qim, cs)), ri);
-                    if (POT) {
-                        pr = __fadd2_rn(pr, wr);
-                        pim = __fadd2_rn(pim, wi);
-                    }
-                    if (GRAD) {
-                        // z = w (i k r - 1) / r^2 = -(w + ... ): zr = -(wr + kr wi) ri^2, zi = -(wi - kr wr) ri^2
-                        const float2 nri2 = __fmul2_rn(ri, __fmul2_rn(ri, make_float2(-1.f, -1.f)));
-                        const float2 nkr = __fmul2_rn(kr, make_float2(-1.f, -1.f));
-                        const float2 zr = __fmul2_rn(__ffma2_rn(kr, wi, wr), nri2);
-                        const float2 zi = __fmul2_rn(__ffma2_rn(nkr, wr, wi), nri2);
-                        gxr = __ffma2_rn(zr, dx, gxr), gxi = __ffma2_rn(zi, dx, gxi);
-                        gyr = __ffma2_rn(zr, dy, gyr), gyi = __ffma2_rn(zi, dy, gyi);
-                        gzr = __ffma2_rn(zr, dz, gzr), gzi = __ffma2_rn(zi, dz, gzi);
-                    }
+                if (GRAD) {
+                    // z = w (i k r - 1) / r^2: zr = -(wr + kr wi) / r^2, zi = -(wi - kr wr) / r^2
+                    const float2 nri2 = __fmul2_rn(ri, __fmul2_rn(ri, make_float2(-1.f, -1.f)));
+                    const float2 nkr = __fmul2_rn(kr, make_float2(-1.f, -1.f));
+                    const float2 zr = __fmul2_rn(__ffma2_rn(kr, wi, wr), nri2);
+                    const float2 zi = __fmul2_rn(__ffma2_rn(nkr, wr, wi), nri2);
+                    gxr = __ffma2_rn(zr, dx, gxr), gxi = __ffma2_rn(zi, dx, gxi);
+                    gyr = __ffma2_rn(zr, dy, gyr), gyi = __ffma2_rn(zi, dy, gyi);
+                    gzr = __ffma2_rn(zr, dz, gzr), gzi = __ffma2_rn(zi, dz, gzi);
                 }
             }
         }
