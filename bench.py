@@ -289,6 +289,76 @@ def run_partition_bench(args, w, fmm, x, q, phi, grad, flush, stream, ws, rank):
     return 0
 
 
+def measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream, steps=10):
+    """The headline workload's other forms, each timed like the step (3 warm-up, `steps` timed,
+    L2 flushed between steps, CUDA events): the gradient-only evaluation, the modified Helmholtz
+    kernel, and the evaluation partitioned over 64 virtual ranks at depth 3.  A failure is reported
+    in place of the variant's numbers; the headline line is unaffected."""
+    import torch
+    import paper_2604_19243_gb300 as pkg
+    from oracle import direct
+
+    def timed(fn):
+        for _ in range(3):
+            flush.fill_(1)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.fill_(k & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = {}
+    try:   # gradient only: the same tree and step
+        ms = timed(lambda: (fmm.build_tree(x), fmm.evaluate_into(q, None, grad)))
+        out["gradient_only"] = {"points_per_s": w.n / (ms * 1e-3), "ms_per_step": ms,
+                                "step": "build_tree + evaluate(gradient)"}
+    except Exception as e:   # noqa: BLE001 - reported, not raised
+        out["gradient_only"] = {"error": str(e)}
+    try:   # modified Helmholtz, kappa = 3
+        fy = pkg.FMM(p=w.p, depth=w.depth, precision=args.precision, domain=(w.origin, w.side),
+                     stream=stream.cuda_stream, kernel="yukawa", kappa=3.0)
+        t0 = time.perf_counter()
+        fy.precompute()
+        pre_s = time.perf_counter() - t0
+        ms = timed(lambda: (fy.build_tree(x), fy.evaluate_into(q, phi, grad)))
+        acc = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
+                             grad.cpu().numpy().astype(np.float64), m=64, kappa=3.0)
+        fy.close()
+        out["yukawa_kappa3"] = {"points_per_s": w.n / (ms * 1e-3), "ms_per_step": ms,
+                                "precompute_s": round(pre_s, 2), "accuracy": acc,
+                                "step": "build_tree + evaluate(potential+gradient)"}
+    except Exception as e:   # noqa: BLE001
+        out["yukawa_kappa3"] = {"error": str(e)}
+    try:   # the distributed scheme on 64 virtual ranks (tree and partition built once)
+        fmm.build_tree(x)
+        fmm.evaluate_into(q, phi, grad)
+        ref_phi, ref_grad = phi.clone(), grad.clone()
+        t0 = time.perf_counter()
+        fmm.partition_setup(3, 64)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        ms = timed(lambda: fmm.partition_evaluate_into(q, phi, grad))
+        base = timed(lambda: fmm.evaluate_into(q, phi, grad))
+        fmm.partition_evaluate_into(q, phi, grad)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(phi, ref_phi) and torch.equal(grad, ref_grad))
+        out["partition_dg3_ranks64"] = {"points_per_s": w.n / (ms * 1e-3), "ms_per_evaluate": ms,
+                                        "unpartitioned_ms_per_evaluate": base, "setup_s": round(setup_s, 3),
+                                        "phases_ms": fmm.partition_timings(),
+                                        "bit_identical_to_unpartitioned": same,
+                                        "step": "evaluate on a built tree and partition"}
+    except Exception as e:   # noqa: BLE001
+        out["partition_dg3_ranks64"] = {"error": str(e)}
+    return out
+
+
 def kernel_params(args):
     """(kappa, wavenumber) of the oracle for the chosen kernel."""
     return (args.kappa if args.kernel == "yukawa" else 0.0, args.kappa if args.kernel == "helmholtz" else 0.0)
@@ -309,6 +379,9 @@ def main():
     ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variants measured after the headline (gradient only, modified "
+                         "Helmholtz, partitioned evaluation)")
     ap.add_argument("--kernel", default="laplace", choices=["laplace", "yukawa", "helmholtz"],
                     help="laplace: 1/(4 pi r); yukawa: exp(-kappa r)/(4 pi r); helmholtz: "
                          "exp(i kappa r)/(4 pi r) with complex densities")
@@ -568,6 +641,9 @@ def main():
         line["accuracy"] = accuracy_check(w, x_np, q_np, None if grad_only else phi.cpu().numpy().astype(odt),
                                           grad.cpu().numpy().astype(odt), kappa=kernel_params(args)[0],
                                           wavenumber=kernel_params(args)[1])
+    if (not args.no_variants and ws == 1 and args.kernel == "laplace" and args.outputs == "potential+gradient"
+            and w.name == "sphere8m_p6_d7"):
+        line["variants"] = measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(w.p, *kernel_params(args))
     if rank == 0:
