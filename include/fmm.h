@@ -57,10 +57,12 @@ typedef enum {
     FMM_TF32X3 = 2,        /* contractions on tcgen05 tensor cores, 3 TF32 products (big/small split) */
     FMM_BF16X3 = 3,        /* contractions on tcgen05 tensor cores, 3 BF16 products (hi/lo split) */
     FMM_BF16X6 = 4,        /* contractions on tcgen05 tensor cores, 6 BF16 products (hi/mid/lo split) */
-    FMM_FP16X3 = 5         /* as FMM_BF16X6, except the M2L stencil products (the VLI's bulk): FP16
-                              hi/lo splits of power-of-two scaled operands (the compressed vectors
-                              scaled per box and 64-column chunk, the operators per chunk), 3 FP16
-                              products, about 2^-22 relative per term, scales applied in FP32 */
+    FMM_FP16X3 = 5         /* contractions on tcgen05 tensor cores from FP16 hi/lo splits of power-of-two
+                              scaled operands (every box row scaled per box and 64-column chunk by the
+                              step that writes it, the operators per chunk), 3 FP16 products, about
+                              2^-22 relative per term, scales applied in FP32.  The leaf closing (the
+                              pseudo-inverse of the downward check potentials) stays in FP32 SIMT, as
+                              in every tensor-core mode.  No mean_free (FMM_EUNSUPPORTED). */
 } fmm_precision;
 
 /* Kernel of Eq. 1 (option `kernel`). */
@@ -114,7 +116,7 @@ typedef struct {
 typedef struct {
     int64_t n_points;
     int32_t depth;
-    int32_t n_surface;         /* 6(p-1)^2+2 */
+    int32_t n_surface;         /* 6(p-1)^2+2 surface points (a box vector holds twice that under FMM_HELMHOLTZ) */
     int32_t m2l_rank_in;       /* rank of the compressed M2L on the source side (0 before precompute) */
     int32_t m2l_rank_out;      /* rank on the target side (0 before precompute) */
     int64_t n_boxes[11];       /* non-empty boxes per level 0..depth */
@@ -211,7 +213,7 @@ typedef struct {
 
 /* Build the partition: 2 <= d_global < depth, 1 <= n_ranks <= the number of local roots.
  * Needs fmm_build_tree and fmm_precompute; a new fmm_build_tree drops the partition.
- * Errors: ESTATE, EINVAL (ranges), EUNSUPPORTED (mean_free), ENOMEM, ECUDA. */
+ * Errors: ESTATE, EINVAL (ranges), EUNSUPPORTED (mean_free, FMM_HELMHOLTZ), ENOMEM, ECUDA. */
 fmm_status fmm_partition_setup(fmm_ctx *ctx, int d_global, int n_ranks);
 
 /* fmm_evaluate through the partition (same arguments and output rules; phi may be NULL when grad
@@ -260,7 +262,8 @@ fmm_status fmm_export_level(fmm_ctx *ctx, int level, uint64_t *keys, int64_t *v_
                             int64_t *v_idx, int32_t *v_tvec, int64_t *n_v_entries);
 
 /* Copy the check potentials of the last fmm_evaluate (with its far field) at `level` in [2, d]
- * to host memory: n_boxes[level] x n_surface values, row-major, float or double.
+ * to host memory: n_boxes[level] x n_surface values, row-major, float or double (FMM_HELMHOLTZ:
+ * n_boxes[level] x 2 n_surface, each row the real parts then the imaginary parts).
  *  kind 0 (upward): row b approximates sum_{j in b} K(x^{uc}_b, x_j) s_j, the potential of the
  *          sources inside box b on its upward check surface (exact at the leaf level);
  *  kind 1 (downward): row b approximates the potential on b's downward check surface of the

@@ -297,9 +297,11 @@ class FMM:
         return {"keys": keys, "v_offsets": off, "v_idx": idx, "v_tvec": tv}
 
     def export_check(self, level, kind="upward"):
-        """Check potentials of the last evaluate at `level` (n_boxes x n_surface)."""
+        """Check potentials of the last evaluate at `level`: n_boxes x n_surface, or n_boxes x
+        2 n_surface (real parts, then imaginary parts) for the Helmholtz kernel."""
         inf = self.info()
-        out = np.empty((inf["n_boxes"][level], inf["n_surface"]), dtype=self.dtype)
+        width = inf["n_surface"] * (2 if self.kernel == "helmholtz" else 1)
+        out = np.empty((inf["n_boxes"][level], width), dtype=self.dtype)
         self._check(lib().fmm_export_check(self._ctx, level, {"upward": 0, "downward": 1}[kind],
                                            _ptr(out)))
         return out
