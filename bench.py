@@ -555,7 +555,8 @@ def main():
     p2p["frac"] = p2p["achieved"] / p2p["peak"]
     p2p["traffic"] = None if helm else recorded_traffic("p2p_f32_kernel", source_digest("p2p.cu"))
     # M2L algorithmic flops: compress + stencil products over the real V pairs
-    kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"]
+    # ns: entries of a box vector (twice the surface points for the Helmholtz kernel's complex rows)
+    kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"] * (2 if helm else 1)
     vpairs = 0
     compress_flops = stencil_flops = 0.0
     for level in range(2, w.depth + 1):
