@@ -141,3 +141,24 @@ def test_unsupported_and_invalid():
         pkg.FMM(p=4, depth=3, kernel="helmholtz", kappa=1.0)          # no domain
     with pytest.raises(pkg.FmmError):
         pkg.FMM(p=4, depth=3, kernel="helmholtz", kappa=0.0, domain=dom)
+
+
+def test_leaf_check_values_exported():
+    # S2U input: every leaf's complex check values are a plain kernel sum over its own points,
+    # exported as [Re | Im] rows of 2 n_surface values
+    from oracle import tree as otree
+    x, q, _, _, k, dom = _inputs("sphere")
+    p, depth = 4, 4
+    f = _fmm(x, p, depth, "fp32", dom, k)
+    _run(f, q, gradient=False)
+    got = f.export_check(depth, "upward")
+    tr = otree.build_tree(x.astype(np.float64), depth, *dom)
+    ns = kifmm.n_surface(p)
+    nl = len(tr.leaf_keys)
+    assert got.shape == (nl, 2 * ns)
+    chk = kifmm._leaf_surface_points(tr, p, np.arange(nl), kifmm.ALPHA_OUTER)
+    want, _ = direct.grouped_sum(np.arange(nl + 1) * ns, chk, np.arange(nl + 1),
+                                 np.stack([tr.leaf_offsets[:-1], tr.leaf_offsets[1:]], 1),
+                                 x.astype(np.float64)[tr.perm], q[tr.perm], False, wavenumber=k)
+    want = want.reshape(nl, ns)
+    assert rel(got[:, :ns] + 1j * got[:, ns:], want) < 1e-6
