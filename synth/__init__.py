@@ -36,6 +36,17 @@ def sphere_points(n: int, seed: int = SEED_POINTS) -> np.ndarray:
     return g.astype(np.float32)
 
 
+def mixed_points(n: int, seed: int = SEED_POINTS, radius: float = 0.15) -> np.ndarray:
+    """n points of the two families in one cube, for strongly non-uniform trees: the first n // 2
+    uniform in [0,1)^3, the rest uniform on the sphere of the given radius centred at
+    (0.5, 0.5, 0.5).  float32, shape (n, 3)."""
+    rng = np.random.default_rng(seed)
+    a = rng.random((n // 2, 3))
+    g = rng.standard_normal((n - n // 2, 3))
+    g = 0.5 + radius * g / np.linalg.norm(g, axis=1, keepdims=True)
+    return np.concatenate([a, g]).astype(np.float32)
+
+
 def charges(n: int, kind: str, seed: int = SEED_CHARGES) -> np.ndarray:
     """n charges, float32.  kind: 'u01' (U[0,1)), 'u11' (U[-1,1)) or 'normal' (N(0,1))."""
     rng = np.random.default_rng(seed)
