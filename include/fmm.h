@@ -239,6 +239,53 @@ fmm_status fmm_partition_export(fmm_ctx *ctx, int rank, int level, int kind, uin
  * device copy in and out per call) and replayed. */
 fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n);
 
+/* ---- Adaptive tree and its interaction lists (Section 2.1: adaptive refinement; Table 1 and
+ * Algorithm 1: the U, V, W and X lists of the adaptive branches) ----
+ *
+ * Built on the device from the uniform tree of fmm_build_tree (its depth D is the deepest level
+ * allowed).  The adaptive tree keeps the root and the children of every kept box of level < D
+ * that holds more than `capacity` points; a kept box that is not refined is a leaf.
+ *   U(b), leaf b:      kept leaves adjacent to b (sharing a vertex, edge or face), b included;
+ *   V(b), level >= 2:  kept boxes of b's level whose parents are adjacent to b's parent and that
+ *                      are not adjacent to b;
+ *   W(b), leaf b:      kept boxes below b's colleagues that are not adjacent to b while their
+ *                      parents are;
+ *   X(b):              the leaves whose W list holds b.
+ * Boxes are named by their row: the boxes of the uniform tree, level by level from the root,
+ * ascending Morton key within a level (fmm_export_level gives each level's keys); rows of boxes
+ * that the adaptive tree does not keep have empty lists.  Every list is sorted by row.
+ * The far-field evaluation over the adaptive tree (XLI, WLI) is not provided by this library. */
+typedef enum {
+    FMM_ADAPTIVE_STATE = 0,   /* per row: 0 not kept, 1 leaf, 2 refined */
+    FMM_ADAPTIVE_COUNT = 1,   /* per row: points in the box */
+    FMM_ADAPTIVE_U = 2,       /* U lists (CSR over rows) */
+    FMM_ADAPTIVE_V = 3,       /* V lists */
+    FMM_ADAPTIVE_W = 4,       /* W lists */
+    FMM_ADAPTIVE_X = 5        /* X lists */
+} fmm_adaptive_export_kind;
+
+typedef struct {
+    int32_t capacity;
+    int64_t n_rows;            /* boxes of the uniform tree over all levels (the row space) */
+    int64_t n_leaves[11];      /* leaves of the adaptive tree per level 0..depth */
+    int64_t n_refined[11];     /* refined boxes of the adaptive tree per level */
+    int64_t n_entries[4];      /* total lengths of the U, V, W and X lists */
+} fmm_adaptive_tree_info;
+
+/* Refine by `capacity` (>= 0) and build the four lists; replaces an earlier adaptive tree of this
+ * context.  It belongs to the current tree: fmm_build_tree discards it.
+ * Errors: ESTATE before fmm_build_tree; EINVAL for capacity < 0; ECUDA, ENOMEM. */
+fmm_status fmm_adaptive_setup(fmm_ctx *ctx, int capacity);
+
+/* Summary counts of the adaptive tree.  ESTATE before fmm_adaptive_setup. */
+fmm_status fmm_adaptive_info(fmm_ctx *ctx, fmm_adaptive_tree_info *info);
+
+/* Copy one fmm_adaptive_export_kind to host arrays (any pointer may be NULL to skip it):
+ *  count[0] = rows, count[1] = entries (rows for STATE and COUNT, the list length otherwise);
+ *  offsets[rows + 1]: the CSR offsets (lists only); idx[entries]: the per-row values or the
+ *  members (rows).  ESTATE before fmm_adaptive_setup; EINVAL for an unknown kind. */
+fmm_status fmm_adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count);
+
 /* Sizes of the built tree and operators.  ESTATE before fmm_build_tree. */
 fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info);
 

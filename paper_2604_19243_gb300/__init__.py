@@ -38,6 +38,7 @@ ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_prec
                 "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches",
                 "fmm_measure_fp32_peak", "fmm_partition_setup", "fmm_partition_evaluate",
                 "fmm_partition_info", "fmm_partition_export", "fmm_partition_timings",
+                "fmm_adaptive_setup", "fmm_adaptive_info", "fmm_adaptive_export",
                 "fmm_last_error", "fmm_destroy")
 
 
@@ -68,6 +69,15 @@ class RankInfo(ctypes.Structure):
                 ("bytes_u", ctypes.c_int64), ("bytes_v", ctypes.c_int64),
                 ("bytes_gather", ctypes.c_int64), ("bytes_scatter", ctypes.c_int64)]
 
+
+class AdaptiveTreeInfo(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int32), ("n_rows", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64 * 11), ("n_refined", ctypes.c_int64 * 11),
+                ("n_entries", ctypes.c_int64 * 4)]
+
+
+# fmm_adaptive_export kinds
+ADAPTIVE_STATE, ADAPTIVE_COUNT, ADAPTIVE_U, ADAPTIVE_V, ADAPTIVE_W, ADAPTIVE_X = range(6)
 
 # fmm_partition_export kinds
 PARTITION_OWN, PARTITION_GHOST_V, PARTITION_GHOST_U = 0, 1, 2
@@ -115,6 +125,9 @@ def lib():
             "fmm_partition_info": [vp, i32, ctypes.POINTER(RankInfo)],
             "fmm_partition_export": [vp, i32, i32, i32, vp, vp],
             "fmm_partition_timings": [vp, vp, i32],
+            "fmm_adaptive_setup": [vp, i32],
+            "fmm_adaptive_info": [vp, ctypes.POINTER(AdaptiveTreeInfo)],
+            "fmm_adaptive_export": [vp, i32, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -353,6 +366,32 @@ class FMM:
         ms = np.zeros(len(PARTITION_PHASES), np.float64)
         self._check(lib().fmm_partition_timings(self._ctx, _ptr(ms), len(ms)))
         return dict(zip(PARTITION_PHASES, ms.tolist()))
+
+    def adaptive_setup(self, capacity):
+        """Adaptive tree of the current tree (refined while a box holds more than `capacity`
+        points, down to the tree's depth) and its U, V, W and X lists."""
+        self._check(lib().fmm_adaptive_setup(self._ctx, int(capacity)))
+
+    def adaptive_info(self):
+        ai = AdaptiveTreeInfo()
+        self._check(lib().fmm_adaptive_info(self._ctx, ctypes.byref(ai)))
+        depth = self.info()["depth"]
+        return {"capacity": ai.capacity, "n_rows": ai.n_rows, "n_leaves": list(ai.n_leaves)[: depth + 1],
+                "n_refined": list(ai.n_refined)[: depth + 1], "n_entries": list(ai.n_entries)}
+
+    def adaptive_export(self, kind):
+        """Per-row values (ADAPTIVE_STATE, ADAPTIVE_COUNT) as an array, or a list kind
+        (ADAPTIVE_U .. ADAPTIVE_X) as (offsets[rows + 1], members): rows are the boxes of all
+        levels, level by level, ascending Morton key within a level."""
+        cnt = np.zeros(2, np.int64)
+        self._check(lib().fmm_adaptive_export(self._ctx, int(kind), None, None, _ptr(cnt)))
+        idx = np.empty(int(cnt[1]), np.int64)
+        if kind < ADAPTIVE_U:
+            self._check(lib().fmm_adaptive_export(self._ctx, int(kind), None, _ptr(idx), _ptr(cnt)))
+            return idx
+        off = np.empty(int(cnt[0]) + 1, np.int64)
+        self._check(lib().fmm_adaptive_export(self._ctx, int(kind), _ptr(off), _ptr(idx), _ptr(cnt)))
+        return off, idx
 
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""

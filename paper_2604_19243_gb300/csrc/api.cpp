@@ -445,6 +445,7 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const void *xyz, int64_t n) {
     if (n <= 0 || n > 2147483647LL) return fail(ctx, FMM_EINVAL, "n must be in [1, 2^31 - 1]");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     split_free(ctx);   // a partition belongs to the tree it was built on
+    adaptive_free(ctx);
     free_tree(ctx);
     ctx->n = n;
     const size_t bytes = (size_t)n * 3 * elem_size(ctx);
@@ -602,6 +603,35 @@ fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n) {
     return split_timings(ctx, ms, n);
 }
 
+fmm_status fmm_adaptive_setup(fmm_ctx *ctx, int capacity) {
+    if (!ctx) return FMM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    try {
+        return adaptive_setup(ctx, capacity);
+    } catch (const std::bad_alloc &) {
+        adaptive_free(ctx);
+        return fail(ctx, FMM_ENOMEM, "host memory exhausted in the adaptive setup");
+    }
+}
+
+fmm_status fmm_adaptive_info(fmm_ctx *ctx, fmm_adaptive_tree_info *info) {
+    if (!ctx || !info) return FMM_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    fmm_status st = adaptive_info(ctx, &info->capacity, info->n_leaves, info->n_refined, info->n_entries);
+    if (st == FMM_OK) info->n_rows = ctx->total_rows;
+    return st;
+}
+
+fmm_status fmm_adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count) {
+    if (!ctx) return FMM_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    try {
+        return adaptive_export(ctx, kind, offsets, idx, count);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, FMM_ENOMEM, "host memory exhausted in the adaptive export");
+    }
+}
+
 fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info) {
     if (!ctx || !info) return FMM_EINVAL;
     if (!ctx->have_tree) return FMM_ESTATE;
@@ -747,6 +777,7 @@ void fmm_destroy(fmm_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     split_free(ctx);
+    adaptive_free(ctx);
     free_tree(ctx);
     free_workspace(ctx);
     free_ops(ctx);

@@ -75,6 +75,7 @@ struct TcOpSet {
 
 struct HostOps;  // FP64 host operators (precompute.cpp)
 struct SplitState;  // virtual-rank partition (split.cu)
+struct AdaptiveState;  // adaptive tree and its lists (adaptive.cu)
 
 // Tile of output rows for the GEMM kernels: rows [row0, row0+nrows) of a level's row list,
 // all of one child octant class `cls` (or -1 when not class-ordered); `mask` indexes the
@@ -185,6 +186,7 @@ struct fmm_ctx {
     std::vector<void *> op_allocs;
 
     fmm::SplitState *split = nullptr;   // partitioned evaluation on virtual ranks (split.cu)
+    fmm::AdaptiveState *adaptive = nullptr;   // adaptive tree and its lists (adaptive.cu)
 
     bool last_adjoint = false;  // what the last evaluation left in the workspaces
     bool last_far = false;
@@ -248,6 +250,14 @@ void split_free(fmm_ctx *ctx);
 fmm_status split_info(fmm_ctx *ctx, int rank, fmm_rank_info *out);
 fmm_status split_export(fmm_ctx *ctx, int rank, int level, int kind, uint64_t *out, int64_t *count);
 fmm_status split_timings(fmm_ctx *ctx, double *ms, int n);
+
+// ---- adaptive.cu ----
+// Adaptive tree of the current uniform tree and its U, V, W and X lists; the message of a
+// failure goes to ctx->err.
+fmm_status adaptive_setup(fmm_ctx *ctx, int capacity);
+void adaptive_free(fmm_ctx *ctx);
+fmm_status adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count);
+fmm_status adaptive_info(fmm_ctx *ctx, int32_t *capacity, int64_t *leaves, int64_t *refined, int64_t *entries);
 
 // ---- tree.cu ----
 cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz);
