@@ -253,8 +253,7 @@ fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n);
  *   X(b):              the leaves whose W list holds b.
  * Boxes are named by their row: the boxes of the uniform tree, level by level from the root,
  * ascending Morton key within a level (fmm_export_level gives each level's keys); rows of boxes
- * that the adaptive tree does not keep have empty lists.  Every list is sorted by row.
- * The far-field evaluation over the adaptive tree (XLI, WLI) is not provided by this library. */
+ * that the adaptive tree does not keep have empty lists.  Every list is sorted by row. */
 typedef enum {
     FMM_ADAPTIVE_STATE = 0,   /* per row: 0 not kept, 1 leaf, 2 refined */
     FMM_ADAPTIVE_COUNT = 1,   /* per row: points in the box */
@@ -285,6 +284,24 @@ fmm_status fmm_adaptive_info(fmm_ctx *ctx, fmm_adaptive_tree_info *info);
  *  offsets[rows + 1]: the CSR offsets (lists only); idx[entries]: the per-row values or the
  *  members (rows).  ESTATE before fmm_adaptive_setup; EINVAL for an unknown kind. */
 fmm_status fmm_adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count);
+
+/* phi = A q over the adaptive tree (Algorithm 1 with its adaptive branches), and grad phi if `grad`
+ * is non-NULL; arguments, layouts and the gradient-only form (phi == NULL) as fmm_evaluate, with
+ * `parts` as fmm_evaluate_parts: FMM_PART_NEAR is the ULI over the adaptive U lists, FMM_PART_FAR
+ * the rest:
+ *   S2U and U2U   as the uniform tree's (the check potentials of a leaf above the deepest level
+ *                 come from its descendants' by U2U, which represents the same sources);
+ *   VLI           over the adaptive V lists (kept boxes only);
+ *   XLI (2b)      the sources of X(b) added to b's downward check potentials before D2D;
+ *   D2D           down to the deepest level: the boxes below a leaf of the adaptive tree take no
+ *                 VLI of their own and carry the leaf's local field to its points by D2D alone;
+ *   D2T           at the deepest level;
+ *   WLI (3a)      the upward equivalent densities of W(b), r (V S^-1)(U^T u) of the upward
+ *                 check potentials, evaluated at the points of leaf b.
+ * Requires fmm_adaptive_setup on the current tree and fmm_precompute.  FMM_FP32 and FMM_FP64 with
+ * the Laplace kernel only (EUNSUPPORTED for the tensor-core precisions, the other kernels and
+ * mean_free).  Errors otherwise as fmm_evaluate_parts. */
+fmm_status fmm_adaptive_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts);
 
 /* Sizes of the built tree and operators.  ESTATE before fmm_build_tree. */
 fmm_status fmm_get_tree_info(const fmm_ctx *ctx, fmm_tree_info *info);

@@ -38,7 +38,7 @@ ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_prec
                 "fmm_sync", "fmm_sort_points_noalloc", "fmm_kernel_launches",
                 "fmm_measure_fp32_peak", "fmm_partition_setup", "fmm_partition_evaluate",
                 "fmm_partition_info", "fmm_partition_export", "fmm_partition_timings",
-                "fmm_adaptive_setup", "fmm_adaptive_info", "fmm_adaptive_export",
+                "fmm_adaptive_setup", "fmm_adaptive_info", "fmm_adaptive_export", "fmm_adaptive_evaluate",
                 "fmm_last_error", "fmm_destroy")
 
 
@@ -128,6 +128,7 @@ def lib():
             "fmm_adaptive_setup": [vp, i32],
             "fmm_adaptive_info": [vp, ctypes.POINTER(AdaptiveTreeInfo)],
             "fmm_adaptive_export": [vp, i32, vp, vp, vp],
+            "fmm_adaptive_evaluate": [vp, vp, vp, vp, i32],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -392,6 +393,14 @@ class FMM:
         off = np.empty(int(cnt[0]) + 1, np.int64)
         self._check(lib().fmm_adaptive_export(self._ctx, int(kind), _ptr(off), _ptr(idx), _ptr(cnt)))
         return off, idx
+
+    def adaptive_evaluate(self, q, gradient=True, parts=PART_ALL, potential=True):
+        """(phi, grad) over the adaptive tree of `adaptive_setup` (fmm_adaptive_evaluate)."""
+        q = self._as_input(q, values=True)
+        phi = self._like(q, (self.n,)) if potential else None
+        grad = self._like(q, (self.n, 3)) if gradient else None
+        self._check(lib().fmm_adaptive_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+        return phi, grad
 
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""

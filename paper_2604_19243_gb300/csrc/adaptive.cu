@@ -35,6 +35,12 @@ struct AdaptiveState {
     int *idx[4] = {};                      // U, V, W, X members (rows)
     int64_t entries[4] = {};
     std::vector<int> host_state;           // copy of state, for the summary counts
+    int *begin = nullptr;                  // [rows] first sorted point of each box
+    int *dense_kept[kMaxDepth + 1] = {};   // levels >= 2: the level's dense table without unkept boxes
+    // evaluation workspaces (allocated by the first evaluation)
+    void *ue = nullptr;                    // [rows x nsp] upward equivalent densities
+    void *y1 = nullptr;                    // [max level size x rclup] closing intermediate
+    size_t ue_bytes = 0, y1_bytes = 0;
 };
 
 namespace {
@@ -93,20 +99,33 @@ __device__ inline void sort_segment(int *a, int n) {
     }
 }
 
-__global__ void leaf_count_kernel(const int *leaf_off, int n, int *count) {
+__global__ void leaf_count_kernel(const int *leaf_off, int n, int *count, int *begin) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) count[i] = leaf_off[i + 1] - leaf_off[i];
+    if (i >= n) return;
+    count[i] = leaf_off[i + 1] - leaf_off[i];
+    begin[i] = leaf_off[i];
 }
 
-__global__ void parent_count_kernel(const int *child, int n, const int *count_child, int *count) {
+__global__ void parent_count_kernel(const int *child, int n, const int *count_child, const int *begin_child,
+                                    int *count, int *begin) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
-    int s = 0;
+    int s = 0, first = -1;
     for (int c = 0; c < 8; ++c) {
         const int ch = child[(size_t)b * 8 + c];
-        if (ch >= 0) s += count_child[ch];
+        if (ch >= 0) {
+            s += count_child[ch];
+            if (first < 0) first = begin_child[ch];
+        }
     }
     count[b] = s;
+    begin[b] = first;
+}
+
+// the dense table of a level without the boxes the adaptive tree does not keep
+__global__ void mask_dense_kernel(const uint32_t *keys, int n, const int *state, int *dense) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && state[b] == 0) dense[keys[b]] = -1;
 }
 
 __global__ void state_kernel(int level, int depth, const int *parent, int n, const int *state_parent,
@@ -227,6 +246,197 @@ __global__ void sort_segments_kernel(int rows, const int *off, int *idx) {
     if (r < rows) sort_segment(idx + off[r], off[r + 1] - off[r]);
 }
 
+// ---------------------------------------------------------------------------------------
+// Evaluation over the adaptive tree: the parts that the uniform pipeline does not have.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct Pt4;
+template <> struct Pt4<float> { using type = float4; };
+template <> struct Pt4<double> { using type = double4; };
+template <typename T> __device__ inline T inv_sqrt(T x);
+template <> __device__ inline float inv_sqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
+template <typename T> __host__ __device__ constexpr T one_over_4pi() { return (T)0.079577471545947667884441881686257181; }
+
+constexpr int kEvalThreads = 128;
+constexpr int kEvalChunk = 512;     // sources staged per round
+constexpr int kMaxSurface = 488;    // 6 (p - 1)^2 + 2 for p <= 10
+
+// centre of box `key` of a level whose boxes are `width` wide
+__device__ inline void box_centre(uint32_t key, double ox, double oy, double oz, double width, double c[3]) {
+    int ax, ay, az;
+    demorton3(key, ax, ay, az);
+    c[0] = ox + (ax + 0.5) * width, c[1] = oy + (ay + 0.5) * width, c[2] = oz + (az + 0.5) * width;
+}
+
+// XLI (Algorithm 1, step 2b): the sources of every leaf in X(b) on the downward check surface
+// (1.05) of b, added to b's downward check potentials.  One block per box of the level.
+template <typename T>
+__global__ void __launch_bounds__(kEvalThreads)
+xli_kernel(const typename Pt4<T>::type *__restrict__ pts, const uint32_t *__restrict__ keys, int base,
+           const int *__restrict__ x_off, const int *__restrict__ x_idx, const int *__restrict__ begin,
+           const int *__restrict__ count, const T *__restrict__ grid, int ns, double ox, double oy, double oz,
+           double width, double radius, T *__restrict__ D, int ld) {
+    using P = typename Pt4<T>::type;
+    __shared__ P src[kEvalChunk];
+    const int b = blockIdx.x, r = base + b;
+    const int m0 = x_off[r], m1 = x_off[r + 1];
+    if (m0 == m1) return;
+    double c[3];
+    box_centre(keys[b], ox, oy, oz, width, c);
+    for (int i0 = 0; i0 < ns; i0 += kEvalThreads) {
+        const int i = i0 + threadIdx.x;
+        T px = 0, py = 0, pz = 0, acc = 0;
+        if (i < ns) {
+            px = (T)(c[0] + radius * (double)grid[3 * i]);
+            py = (T)(c[1] + radius * (double)grid[3 * i + 1]);
+            pz = (T)(c[2] + radius * (double)grid[3 * i + 2]);
+        }
+        for (int m = m0; m < m1; ++m) {
+            const int a = x_idx[m], s0 = begin[a], s1 = s0 + count[a];
+            for (int c0 = s0; c0 < s1; c0 += kEvalChunk) {
+                const int c1 = min(s1, c0 + kEvalChunk);
+                __syncthreads();
+                for (int e = c0 + threadIdx.x; e < c1; e += kEvalThreads) src[e - c0] = pts[e];
+                __syncthreads();
+                if (i < ns)
+                    for (int e = 0; e < c1 - c0; ++e) {
+                        const P y = src[e];
+                        const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > (T)0) acc += y.w * inv_sqrt<T>(r2);
+                    }
+            }
+        }
+        if (i < ns) D[(size_t)b * ld + i] += acc * one_over_4pi<T>();
+    }
+}
+
+// WLI (Algorithm 1, step 3a): the upward equivalent densities (1.05 surface) of every box in
+// W(b) evaluated at the points of leaf b, added to the far-field outputs.  One block per row.
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(kEvalThreads)
+wli_kernel(const typename Pt4<T>::type *__restrict__ pts, Levels L, const int *__restrict__ w_off,
+           const int *__restrict__ w_idx, const int *__restrict__ begin, const int *__restrict__ count,
+           const T *__restrict__ grid, int ns, double ox, double oy, double oz, double side,
+           const T *__restrict__ ue, int ldu, T *__restrict__ phi, T *__restrict__ grad) {
+    using P = typename Pt4<T>::type;
+    __shared__ P src[kMaxSurface];
+    const int r = blockIdx.x;
+    const int m0 = w_off[r], m1 = w_off[r + 1];
+    if (m0 == m1) return;
+    const int t0 = begin[r], t1 = t0 + count[r];
+    for (int i0 = t0; i0 < t1; i0 += kEvalThreads) {
+        const int i = i0 + threadIdx.x;
+        const P x = pts[min(i, t1 - 1)];
+        T pot = 0, gx = 0, gy = 0, gz = 0;
+        for (int m = m0; m < m1; ++m) {
+            const int a = w_idx[m], la = row_level(L, a);
+            const double width = side / (double)(1 << la), radius = 1.05 * 0.5 * width;
+            double c[3];
+            box_centre(L.keys[la][a - L.base[la]], ox, oy, oz, width, c);
+            __syncthreads();
+            for (int j = threadIdx.x; j < ns; j += kEvalThreads) {
+                P y;
+                y.x = (T)(c[0] + radius * (double)grid[3 * j]);
+                y.y = (T)(c[1] + radius * (double)grid[3 * j + 1]);
+                y.z = (T)(c[2] + radius * (double)grid[3 * j + 2]);
+                y.w = ue[(size_t)a * ldu + j];
+                src[j] = y;
+            }
+            __syncthreads();
+            for (int j = 0; j < ns; ++j) {
+                const P y = src[j];
+                const T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                const T ri = inv_sqrt<T>(dx * dx + dy * dy + dz * dz), w = y.w * ri;
+                pot += w;
+                if (GRAD) {
+                    const T w3 = w * ri * ri;
+                    gx -= w3 * dx, gy -= w3 * dy, gz -= w3 * dz;
+                }
+            }
+        }
+        if (i < t1) {
+            if (phi) phi[i] += pot * one_over_4pi<T>();
+            if (GRAD) {
+                grad[3 * (size_t)i] += gx * one_over_4pi<T>();
+                grad[3 * (size_t)i + 1] += gy * one_over_4pi<T>();
+                grad[3 * (size_t)i + 2] += gz * one_over_4pi<T>();
+            }
+        }
+    }
+}
+
+// ULI over the adaptive U lists: every point of leaf b against the points of every leaf in
+// U(b) (pairs at distance zero skipped).  One block per row; rows that are not leaves return.
+template <typename T, bool POT, bool GRAD>
+__global__ void __launch_bounds__(kEvalThreads)
+uli_kernel(const typename Pt4<T>::type *__restrict__ pts, const int *__restrict__ state,
+           const int *__restrict__ u_off, const int *__restrict__ u_idx, const int *__restrict__ begin,
+           const int *__restrict__ count, T *__restrict__ phi, T *__restrict__ grad) {
+    using P = typename Pt4<T>::type;
+    __shared__ P src[kEvalChunk];
+    const int r = blockIdx.x;
+    if (state[r] != 1) return;
+    const int t0 = begin[r], t1 = t0 + count[r];
+    for (int i0 = t0; i0 < t1; i0 += kEvalThreads) {
+        const int i = i0 + threadIdx.x;
+        const P x = pts[min(i, t1 - 1)];
+        T pot = 0, gx = 0, gy = 0, gz = 0;
+        for (int m = u_off[r]; m < u_off[r + 1]; ++m) {
+            const int a = u_idx[m], s0 = begin[a], s1 = s0 + count[a];
+            for (int c0 = s0; c0 < s1; c0 += kEvalChunk) {
+                const int c1 = min(s1, c0 + kEvalChunk);
+                __syncthreads();
+                for (int e = c0 + threadIdx.x; e < c1; e += kEvalThreads) src[e - c0] = pts[e];
+                __syncthreads();
+                for (int e = 0; e < c1 - c0; ++e) {
+                    const P y = src[e];
+                    const T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 > (T)0) {
+                        const T ri = inv_sqrt<T>(r2), w = y.w * ri;
+                        if (POT) pot += w;
+                        if (GRAD) {
+                            const T w3 = w * ri * ri;
+                            gx -= w3 * dx, gy -= w3 * dy, gz -= w3 * dz;
+                        }
+                    }
+                }
+            }
+        }
+        if (i < t1) {
+            if (POT) phi[i] = pot * one_over_4pi<T>();
+            if (GRAD) {
+                grad[3 * (size_t)i] = gx * one_over_4pi<T>();
+                grad[3 * (size_t)i + 1] = gy * one_over_4pi<T>();
+                grad[3 * (size_t)i + 2] = gz * one_over_4pi<T>();
+            }
+        }
+    }
+}
+
+// zero the rows of a level's boxes that the adaptive tree does not keep
+template <typename T>
+__global__ void zero_unkept_kernel(T *rows, int ld, int width, const int *state, int n) {
+    const int b = blockIdx.x, j = threadIdx.x;
+    if (b < n && state[b] == 0)
+        for (int k = j; k < width; k += blockDim.x) rows[(size_t)b * ld + k] = (T)0;
+}
+
+Levels make_levels(const fmm_ctx *ctx) {
+    Levels L{};
+    const int D = ctx->opt.depth;
+    for (int l = 0; l <= D; ++l) {
+        L.keys[l] = ctx->lev[l].keys;
+        L.child[l] = ctx->lev[l].child;
+        L.dense[l] = ctx->lev[l].dense;
+        L.base[l] = (int)ctx->lev[l].row_base;
+    }
+    L.base[D + 1] = (int)ctx->total_rows;
+    L.depth = D;
+    return L;
+}
+
 unsigned grid_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 fmm_status afail(fmm_ctx *ctx, fmm_status st, const std::string &m) {
@@ -239,6 +449,7 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     const int D = ctx->opt.depth;
     const int64_t rows = A->rows;
     FMM_CUDA_TRY(cudaMalloc(&A->count, rows * sizeof(int)));
+    FMM_CUDA_TRY(cudaMalloc(&A->begin, rows * sizeof(int)));
     FMM_CUDA_TRY(cudaMalloc(&A->state, rows * sizeof(int)));
     for (int k = 0; k < 4; ++k) FMM_CUDA_TRY(cudaMalloc(&A->off[k], (rows + 1) * sizeof(int)));
     Scratch<int> flag;
@@ -246,12 +457,14 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     FMM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
     // point counts, leaves up
     const LevelTables &LD = ctx->lev[D];
-    leaf_count_kernel<<<grid_for(LD.n, 256), 256, 0, s>>>(ctx->leaf_off, (int)LD.n, A->count + LD.row_base);
+    leaf_count_kernel<<<grid_for(LD.n, 256), 256, 0, s>>>(ctx->leaf_off, (int)LD.n, A->count + LD.row_base,
+                                                          A->begin + LD.row_base);
     count_launch();
     for (int l = D - 1; l >= 0; --l) {
         const LevelTables &T = ctx->lev[l];
-        parent_count_kernel<<<grid_for(T.n, 256), 256, 0, s>>>(T.child, (int)T.n, A->count + ctx->lev[l + 1].row_base,
-                                                                A->count + T.row_base);
+        const int64_t cb = ctx->lev[l + 1].row_base;
+        parent_count_kernel<<<grid_for(T.n, 256), 256, 0, s>>>(T.child, (int)T.n, A->count + cb, A->begin + cb,
+                                                                A->count + T.row_base, A->begin + T.row_base);
         count_launch();
     }
     // kept / leaf / refined, root down
@@ -263,15 +476,7 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
         count_launch();
     }
     FMM_CUDA_TRY(cudaGetLastError());
-    Levels L{};
-    for (int l = 0; l <= D; ++l) {
-        L.keys[l] = ctx->lev[l].keys;
-        L.child[l] = ctx->lev[l].child;
-        L.dense[l] = ctx->lev[l].dense;
-        L.base[l] = (int)ctx->lev[l].row_base;
-    }
-    L.base[D + 1] = (int)rows;
-    L.depth = D;
+    const Levels L = make_levels(ctx);
     const unsigned g = grid_for(rows, 128);
     lists_kernel<false><<<g, 128, 0, s>>>(L, (int)rows, A->state, A->off[0], nullptr, A->off[1], nullptr, A->off[2],
                                           nullptr, flag.p);
@@ -306,6 +511,16 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     sort_segments_kernel<<<grid_for(rows, 256), 256, 0, s>>>((int)rows, A->off[3], A->idx[3]);
     count_launch();
     FMM_CUDA_TRY(cudaGetLastError());
+    // the stencil's source tables: unkept boxes removed
+    for (int l = 2; l <= D; ++l) {
+        const LevelTables &T = ctx->lev[l];
+        const size_t sz = (size_t)1 << (3 * l);
+        FMM_CUDA_TRY(cudaMalloc(&A->dense_kept[l], sz * sizeof(int)));
+        FMM_CUDA_TRY(cudaMemcpyAsync(A->dense_kept[l], T.dense, sz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        mask_dense_kernel<<<grid_for(T.n, 256), 256, 0, s>>>(T.keys, (int)T.n, A->state + T.row_base, A->dense_kept[l]);
+        count_launch();
+    }
+    FMM_CUDA_TRY(cudaGetLastError());
     int hflag = 0;
     A->host_state.resize(rows);
     FMM_CUDA_TRY(cudaMemcpyAsync(A->host_state.data(), A->state, rows * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -321,11 +536,15 @@ void adaptive_free(fmm_ctx *ctx) {
     if (!A) return;
     cudaStreamSynchronize(ctx->stream);
     cudaFree(A->count);
+    cudaFree(A->begin);
     cudaFree(A->state);
     for (int k = 0; k < 4; ++k) {
         cudaFree(A->off[k]);
         cudaFree(A->idx[k]);
     }
+    for (int l = 0; l <= kMaxDepth; ++l) cudaFree(A->dense_kept[l]);
+    cudaFree(A->ue);
+    cudaFree(A->y1);
     delete A;
     ctx->adaptive = nullptr;
 }
@@ -401,5 +620,116 @@ fmm_status adaptive_info(fmm_ctx *ctx, int32_t *capacity, int64_t *leaves, int64
         for (int k = 0; k < 4; ++k) entries[k] = A->entries[k];
     return FMM_OK;
 }
+
+// ---- evaluation hooks (called by run_far and run_evaluate while an adaptive evaluation runs) ----
+
+const int *adaptive_dense(const fmm_ctx *ctx, int level) { return ctx->adaptive->dense_kept[level]; }
+
+template <typename T>
+cudaError_t adaptive_zero_unkept(const fmm_ctx *ctx, int level, T *rows, int ld, int width, cudaStream_t s) {
+    const LevelTables &T_ = ctx->lev[level];
+    if (T_.n == 0) return cudaSuccess;
+    zero_unkept_kernel<T><<<(unsigned)T_.n, 128, 0, s>>>(rows, ld, width, ctx->adaptive->state + T_.row_base,
+                                                         (int)T_.n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adaptive_xli(const fmm_ctx *ctx, int level, T *D, int ld, cudaStream_t s) {
+    const AdaptiveState *A = ctx->adaptive;
+    const LevelTables &T_ = ctx->lev[level];
+    if (T_.n == 0 || A->entries[3] == 0) return cudaSuccess;
+    const double width = ctx->side / (double)(1 << level);
+    xli_kernel<T><<<(unsigned)T_.n, kEvalThreads, 0, s>>>(
+        (const typename Pt4<T>::type *)ctx->pts, T_.keys, (int)T_.row_base, A->off[3], A->idx[3], A->begin, A->count,
+        (const T *)ctx->grid_dev, ctx->npts, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, 1.05 * 0.5 * width,
+        D, ld);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
+    AdaptiveState *A = ctx->adaptive;
+    const int D = ctx->opt.depth;
+    if (A->entries[2] == 0 || D < 2) return cudaSuccess;
+    const int nsp = ctx->nsp;
+    // upward equivalent densities of every box of levels 2..D: r_l (V S^-1)(U^T U_l)
+    for (int l = 2; l <= D; ++l) {
+        const OpSet &o = ctx->fwd[l];
+        GemmCall c1;
+        c1.mode = GM_IDENTITY, c1.level = l, c1.n_out = o.rclup;
+        c1.X0 = (T *)ctx->Uc + (size_t)ctx->lev[l].row_base * nsp, c1.ldx0 = nsp, c1.k0 = nsp, c1.W0 = o.uclose1;
+        c1.Y = A->y1, c1.ldy = o.rclup;
+        FMM_CUDA_TRY(gemm_simt<T>(ctx, c1, s));
+        GemmCall c2;
+        c2.mode = GM_IDENTITY, c2.level = l, c2.n_out = nsp, c2.alpha = ctx->side / (double)(1 << l) * 0.5;
+        c2.X0 = A->y1, c2.ldx0 = o.rclup, c2.k0 = o.rclup, c2.W0 = o.uclose2;
+        c2.Y = (T *)A->ue + (size_t)ctx->lev[l].row_base * nsp, c2.ldy = nsp;
+        FMM_CUDA_TRY(gemm_simt<T>(ctx, c2, s));
+    }
+    const Levels L = make_levels(ctx);
+    auto go = [&](auto kern, T *g) {
+        kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, L, A->off[2], A->idx[2],
+                                                        A->begin, A->count, (const T *)ctx->grid_dev, ctx->npts,
+                                                        ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->side,
+                                                        (const T *)A->ue, nsp, phi, g);
+    };
+    grad ? go(wli_kernel<T, true>, grad) : go(wli_kernel<T, false>, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adaptive_uli(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
+    const AdaptiveState *A = ctx->adaptive;
+    auto go = [&](auto kern) {
+        kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, A->state, A->off[0],
+                                                        A->idx[0], A->begin, A->count, phi, grad);
+    };
+    if (phi && grad) go(uli_kernel<T, true, true>);
+    else if (grad) go(uli_kernel<T, false, true>);
+    else go(uli_kernel<T, true, false>);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// workspaces of the W-list step for the current operators
+fmm_status adaptive_prepare(fmm_ctx *ctx) {
+    AdaptiveState *A = ctx->adaptive;
+    const size_t es = ctx->fp64 ? sizeof(double) : sizeof(float);
+    const int D = ctx->opt.depth;
+    int64_t maxn = 1;
+    int rclup = 16;
+    for (int l = 2; l <= D; ++l) {
+        maxn = std::max<int64_t>(maxn, ctx->lev[l].n);
+        rclup = std::max(rclup, ctx->fwd[l].rclup);
+        if (!ctx->fwd[l].uclose1) return afail(ctx, FMM_ESTATE, "the upward closing operators are missing");
+    }
+    const size_t ue_bytes = (size_t)A->rows * ctx->nsp * es, y1_bytes = (size_t)maxn * rclup * es;
+    if (A->ue_bytes < ue_bytes) {
+        cudaFree(A->ue);
+        A->ue = nullptr, A->ue_bytes = 0;
+        if (cudaMalloc(&A->ue, ue_bytes) != cudaSuccess) return cudaGetLastError(), afail(ctx, FMM_ENOMEM, "adaptive workspace");
+        A->ue_bytes = ue_bytes;
+    }
+    if (A->y1_bytes < y1_bytes) {
+        cudaFree(A->y1);
+        A->y1 = nullptr, A->y1_bytes = 0;
+        if (cudaMalloc(&A->y1, y1_bytes) != cudaSuccess) return cudaGetLastError(), afail(ctx, FMM_ENOMEM, "adaptive workspace");
+        A->y1_bytes = y1_bytes;
+    }
+    return FMM_OK;
+}
+
+#define FMM_ADAPTIVE_INST(T)                                                                          \
+    template cudaError_t adaptive_zero_unkept<T>(const fmm_ctx *, int, T *, int, int, cudaStream_t); \
+    template cudaError_t adaptive_xli<T>(const fmm_ctx *, int, T *, int, cudaStream_t);               \
+    template cudaError_t adaptive_wli<T>(fmm_ctx *, T *, T *, cudaStream_t);                          \
+    template cudaError_t adaptive_uli<T>(const fmm_ctx *, T *, T *, cudaStream_t);
+FMM_ADAPTIVE_INST(float)
+FMM_ADAPTIVE_INST(double)
+#undef FMM_ADAPTIVE_INST
 
 }  // namespace fmm

@@ -301,8 +301,11 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
         cudaEventRecord(ctx->ev[2], fs), cudaEventRecord(ctx->ev[3], fs), cudaEventRecord(ctx->ev[4], fs);
     }
     cudaEventRecord(ctx->ev[5], fs);
-    if (near && (e = launch_p2p<T>(ctx, phi ? (T *)ctx->near_phi : nullptr, ng, ns)) != cudaSuccess)
-        return cuda_fail(ctx, e, "near field");
+    if (near) {
+        T *np = phi ? (T *)ctx->near_phi : nullptr;
+        e = ctx->adaptive_eval ? adaptive_uli<T>(ctx, np, ng, ns) : launch_p2p<T>(ctx, np, ng, ns);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "near field");
+    }
     cudaEventRecord(ctx->ev[1], ns);
     cudaStreamWaitEvent(s, ctx->ev[5], 0);   // join the far field
     cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
@@ -537,6 +540,24 @@ fmm_status fmm_evaluate_parts(fmm_ctx *ctx, const void *q, void *phi, void *grad
     if (parts < 1 || parts > FMM_PART_ALL) return fail(ctx, FMM_EINVAL, "parts must be a nonempty subset of near|far");
     return ctx->fp64 ? run_evaluate<double>(ctx, q, phi, grad, parts, false)
                      : run_evaluate<float>(ctx, q, phi, grad, parts, false);
+}
+
+fmm_status fmm_adaptive_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int parts) {
+    fmm_status st = check_ready(ctx, q, phi ? phi : grad);
+    if (st != FMM_OK) return st;
+    if (!ctx->adaptive) return fail(ctx, FMM_ESTATE, "fmm_adaptive_setup has not been called");
+    if (ctx->tensor) return fail(ctx, FMM_EUNSUPPORTED, "the adaptive evaluation runs in FMM_FP32 or FMM_FP64");
+    if (ctx->opt.kernel != FMM_LAPLACE) return fail(ctx, FMM_EUNSUPPORTED, "the adaptive evaluation is for the Laplace kernel");
+    if (ctx->opt.mean_free) return fail(ctx, FMM_EUNSUPPORTED, "the adaptive evaluation does not take mean_free");
+    if (grad && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
+    if (parts < 1 || parts > FMM_PART_ALL) return fail(ctx, FMM_EINVAL, "parts must be a nonempty subset of near|far");
+    if ((st = adaptive_prepare(ctx)) != FMM_OK) return st;
+    ctx->adaptive_eval = true;
+    st = ctx->fp64 ? run_evaluate<double>(ctx, q, phi, grad, parts, false)
+                   : run_evaluate<float>(ctx, q, phi, grad, parts, false);
+    ctx->adaptive_eval = false;
+    ctx->last_far = false;   // the check rows of an adaptive evaluation are not exported
+    return st;
 }
 
 fmm_status fmm_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad) {

@@ -40,7 +40,7 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c) {
     g.child = L.child;
     g.parent = L.parent;
     g.keys = L.keys;
-    g.dense = L.dense;
+    g.dense = c.dense ? c.dense : L.dense;
     g.class_slots = ctx->class_slots;
     g.class_delta = ctx->class_delta;
     return g;
@@ -192,6 +192,7 @@ cudaError_t FarSteps<T>::stencil(int l, cudaStream_t s) {
     st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
     st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
     st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
+    if (ctx->adaptive_eval) st.dense = adaptive_dense(ctx, l);   // V lists of the adaptive tree
     if (ctx->tensor) {
         st.Xp = utP(l), st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
         st.xp_scale = utS(l), st.xp_scale_ld = nck_k;
@@ -275,14 +276,20 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
         FMM_CUDA_TRY(f.compress(l, ls));
         FMM_CUDA_TRY(f.stencil(l, ls));
+        // adaptive tree: boxes below a leaf take no VLI of their own; their downward rows carry
+        // the leaf's local field down by D2D alone
+        if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_zero_unkept<T>(ctx, l, rows_at<T>(ctx->Ct, ctx, l, f.kw), f.kw, f.kw, ls));
         FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
     }
     for (int l = 2; l <= d; ++l) {
         FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
         if (l == d) cudaEventRecord(ctx->ev[4], s);
         FMM_CUDA_TRY(f.down(l, s));
+        if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_xli<T>(ctx, l, rows_at<T>(f.B, ctx, l, f.nsp), f.nsp, s));
     }
-    return f.leaf_out(far_phi, far_grad, s);
+    FMM_CUDA_TRY(f.leaf_out(far_phi, far_grad, s));
+    if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_wli<T>(ctx, far_phi, far_grad, s));
+    return cudaSuccess;
 }
 
 template struct FarSteps<float>;
@@ -335,6 +342,11 @@ cudaError_t upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, OpSet &o) {
                                   &o.decompress));
     FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close1 : h.close1, h.rcl, ns, o.rclp, nsp, 1, &o.close1));
     FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close2 : h.close2, ns, h.rcl, nsp, o.rclp, 1, &o.close2));
+    if (!adjoint && h.rclu > 0) {
+        o.rclu = h.rclu, o.rclup = round_up(h.rclu, 16);
+        FMM_CUDA_TRY(upload_padded<T>(ctx, h.uclose1, h.rclu, ns, o.rclup, nsp, 1, &o.uclose1));
+        FMM_CUDA_TRY(upload_padded<T>(ctx, h.uclose2, ns, h.rclu, nsp, o.rclup, 1, &o.uclose2));
+    }
     return cudaSuccess;
 }
 

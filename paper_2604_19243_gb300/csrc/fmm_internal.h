@@ -53,6 +53,11 @@ struct OpSet {
     void *decompress = nullptr; // [nsp x koutp]
     void *close1 = nullptr;     // [rclp x nsp]  (U^T)          forward: applied before D2T
     void *close2 = nullptr;     // [nsp x rclp]  (V S^-1)
+    // upward closing (forward sets only): equivalent densities from the upward check potentials,
+    // read by the W-list step of the adaptive evaluation
+    int rclu = 0, rclup = 0;
+    void *uclose1 = nullptr;    // [rclup x nsp] (U^T)
+    void *uclose2 = nullptr;    // [nsp x rclup] (V S^-1)
 };
 
 // Split operand planes for the tcgen05 GEMMs (gemm_tc.cu): planes[0] holds `count` operators,
@@ -187,6 +192,7 @@ struct fmm_ctx {
 
     fmm::SplitState *split = nullptr;   // partitioned evaluation on virtual ranks (split.cu)
     fmm::AdaptiveState *adaptive = nullptr;   // adaptive tree and its lists (adaptive.cu)
+    bool adaptive_eval = false;               // an evaluation over the adaptive tree is running
 
     bool last_adjoint = false;  // what the last evaluation left in the workspaces
     bool last_far = false;
@@ -223,6 +229,8 @@ struct HostOps {
     std::vector<double> stencil;                      // [316][kout x kin]
     std::vector<double> decompress;                   // [ns x kout]  Uo
     std::vector<double> close1, close2;               // [rcl x ns], [ns x rcl] (unit box)
+    int rclu = 0;                                     // rank of the upward check-to-equivalent map
+    std::vector<double> uclose1, uclose2;             // [rclu x ns], [ns x rclu] (unit box)
     // adjoint (transposes)
     std::vector<double> a_up[8], a_down[8], a_compress, a_stencil, a_decompress, a_close1,
         a_close2;
@@ -258,6 +266,18 @@ fmm_status adaptive_setup(fmm_ctx *ctx, int capacity);
 void adaptive_free(fmm_ctx *ctx);
 fmm_status adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count);
 fmm_status adaptive_info(fmm_ctx *ctx, int32_t *capacity, int64_t *leaves, int64_t *refined, int64_t *entries);
+// Evaluation over the adaptive tree (FMM_FP32 / FMM_FP64, Laplace): workspaces, then the hooks
+// that run_far and run_evaluate call while ctx->adaptive_eval is set.
+fmm_status adaptive_prepare(fmm_ctx *ctx);
+const int *adaptive_dense(const fmm_ctx *ctx, int level);   // VLI source table: kept boxes only
+template <typename T>
+cudaError_t adaptive_zero_unkept(const fmm_ctx *ctx, int level, T *rows, int ld, int width, cudaStream_t s);
+template <typename T>
+cudaError_t adaptive_xli(const fmm_ctx *ctx, int level, T *D, int ld, cudaStream_t s);
+template <typename T>
+cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
+template <typename T>
+cudaError_t adaptive_uli(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
 
 // ---- tree.cu ----
 cudaError_t build_tree(fmm_ctx *ctx, const void *d_xyz);
@@ -322,6 +342,7 @@ struct GemmCall {
     const void *X1 = nullptr; int ldx1 = 0; int k1 = 0;
     void *const *W1_by_cls = nullptr;                     // array of 8 device pointers
     void *Y = nullptr; int ldy = 0;
+    const int *dense = nullptr;  // GM_STENCIL: source lookup table in place of the level's own
     // tensor-core only: A rows read from split planes through TMA row gathers (segment 0), and/or
     // the output written as split planes instead of FP32 Y.  Plane p of row r, column k is at
     // byte (r * ld + k) * esize + p * plane within the buffer (esize 2 for BF16, 4 for TF32).

@@ -323,6 +323,9 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     h->rcl = r_dc;
     h->close1 = dc_ut;   // [r_dc x ns]
     h->close2 = dc_vs;   // [ns x r_dc]
+    h->rclu = r_uc;
+    h->uclose1 = uc_ut;  // [r_uc x ns]
+    h->uclose2 = uc_vs;  // [ns x r_uc]
 
     // A child box of half-width 1/2 sees the kernel K_{kappa_u}(x/2, y/2) = 2 K_{kappa_u/2}(x, y)
     // of its own unit box (for the Helmholtz kernel with the wavenumber in place of kappa), so

@@ -106,3 +106,85 @@ def test_adaptive_state_errors():
     with pytest.raises(pkg.FmmError) as e:
         f.adaptive_info()
     assert e.value.status == 4
+
+
+# ---- evaluation over the adaptive tree (Algorithm 1 with XLI and WLI) ----
+
+def _adaptive_fmm(x, p, depth, precision, domain, capacity):
+    from gpu_helpers import make_fmm
+    f = make_fmm(x, p, depth, precision, domain)
+    f.adaptive_setup(capacity)
+    return f
+
+
+def _dev(a, precision):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float64 if precision == "fp64" else torch.float32)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["mixed", "sphere"])
+def test_adaptive_evaluate_matches_oracle(case, precision):
+    import paper_2604_19243_gb300 as pkg
+    from gpu_helpers import rel
+    from oracle import direct
+    from synth import charges
+    if case == "mixed":
+        n, cap, depth, dom, x = 4000, 32, 6, UNIT, mixed_points(4000)
+        qv = charges(n, "u11")
+    else:
+        n, cap, depth, dom, x = 3000, 24, 5, SPHERE, sphere_points(3000)
+        qv = charges(n, "u01")
+    p = 6
+    f = _adaptive_fmm(x, p, depth, precision, dom, cap)
+    x64, q64 = x.astype(np.float64), qv.astype(np.float64)
+    qd = _dev(qv, precision)
+    # near part: the ULI over the adaptive U lists, to rounding
+    phi_n, grad_n = f.adaptive_evaluate(qd, parts=pkg.PART_NEAR)
+    o_phi_n, o_grad_n, _, il = ad.evaluate(x64, q64, p, cap, depth, *dom, lists=("U",))
+    tol_near = 1e-12 if precision == "fp64" else 2e-6
+    assert rel(phi_n.cpu().numpy(), o_phi_n) < tol_near
+    assert rel(grad_n.cpu().numpy(), o_grad_n) < tol_near
+    # the whole field against the FP64 adaptive oracle at the same p
+    phi, grad = f.adaptive_evaluate(qd)
+    o_phi, o_grad, _, _ = ad.evaluate(x64, q64, p, cap, depth, *dom)
+    assert sum(len(m) for m in il.w.values()) > 0 and il.x
+    e_phi, e_grad = rel(phi.cpu().numpy(), o_phi), rel(grad.cpu().numpy(), o_grad)
+    assert e_phi < 1e-5 and e_grad < 1e-4, (e_phi, e_grad)
+    # and against the direct sum
+    d_phi, d_grad = direct.direct_self(x64, q64)
+    assert rel(phi.cpu().numpy(), d_phi) < 2e-5 and rel(grad.cpu().numpy(), d_grad) < 1e-4
+    # gradient only: the same gradients
+    none, grad_only = f.adaptive_evaluate(qd, potential=False)
+    assert none is None and torch.equal(grad_only, grad)
+
+
+def test_adaptive_evaluate_on_the_fully_refined_tree_is_the_uniform_evaluation():
+    from gpu_helpers import rel
+    from synth import charges
+    x, qv = mixed_points(3000), charges(3000, "u11")
+    f = _adaptive_fmm(x, 6, 4, "fp64", UNIT, 0)
+    qd = _dev(qv, "fp64")
+    phi_a, grad_a = f.adaptive_evaluate(qd)
+    phi_u, grad_u = f.evaluate(qd)
+    assert rel(phi_a.cpu().numpy(), phi_u.cpu().numpy()) < 1e-13
+    assert rel(grad_a.cpu().numpy(), grad_u.cpu().numpy()) < 1e-13
+
+
+def test_adaptive_evaluate_refusals():
+    import paper_2604_19243_gb300 as pkg
+    from gpu_helpers import make_fmm
+    from synth import charges
+    x, qv = mixed_points(1000), charges(1000, "u11")
+    f = make_fmm(x, 4, 4, "fp32", UNIT)
+    with pytest.raises(pkg.FmmError) as e:
+        f.adaptive_evaluate(_dev(qv, "fp32"))             # no adaptive tree yet
+    assert e.value.status == 4
+    f.adaptive_setup(16)
+    with pytest.raises(pkg.FmmError) as e:
+        f.adaptive_evaluate(_dev(qv, "fp32"), parts=0)
+    assert e.value.status == 1
+    g = make_fmm(x, 4, 4, "fp16x3", UNIT)
+    g.adaptive_setup(16)
+    with pytest.raises(pkg.FmmError) as e:
+        g.adaptive_evaluate(_dev(qv, "fp32"))
+    assert e.value.status == 6
