@@ -292,8 +292,9 @@ def run_partition_bench(args, w, fmm, x, q, phi, grad, flush, stream, ws, rank):
 def measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream, steps=10):
     """The headline workload's other forms, each timed like the step (3 warm-up, `steps` timed,
     L2 flushed between steps, CUDA events): the gradient-only evaluation, the modified Helmholtz
-    kernel, and the evaluation partitioned over 64 virtual ranks at depth 3.  A failure is reported
-    in place of the variant's numbers; the headline line is unaffected."""
+    kernel, the evaluation partitioned over 64 virtual ranks at depth 3, and the evaluation over
+    the adaptive tree of capacity 64.  A failure is reported in place of the variant's numbers;
+    the headline line is unaffected."""
     import torch
     import paper_2604_19243_gb300 as pkg
     from oracle import direct
@@ -356,6 +357,31 @@ def measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream, s
                                         "step": "evaluate on a built tree and partition"}
     except Exception as e:   # noqa: BLE001
         out["partition_dg3_ranks64"] = {"error": str(e)}
+    try:   # the adaptive tree (capacity 64) over the same depth-7 tree, in FP32 (the adaptive
+        # evaluation runs in the SIMT precisions), with the uniform FP32 evaluation beside it
+        fa = pkg.FMM(p=w.p, depth=w.depth, precision="fp32", domain=(w.origin, w.side), stream=stream.cuda_stream)
+        fa.precompute()
+        fa.build_tree(x)
+        uniform = timed(lambda: fa.evaluate_into(q, phi, grad))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fa.adaptive_setup(64)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        ms = timed(lambda: fa.adaptive_evaluate_into(q, phi, grad))
+        near = timed(lambda: fa.adaptive_evaluate_into(q, phi, grad, parts=pkg.PART_NEAR))
+        fa.adaptive_evaluate_into(q, phi, grad)
+        torch.cuda.synchronize()
+        acc = accuracy_check(w, x_np, q_np, phi.cpu().numpy().astype(np.float64),
+                             grad.cpu().numpy().astype(np.float64), m=64)
+        info = fa.adaptive_info()
+        fa.close()
+        out["adaptive_q64_fp32"] = {"points_per_s": w.n / (ms * 1e-3), "ms_per_evaluate": ms, "near_ms": near,
+                                    "uniform_fp32_ms_per_evaluate": uniform, "setup_ms": round(setup_ms, 3),
+                                    "leaves_per_level": info["n_leaves"], "list_entries_uvwx": info["n_entries"],
+                                    "accuracy": acc, "step": "adaptive evaluate on a built tree and adaptive tree"}
+    except Exception as e:   # noqa: BLE001
+        out["adaptive_q64_fp32"] = {"error": str(e)}
     return out
 
 

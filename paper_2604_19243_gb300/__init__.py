@@ -402,6 +402,10 @@ class FMM:
         self._check(lib().fmm_adaptive_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
         return phi, grad
 
+    def adaptive_evaluate_into(self, q, phi, grad=None, parts=PART_ALL):
+        """fmm_adaptive_evaluate on caller-owned arrays; phi may be None when grad is given."""
+        self._check(lib().fmm_adaptive_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""
         ms = np.zeros(5, np.float64)
