@@ -76,6 +76,13 @@ def test_default_options_and_validation_without_gpu(libpath):
         assert o.kernel == 0 and o.kappa == 0.0
         o.kernel, o.kappa, o.has_domain, o.side, o.mean_free = kernel, kappa, has_domain, 1.0, mean_free
         assert lib.fmm_create(ctypes.byref(o), None, ctypes.byref(ctx)) == want, (kernel, kappa, has_domain)
+    # null contexts are refused before any CUDA call
+    ainfo = pkg.AdaptiveTreeInfo()
+    assert lib.fmm_adaptive_setup(None, 8) == 1
+    assert lib.fmm_adaptive_info(None, ctypes.byref(ainfo)) == 1
+    assert lib.fmm_adaptive_export(None, pkg.ADAPTIVE_U, None, None, None) == 1
+    assert lib.fmm_adaptive_evaluate(None, None, None, None, pkg.PART_ALL) == 1
+    assert lib.fmm_partition_setup(None, 2, 4) == 1
     assert lib.fmm_last_error(None) == b"null context"
     lib.fmm_destroy(None)
 
