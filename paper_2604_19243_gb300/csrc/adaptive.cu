@@ -18,6 +18,12 @@
 // a level), and every list is sorted by row.  One thread builds the U, V and W lists of one box:
 // the same-level positions through the dense tables, coarser leaves by walking up from an empty
 // position, and finer boxes by a depth-first walk below each refined colleague.
+//
+// The evaluation over the adaptive tree reuses the uniform far pass (evaluate.cu) with the hooks
+// defined at the end of this file: the VLI reads a dense table of the kept boxes only; boxes below
+// a leaf lose their own VLI output and carry the leaf's local field down by D2D; XLI adds the X
+// lists' sources to the downward check potentials (step 2b); WLI evaluates the upward equivalent
+// densities of the W lists at the leaves' points (step 3a); the ULI runs over the adaptive U lists.
 #include <algorithm>
 #include <vector>
 
