@@ -5,7 +5,10 @@ Plain, slow, obviously correct restatements of what the GPU path computes:
   * `tree`    - domain, Morton keys, stable sort, leaves, levels, U and V lists (Section 2.1,
                 Table 1), with brute-force list constructions straight from the definitions;
   * `kifmm`   - Algorithm 1 (uniform branches) with per-level operators built from actual box
-                geometry, uncompressed M2L, and its transpose (the adjoint pass).
+                geometry, uncompressed M2L, and its transpose (the adjoint pass);
+  * `adaptive` - the adaptive tree, its U, V, W and X lists, and Algorithm 1 with XLI and WLI;
+  * `partition`, `distributed` - Section 3's setup and runtime over ranks;
+  * `fft_m2l` - the M2L as a lattice convolution evaluated by FFT.
 
 It shares no code with the CUDA library and never imports it.  Only the tests, the smoke
 check and the benchmark's CPU-baseline leg may use it.  Inputs come from the `synth` module.
