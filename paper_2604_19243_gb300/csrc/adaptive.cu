@@ -714,18 +714,19 @@ fmm_status adaptive_prepare(fmm_ctx *ctx) {
         if (!ctx->fwd[l].uclose1) return afail(ctx, FMM_ESTATE, "the upward closing operators are missing");
     }
     const size_t ue_bytes = (size_t)A->rows * ctx->nsp * es, y1_bytes = (size_t)maxn * rclup * es;
-    if (A->ue_bytes < ue_bytes) {
-        cudaFree(A->ue);
-        A->ue = nullptr, A->ue_bytes = 0;
-        if (cudaMalloc(&A->ue, ue_bytes) != cudaSuccess) return cudaGetLastError(), afail(ctx, FMM_ENOMEM, "adaptive workspace");
-        A->ue_bytes = ue_bytes;
-    }
-    if (A->y1_bytes < y1_bytes) {
-        cudaFree(A->y1);
-        A->y1 = nullptr, A->y1_bytes = 0;
-        if (cudaMalloc(&A->y1, y1_bytes) != cudaSuccess) return cudaGetLastError(), afail(ctx, FMM_ENOMEM, "adaptive workspace");
-        A->y1_bytes = y1_bytes;
-    }
+    auto grow = [&](void **p, size_t *have, size_t need) {
+        if (*have >= need) return true;
+        cudaFree(*p);
+        *p = nullptr, *have = 0;
+        if (cudaMalloc(p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        *have = need;
+        return true;
+    };
+    if (!grow(&A->ue, &A->ue_bytes, ue_bytes) || !grow(&A->y1, &A->y1_bytes, y1_bytes))
+        return afail(ctx, FMM_ENOMEM, "adaptive workspace");
     return FMM_OK;
 }
 
