@@ -98,14 +98,8 @@ def _leaf_ranges(tr):
     return pos, span, len(leaf_id)
 
 
-@pytest.mark.parametrize("case", ["mixed", "sphere"])
-def test_lists_account_for_every_leaf_pair_once(case):
-    if case == "sphere":
-        x, q, depth, dom = sphere_points(1500).astype(np.float64), 20, 5, ((-1.0, -1.0, -1.0), 2.0)
-    else:
-        x, q, depth, dom = _mixed(2000)[0], 16, 6, DOMAIN
-    tr = ad.build_tree(x, q, depth, *dom)
-    il = ad.interaction_lists(tr)
+def _cover(tr, il):
+    """How often each ordered pair of leaves (target, source) is accounted for by the lists."""
     pos, span, n = _leaf_ranges(tr)
     cover = np.zeros((n, n), np.int64)
     for t, members in il.u.items():
@@ -123,9 +117,48 @@ def test_lists_account_for_every_leaf_pair_once(case):
         for s in members:
             b0, b1 = span[b]
             cover[b0:b1, pos[int(s)]] += 1
+    return cover
+
+
+@pytest.mark.parametrize("case", ["mixed", "sphere"])
+def test_lists_account_for_every_leaf_pair_once(case):
+    if case == "sphere":
+        x, q, depth, dom = sphere_points(1500).astype(np.float64), 20, 5, ((-1.0, -1.0, -1.0), 2.0)
+    else:
+        x, q, depth, dom = _mixed(2000)[0], 16, 6, DOMAIN
+    tr = ad.build_tree(x, q, depth, *dom)
+    il = ad.interaction_lists(tr)
+    cover = _cover(tr, il)
     assert (cover == 1).all(), np.argwhere(cover != 1)[:5]
     assert sum(len(m) for m in il.w.values()) > 0        # the adaptive branches are exercised
     assert sum(len(m) for m in il.x.values()) > 0
+
+
+@pytest.mark.parametrize("mistake", ["w_without_parent_condition", "v_with_adjacent_box", "u_missing_coarser_leaf"])
+def test_pair_coverage_catches_planted_list_mistakes(mistake):
+    """Plausible slips in the list definitions, planted in the oracle's lists: each breaks the
+    exact coverage of the leaf pairs."""
+    tr = ad.build_tree(_mixed(2000)[0], 16, 6, *DOMAIN)
+    il = ad.interaction_lists(tr)
+    lv, ix = tr.boxes()
+    base = np.concatenate([[0], np.cumsum([len(k) for k in tr.level_keys])])
+    anc = np.concatenate(tr.level_anchors)
+    par = np.full(len(lv), -1)
+    for l in range(1, tr.depth + 1):
+        par[base[l]:base[l + 1]] = base[l - 1] + tr.parent(l)
+    if mistake == "w_without_parent_condition":      # a W member's child joins the list too
+        t, a = next((t, a) for t, m in il.w.items() for a in m if (par == a).any())
+        child = int(np.nonzero(par == a)[0][0])
+        il.w[t] = np.sort(np.append(il.w[t], child))
+        il.x.setdefault(child, np.zeros(0, np.int64))
+        il.x[child] = np.sort(np.append(il.x[child], t))
+    elif mistake == "v_with_adjacent_box":           # a colleague (adjacent, same level) enters V
+        b, c = next((b, c) for b in il.v for c in np.nonzero((lv == lv[b]) & (np.abs(anc - anc[b]).max(axis=1) == 1))[0])
+        il.v[b] = np.sort(np.append(il.v[b], c))
+    else:                                            # a coarser adjacent leaf drops out of U
+        t, s_ = next((t, s_) for t, m in il.u.items() for s_ in m if lv[s_] < lv[t])
+        il.u[t] = il.u[t][il.u[t] != s_]
+    assert not (_cover(tr, il) == 1).all()
 
 
 def test_list_geometry():
