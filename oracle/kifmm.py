@@ -23,7 +23,9 @@ Operators (Table 1), all built from the actual box sizes of each level:
   ULI   f_i += sum_{a in U(b)} sum_{j in a, j != i} K(x_i, y_j) s_j
 The VLI sum is evaluated one transfer vector at a time, using that interactions sharing a
 transfer vector share one operator (Section 2.2); `m2l="pairwise"` instead builds every
-pair's matrix from the two boxes' own coordinates (slow; used to pin the grouped form).
+pair's matrix from the two boxes' own coordinates (slow; used to pin the grouped form), and
+`m2l="fft"` evaluates each transfer vector's M2L as a lattice convolution by FFT (fft_m2l; it
+needs operators built with the lattice radius as `alpha_inner`).
 The M2L is not compressed here, so the GPU path's SVD truncation error is inside the budget.
 
 With `kappa` > 0 every K above is the modified Helmholtz (Yukawa) kernel
@@ -102,6 +104,7 @@ class Operators:
     m2l: dict         # (level, t) -> K(dc_b, ue_{b + t})
     kappa: float = 0.0  # kernel: 0 Laplace, > 0 modified Helmholtz exp(-kappa r) / (4 pi r)
     wavenumber: float = 0.0   # > 0: Helmholtz exp(i k r) / (4 pi r), complex operators and data
+    alpha_inner: float = ALPHA_INNER   # radius of the upward-equivalent and downward-check surfaces
 
     @property
     def dtype(self):
@@ -113,30 +116,33 @@ def child_offset(c):
     return np.array([(c >> 2) & 1, (c >> 1) & 1, c & 1], dtype=np.float64)
 
 
-def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None, kappa=0.0, wavenumber=0.0):
+def build_operators(p, side, depth, rtol=DEFAULT_PINV_RTOL, m2l_levels=None, kappa=0.0, wavenumber=0.0,
+                    alpha_inner=ALPHA_INNER):
+    """Operators of every level.  `alpha_inner` moves the upward-equivalent and downward-check
+    surfaces (1.05 by default; the FFT form of the M2L needs the lattice radius of fft_m2l)."""
     tv = otree.transfer_vectors()
-    ops = Operators(p, {}, {}, {}, {}, {}, kappa, wavenumber)
+    ops = Operators(p, {}, {}, {}, {}, {}, kappa, wavenumber, alpha_inner)
     km = lambda a, b: kernel_matrix(a, b, kappa, wavenumber)
     zero = np.zeros(3)
     for level in range(0, depth + 1):
         r = side / 2.0 ** (level + 1)
         ops.uc2e[level] = pinv(km(surface(p, zero, r, ALPHA_OUTER),
-                                             surface(p, zero, r, ALPHA_INNER)), rtol)
-        ops.dc2e[level] = pinv(km(surface(p, zero, r, ALPHA_INNER),
+                                             surface(p, zero, r, alpha_inner)), rtol)
+        ops.dc2e[level] = pinv(km(surface(p, zero, r, alpha_inner),
                                              surface(p, zero, r, ALPHA_OUTER)), rtol)
     for level in range(0, depth):
         r_p, r_c = side / 2.0 ** (level + 1), side / 2.0 ** (level + 2)
         for c in range(8):
             cc = (2.0 * child_offset(c) - 1.0) * r_c          # child centre relative to parent
             ops.m2m[(level, c)] = km(surface(p, zero, r_p, ALPHA_OUTER),
-                                                surface(p, cc, r_c, ALPHA_INNER))
-            ops.l2l[(level + 1, c)] = km(surface(p, cc, r_c, ALPHA_INNER),
+                                                surface(p, cc, r_c, alpha_inner))
+            ops.l2l[(level + 1, c)] = km(surface(p, cc, r_c, alpha_inner),
                                                     surface(p, zero, r_p, ALPHA_OUTER))
     for level in (range(2, depth + 1) if m2l_levels is None else m2l_levels):
         r = side / 2.0 ** (level + 1)
-        tgt = surface(p, zero, r, ALPHA_INNER)
+        tgt = surface(p, zero, r, alpha_inner)
         for t, delta in enumerate(tv):
-            ops.m2l[(level, t)] = km(tgt, surface(p, 2.0 * r * delta, r, ALPHA_INNER))
+            ops.m2l[(level, t)] = km(tgt, surface(p, 2.0 * r * delta, r, alpha_inner))
     return ops
 
 
@@ -205,13 +211,22 @@ def downward(tr, u, ops, leaves, m2l="grouped"):
             for t in np.unique(tvec):
                 sel = tvec == t
                 q_dc[rows[sel]] += u[level][idx[sel]] @ ops.m2l[(level, int(t))].T
+        elif m2l == "fft":   # each transfer vector's M2L as a lattice convolution (fft_m2l)
+            from . import fft_m2l
+            assert ops.alpha_inner == fft_m2l.lattice_alpha(p) and ops.wavenumber == 0.0
+            tv = otree.transfer_vectors()
+            r = tr.halfwidth(level)
+            for t in np.unique(tvec):
+                sel = tvec == t
+                ghat = fft_m2l.kernel_transform(p, r, tv[int(t)], ops.kappa)
+                q_dc[rows[sel]] += fft_m2l.m2l_fft(p, r, tv[int(t)], u[level][idx[sel]], ops.kappa, ghat)
         else:
             r = tr.halfwidth(level)
             ctr = tr.centres(level)
             for k in range(len(idx)):
                 b, a = boxes[rows[k]], idx[k]
-                kmat = kernel_matrix(surface(p, ctr[b], r, ALPHA_INNER),
-                                     surface(p, ctr[a], r, ALPHA_INNER), ops.kappa, ops.wavenumber)
+                kmat = kernel_matrix(surface(p, ctr[b], r, ops.alpha_inner),
+                                     surface(p, ctr[a], r, ops.alpha_inner), ops.kappa, ops.wavenumber)
                 q_dc[rows[k]] += kmat @ u[level][a]
         if level >= 3:
             par = tr.parent(level)[boxes]

@@ -65,3 +65,29 @@ def test_fitted_densities_reproduce_the_far_field():
         errs.append(worst)
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] < 1e-4 and errs[2] < 1e-5
+
+
+def test_kifmm_with_fft_m2l_equals_the_dense_form():
+    """The whole method with every VLI evaluated as lattice convolutions equals the grouped dense
+    M2L on the same (lattice) surfaces."""
+    from synth import cube_points, charges
+    x = cube_points(1500).astype(np.float64)
+    q = charges(1500, "u11").astype(np.float64)
+    p, depth = 4, 3
+    ops = kifmm.build_operators(p, 1.0, depth, alpha_inner=fft_m2l.lattice_alpha(p))
+    a = kifmm.evaluate(x, q, p, depth, (0, 0, 0), 1.0, ops=ops, m2l="fft")
+    b = kifmm.evaluate(x, q, p, depth, (0, 0, 0), 1.0, ops=ops, m2l="grouped")
+    assert np.linalg.norm(a.phi - b.phi) / np.linalg.norm(b.phi) < 1e-10
+    assert np.linalg.norm(a.grad - b.grad) / np.linalg.norm(b.grad) < 1e-10
+
+
+def test_lattice_surfaces_meet_the_accuracy_bar_at_p6():
+    from oracle import direct
+    from synth import cube_points, charges
+    x = cube_points(4000).astype(np.float64)
+    q = charges(4000, "u11").astype(np.float64)
+    ref, gref = direct.direct_self(x, q)
+    ops = kifmm.build_operators(6, 1.0, 4, alpha_inner=fft_m2l.lattice_alpha(6))
+    r = kifmm.evaluate(x, q, 6, 4, (0, 0, 0), 1.0, ops=ops)
+    assert np.linalg.norm(r.phi - ref) / np.linalg.norm(ref) < 1e-5
+    assert np.linalg.norm(r.grad - gref) / np.linalg.norm(gref) < 5e-5
