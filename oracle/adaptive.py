@@ -78,8 +78,10 @@ class AdaptiveTree:
         return lv[order], ix[order]
 
 
-def build_tree(points, capacity, depth, origin=None, side=None):
-    """Refine the bounding cube while a box holds more than `capacity` points, down to `depth`."""
+def build_tree(points, capacity, depth, origin=None, side=None, min_level=0):
+    """Refine the bounding cube while a box holds more than `capacity` points, down to `depth`.
+    Boxes above `min_level` are refined whatever they hold (the uniform global levels of the
+    distributed scheme, Section 2.3)."""
     if origin is None or side is None:
         origin, side = otree.domain_from_points(points)
     origin = np.asarray(origin, dtype=np.float64).reshape(3)
@@ -97,7 +99,7 @@ def build_tree(points, capacity, depth, origin=None, side=None):
         kl = np.unique(pk[active])
         begin = np.searchsorted(pk, kl, side="left")
         end = np.searchsorted(pk, kl, side="right")
-        leaf = (end - begin <= capacity) | (level == depth)
+        leaf = ((end - begin <= capacity) & (level >= min_level)) | (level == depth)
         for b, e in zip(begin[leaf], end[leaf]):
             active[b:e] = False
         lk.append(kl)

@@ -14,6 +14,9 @@ roots) and P ranks:
   * the neighbourhoods (step 5): the ranks a rank's U and V packets address;
   * the existence answers (step 6): the queried positions that hold a box.
 
+`adaptive_let` gives the same split for an adaptive tree (Section 2.3: the global levels are
+uniform, the local trees adaptive), with the U, V, W and X lists of oracle.adaptive.
+
 Readings where the paper is silent or leaves a choice:
   * layout: contiguous runs of local roots in Morton order, balanced by point counts: rank r
     starts at the first root i whose preceding roots hold at least ceil(r N / P) points, kept at
@@ -39,6 +42,11 @@ def layout(tr, d_global, n_ranks):
     counts = np.diff(tr.leaf_offsets)
     pts = np.zeros(len(roots), np.int64)
     np.add.at(pts, np.searchsorted(roots, leaf_root), counts)
+    return layout_from_counts(pts, n_ranks)
+
+
+def layout_from_counts(pts, n_ranks):
+    """The layout rule over local roots holding pts[i] points each (Morton order)."""
     prefix = np.concatenate([[0], np.cumsum(pts)])
     n = int(prefix[-1])
     first = [0]
@@ -46,13 +54,50 @@ def layout(tr, d_global, n_ranks):
         target = math.ceil(n * r / n_ranks)
         i = int(np.searchsorted(prefix, target, side="left"))
         i = max(i, first[-1] + 1)
-        i = min(i, len(roots) - (n_ranks - r))
+        i = min(i, len(pts) - (n_ranks - r))
         first.append(i)
-    first.append(len(roots))
-    owner = np.zeros(len(roots), np.int64)
+    first.append(len(pts))
+    owner = np.zeros(len(pts), np.int64)
     for r in range(n_ranks):
         owner[first[r]:first[r + 1]] = r
     return np.asarray(first, np.int64), owner
+
+
+def adaptive_let(tr, il, d_global, n_ranks):
+    """Local essential trees of an adaptive tree split at d_global (every box above d_global
+    refined, so the local roots are the boxes of level d_global): per rank, its own boxes and the
+    ghosts its U, V, W and X lists name.  U and X members carry source points and densities (s
+    ghosts); V and W members carry upward densities (u ghosts).  Boxes are global ids of
+    `AdaptiveTree.boxes()`; `tr` and `il` come from oracle.adaptive."""
+    lv, ix = tr.boxes()
+    base = np.concatenate([[0], np.cumsum([len(k) for k in tr.level_keys])])
+    keys = np.concatenate(tr.level_keys)
+    assert all(not tr.level_leaf[l].any() for l in range(d_global)), "levels above d_global must be refined"
+    counts = np.diff(tr.level_ranges[d_global], axis=1)[:, 0]
+    first, owner = layout_from_counts(counts, n_ranks)
+    root = np.full(len(lv), -1, np.int64)          # local root (index at d_global) of every box
+    deep = lv >= d_global
+    root[deep] = np.searchsorted(tr.level_keys[d_global],
+                                 keys[deep] >> (np.uint64(3) * (lv[deep] - d_global).astype(np.uint64)))
+    box_owner = np.where(deep, owner[np.maximum(root, 0)], -1)
+    out = {"first_root": first, "owner": owner, "root": root, "box_owner": box_owner, "ranks": []}
+    for r in range(n_ranks):
+        # own: the rank's local roots and everything below them.  The leaves' U and W lists are
+        # local work at every level; V and X below d_global (the V lists of level d_global belong
+        # to the global stage, and a local root has no X list: X members are coarser than it)
+        own = np.nonzero((box_owner == r) & (lv >= d_global))[0]
+        need_s, need_u = set(), set()
+        for b in own:
+            need_s.update(il.u.get(int(b), []))
+            need_u.update(il.w.get(int(b), []))
+            if lv[b] > d_global:
+                need_s.update(il.x.get(int(b), []))
+                need_u.update(il.v.get(int(b), []))
+        ghost_s = np.array(sorted(a for a in need_s if box_owner[a] != r), np.int64)
+        ghost_u = np.array(sorted(a for a in need_u if box_owner[a] != r), np.int64)
+        nb = sorted(set(box_owner[ghost_s].tolist()) | set(box_owner[ghost_u].tolist()))
+        out["ranks"].append({"own": own, "ghost_s": ghost_s, "ghost_u": ghost_u, "neighbours": nb})
+    return out
 
 
 def message_bytes(n_roots, p, bits):
