@@ -170,11 +170,12 @@ def _surfaces(tr, level, boxes, p, alpha):
 
 def evaluate(points, charges, p, capacity, depth, origin=None, side=None, gradient=True,
              pinv_rtol=kifmm.DEFAULT_PINV_RTOL, ops=None, kappa=0.0, wavenumber=0.0,
-             lists=("U", "V", "W", "X")):
+             lists=("U", "V", "W", "X"), min_level=0):
     """FP64 adaptive kiFMM field at every point (input order): Algorithm 1 with its adaptive
-    branches.  `lists` selects which interaction lists contribute (all four by default)."""
+    branches.  `lists` selects which interaction lists contribute (all four by default);
+    `min_level` as in build_tree."""
     xs_in = np.asarray(points, dtype=np.float64).reshape(-1, 3)
-    tr = build_tree(xs_in, capacity, depth, origin, side)
+    tr = build_tree(xs_in, capacity, depth, origin, side, min_level)
     il = interaction_lists(tr)
     if ops is None:
         ops = kifmm.build_operators(p, tr.side, depth, pinv_rtol, kappa=kappa, wavenumber=wavenumber)

@@ -241,3 +241,152 @@ def _downward_level(tr, ops, level, boxes, u_level, d_parent, ns):
             sel = oct_ == c
             q[sel] += d_parent[par[sel]] @ ops.l2l[(level, c)].T
     return q @ ops.dc2e[level].T
+
+
+# ---- the scheme over an adaptive tree ---------------------------------------------------------
+def run_adaptive(points, charges, p, capacity, depth, origin, side, d_global, pinv_rtol=kifmm.DEFAULT_PINV_RTOL):
+    """This rank's part of the distributed evaluation over an adaptive tree (Section 2.3: the
+    global levels 0..d_global uniform, the local trees below them adaptive), with the lists and
+    arithmetic of oracle.adaptive.  Every rank builds the global tree and lists from the same
+    points (as `run` does); the ghosts of its local essential tree (oracle.partition.adaptive_let)
+    are requested from their owners and arrive as messages: points and densities for the U and X
+    members, upward densities for the V and W members.  Returns (sorted positions of its points,
+    their potentials, their gradients, the rank's local essential tree)."""
+    from . import adaptive as ad
+    P, me = dist.get_world_size(), dist.get_rank()
+    xs_in = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    q_in = np.asarray(charges, dtype=np.float64).reshape(-1)
+    dg = d_global
+    tr = ad.build_tree(xs_in, capacity, depth, origin, side, min_level=dg)
+    il = ad.interaction_lists(tr)
+    let = opart.adaptive_let(tr, il, dg, P)
+    rk = let["ranks"][me]
+    owner = let["box_owner"]
+    lv, ix = tr.boxes()
+    base = np.concatenate([[0], np.cumsum([len(k) for k in tr.level_keys])])
+    leaf = np.concatenate(tr.level_leaf)
+    keys = np.concatenate(tr.level_keys)
+    xs, qs = xs_in[tr.perm], q_in[tr.perm]
+    ops = kifmm.build_operators(p, tr.side, depth, pinv_rtol)
+    ns = kifmm.n_surface(p)
+    rng = {int(b): tr.level_ranges[lv[b]][ix[b]] for b in range(len(lv))}
+    own = rk["own"]
+
+    def fetch(ghosts, payload, width):
+        """Ghost data from their owners: the requests (box ids) go out, each owner answers with
+        the payloads in the order asked; returns box id -> payload."""
+        req = {int(o): ghosts[owner[ghosts] == o] for o in np.unique(owner[ghosts])}
+        asked = _exchange({o: a.astype(np.int64) for o, a in req.items()}, np.int64)
+        reply = _exchange({s: np.concatenate([payload(int(b)) for b in ids]) for s, ids in asked.items()}, np.float64)
+        out = {}
+        for o, ids in req.items():
+            buf, k = reply[o], 0
+            for b in ids:
+                w = width(int(b))
+                out[int(b)] = buf[k:k + w]
+                k += w
+        return out
+
+    # s ghosts (U and X members): their points and densities
+    npts = lambda b: int(rng[b][1] - rng[b][0])
+    got = fetch(rk["ghost_s"], lambda b: np.concatenate([xs[rng[b][0]:rng[b][1]].ravel(), qs[rng[b][0]:rng[b][1]]]),
+                lambda b: 4 * npts(b))
+    src = {b: (v[:3 * npts(b)].reshape(-1, 3), v[3 * npts(b):]) for b, v in got.items()}
+    for b in own:
+        if leaf[b]:
+            src[int(b)] = (xs[rng[int(b)][0]:rng[int(b)][1]], qs[rng[int(b)][0]:rng[int(b)][1]])
+
+    def surface(b, alpha):
+        level = lv[b]
+        c = tr.centres(level, np.array([ix[b]]))[0]
+        return kifmm.surface(p, c, tr.halfwidth(level), alpha)
+
+    def sums(targets, sources):
+        """Potential (and gradient) at `targets` of the (points, densities) pairs in `sources`."""
+        pot, grd = np.zeros(len(targets)), np.zeros((len(targets), 3))
+        for sx, sq in sources:
+            direct.grouped_sum([0, len(targets)], targets, [0, 1], [[0, len(sq)]], sx, sq, True, pot, grd)
+        return pot, grd
+
+    # local upward stage: S2U at the own leaves, U2U at the own refined boxes, down to the local roots
+    u = {}
+    for level in range(depth, dg - 1, -1):
+        for b in own[lv[own] == level]:
+            b = int(b)
+            if leaf[b]:
+                q_uc = sums(surface(b, kifmm.ALPHA_OUTER), [src[b]])[0]
+            else:
+                q_uc = np.zeros(ns)
+                kids = np.nonzero((lv == level + 1) & ((keys >> np.uint64(3)) == keys[b]))[0]
+                for c in kids:
+                    q_uc += ops.m2m[(level, int(keys[c] & np.uint64(7)))] @ u[int(c)]
+            u[b] = ops.uc2e[level] @ q_uc
+    # u ghosts (V and W members), from their owners once they have them
+    u.update(fetch(rk["ghost_u"], lambda b: u[b], lambda b: ns))
+
+    # global stage at rank 0: the local roots' u gathered, U2U up to level 2, VLI and D2D down to
+    # the local roots, their d scattered back
+    roots = own[lv[own] == dg]
+    allu = _gatherv(np.concatenate([u[int(b)] for b in roots]) if len(roots) else np.zeros(0))
+    dvec = {}
+    parts = None
+    if me == 0:
+        ug = {int(base[dg]) + i: v for i, v in enumerate(np.concatenate(allu).reshape(-1, ns))}
+        for level in range(dg - 1, 1, -1):
+            for b in range(base[level], base[level + 1]):
+                q_uc = np.zeros(ns)
+                for c in np.nonzero((lv == level + 1) & ((keys >> np.uint64(3)) == keys[b]))[0]:
+                    q_uc += ops.m2m[(level, int(keys[c] & np.uint64(7)))] @ ug[int(c)]
+                ug[b] = ops.uc2e[level] @ q_uc
+        dgl = {}
+        for level in range(2, dg + 1):
+            for b in range(base[level], base[level + 1]):
+                assert len(il.x.get(b, ())) == 0      # no leaf is coarser than d_global
+                dgl[b] = ops.dc2e[level] @ _adaptive_check(tr, ops, il, b, lv, keys, base, ug, dgl, None, ns)
+        parts = [np.concatenate([dgl[int(base[dg]) + i] for i in range(let["first_root"][r], let["first_root"][r + 1])])
+                 for r in range(P)]
+    mine = _scatterv(parts, len(roots) * ns).reshape(-1, ns)
+    for i, b in enumerate(roots):
+        dvec[int(b)] = mine[i]
+    # local downward stage: VLI, XLI and D2D into the own boxes below d_global
+    for level in range(dg + 1, depth + 1):
+        for b in own[lv[own] == level]:
+            b = int(b)
+            q_dc = _adaptive_check(tr, ops, il, b, lv, keys, base, u, dvec, (src, surface), ns)
+            dvec[b] = ops.dc2e[level] @ q_dc
+    # leaf evaluation: D2T, WLI and ULI at the own points
+    lo, hi = rng[int(roots[0])][0], rng[int(roots[-1])][1]
+    pot, grd = np.zeros(hi - lo), np.zeros((hi - lo, 3))
+    for b in own[leaf[own]]:
+        b = int(b)
+        t0, t1 = rng[b]
+        tx = xs[t0:t1]
+        terms = [(surface(b, kifmm.ALPHA_OUTER), dvec[b])]
+        terms += [(surface(int(a), kifmm.ALPHA_INNER), u[int(a)]) for a in il.w.get(b, [])]
+        terms += [src[int(a)] for a in il.u.get(b, [])]
+        ph, gr = sums(tx, terms)
+        pot[t0 - lo:t1 - lo], grd[t0 - lo:t1 - lo] = ph, gr
+    return np.arange(lo, hi), pot, grd, rk
+
+
+def _adaptive_check(tr, ops, il, b, lv, keys, base, u, dvec, x_sources, ns):
+    """Downward check potentials of box b: VLI from the u of its V list, XLI from the points of
+    its X list (x_sources = (sources, surface function) below d_global), D2D from its parent's d."""
+    level = int(lv[b])
+    anc = tr.level_anchors[level]
+    q = np.zeros(ns)
+    members = np.asarray(il.v.get(b, ()), np.int64)
+    if len(members):
+        tvec = otree.transfer_index(anc[members - base[level]] - anc[b - base[level]])
+        for a, t in zip(members, tvec):
+            q += ops.m2l[(level, int(t))] @ u[int(a)]
+    if x_sources is not None and len(il.x.get(b, ())):
+        src, surface = x_sources
+        dc = surface(b, kifmm.ALPHA_INNER)
+        for a in il.x[b]:
+            sx, sq = src[int(a)]
+            direct.grouped_sum([0, len(dc)], dc, [0, 1], [[0, len(sq)]], sx, sq, False, q, None)
+    if level >= 3:
+        parent = int(base[level - 1]) + int(np.searchsorted(tr.level_keys[level - 1], keys[b] >> np.uint64(3)))
+        q += ops.l2l[(level, int(keys[b] & np.uint64(7)))] @ dvec[parent]
+    return q
