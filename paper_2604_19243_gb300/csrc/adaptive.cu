@@ -660,6 +660,7 @@ cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     AdaptiveState *A = ctx->adaptive;
     const int D = ctx->opt.depth;
     if (A->entries[2] == 0 || D < 2) return cudaSuccess;
+    if (ctx->npts > kMaxSurface) return cudaErrorInvalidValue;   // p <= 10 is checked at fmm_create
     const int nsp = ctx->nsp;
     // upward equivalent densities of every box of levels 2..D: r_l (V S^-1)(U^T U_l)
     for (int l = 2; l <= D; ++l) {
