@@ -264,3 +264,15 @@ def test_modified_helmholtz_kernel():
     phi, g, _, _ = ad.evaluate(x, qv, 6, 24, 6, *DOMAIN, kappa=kappa)
     assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-5
     assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 1e-5
+
+
+def test_helmholtz_kernel():
+    """Complex densities and operators through the same adaptive steps (wavenumber 2)."""
+    x = _mixed(2000)[0]
+    rng = np.random.default_rng(11)
+    qc = rng.uniform(-1, 1, 2000) + 1j * rng.uniform(-1, 1, 2000)
+    ref, gref = direct.direct_self(x, qc, wavenumber=2.0)
+    phi, g, _, il = ad.evaluate(x, qc, 6, 24, 6, *DOMAIN, wavenumber=2.0)
+    assert np.iscomplexobj(phi) and sum(len(m) for m in il.w.values()) > 0
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-5
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) < 1e-5
