@@ -7,7 +7,8 @@ Plain, slow, obviously correct restatements of what the GPU path computes:
   * `kifmm`   - Algorithm 1 (uniform branches) with per-level operators built from actual box
                 geometry, uncompressed M2L, and its transpose (the adjoint pass);
   * `adaptive` - the adaptive tree, its U, V, W and X lists, and Algorithm 1 with XLI and WLI;
-  * `partition`, `distributed` - Section 3's setup and runtime over ranks;
+  * `partition`, `distributed`, `samplesort` - Section 3's setup (with the sample sort of its
+                step 1) and runtime over ranks;
   * `fft_m2l` - the M2L as a lattice convolution evaluated by FFT.
 
 It shares no code with the CUDA library and never imports it.  Only the tests, the smoke
