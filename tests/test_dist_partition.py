@@ -47,8 +47,10 @@ def _worker(rank, ws, port, case, out):
 
 @pytest.mark.parametrize("ws", [2, 4])
 @pytest.mark.parametrize("case", ["cube", "sphere"])
-def test_distributed_scheme_equals_single_process(case, ws):
+def test_distributed_scheme_equals_single_process(case, ws, monkeypatch):
     from oracle import kifmm, partition as opart, tree as otree
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):   # one thread per rank
+        monkeypatch.setenv(var, "1")
     out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(ws, _free_port(), case, out), nprocs=ws, join=True)
     x, q, p, depth, dg, dom = _inputs(case)
