@@ -343,8 +343,8 @@ def run_adaptive(points, charges, p, capacity, depth, origin, side, d_global, pi
             for b in range(base[level], base[level + 1]):
                 assert len(il.x.get(b, ())) == 0      # no leaf is coarser than d_global
                 dgl[b] = ops.dc2e[level] @ _adaptive_check(tr, ops, il, b, lv, keys, base, ug, dgl, None, ns)
-        parts = [np.concatenate([dgl[int(base[dg]) + i] for i in range(let["first_root"][r], let["first_root"][r + 1])])
-                 for r in range(P)]
+        parts = [np.concatenate([dgl[int(base[dg]) + i] for i in range(let["first_root"][r], let["first_root"][r + 1])]
+                                + [np.zeros(0)]) for r in range(P)]
     mine = _scatterv(parts, len(roots) * ns).reshape(-1, ns)
     for i, b in enumerate(roots):
         dvec[int(b)] = mine[i]
@@ -355,6 +355,8 @@ def run_adaptive(points, charges, p, capacity, depth, origin, side, d_global, pi
             q_dc = _adaptive_check(tr, ops, il, b, lv, keys, base, u, dvec, (src, surface), ns)
             dvec[b] = ops.dc2e[level] @ q_dc
     # leaf evaluation: D2T, WLI and ULI at the own points
+    if len(roots) == 0:   # a rank that owns no local root (more ranks than occupied roots)
+        return np.zeros(0, np.int64), np.zeros(0), np.zeros((0, 3)), rk
     lo, hi = rng[int(roots[0])][0], rng[int(roots[-1])][1]
     pot, grd = np.zeros(hi - lo), np.zeros((hi - lo, 3))
     for b in own[leaf[own]]:

@@ -5,7 +5,7 @@ it; on one GPU the whole sort is the library's radix sort.
 
 Every rank holds a slice of the input points.  It computes their Morton keys at the leaf depth d
 and at d_global (the local roots' level), draws b of its coarse keys at random, and sends them to
-rank 0.  Rank 0 sorts the P b samples and takes every b-th as one of the P - 1 splitters, which
+rank 0.  Rank 0 sorts the samples and takes the P - 1 splitters at the P-quantiles of them, which
 every rank receives.  A point goes to the bucket (rank) whose splitter range holds its coarse key,
 so all points of one local root land on one rank.  The buckets are exchanged all-to-all and every
 rank sorts its bucket by (leaf key, input index).  Concatenated in rank order the buckets are the
@@ -13,8 +13,10 @@ stable global sort by leaf key.
 
 Readings where the paper is silent:
   * the b samples of a rank are drawn without replacement (all of its keys if it holds fewer);
-  * splitter k (k = 1 .. P - 1) is the (k b)-th smallest sample, and a key equal to a splitter goes
-    to the higher bucket: bucket(key) = number of splitters <= key;
+  * with m samples in all, splitter k (k = 1 .. P - 1) is the sample of 0-based rank floor(k m / P)
+    in ascending order (m = P b when every rank holds at least b points; a rank holding fewer sends
+    all of its keys, and the quantiles then follow the samples actually drawn), and a key equal to a
+    splitter goes to the higher bucket: bucket(key) = number of splitters <= key;
   * ties between equal leaf keys keep the input order (as the single-process sort does).
 """
 from __future__ import annotations
@@ -44,7 +46,7 @@ def samplesort(points, index, depth, d_global, origin, side, b, seed=0):
     if me == 0:
         samples = np.sort(np.concatenate(gathered))
         for k in range(1, P):
-            spl[k - 1] = float(samples[min(k * b, len(samples) - 1)])
+            spl[k - 1] = float(samples[(k * len(samples)) // P]) if len(samples) else 0.0
     if P > 1:
         dist.broadcast(spl, 0)
     splitters = spl.numpy().astype(np.uint64)

@@ -66,3 +66,44 @@ def test_distributed_adaptive_equals_single_process(ws, monkeypatch):
     assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-12
     assert np.linalg.norm(grad - gref) / np.linalg.norm(gref) < 1e-12
     assert all(out[r][3] > 0 and out[r][4] > 0 for r in range(ws))   # every rank exchanged ghosts
+
+
+def _worker_one_root(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        from oracle import distributed
+        x, q = _inputs_one_root()
+        pos, pot, grd, _ = distributed.run_adaptive(x, q, P_ORDER, CAPACITY, DEPTH, *DOMAIN, D_GLOBAL)
+        out[rank] = (pos, pot, grd)
+    finally:
+        dist.destroy_process_group()
+
+
+def _inputs_one_root():
+    # every point inside one level-2 box: a single occupied local root for two ranks
+    from synth import charges, cube_points
+    n = 800
+    return 0.26 + 0.23 * cube_points(n, seed=7).astype(np.float64), charges(n, "u11").astype(np.float64)
+
+
+def test_distributed_adaptive_rank_without_local_roots(monkeypatch):
+    from oracle import adaptive as ad
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.setenv(var, "1")
+    out = mp.get_context("spawn").Manager().dict()
+    mp.spawn(_worker_one_root, args=(2, _free_port(), out), nprocs=2, join=True)
+    x, q = _inputs_one_root()
+    assert min(len(out[r][0]) for r in range(2)) == 0       # one rank owns nothing
+    tr = ad.build_tree(x, CAPACITY, DEPTH, *DOMAIN, min_level=D_GLOBAL)
+    n = len(x)
+    phi_s, grad_s = np.full(n, np.nan), np.full((n, 3), np.nan)
+    for r in range(2):
+        pos, pot, grd = out[r]
+        phi_s[pos], grad_s[pos] = pot, grd
+    assert not np.isnan(phi_s).any()
+    phi, grad = np.empty(n), np.empty((n, 3))
+    phi[tr.perm], grad[tr.perm] = phi_s, grad_s
+    ref, gref, _, _ = ad.evaluate(x, q, P_ORDER, CAPACITY, DEPTH, *DOMAIN, min_level=D_GLOBAL)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-12
+    assert np.linalg.norm(grad - gref) / np.linalg.norm(gref) < 1e-12

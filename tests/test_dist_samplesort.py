@@ -82,3 +82,33 @@ def test_balance_improves_with_the_sample_size(monkeypatch):
         dev[b] = np.mean([max(abs(len(res[r][(b, s)][0]) - n / ws) for r in range(ws)) / (n / ws) for s in seeds])
     assert dev[512] < dev[8] / 2.5, dev
     assert dev[512] < 0.05, dev
+
+
+def _worker_uneven(rank, ws, port, n, b, out):
+    # rank 0 holds 10 points, fewer than the b samples it is asked for: it sends all of them
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        from oracle import samplesort
+        x, dom = _points("cube", n)
+        cuts = [0, 10] + [10 + (n - 10) * k // (ws - 1) for k in range(2, ws)] + [n]
+        lo, hi = cuts[rank], cuts[rank + 1]
+        idx, keys, _, _ = samplesort.samplesort(x[lo:hi], np.arange(lo, hi), DEPTH, D_GLOBAL, *dom, b, 0)
+        out[rank] = (idx, keys)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_rank_with_fewer_points_than_samples(monkeypatch):
+    from oracle import tree as otree
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.setenv(var, "1")
+    ws, n, b = 4, 40_000, 512
+    out = mp.get_context("spawn").Manager().dict()
+    mp.spawn(_worker_uneven, args=(ws, _free_port(), n, b, out), nprocs=ws, join=True)
+    x, dom = _points("cube", n)
+    tr = otree.build_tree(x, DEPTH, *dom)
+    np.testing.assert_array_equal(np.concatenate([out[r][0] for r in range(ws)]), tr.perm)
+    # splitters at the quantiles of the samples actually drawn keep the buckets near n / ws
+    sizes = [len(out[r][0]) for r in range(ws)]
+    assert max(abs(s - n / ws) for s in sizes) / (n / ws) < 0.15, sizes
