@@ -360,14 +360,17 @@ fmm_status fmm_sync(fmm_ctx *ctx);
  * sort by key) on caller-owned device arrays:
  *   xyz[n x 3]  float coordinates (device);  perm[n]  receives the input index of each sorted
  *   position;  keys[n]  receives the sorted Morton keys (x bit most significant per triple).
- * Its scratch is a file-scope device array of 8,651,008 bytes (every GPU that loads the library
+ * Its scratch is a file-scope device array of 8,651,012 bytes (every GPU that loads the library
  * holds it until the process exits), so n is limited to 1,048,576: larger n, n <= 0, a
  * depth outside 0..10, a non-positive side or a non-finite origin return FMM_EINVAL.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call shares the array: calls that
- * overlap on the GPU (different streams, or different threads on one device) race and must be
- * serialised by the caller.  Work is enqueued on `cuda_stream`; the call returns without
- * waiting.  FMM_ECUDA reports a CUDA failure. */
+ * A non-finite coordinate also returns FMM_EINVAL, as in fmm_build_tree; perm and keys are
+ * then written but meaningless.
+ * The first call on a device (and the first after a device reset) looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream capture.  Every
+ * call shares the array: calls that overlap on the GPU (different streams, or different threads
+ * on one device) race and must be serialised by the caller.  Work is enqueued on `cuda_stream`,
+ * and the call waits for that stream once at the end to read the non-finite flag back.
+ * FMM_ECUDA reports a CUDA failure. */
 fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int depth, const double origin[3],
                                    double side, int32_t *perm, uint32_t *keys, void *cuda_stream);
 

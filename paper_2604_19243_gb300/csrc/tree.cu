@@ -875,29 +875,55 @@ constexpr int64_t kNoAllocMaxPoints = 1 << 20;
 constexpr int64_t kNoAllocTiles = (kNoAllocMaxPoints + kSortTile - 1) / kSortTile;   // radix tiles
 constexpr int64_t kNoAllocHist = 256 * kNoAllocTiles;                                // digit counts
 constexpr int64_t kNoAllocSums = (kNoAllocHist + kScanBlock - 1) / kScanBlock;      // scan blocks
-constexpr size_t kNoAllocBytes =
-    (size_t)kNoAllocMaxPoints * (sizeof(uint32_t) + sizeof(int)) + (size_t)(kNoAllocHist + kNoAllocSums) * sizeof(int);
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxPoints * (sizeof(uint32_t) + sizeof(int)) +
+                                 (size_t)(kNoAllocHist + kNoAllocSums + 1) * sizeof(int);
 
-// keys copy | values copy | digit counts | scan block sums.  Every pass overwrites the part it
-// reads, so nothing has to be cleared between calls.
+// keys copy | values copy | digit counts | scan block sums | non-finite flag.  Every pass
+// overwrites the part it reads; only the flag is cleared at the start of every call.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char *g_noalloc_addr[kMaxDevices] = {};
+struct NoAllocAddr {
+    void *ctx;               // the context the address was taken in
+    unsigned char *addr;
+};
+NoAllocAddr g_noalloc_addr[kMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
-// Device address of the scratch array on the current device (looked up once per device).
+// The calling thread's current context (driver handle), or null.
+void *current_context() {
+    using GetCurrent = int (*)(void **);
+    static GetCurrent fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (GetCurrent)f;
+    }();
+    void *c = nullptr;
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
+
+// Device address of the scratch array on the current device.  It is looked up once per device
+// and context: after a device reset the runtime makes a new primary context, in which the array
+// has a new address, so a cached address is used only while the context it was taken in is
+// still the current one.
 cudaError_t noalloc_scratch(unsigned char **out) {
     int dev = 0;
     FMM_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocAddr &e = g_noalloc_addr[dev];
+    void *cur = current_context();
+    if (!e.addr || !cur || e.ctx != cur) {
         void *p = nullptr;
-        FMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = (unsigned char *)p;
+        FMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));   // makes the primary context current
+        e.addr = (unsigned char *)p;
+        e.ctx = current_context();
     }
-    *out = g_noalloc_addr[dev];
+    *out = e.addr;
     return cudaSuccess;
 }
 
@@ -937,9 +963,14 @@ extern "C" fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int d
     int *v2 = (int *)(base + (size_t)kNoAllocMaxPoints * sizeof(uint32_t));
     int *hist = v2 + kNoAllocMaxPoints;
     int *sums = hist + kNoAllocHist;
+    int *bad = sums + kNoAllocSums;   // set by the key kernel on a non-finite coordinate
     const double scale = std::ldexp(1.0, depth) / side;
+    if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return FMM_ECUDA;
+    }
     morton_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, origin[0], origin[1], origin[2], scale, depth,
-                                                           keys, perm, nullptr, (float)origin[0], (float)origin[1],
+                                                           keys, perm, bad, (float)origin[0], (float)origin[1],
                                                            (float)origin[2], (float)scale);
     count_launch();
     // stable LSD radix sort of (keys, perm), 8-bit digits, ping-ponging with the scratch copies
@@ -961,6 +992,13 @@ extern "C" fmm_status fmm_sort_points_noalloc(const float *xyz, int64_t n, int d
             return FMM_ECUDA;
         }
     }
+    // the non-finite flag, read back as fmm_build_tree reads its counts (one wait on the stream)
+    int h_bad = 0;
+    if (cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FMM_ECUDA;
+    }
     if (cudaGetLastError() != cudaSuccess) return FMM_ECUDA;
-    return FMM_OK;
+    return h_bad ? FMM_EINVAL : FMM_OK;
 }

@@ -40,9 +40,13 @@ def _reference(x, depth, origin, side):
 
 
 def test_noalloc_sort_matches_build_tree_twice():
-    # two calls in a row with different inputs: the shared scratch must not leak between them
+    # calls in a row with different inputs: the shared scratch must not leak between them, a
+    # small call after the largest one included, and depth 0, where no radix pass runs and the
+    # keys never leave the caller's buffer
     cases = [(sphere_points(300_007, seed=21), 7, (-1.0, -1.0, -1.0), 2.0),
-             (cube_points(MAX_POINTS, seed=22), 6, (0.0, 0.0, 0.0), 1.0)]
+             (cube_points(MAX_POINTS, seed=22), 6, (0.0, 0.0, 0.0), 1.0),
+             (sphere_points(5_003, seed=23), 5, (-1.0, -1.0, -1.0), 2.0),
+             (cube_points(1_000, seed=24), 0, (0.0, 0.0, 0.0), 1.0)]
     for xs, depth, origin, side in cases:
         x = torch.from_numpy(xs).cuda()
         st, perm, keys = _noalloc(x, depth, origin, side)
@@ -58,3 +62,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert st == 1   # FMM_EINVAL
     st, _, _ = _noalloc(x[:10], 11, (0.0, 0.0, 0.0), 1.0)
     assert st == 1
+
+
+def test_noalloc_rejects_non_finite_coordinates():
+    # as fmm_build_tree does; the call after it must sort normally again
+    for bad in (float("nan"), float("inf")):
+        xs = cube_points(4_096, seed=25)
+        xs[1234, 1] = bad
+        st, _, _ = _noalloc(torch.from_numpy(xs).cuda(), 5, (0.0, 0.0, 0.0), 1.0)
+        assert st == 1   # FMM_EINVAL
+    x = torch.from_numpy(cube_points(4_096, seed=26)).cuda()
+    st, perm, keys = _noalloc(x, 5, (0.0, 0.0, 0.0), 1.0)
+    assert st == 0
+    rperm, rkeys = _reference(x, 5, (0.0, 0.0, 0.0), 1.0)
+    np.testing.assert_array_equal(perm, rperm)
+    np.testing.assert_array_equal(keys, rkeys)
