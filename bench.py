@@ -10,8 +10,10 @@ region starts; L2 (129 MB) is flushed between steps by writing a 256 MB buffer o
 timed events.  `e2e` repeats the step through the same C entry points with pinned host
 buffers, host<->device copies included.
 
-Default: 1 GPU, 3 warm-up steps, 10 timed steps, then the FP64 CPU oracle on a bounded sample
-(the cpu_baseline leg).  `--impl reference` times only that oracle (the reference arm).
+Default: 1 GPU, 3 warm-up steps, 30 timed steps, then the FP64 CPU oracle once on the whole
+workload (the cpu_baseline leg, whose field at every point is also the reference of the
+all-points accuracy).  `--impl reference` times only the oracle (the reference arm), each step on
+the workload's points in one octant of its bounding cube, a bounded sample of the same workload.
 Under torchrun with N > 1 every rank runs an independent replica (the path has no exchange
 step on one GPU per process); value = all ranks' points / the slowest rank's time.
 `--kernel yukawa --kappa K` runs the same workload and step with the modified Helmholtz kernel
@@ -46,8 +48,6 @@ FLOPS_PER_PAIR_YUKAWA = FLOPS_PER_PAIR + 7
 # (one flop each), the complex product w = q e^{ikr} / r (8), the potential (2), the gradient
 # factor w (ikr - 1) / r^2 (7) and the six gradient components (12)
 FLOPS_PER_PAIR_HELMHOLTZ = 42
-SAMPLE_N = 2_097_152         # CPU sample: same sphere distribution, depth 6 -> ~112 points/leaf
-SAMPLE_DEPTH = 6
 
 
 def read_peaks():
@@ -156,25 +156,50 @@ def complex_charges(n, seed=1):
     return charges(n, "u01", seed=seed) + 1j * charges(n, "u01", seed=seed + 100)
 
 
-def cpu_baseline_sample(p, kappa=0.0, wavenumber=0.0):
-    """The FP64 oracle kiFMM on a bounded sample of the same workload family."""
+def oracle_inputs(w, helm):
+    x = w.points().astype(np.float64)
+    q = complex_charges(w.n) if helm else w.charges().astype(np.float64)
+    return x, q
+
+
+def cpu_baseline_full(w, kappa=0.0, wavenumber=0.0):
+    """The FP64 oracle kiFMM on the whole workload (the cpu_baseline leg), timed on the host
+    cores; its field at every point is also the reference of the all-points accuracy check."""
     from oracle import direct, kifmm
-    x = sphere_points(SAMPLE_N)
-    q = complex_charges(SAMPLE_N) if wavenumber > 0 else charges(SAMPLE_N, "u01").astype(np.float64)
+    x, q = oracle_inputs(w, wavenumber > 0)
     t0 = time.perf_counter()
-    kifmm.evaluate(x.astype(np.float64), q, p, SAMPLE_DEPTH, (-1, -1, -1), 2.0,
-                   pinv_rtol=1e-7, gradient=True, kappa=kappa, wavenumber=wavenumber)
+    r = kifmm.evaluate(x, q, w.p, w.depth, w.origin, w.side, pinv_rtol=1e-7, gradient=True,
+                       kappa=kappa, wavenumber=wavenumber)
     dt = time.perf_counter() - t0
     kern = (f"modified Helmholtz kappa={kappa:g}, " if kappa > 0 else
             f"Helmholtz k={wavenumber:g}, complex densities, " if wavenumber > 0 else "")
-    return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": direct.num_threads(),
+    info = {"value": w.n / dt, "unit": UNIT, "cores": direct.num_threads(),
             "host_cpus": os.cpu_count(), "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"FP64 oracle kiFMM ({kern}p={p}, potentials+gradients, tree and operators "
-                      f"included) on {SAMPLE_N:,} points of the same unit-sphere distribution at "
-                      f"depth {SAMPLE_DEPTH} (~112 points per leaf, as in the full workload)"}
+            "sample": f"the whole workload: FP64 oracle kiFMM ({kern}p={w.p}, depth {w.depth}, "
+                      f"potentials+gradients at all {w.n:,} points, tree and operators included)"}
+    return info, r.phi, r.grad
 
 
-def accuracy_check(w, x, q, phi, grad, m=256, kappa=0.0, wavenumber=0.0):
+def octant_sample(w):
+    """A bounded sample of the workload for the reference arm's steps: its points in the first
+    octant of the bounding cube (a leaf-aligned sub-cube, so every sampled leaf keeps the full
+    workload's points and density), as an FMM problem of its own on the same domain and depth."""
+    x = w.points()
+    half = [o + 0.5 * w.side for o in w.origin]
+    keep = (x[:, 0] < half[0]) & (x[:, 1] < half[1]) & (x[:, 2] < half[2])
+    return keep
+
+
+def cpu_reference_step(w, keep, kappa=0.0, wavenumber=0.0):
+    from oracle import kifmm
+    x, q = oracle_inputs(w, wavenumber > 0)
+    t0 = time.perf_counter()
+    kifmm.evaluate(x[keep], q[keep], w.p, w.depth, w.origin, w.side, pinv_rtol=1e-7, gradient=True,
+                   kappa=kappa, wavenumber=wavenumber)
+    return time.perf_counter() - t0
+
+
+def accuracy_check(w, x, q, phi, grad, m=4096, kappa=0.0, wavenumber=0.0):
     """Relative L2 error of the GPU result at m sampled targets against the FP64 direct sum
     (phi None: gradient only)."""
     from oracle import direct
@@ -192,21 +217,24 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import direct
+    keep = octant_sample(w)
+    m = int(keep.sum())
     times = []
-    info = None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline_sample(w.p, *kernel_params(args))
+        dt = cpu_reference_step(w, keep, *kernel_params(args))
         if i >= args.warmup:
-            times.append(info["seconds"])
+            times.append(dt)
     mean_s = sum(times) / len(times)
-    value = SAMPLE_N / mean_s
+    value = m / mean_s
+    sample = (f"FP64 oracle kiFMM (p={w.p}, depth {w.depth}, potentials+gradients, tree and operators "
+              f"included) on the {m:,} points of the workload in the first octant of its bounding cube "
+              f"(a leaf-aligned sub-cube: the workload's own leaves and density), per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "p": w.p,
-                                            "depth": w.depth, "dist": w.dist, "kernel": args.kernel,
-                                            **kernel_config(args)},
-            "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
+            "data": "synthetic", "config": run_config(args, w, ws),
+            "cpu_baseline": {"kind": "oracle", "cores": direct.num_threads(), "sample": sample,
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -383,6 +411,15 @@ def measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream, s
     except Exception as e:   # noqa: BLE001
         out["adaptive_q64_fp32"] = {"error": str(e)}
     return out
+
+
+def run_config(args, w, ws):
+    """The workload and step of a run; both arms report the same dict."""
+    return {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
+            "precision": args.precision, "kernel": args.kernel, **kernel_config(args),
+            "l2": "flushed (256 MB write) between steps",
+            "step": f"build_tree + evaluate({args.outputs})", "outputs": args.outputs,
+            "parallelism": f"replicas x{ws}"}
 
 
 def kernel_params(args):
@@ -645,12 +682,7 @@ def main():
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
-            "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
-                       "precision": args.precision, "kernel": args.kernel, **kernel_config(args),
-                       "l2": "flushed (256 MB write) between steps",
-                       "step": f"build_tree + evaluate({args.outputs})", "outputs": args.outputs,
-                       "parallelism": f"replicas x{ws}"},
+            "data": "synthetic", "config": run_config(args, w, ws),
             "phases_ms": {"near_p2p": near_ms, "upward": up_ms, "m2l": m2l_ms,
                           "downward": down_ms,
                           "evaluate_total": statistics.median(p["total"] for p in phases),
@@ -665,14 +697,22 @@ def main():
             fmm.evaluate_into(q, None, grad)
             torch.cuda.synchronize()
         odt = np.complex128 if helm else np.float64
-        line["accuracy"] = accuracy_check(w, x_np, q_np, None if grad_only else phi.cpu().numpy().astype(odt),
-                                          grad.cpu().numpy().astype(odt), kappa=kernel_params(args)[0],
-                                          wavenumber=kernel_params(args)[1])
+        phi_h = None if grad_only else phi.cpu().numpy().astype(odt)
+        grad_h = grad.cpu().numpy().astype(odt)
+        line["accuracy"] = {"direct_sum": accuracy_check(w, x_np, q_np, phi_h, grad_h,
+                                                         kappa=kernel_params(args)[0],
+                                                         wavenumber=kernel_params(args)[1])}
     if (not args.no_variants and ws == 1 and args.kernel == "laplace" and args.outputs == "potential+gradient"
             and w.name == "sphere8m_p6_d7"):
         line["variants"] = measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(w.p, *kernel_params(args))
+        # the oracle on the whole workload: the timed CPU baseline, and the reference of the
+        # all-points accuracy (relative L2 over every point against the FP64 kiFMM at the same p)
+        line["cpu_baseline"], o_phi, o_grad = cpu_baseline_full(w, *kernel_params(args))
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        line["accuracy"]["oracle_kifmm"] = {
+            "phi": None if grad_only else rel(phi_h, o_phi), "grad": rel(grad_h, o_grad), "targets": w.n,
+            "reference": f"FP64 CPU kiFMM (the oracle) at the same p = {w.p} and depth, every point"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     fmm.close()

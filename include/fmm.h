@@ -30,6 +30,7 @@
 #ifndef FMM_H
 #define FMM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -351,6 +352,23 @@ fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n);
  * kernel then skipped its remaining work, so the outputs of those calls are invalid); FMM_ECUDA
  * for a CUDA error.  Calls with host pointers already synchronize but do not read the flag. */
 fmm_status fmm_sync(fmm_ctx *ctx);
+
+/* Failure injection for tests and deployment checks (no counterpart in the paper).
+ *
+ * fmm_set_wait_limit: the bound on every barrier wait of ctx's tensor-core kernels (default 1 s;
+ * seconds in [0, 60], else EINVAL).  A wait that exceeds it makes the kernel record FMM_ETIMEOUT,
+ * stop issuing copies and MMAs, wait for the copies and MMAs it already issued, free its tensor
+ * memory and return; fmm_sync then reports FMM_ETIMEOUT and the outputs of that call are
+ * invalid.  0 gives up at the first wait that does not complete at once, which forces the
+ * failure path; the context stays usable and later calls with a normal limit are correct.
+ *
+ * fmm_set_alloc_limit: process-wide cap on any single device allocation the library makes
+ * (SIZE_MAX, the default, is no cap).  A larger request fails as out of memory: the call that
+ * needed it returns FMM_ENOMEM (fmm_build_tree leaves the context without a tree, fmm_precompute
+ * without operators) and frees what it had allocated, so the same call succeeds once the cap is
+ * lifted. */
+fmm_status fmm_set_wait_limit(fmm_ctx *ctx, double seconds);
+void fmm_set_alloc_limit(size_t bytes);
 
 /* Morton keys and stable sort of n points, allocating nothing.  The paper has no counterpart:
  * this entry point is for callers that cannot let a library allocate device memory, because

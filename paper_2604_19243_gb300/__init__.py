@@ -39,7 +39,7 @@ ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_prec
                 "fmm_measure_fp32_peak", "fmm_partition_setup", "fmm_partition_evaluate",
                 "fmm_partition_info", "fmm_partition_export", "fmm_partition_timings",
                 "fmm_adaptive_setup", "fmm_adaptive_info", "fmm_adaptive_export", "fmm_adaptive_evaluate",
-                "fmm_last_error", "fmm_destroy")
+                "fmm_set_wait_limit", "fmm_set_alloc_limit", "fmm_last_error", "fmm_destroy")
 
 
 class Options(ctypes.Structure):
@@ -134,6 +134,10 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        L.fmm_set_wait_limit.argtypes = [vp, ctypes.c_double]
+        L.fmm_set_wait_limit.restype = ctypes.c_int
+        L.fmm_set_alloc_limit.argtypes = [ctypes.c_size_t]
+        L.fmm_set_alloc_limit.restype = None
         L.fmm_kernel_launches.argtypes = []
         L.fmm_kernel_launches.restype = ctypes.c_longlong
         L.fmm_last_error.argtypes = [vp]
@@ -158,6 +162,12 @@ def _ptr(a):
 def kernel_launches():
     """Kernels launched by libfmm in this process so far."""
     return int(lib().fmm_kernel_launches())
+
+
+def set_alloc_limit(nbytes=None):
+    """Process-wide cap on any single device allocation of the library (None: no cap); a larger
+    request makes the call that needed it fail with FMM_ENOMEM (failure injection)."""
+    lib().fmm_set_alloc_limit(ctypes.c_size_t(-1).value if nbytes is None else int(nbytes))
 
 
 def measure_fp32_peak(iters=2048):
@@ -405,6 +415,11 @@ class FMM:
     def adaptive_evaluate_into(self, q, phi, grad=None, parts=PART_ALL):
         """fmm_adaptive_evaluate on caller-owned arrays; phi may be None when grad is given."""
         self._check(lib().fmm_adaptive_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+
+    def set_wait_limit(self, seconds):
+        """Bound on the tensor-core kernels' barrier waits (default 1 s; 0 forces the timeout path)."""
+        self._check(lib().fmm_set_wait_limit(self._ctx, float(seconds)))
+        return self
 
     def timings(self):
         """Milliseconds of the last evaluate/adjoint: near, upward, m2l, downward, total."""

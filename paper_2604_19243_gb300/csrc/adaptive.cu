@@ -454,10 +454,10 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     cudaStream_t s = ctx->stream;
     const int D = ctx->opt.depth;
     const int64_t rows = A->rows;
-    FMM_CUDA_TRY(cudaMalloc(&A->count, rows * sizeof(int)));
-    FMM_CUDA_TRY(cudaMalloc(&A->begin, rows * sizeof(int)));
-    FMM_CUDA_TRY(cudaMalloc(&A->state, rows * sizeof(int)));
-    for (int k = 0; k < 4; ++k) FMM_CUDA_TRY(cudaMalloc(&A->off[k], (rows + 1) * sizeof(int)));
+    FMM_CUDA_TRY(dev_malloc(&A->count, rows * sizeof(int)));
+    FMM_CUDA_TRY(dev_malloc(&A->begin, rows * sizeof(int)));
+    FMM_CUDA_TRY(dev_malloc(&A->state, rows * sizeof(int)));
+    for (int k = 0; k < 4; ++k) FMM_CUDA_TRY(dev_malloc(&A->off[k], (rows + 1) * sizeof(int)));
     Scratch<int> flag;
     FMM_CUDA_TRY(flag.alloc(1, s));
     FMM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
@@ -495,7 +495,7 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     for (int k = 0; k < 3; ++k) {
         A->entries[k] = tot[k];
-        FMM_CUDA_TRY(cudaMalloc(&A->idx[k], std::max(tot[k], 1) * sizeof(int)));
+        FMM_CUDA_TRY(dev_malloc(&A->idx[k], std::max(tot[k], 1) * sizeof(int)));
     }
     lists_kernel<true><<<g, 128, 0, s>>>(L, (int)rows, A->state, A->off[0], A->idx[0], A->off[1], A->idx[1],
                                          A->off[2], A->idx[2], flag.p);
@@ -508,7 +508,7 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     FMM_CUDA_TRY(cudaGetLastError());
     FMM_CUDA_TRY(exclusive_scan<int>(A->off[3], rows, A->off[3] + rows, s));
     A->entries[3] = A->entries[2];
-    FMM_CUDA_TRY(cudaMalloc(&A->idx[3], std::max<int64_t>(A->entries[3], 1) * sizeof(int)));
+    FMM_CUDA_TRY(dev_malloc(&A->idx[3], std::max<int64_t>(A->entries[3], 1) * sizeof(int)));
     Scratch<int> cursor;
     FMM_CUDA_TRY(cursor.alloc(rows, s));
     FMM_CUDA_TRY(cudaMemcpyAsync(cursor.p, A->off[3], rows * sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -521,7 +521,7 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
     for (int l = 2; l <= D; ++l) {
         const LevelTables &T = ctx->lev[l];
         const size_t sz = (size_t)1 << (3 * l);
-        FMM_CUDA_TRY(cudaMalloc(&A->dense_kept[l], sz * sizeof(int)));
+        FMM_CUDA_TRY(dev_malloc(&A->dense_kept[l], sz * sizeof(int)));
         FMM_CUDA_TRY(cudaMemcpyAsync(A->dense_kept[l], T.dense, sz * sizeof(int), cudaMemcpyDeviceToDevice, s));
         mask_dense_kernel<<<grid_for(T.n, 256), 256, 0, s>>>(T.keys, (int)T.n, A->state + T.row_base, A->dense_kept[l]);
         count_launch();
@@ -719,7 +719,7 @@ fmm_status adaptive_prepare(fmm_ctx *ctx) {
         if (*have >= need) return true;
         cudaFree(*p);
         *p = nullptr, *have = 0;
-        if (cudaMalloc(p, need) != cudaSuccess) {
+        if (dev_malloc(p, need) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }

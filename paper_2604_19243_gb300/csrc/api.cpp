@@ -20,9 +20,16 @@ namespace fmm {
 namespace {
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64] = {};
+std::atomic<size_t> g_alloc_cap{SIZE_MAX};   // fmm_set_alloc_limit
 }  // namespace
 
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (bytes > g_alloc_cap.load()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    if (bytes > g_alloc_cap.load()) return cudaErrorMemoryAllocation;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -69,8 +76,8 @@ fmm_status fail(fmm_ctx *ctx, fmm_status st, const std::string &msg) {
 
 fmm_status cuda_fail(fmm_ctx *ctx, cudaError_t e, const char *where) {
     cudaGetLastError();   // clear a non-sticky error
-    return fail(ctx, FMM_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
-                                    cudaGetErrorString(e) + ")");
+    return fail(ctx, e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA,
+                std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
 bool is_device_ptr(const void *p) {
@@ -507,7 +514,7 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
         ctx->host_ops[l] = lap ? hs[0] : hs[std::min(std::max(l, lo), d) - lo];
     cudaError_t e;
     if (!ctx->dev_flag) {
-        if (cudaMalloc((void **)&ctx->dev_flag, sizeof(int)) != cudaSuccess) {
+        if (dev_malloc((void **)&ctx->dev_flag, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, FMM_ENOMEM, "flag allocation failed");
         }
@@ -790,6 +797,15 @@ fmm_status fmm_last_timings(fmm_ctx *ctx, double *ms, int n) {
 }
 
 long long fmm_kernel_launches(void) { return launches(); }
+
+fmm_status fmm_set_wait_limit(fmm_ctx *ctx, double seconds) {
+    if (!ctx) return FMM_EINVAL;
+    if (!(seconds >= 0) || !(seconds <= 60)) return fail(ctx, FMM_EINVAL, "wait limit must be in [0, 60] s");
+    ctx->tc_wait_ns = (unsigned long long)(seconds * 1e9);
+    return FMM_OK;
+}
+
+void fmm_set_alloc_limit(size_t bytes) { g_alloc_cap.store(bytes); }
 
 const char *fmm_last_error(const fmm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 

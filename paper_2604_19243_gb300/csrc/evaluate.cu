@@ -312,7 +312,7 @@ cudaError_t upload_padded(fmm_ctx *ctx, const std::vector<double> &w, int rows, 
                 h[(size_t)m * rows_p * cols_p + (size_t)i * cols_p + j] =
                     (T)w[(size_t)m * rows * cols + (size_t)i * cols + j];
     void *p = nullptr;
-    FMM_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(T)));
+    FMM_CUDA_TRY(dev_malloc(&p, h.size() * sizeof(T)));
     ctx->op_allocs.push_back(p);
     FMM_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     *out = p;
@@ -376,7 +376,7 @@ cudaError_t upload_operators(fmm_ctx *ctx) {
     // unit surface grid in the storage type
     std::vector<double> g = surface_grid(ctx->opt.order_p);
     size_t bytes = g.size() * (ctx->fp64 ? sizeof(double) : sizeof(float));
-    FMM_CUDA_TRY(cudaMalloc(&ctx->grid_dev, bytes));
+    FMM_CUDA_TRY(dev_malloc(&ctx->grid_dev, bytes));
     ctx->op_allocs.push_back(ctx->grid_dev);
     if (ctx->fp64) {
         FMM_CUDA_TRY(cudaMemcpy(ctx->grid_dev, g.data(), bytes, cudaMemcpyHostToDevice));

@@ -92,6 +92,12 @@ struct Tile {
 // Stream-ordered allocation from the library's per-device pool (memory is kept cached for
 // reuse); freed with cudaFreeAsync.  pool_trim returns the unused memory to the driver.
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+// cudaMalloc under the process-wide cap of fmm_set_alloc_limit (the library's other allocations)
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
 void pool_trim();
 
 struct LevelTables {
@@ -206,6 +212,7 @@ struct fmm_ctx {
     cudaEvent_t ev[8] = {};
     float last_ms[5] = {};
     int *dev_flag = nullptr;    // device error flag (bounded waits, bounds checks)
+    unsigned long long tc_wait_ns = 1000000000ull;   // bound on the tensor-core kernels' barrier waits
 };
 
 namespace fmm {

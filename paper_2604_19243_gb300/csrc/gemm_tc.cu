@@ -62,6 +62,7 @@ struct TcDev {
     int ncta;                       // output columns per CTA (grid.y splits wider N)
     int tmem_cols;
     int *err;                       // device error flag
+    unsigned long long wait_ns;     // bound on every pipeline barrier wait (default 1 s)
     int a_planes;                   // A rows arrive pre-split from xp (cp.async copies)
     const unsigned char *xp;        // split planes of the A rows
     long long xp_plane;             // bytes between planes
@@ -118,8 +119,10 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait until the barrier's phase with the given parity has completed; false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait until the barrier's phase with the given parity has completed; false once limit_ns of
+// %globaltimer have passed (checked every 256 polls; a limit of 0 gives up at the first poll
+// that finds the phase incomplete).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     const uint32_t a = smem_u32(bar);
     uint32_t done = 0;
     uint64_t t0 = 0;
@@ -130,8 +133,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (limit_ns == 0) return false;
         if (it == 0) t0 = global_ns();
-        else if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
+        else if ((it & 255) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -157,6 +161,9 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_b
 __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+
+// wait for all of this thread's cp.async copies (the hardware tracks them; no polling)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -244,6 +251,15 @@ __device__ __forceinline__ uint32_t tf32_round(float x) {
     return r & 0xffffe000u;   // keep the 10 explicit mantissa bits only
 }
 
+// Teardown: wait (at most 1 s each) until the operator copies this thread started have landed,
+// so that no copy is still writing into shared memory when the CTA exits, also after an abort.
+__device__ __forceinline__ bool wait_bulk_copies(uint64_t *bulk_bar, const int *started, int nstages) {
+    bool ok = true;
+    for (int s = 0; s < nstages; ++s)
+        if (started[s] > 0) ok = mbar_wait(&bulk_bar[s], (uint32_t)(started[s] - 1) & 1u, kWaitNs) && ok;
+    return ok;
+}
+
 // ---------------------------------------------------------------- work list helpers
 struct SegInfo {
     const float *X;
@@ -314,7 +330,9 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
     constexpr int DC = PL ? kTcMaxN / 2 : kTcMaxN;   // columns a drain thread holds
     constexpr int NDRAIN = PL ? 8 : 4;               // drain warps
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t full_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2];
+    // full: the producers' A rows of a stage; bulk: its operator copy; empty: the stage's MMAs
+    // done; tfull / tempty: an accumulator's MMAs done / drained; fin: every MMA of the CTA done
+    __shared__ uint64_t full_bar[4], bulk_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2], fin_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int box[kTcRows];
     __shared__ int srcs[2][kTcRows];
@@ -338,11 +356,12 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
 
     if (tid == 0) {
         for (int s = 0; s < p.nstages; ++s) {
-            // register gather: 4 producer warps + the B copy's expect_tx arrive;
-            // plane copies: 96 cp.async arrivals (3 producer warps) + the B copy's expect_tx arrive
-            mbar_init(&full_bar[s], p.a_planes ? kPlaneProducers + 1 : 4 + 1);
+            // register gather: 4 producer warps; plane copies: 96 cp.async arrivals (3 producer warps)
+            mbar_init(&full_bar[s], p.a_planes ? kPlaneProducers : 4);
+            mbar_init(&bulk_bar[s], 1);       // thread 0's expect_tx arrive, then the copy's bytes
             mbar_init(&empty_bar[s], 1);      // tcgen05.commit
         }
+        mbar_init(&fin_bar, 1);               // tcgen05.commit after the last MMA
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull_bar[b], 1);      // tcgen05.commit
             mbar_init(&tempty_bar[b], NDRAIN);   // the accumulator warps
@@ -413,6 +432,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
         // The source row of the next active segment is looked up while the current one is copied.
         // Three warps (96 threads) cover the 128 rows: thread i looks up rows i and i + 96.
         int item = 0, sidx = 0;
+        int bulk_started[4] = {0, 0, 0, 0};   // operator copies thread 0 started per stage
         bool ok = true;
         const bool two = tid + kPlaneProducers < kTcRows;
         const RowRef me = row_ref(g, box[tid]);
@@ -453,7 +473,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             for (int c = 0; c < si.nchunks; ++c, ++item) {
                 const int stage = item % p.nstages;
                 if (!ok) continue;
-                if ((item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1)) ||
+                if ((item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1, p.wait_ns)) ||
                     *(volatile int *)&abort_flag) {
                     ok = false;
                     continue;
@@ -461,16 +481,17 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                 unsigned char *sa = base + (size_t)stage * stage_bytes;
                 unsigned char *sb = sa + p.nplanes * a_plane_bytes;
                 if (tid == 0) {
-                    mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    mbar_arrive_tx(&bulk_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    ++bulk_started[stage];
                     const size_t plane_full = (size_t)g.n_out * kAtomBytes;
                     if ((size_t)b_plane_bytes == plane_full)   // the chunk's planes are contiguous: one copy
                         bulk_g2s(sb, si.Wt + (size_t)c * p.nplanes * plane_full,
-                                 (uint32_t)(p.nplanes * b_plane_bytes), &full_bar[stage]);
+                                 (uint32_t)(p.nplanes * b_plane_bytes), &bulk_bar[stage]);
                     else
                         for (int pl = 0; pl < p.nplanes; ++pl)
                             bulk_g2s(sb + pl * b_plane_bytes,
                                      si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
-                                     (uint32_t)b_plane_bytes, &full_bar[stage]);
+                                     (uint32_t)b_plane_bytes, &bulk_bar[stage]);
                 }
                 const int k0 = c * chunk_elems;
                 const int kval = min(chunk_elems, si.K - k0);
@@ -519,6 +540,9 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             atomicExch(p.err, FMM_ETIMEOUT);
             *(volatile int *)&abort_flag = 1;
         }
+        // nothing of this thread's may still be in flight when the CTA exits
+        cp_async_wait_all();
+        if (tid == 0 && !wait_bulk_copies(bulk_bar, bulk_started, p.nstages)) atomicExch(p.err, FMM_ETIMEOUT);
     } else if (warp == 3 && p.a_planes) {
         // ------------------------------------------------------------ MMA issuer (plane mode)
         // A warp of its own issues the MMAs, so the tensor pipe runs while the accumulator
@@ -531,8 +555,9 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
             for (int item = 0; item < n_items; ++item) {
                 const int stage = item % p.nstages, b = item & 1;
-                if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1) ||
-                    (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1)) ||
+                if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
+                    !mbar_wait(&bulk_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
+                    (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1, p.wait_ns)) ||
                     *(volatile int *)&abort_flag) {
                     ok = false;
                     break;
@@ -549,10 +574,14 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                 atomicExch(p.err, FMM_ETIMEOUT);
                 *(volatile int *)&abort_flag = 1;
             }
+            // every MMA issued (also before an abort) completes before the tensor memory is freed
+            mma_commit(&fin_bar);
+            if (!mbar_wait(&fin_bar, 0, kWaitNs)) atomicExch(p.err, FMM_ETIMEOUT);
         }
     } else if (!PL && warp < 4) {
         // ------------------------------------------------------------ producers
         int item = 0;
+        int bulk_started[4] = {0, 0, 0, 0};   // operator copies thread 0 started per stage
         bool ok = true;
         const RowRef me = row_ref(g, box[tid]);
         int seg0 = 0;
@@ -568,7 +597,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             src_next = seg2 < nseg ? src_fast(g, t, tt, me, seg2) : -1;
             for (int c = 0; c < si.nchunks; ++c, ++item) {
                 const int stage = item % p.nstages;
-                if (item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1)) {
+                if (item >= p.nstages && !mbar_wait(&empty_bar[stage], ((item / p.nstages) - 1) & 1, p.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -578,16 +607,17 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                 if (tid == 0) {
                     // rows [n_lo, n_lo + N) of every plane of chunk c: contiguous per plane, and
                     // all planes contiguous when the CTA covers every row (one copy then)
-                    mbar_arrive_tx(&full_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    mbar_arrive_tx(&bulk_bar[stage], (uint32_t)(p.nplanes * b_plane_bytes));
+                    ++bulk_started[stage];
                     const size_t plane_full = (size_t)g.n_out * kAtomBytes;
                     if ((size_t)b_plane_bytes == plane_full)
                         bulk_g2s(sb, si.Wt + (size_t)c * p.nplanes * plane_full,
-                                 (uint32_t)(p.nplanes * b_plane_bytes), &full_bar[stage]);
+                                 (uint32_t)(p.nplanes * b_plane_bytes), &bulk_bar[stage]);
                     else
                         for (int pl = 0; pl < p.nplanes; ++pl)
                             bulk_g2s(sb + pl * b_plane_bytes,
                                      si.Wt + ((size_t)c * p.nplanes + pl) * plane_full + (size_t)n_lo * kAtomBytes,
-                                     (uint32_t)b_plane_bytes, &full_bar[stage]);
+                                     (uint32_t)b_plane_bytes, &bulk_bar[stage]);
                 }
                 // gather: each warp covers its 32 rows; lanes split a row into 16-byte pieces.
                 // All loads of the warp are issued before any is used (memory-level parallelism).
@@ -655,6 +685,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             atomicExch(p.err, FMM_ETIMEOUT);
             *(volatile int *)&abort_flag = 1;
         }
+        if (tid == 0 && !wait_bulk_copies(bulk_bar, bulk_started, p.nstages)) atomicExch(p.err, FMM_ETIMEOUT);
     } else {
         // ------------------------------------------------------------ accumulators / epilogue
         // Each stage item's products land in one of two TMEM accumulators; these warps add the
@@ -708,7 +739,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             const float f = f_cur;
             f_cur = advance();
             const int b = item & 1;
-            if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1)) return false;
+            if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1, p.wait_ns)) return false;
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.ncta);
             if constexpr (PL) {
@@ -753,8 +784,9 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                 int good = 1;
                 if (lane == 0) {
                     const int stage = item % p.nstages, b = item & 1;
-                    if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1) ||
-                        (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1)) ||
+                    if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
+                        !mbar_wait(&bulk_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
+                        (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1, p.wait_ns)) ||
                         *(volatile int *)&abort_flag) {
                         good = 0;
                     } else {
@@ -771,6 +803,12 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                 if (ok && item >= 1) ok = drain(item - 1);
             }
             if (ok && n_items >= 1) ok = drain(n_items - 1);
+            // every MMA issued (also before an abort) completes before the tensor memory is freed
+            if (lane == 0) {
+                mma_commit(&fin_bar);
+                if (!mbar_wait(&fin_bar, 0, kWaitNs)) atomicExch(p.err, FMM_ETIMEOUT);
+            }
+            __syncwarp();
         }
         // epilogue: this thread's row (q * 32 + lane) and columns [c0, c0 + DC)
         const int row = q * 32 + lane;
@@ -1090,7 +1128,7 @@ static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int 
     for (int k = 0; k < count; ++k)
         tc_pack(ctx->opt.precision, f16, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h, scales);
     void *d = nullptr;
-    FMM_CUDA_TRY(cudaMalloc(&d, h.size()));
+    FMM_CUDA_TRY(dev_malloc(&d, h.size()));
     ctx->op_allocs.push_back(d);
     FMM_CUDA_TRY(cudaMemcpy(d, h.data(), h.size(), cudaMemcpyHostToDevice));
     out->planes[0] = d;
@@ -1100,7 +1138,7 @@ static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int 
     out->bytes = h.size() / count;   // bytes of one operator (the stride)
     if (f16) {
         void *ds = nullptr;
-        FMM_CUDA_TRY(cudaMalloc(&ds, scales.size() * sizeof(float)));
+        FMM_CUDA_TRY(dev_malloc(&ds, scales.size() * sizeof(float)));
         ctx->op_allocs.push_back(ds);
         FMM_CUDA_TRY(cudaMemcpy(ds, scales.data(), scales.size() * sizeof(float), cudaMemcpyHostToDevice));
         out->scale = (float *)ds;
@@ -1247,6 +1285,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     while (cols < 2 * p.ncta + 16) cols <<= 1;
     p.tmem_cols = cols;
     p.err = ctx->dev_flag;
+    p.wait_ns = ctx->tc_wait_ns;
     if (c.Xp) {
         // A rows from split planes: K of the segment must be the planes' width
         if (c.mode == GM_PARENT2 && c.X1 && !c.Xp1) return cudaErrorInvalidValue;

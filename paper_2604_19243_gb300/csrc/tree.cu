@@ -573,14 +573,14 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t
 
 // Per-context constant tables and count buffers (allocated on the first build).
 static cudaError_t ensure_build_buffers(fmm_ctx *ctx) {
-    if (!ctx->dev_counts) FMM_CUDA_TRY(cudaMalloc((void **)&ctx->dev_counts, kCntSize * sizeof(int)));
+    if (!ctx->dev_counts) FMM_CUDA_TRY(dev_malloc((void **)&ctx->dev_counts, kCntSize * sizeof(int)));
     if (!ctx->host_counts) FMM_CUDA_TRY(cudaMallocHost((void **)&ctx->host_counts, kCntSize * sizeof(int)));
-    if (!ctx->dev_pairs) FMM_CUDA_TRY(cudaMalloc((void **)&ctx->dev_pairs, sizeof(unsigned long long)));
+    if (!ctx->dev_pairs) FMM_CUDA_TRY(dev_malloc((void **)&ctx->dev_pairs, sizeof(unsigned long long)));
     if (!ctx->class_slots) {
         std::vector<int> slots, deltas;
         class_slot_table(slots, deltas);
-        FMM_CUDA_TRY(cudaMalloc((void **)&ctx->class_slots, slots.size() * sizeof(int)));
-        FMM_CUDA_TRY(cudaMalloc((void **)&ctx->class_delta, deltas.size() * sizeof(int)));
+        FMM_CUDA_TRY(dev_malloc((void **)&ctx->class_slots, slots.size() * sizeof(int)));
+        FMM_CUDA_TRY(dev_malloc((void **)&ctx->class_delta, deltas.size() * sizeof(int)));
         FMM_CUDA_TRY(cudaMemcpy(ctx->class_slots, slots.data(), slots.size() * sizeof(int), cudaMemcpyHostToDevice));
         FMM_CUDA_TRY(cudaMemcpy(ctx->class_delta, deltas.data(), deltas.size() * sizeof(int), cudaMemcpyHostToDevice));
     }

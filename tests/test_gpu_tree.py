@@ -53,8 +53,10 @@ def _check_tree(x, depth, domain, full_lists=True, sample=None):
 
 
 @pytest.mark.parametrize("dist", ["cube", "sphere"])
-@pytest.mark.parametrize("depth", [0, 1, 2, 3, 5])
+@pytest.mark.parametrize("depth", [0, 1, 2, 3, 5, 6, 8])
 def test_tree_small(dist, depth):
+    # depths 6 and 8: the levels of the 8.39M sphere below its leaves' parents and of the 33.5M
+    # cube, with every list compared in full
     n = 30_000
     x = cube_points(n) if dist == "cube" else sphere_points(n)
     domain = ((0, 0, 0), 1.0) if dist == "cube" else ((-1, -1, -1), 2.0)
@@ -78,10 +80,10 @@ def test_tree_explicit_domain_clamps_boundary():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name", ["cube1m_p6_d5", "sphere8m_p6_d7"])
+@pytest.mark.parametrize("name", ["cube1m_p6_d5", "sphere8m_p6_d7", "cube33m_p8_d8"])
 def test_tree_full_size_sampled(name):
     w = WORKLOADS[name]
     x = w.points()
-    o_leaves = 40_000 if w.dist == "sphere" else 30_000
+    o_leaves = {"sphere8m_p6_d7": 40_000, "cube1m_p6_d5": 30_000, "cube33m_p8_d8": 14_000_000}[name]
     sample = sample_indices(o_leaves, 200)
     _check_tree(x, w.depth, (w.origin, w.side), full_lists=False, sample=sample)
