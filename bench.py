@@ -417,6 +417,7 @@ def run_config(args, w, ws):
     """The workload and step of a run; both arms report the same dict."""
     return {"workload": w.name, "n": w.n, "dist": w.dist, "p": w.p, "depth": w.depth,
             "precision": args.precision, "kernel": args.kernel, **kernel_config(args),
+            **({"m2l": "fft"} if args.m2l == "fft" else {}),
             "l2": "flushed (256 MB write) between steps",
             "step": f"build_tree + evaluate({args.outputs})", "outputs": args.outputs,
             "parallelism": f"replicas x{ws}"}
@@ -441,6 +442,9 @@ def main():
     ap.add_argument("--workload", default="sphere8m_p6_d7", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "fp64", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
+    ap.add_argument("--m2l", default="dense", choices=["dense", "fft"],
+                    help="form of the M2L: SVD-compressed operators (dense) or lattice convolution by FFT "
+                         "(fp32/fp64 only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the variants measured after the headline (gradient only, modified "
@@ -494,7 +498,7 @@ def main():
     phi = torch.empty(w.n, device=dev, dtype=vdt)
     grad = torch.empty(w.n, 3, device=dev, dtype=vdt)
     fmm = pkg.FMM(p=w.p, depth=w.depth, precision=args.precision, domain=(w.origin, w.side),
-                  stream=stream.cuda_stream, kernel=args.kernel, kappa=args.kappa)
+                  stream=stream.cuda_stream, kernel=args.kernel, kappa=args.kappa, m2l=args.m2l)
     fmm.precompute()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     if args.partition:
@@ -568,8 +572,8 @@ def main():
     g_adj = torch.empty_like(phi)
     torch.cuda.synchronize()
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    adjoint_ms = None   # the Helmholtz kernel has no adjoint
-    if not helm:
+    adjoint_ms = None   # the Helmholtz kernel and the FFT form of the M2L have no adjoint
+    if not helm and args.m2l != "fft":
         a0.record(stream)
         psi, _ = fmm.adjoint(q)
         a1.record(stream)
@@ -624,12 +628,14 @@ def main():
     compress_flops = stencil_flops = 0.0
     for level in range(2, w.depth + 1):
         nl = info["n_boxes"][level]
-        lv = fmm.export_level(level, lists=True)
-        nv = len(lv["v_idx"])
+        nv = fmm.v_count(level)
         vpairs += nv
         compress_flops += 2.0 * kin * ns * nl
         stencil_flops += 2.0 * kout * kin * nv
     m2l_flops = compress_flops + stencil_flops
+    if args.m2l == "fft":   # products with the kernel's transforms: one complex multiply-add (8 flops)
+        nfft = 2 * w.p          # per frequency of the half spectrum, per V pair
+        m2l_flops = 8.0 * vpairs * nfft * nfft * (nfft // 2 + 1)
     tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3", "fp16x3")
     if tensor:
         # products per contraction: BF16x6 six, the other split modes three (FP16X3 runs every

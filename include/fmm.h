@@ -106,7 +106,21 @@ typedef struct {
                               (FMM_EUNSUPPORTED). */
     double kappa;          /* FMM_YUKAWA: screening constant; FMM_HELMHOLTZ: wavenumber; finite and > 0,
                               in inverse units of the coordinates.  Ignored for FMM_LAPLACE. */
+    int m2l;               /* an fmm_m2l_form value.  Default FMM_M2L_DENSE. */
 } fmm_options;
+
+/* Form of the M2L (VLI) translation (option `m2l`; Section 2.2 names both). */
+typedef enum {
+    FMM_M2L_DENSE = 0,     /* SVD-compressed operators applied as batched contractions (BLAS form) */
+    FMM_M2L_FFT = 1        /* lattice convolution by FFT: the upward-equivalent and downward-check
+                              surfaces on radius (p-1)/(p-2) half-widths, whose grid spacing divides
+                              the box width; each box's equivalent densities are transformed once
+                              (n = 2p points per axis, zero-padded), the products with the kernel's
+                              transforms summed over the V list, and the sum transformed back at the
+                              check surface.  FMM_FP32 / FMM_FP64 and FMM_LAPLACE with p >= 4 only;
+                              no mean_free, fmm_adjoint, partitioned or adaptive evaluation
+                              (FMM_EUNSUPPORTED). */
+} fmm_m2l_form;
 
 /* Part selectors for fmm_evaluate_parts (Section 1, Eq. 3: near field + far field). */
 #define FMM_PART_NEAR 1    /* ULI: direct sums over the U lists */

@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("svd_rtol", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
                 ("with_gradient", ctypes.c_int), ("has_domain", ctypes.c_int),
                 ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
-                ("mean_free", ctypes.c_int), ("kernel", ctypes.c_int), ("kappa", ctypes.c_double)]
+                ("mean_free", ctypes.c_int), ("kernel", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("m2l", ctypes.c_int)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -184,7 +185,7 @@ class FMM:
 
     def __init__(self, p=6, depth=4, precision="fp32", svd_rtol=1e-6, pinv_rtol=1e-7,
                  with_gradient=True, domain=None, stream=None, mean_free=False, kernel="laplace",
-                 kappa=0.0):
+                 kappa=0.0, m2l="dense"):
         L = lib()
         opt = Options()
         L.fmm_default_options(ctypes.byref(opt))
@@ -195,6 +196,7 @@ class FMM:
         opt.mean_free = int(mean_free)
         opt.kernel = KERNELS[kernel]
         opt.kappa = float(kappa)
+        opt.m2l = {"dense": 0, "fft": 1}[m2l]
         if domain is not None:
             opt.has_domain = 1
             for a in range(3):
@@ -319,6 +321,12 @@ class FMM:
         self._check(lib().fmm_export_level(self._ctx, level, None, None, _ptr(idx), _ptr(tv),
                                            ctypes.addressof(cnt)))
         return {"keys": keys, "v_offsets": off, "v_idx": idx, "v_tvec": tv}
+
+    def v_count(self, level):
+        """Total length of the V lists of `level` (the lists are counted on the device, not copied)."""
+        cnt = ctypes.c_int64()
+        self._check(lib().fmm_export_level(self._ctx, level, None, None, None, None, ctypes.addressof(cnt)))
+        return cnt.value
 
     def export_check(self, level, kind="upward"):
         """Check potentials of the last evaluate at `level`: n_boxes x n_surface, or n_boxes x

@@ -103,6 +103,7 @@ namespace fmm {
 
 void free_workspace(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
+    if (ctx->masks_ev) cudaStreamWaitEvent(s, ctx->masks_ev, 0);   // the side stream's mask kernels
     free_async(ctx->Uc, s), free_async(ctx->Dc, s), free_async(ctx->Ut, s), free_async(ctx->Ct, s);
     free_async(ctx->UtP, s), free_async(ctx->Uscale, s);
     free_async(ctx->UpP, s), free_async(ctx->DnP, s), free_async(ctx->CtP, s);
@@ -129,9 +130,11 @@ void free_tree(fmm_ctx *ctx) {
     for (int l = 0; l <= kMaxDepth; ++l) {
         LevelTables &L = ctx->lev[l];
         free_async(L.keys, s), free_async(L.parent, s), free_async(L.child, s);
-        free_async(L.dense, s), free_async(L.cls_rows, s);
+        free_async(L.dense, s);
+        if (!ctx->cls_all) free_async(L.cls_rows, s);
         L = LevelTables{};
     }
+    free_async(ctx->cls_all, s);
     ctx->have_tree = false;
     ctx->tiles_ok = false;
     ctx->last_far = false;
@@ -405,6 +408,13 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
         // mean_free carries down the tree are exact for Laplace only
         if (!opt->has_domain || opt->mean_free) return FMM_EUNSUPPORTED;
     }
+    if (opt->m2l != FMM_M2L_DENSE && opt->m2l != FMM_M2L_FFT) return FMM_EINVAL;
+    if (opt->m2l == FMM_M2L_FFT) {
+        if (opt->order_p < 4) return FMM_EINVAL;   // the lattice surfaces of boxes 2 apart would touch
+        if ((opt->precision != FMM_FP32 && opt->precision != FMM_FP64) || opt->kernel != FMM_LAPLACE ||
+            opt->mean_free)
+            return FMM_EUNSUPPORTED;
+    }
     if (opt->has_domain) {
         if (!(std::isfinite(opt->side) && opt->side > 0)) return FMM_EINVAL;
         for (int a = 0; a < 3; ++a)
@@ -419,6 +429,7 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
                   opt->precision == FMM_FP16X3;
     ctx->npts = 6 * (opt->order_p - 1) * (opt->order_p - 1) + 2;
     ctx->cplx = opt->kernel == FMM_HELMHOLTZ;
+    ctx->fft = opt->m2l == FMM_M2L_FFT;
     ctx->ns = ctx->cplx ? 2 * ctx->npts : ctx->npts;   // real and imaginary parts of complex values
     ctx->nsp = round_up(ctx->ns, 16);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
@@ -428,6 +439,8 @@ fmm_status fmm_create(const fmm_options *opt, void *cuda_stream, fmm_ctx **out) 
     }
     bool okc = true;
     for (auto &e : ctx->ev) okc = okc && cudaEventCreate(&e) == cudaSuccess;
+    for (cudaEvent_t *e : {&ctx->masks_fork_ev, &ctx->masks_ev})
+        okc = okc && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
     // Far-field streams (aux[0] for the level sweeps, aux[2..] for the VLI of each level) at
     // the highest priority, the near field (aux[kMaxDepth + 1]) at the lowest: the far field's
     // dependent chain of small launches then takes SMs first and the near-field kernel fills
@@ -503,7 +516,8 @@ fmm_status fmm_precompute(fmm_ctx *ctx) {
     if (lap) ku.resize(1);
     std::vector<const HostOps *> hs;
     try {
-        hs = host_operator_levels(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, ctx->opt.kernel, ku, &err);
+        hs = host_operator_levels(ctx->opt.order_p, ctx->opt.pinv_rtol, ctx->opt.svd_rtol, ctx->opt.kernel, ku, &err,
+                                  ctx->fft);
     } catch (const std::bad_alloc &) {
         return fail(ctx, FMM_ENOMEM, "host memory exhausted in precompute");
     } catch (...) {
@@ -575,6 +589,7 @@ fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
     fmm_status st = check_ready(ctx, g, psi);
     if (st != FMM_OK) return st;
     if (ctx->cplx) return fail(ctx, FMM_EUNSUPPORTED, "no adjoint for the Helmholtz kernel");
+    if (ctx->fft) return fail(ctx, FMM_EUNSUPPORTED, "no adjoint with the FFT form of the M2L");
     if (grad_psi && !ctx->opt.with_gradient) return fail(ctx, FMM_EINVAL, "gradients were not enabled (with_gradient = 0)");
     st = ctx->fp64 ? run_evaluate<double>(ctx, g, psi, nullptr, FMM_PART_ALL, true)
                    : run_evaluate<float>(ctx, g, psi, nullptr, FMM_PART_ALL, true);
@@ -598,6 +613,7 @@ fmm_status fmm_adjoint(fmm_ctx *ctx, const void *g, void *psi, void *grad_psi) {
 fmm_status fmm_partition_setup(fmm_ctx *ctx, int d_global, int n_ranks) {
     if (!ctx) return FMM_EINVAL;
     if (ctx->cplx) return fail(ctx, FMM_EUNSUPPORTED, "no partitioned evaluation for the Helmholtz kernel");
+    if (ctx->fft) return fail(ctx, FMM_EUNSUPPORTED, "no partitioned evaluation with the FFT form of the M2L");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     try {
         return split_setup(ctx, d_global, n_ranks);
@@ -633,6 +649,7 @@ fmm_status fmm_partition_timings(fmm_ctx *ctx, double *ms, int n) {
 
 fmm_status fmm_adaptive_setup(fmm_ctx *ctx, int capacity) {
     if (!ctx) return FMM_EINVAL;
+    if (ctx->fft) return fail(ctx, FMM_EUNSUPPORTED, "no adaptive evaluation with the FFT form of the M2L");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
     try {
         return adaptive_setup(ctx, capacity);
@@ -826,6 +843,8 @@ void fmm_destroy(fmm_ctx *ctx) {
     if (ctx->host_counts) cudaFreeHost(ctx->host_counts);
     if (ctx->host_tiles) cudaFreeHost(ctx->host_tiles);
     if (ctx->tiles_ev) cudaEventDestroy(ctx->tiles_ev);
+    if (ctx->masks_fork_ev) cudaEventDestroy(ctx->masks_fork_ev);
+    if (ctx->masks_ev) cudaEventDestroy(ctx->masks_ev);
     pool_trim();
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);

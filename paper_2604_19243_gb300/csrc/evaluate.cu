@@ -260,10 +260,41 @@ cudaError_t FarSteps<T>::leaf_out(T *far_phi, T *far_grad, cudaStream_t s) {
     return launch_leaf_eval<T>(ctx, grid, rows_at<T>(B, ctx, d, nsp), nsp, (T)1, far_phi, nullptr, s, nullptr);
 }
 
+// Downward pass with the FFT form of the M2L (forward only): per level, D2D from the parent (or
+// zero at level 2), then the lattice convolution of the V list added in (fft.cu).
+template <typename T>
+cudaError_t run_far_fft(fmm_ctx *ctx, FarSteps<T> &f, T *far_phi, T *far_grad, cudaStream_t s) {
+    const int d = f.d, nsp = f.nsp;
+    for (int l = 2; l <= d; ++l) {
+        if (l == d) cudaEventRecord(ctx->ev[4], s);
+        T *D = rows_at<T>(f.B, ctx, l, nsp);
+        if (l >= 3) {   // D2D alone: PARENT2 with an empty first segment
+            GemmCall c;
+            c.mode = GM_PARENT2, c.level = l, c.n_out = nsp;
+            c.X0 = D, c.ldx0 = nsp, c.k0 = 0, c.W0 = f.O(l).up[0];
+            c.X1 = rows_at<T>(f.B, ctx, l - 1, nsp), c.ldx1 = nsp, c.k1 = nsp;
+            c.W1_by_cls = f.O(l - 1).down;
+            c.Y = D, c.ldy = nsp;
+            FMM_CUDA_TRY(gemm_simt<T>(ctx, c, s));
+        } else {
+            FMM_CUDA_TRY(cudaMemsetAsync(D, 0, (size_t)ctx->lev[l].n * nsp * sizeof(T), s));
+        }
+        FMM_CUDA_TRY(fft_vli<T>(ctx, l, rows_at<T>(f.A, ctx, l, nsp), D, s));
+    }
+    return f.leaf_out(far_phi, far_grad, s);
+}
+
 template <typename T>
 cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
     FarSteps<T> f(ctx, adjoint);
     const int d = f.d;
+    if (ctx->fft) {
+        FMM_CUDA_TRY(f.leaf_in(s));
+        cudaEventRecord(ctx->ev[2], s);
+        for (int l = d - 1; l >= 2; --l) FMM_CUDA_TRY(f.up(l, s));
+        cudaEventRecord(ctx->ev[3], s);
+        return run_far_fft<T>(ctx, f, far_phi, far_grad, s);
+    }
     FMM_CUDA_TRY(f.leaf_in(s));
     cudaEventRecord(ctx->ev[2], s);
     for (int l = d - 1; l >= 2; --l) FMM_CUDA_TRY(f.up(l, s));
@@ -335,11 +366,13 @@ cudaError_t upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, OpSet &o) {
     FMM_CUDA_TRY(upload_padded<T>(ctx, ups, ns, ns, nsp, nsp, 8, &o.up[0]));
     for (int c = 1; c < 8; ++c) o.up[c] = (T *)o.up[0] + (size_t)c * nsp * nsp;
     for (int c = 0; c < 8; ++c) FMM_CUDA_TRY(upload_padded<T>(ctx, down[c], ns, ns, nsp, nsp, 1, &o.down[c]));
-    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_compress : h.compress, o.kin, ns, o.kinp, nsp, 1, &o.compress));
-    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_stencil : h.stencil, o.kout, o.kin, o.koutp, o.kinp,
-                                  kNumTransfer, &o.stencil));
-    FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_decompress : h.decompress, ns, o.kout, nsp, o.koutp, 1,
-                                  &o.decompress));
+    if (!h.fft_n) {   // the compressed M2L (the FFT form has its own transforms, fft.cu)
+        FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_compress : h.compress, o.kin, ns, o.kinp, nsp, 1, &o.compress));
+        FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_stencil : h.stencil, o.kout, o.kin, o.koutp, o.kinp,
+                                      kNumTransfer, &o.stencil));
+        FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_decompress : h.decompress, ns, o.kout, nsp, o.koutp, 1,
+                                      &o.decompress));
+    }
     FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close1 : h.close1, h.rcl, ns, o.rclp, nsp, 1, &o.close1));
     FMM_CUDA_TRY(upload_padded<T>(ctx, adjoint ? h.a_close2 : h.close2, ns, h.rcl, nsp, o.rclp, 1, &o.close2));
     if (!adjoint && h.rclu > 0) {
@@ -373,6 +406,7 @@ cudaError_t upload_operators(fmm_ctx *ctx) {
         }
     }
     if (ctx->tensor) FMM_CUDA_TRY(tc_upload_operators(ctx));
+    if (ctx->fft) FMM_CUDA_TRY(fft_upload(ctx));
     // unit surface grid in the storage type
     std::vector<double> g = surface_grid(ctx->opt.order_p);
     size_t bytes = g.size() * (ctx->fp64 ? sizeof(double) : sizeof(float));

@@ -128,6 +128,9 @@ struct fmm_ctx {
     bool fp64 = false;
     bool tensor = false;        // tcgen05 contractions
     bool cplx = false;          // complex densities and outputs (FMM_HELMHOLTZ)
+    bool fft = false;           // M2L by FFT (FMM_M2L_FFT)
+    void *fft_ghat = nullptr;   // FFT M2L: the kernel's transforms [316][n n (n/2+1)] complex, storage type
+    int *fft_surf = nullptr;    // FFT M2L: p^3 grid index of every surface point
     int npts = 0;               // surface points, 6(p-1)^2+2
     int ns = 0, nsp = 0;        // box vector length (npts, or 2 npts: real then imaginary parts), padded
 
@@ -157,8 +160,12 @@ struct fmm_ctx {
     fmm::Tile *host_tiles = nullptr;                      // pinned staging of the tile lists
     size_t host_tiles_cap = 0;
     cudaEvent_t tiles_ev = nullptr;                       // completion of the last tile copies
+    cudaEvent_t masks_fork_ev = nullptr, masks_ev = nullptr;   // stencil masks: inputs ready / done
     // P2P schedule: leaves in decreasing work order
     int *p2p_order = nullptr;
+    // class order of every level in one allocation (lev[l].cls_rows point into it); null when
+    // each level owns its own array (the contexts of virtual ranks)
+    int *cls_all = nullptr;
 
     // evaluate workspaces (allocated with the tree once operators are known)
     bool have_ws = false;
@@ -241,13 +248,19 @@ struct HostOps {
     // adjoint (transposes)
     std::vector<double> a_up[8], a_down[8], a_compress, a_stencil, a_decompress, a_close1,
         a_close2;
+    double alpha_inner = 1.05;                        // radius of the upward-equivalent / downward-check surfaces
+    // FFT form of the M2L: transform size n = 2p per axis and the lattice kernel's transforms of
+    // the 316 transfer vectors on the unit box, [316][n][n][n/2 + 1] (re, im)
+    int fft_n = 0;
+    std::vector<double> fft_ghat;
 };
 // Build (or fetch from the process-wide cache) the FP64 operators for (p, pinv_rtol, svd_rtol).
 const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err);
 // One operator set per entry of kappa_u (the kernel's kappa times a level's half-width; 0 =
 // Laplace), all with the M2L ranks of the entry that needs the largest; cached per argument list.
 std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol, int kernel,
-                                                  const std::vector<double> &kappa_u, std::string *err);
+                                                  const std::vector<double> &kappa_u, std::string *err,
+                                                  bool fft = false);
 // Unit surface grid of order p (lexicographic), [n x 3] in [-1,1]^3.
 std::vector<double> surface_grid(int p);
 
@@ -371,6 +384,11 @@ cudaError_t launch_rows_to_planes(const float *x, int ldx, int64_t nrows, int nc
                                   long long plane_bytes, int ldp, float *scales, int lds, cudaStream_t s);
 cudaError_t tc_upload_operators(fmm_ctx *ctx);
 void tc_free(fmm_ctx *ctx);
+
+// ---- fft.cu ----
+cudaError_t fft_upload(fmm_ctx *ctx);
+template <typename T>
+cudaError_t fft_vli(fmm_ctx *ctx, int level, const T *U, T *D, cudaStream_t s);
 
 // ---- evaluate.cu ----
 cudaError_t upload_operators(fmm_ctx *ctx);

@@ -99,6 +99,10 @@ cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &c, cudaStream_t s) {
     if (ts.ntiles == 0) return cudaSuccess;
     g.tiles = ts.tiles;
     g.masks = ts.masks;
+    if (c.mode == GM_STENCIL && ctx->masks_ev) {   // the masks are computed on a side stream
+        cudaError_t e = cudaStreamWaitEvent(s, ctx->masks_ev, 0);
+        if (e != cudaSuccess) return e;
+    }
     const int subs = (ctx->tile_m + BM - 1) / BM;
     dim3 grid(ts.ntiles * subs, (c.n_out + BN - 1) / BN);
     gemm_simt_kernel<T><<<grid, THREADS, 0, s>>>(g, subs); count_launch();

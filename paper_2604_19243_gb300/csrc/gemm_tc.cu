@@ -63,6 +63,11 @@ struct TcDev {
     int tmem_cols;
     int *err;                       // device error flag
     unsigned long long wait_ns;     // bound on every pipeline barrier wait (default 1 s)
+    // Segment accumulation (plane layout): all K chunks of one segment go into one of three
+    // accumulators, drained once per segment; the rows and operators then carry one FP16 scale
+    // each (uniform over their chunks).
+    int seg_acc;
+    int yp_row_scale;               // FP16 output planes: one scale per row (every chunk's entry equal)
     int a_planes;                   // A rows arrive pre-split from xp (cp.async copies)
     const unsigned char *xp;        // split planes of the A rows
     long long xp_plane;             // bytes between planes
@@ -120,22 +125,26 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait until the barrier's phase with the given parity has completed; false once limit_ns of
-// %globaltimer have passed (checked every 256 polls; a limit of 0 gives up at the first poll
+// %globaltimer have passed (checked every 16 polls; a limit of 0 gives up at the first poll
 // that finds the phase incomplete).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     const uint32_t a = smem_u32(bar);
+    // Each poll may suspend the thread until the phase completes (at most `hint` ns), so that
+    // waiting warps take no issue slots from the warps they wait for on the same SM
+    // sub-partition (the MMA issuer above all).
+    const uint32_t hint = limit_ns < 1000000ull ? (uint32_t)limit_ns : 1000000u;
     uint32_t done = 0;
     uint64_t t0 = 0;
     for (int it = 0;; ++it) {
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(hint)
             : "memory");
         if (done) return true;
         if (limit_ns == 0) return false;
         if (it == 0) t0 = global_ns();
-        else if ((it & 255) == 0 && global_ns() - t0 > limit_ns) return false;
+        else if ((it & 15) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -332,7 +341,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
     extern __shared__ unsigned char smem_raw[];
     // full: the producers' A rows of a stage; bulk: its operator copy; empty: the stage's MMAs
     // done; tfull / tempty: an accumulator's MMAs done / drained; fin: every MMA of the CTA done
-    __shared__ uint64_t full_bar[4], bulk_bar[4], empty_bar[4], tfull_bar[2], tempty_bar[2], fin_bar;
+    __shared__ uint64_t full_bar[4], bulk_bar[4], empty_bar[4], tfull_bar[3], tempty_bar[3], fin_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int box[kTcRows];
     __shared__ int srcs[2][kTcRows];
@@ -362,7 +371,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             mbar_init(&empty_bar[s], 1);      // tcgen05.commit
         }
         mbar_init(&fin_bar, 1);               // tcgen05.commit after the last MMA
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 3; ++b) {
             mbar_init(&tfull_bar[b], 1);      // tcgen05.commit
             mbar_init(&tempty_bar[b], NDRAIN);   // the accumulator warps
         }
@@ -391,14 +400,22 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
     const uint32_t idesc = make_idesc(N, TF32 ? 2 : (p.f16 ? 0 : 1));   // kind::f16: 0 = FP16, 1 = BF16
     const int nseg = gemm_nseg(g);
     auto active = [&](int seg) { return g.mode != GM_STENCIL || ((mask[seg >> 5] >> (seg & 31)) & 1u); };
-    // number of stage items (segment chunks) of the tile
-    int n_items = 0;
+    // number of stage items (segment chunks) and of active segments of the tile
+    int n_items = 0, n_segs = 0;
     for (int seg = 0; seg < nseg; ++seg)
-        if (active(seg)) n_items += (gemm_seg_k(g, seg) + chunk_elems - 1) / chunk_elems;
+        if (active(seg)) n_items += (gemm_seg_k(g, seg) + chunk_elems - 1) / chunk_elems, ++n_segs;
+    // accumulator uses: one per item, or one per segment with segment accumulation
+    const int nacc = p.seg_acc ? 3 : 2;
+    const int n_units = p.seg_acc ? n_segs : n_items;
+    // the split products (plane pairs), held in registers
+    int pa[6], pb[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pa[i] = p.prod_a[i], pb[i] = p.prod_b[i];
 
     // One stage item's MMAs into accumulator b, issued by one thread: the split products of the
-    // chunk, then commits that free the stage and mark the accumulator full.
-    auto issue_item = [&](int stage, int b, const SegInfo &si, int chunk) {
+    // chunk, then commits that free the stage and (after the last chunk of the accumulation)
+    // mark the accumulator full.  `first` starts the accumulator afresh.
+    auto issue_item = [&](int stage, int b, const SegInfo &si, int chunk, bool first, bool last) {
         tc_fence_after();
         fence_proxy_async();   // cp.async / st.shared writes (generic proxy) -> tcgen05.mma
         const uint32_t sa = smem_u32(base + (size_t)stage * stage_bytes);
@@ -406,18 +423,22 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
         const uint32_t dt = tmem + (uint32_t)(b * p.ncta);
         const int kval = min(chunk_elems, si.K - chunk * chunk_elems);
         const int ksteps = min(kAtomBytes / 32, (kval * esz + 31) / 32);
-        uint32_t accum = 0;
-        for (int pr = 0; pr < p.nprod; ++pr) {
+        // descriptors of the stage's planes; a K step of 32 bytes adds 2 to the address field
+        const uint64_t a0 = sw128_desc(sa), b0 = sw128_desc(sb);
+        uint32_t accum = first ? 0u : 1u;
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr) {
+            if (pr >= p.nprod) break;
+            const uint64_t ap = a0 + (uint64_t)((pa[pr] * a_plane_bytes) >> 4);
+            const uint64_t bp = b0 + (uint64_t)((pb[pr] * b_plane_bytes) >> 4);
             for (int ks = 0; ks < ksteps; ++ks) {
-                const uint64_t ad = sw128_desc(sa + p.prod_a[pr] * a_plane_bytes + ks * 32);
-                const uint64_t bd = sw128_desc(sb + p.prod_b[pr] * b_plane_bytes + ks * 32);
-                if (TF32) mma_tf32(dt, ad, bd, idesc, accum);
-                else mma_bf16(dt, ad, bd, idesc, accum);
+                if (TF32) mma_tf32(dt, ap + 2 * ks, bp + 2 * ks, idesc, accum);
+                else mma_bf16(dt, ap + 2 * ks, bp + 2 * ks, idesc, accum);
                 accum = 1;
             }
         }
         mma_commit(&empty_bar[stage]);
-        mma_commit(&tfull_bar[b]);
+        if (last) mma_commit(&tfull_bar[b]);
     };
 
     if (warp < 3 && p.a_planes) {
@@ -549,20 +570,23 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
         // warps drain: the issue of an item's MMAs returns only as the tensor pipe takes them.
         if (lane == 0) {
             bool ok = true;
-            int seg = 0, chunk = 0;
+            int seg = 0, chunk = 0, seg_ord = 0;
             while (seg < nseg && !active(seg)) ++seg;
             SegInfo si{};
             if (seg < nseg) si = seg_info(p, t, tt, seg, chunk_elems);
             for (int item = 0; item < n_items; ++item) {
-                const int stage = item % p.nstages, b = item & 1;
+                const int stage = item % p.nstages;
+                const bool first = !p.seg_acc || chunk == 0, last = !p.seg_acc || chunk + 1 == si.nchunks;
+                const int u = p.seg_acc ? seg_ord : item, b = u % nacc;   // accumulator use
                 if (!mbar_wait(&full_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
                     !mbar_wait(&bulk_bar[stage], (item / p.nstages) & 1, p.wait_ns) ||
-                    (item >= 2 && !mbar_wait(&tempty_bar[b], ((item >> 1) - 1) & 1, p.wait_ns)) ||
+                    (first && u >= nacc && !mbar_wait(&tempty_bar[b], ((u / nacc) - 1) & 1, p.wait_ns)) ||
                     *(volatile int *)&abort_flag) {
                     ok = false;
                     break;
                 }
-                issue_item(stage, b, si, chunk);
+                issue_item(stage, b, si, chunk, first, last);
+                if (last) ++seg_ord;
                 if (++chunk == si.nchunks) {
                     chunk = 0;
                     ++seg;
@@ -724,9 +748,9 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
         int d_seg = next_active(-1), d_next = next_active(d_seg), d_chunk = 0;
         int d_src = scaled ? src_of(d_seg) : -1, d_src_next = scaled ? src_of(d_next) : -1;
         float f_cur = factor(d_src, d_seg, 0);
-        auto advance = [&]() -> float {   // step to the next item; its factor, loads issued now
+        auto advance = [&]() -> float {   // step to the next unit; its factor, loads issued now
             if (d_seg >= nseg) return 1.f;
-            if (++d_chunk * chunk_elems >= gemm_seg_k(g, d_seg)) {
+            if (p.seg_acc || ++d_chunk * chunk_elems >= gemm_seg_k(g, d_seg)) {
                 d_chunk = 0;
                 d_seg = d_next;
                 d_next = next_active(d_seg);
@@ -735,11 +759,11 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             }
             return factor(d_src, d_seg, d_chunk);
         };
-        auto drain = [&](int item) -> bool {
+        auto drain = [&](int unit) -> bool {   // one accumulator use: an item, or a segment
             const float f = f_cur;
             f_cur = advance();
-            const int b = item & 1;
-            if (!mbar_wait(&tfull_bar[b], (item >> 1) & 1, p.wait_ns)) return false;
+            const int b = unit % nacc;
+            if (!mbar_wait(&tfull_bar[b], (unit / nacc) & 1, p.wait_ns)) return false;
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.ncta);
             if constexpr (PL) {
@@ -773,7 +797,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             return true;
         };
         if (!issuer) {
-            for (int item = 0; item < n_items && ok; ++item) ok = drain(item);
+            for (int u = 0; u < n_units && ok; ++u) ok = drain(u);
         } else {
             // lane 0 issues item i; the whole warp then drains item i - 1 while item i runs
             int seg = 0, chunk = 0;
@@ -790,7 +814,7 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
                         *(volatile int *)&abort_flag) {
                         good = 0;
                     } else {
-                        issue_item(stage, b, si, chunk);
+                        issue_item(stage, b, si, chunk, true, true);
                         if (++chunk == si.nchunks) {
                             chunk = 0;
                             ++seg;
@@ -854,6 +878,10 @@ __device__ __forceinline__ void tc_body(const TcDev &p) {
             pm0 = fmaxf(pmax[0][0][row], pmax[1][0][row]);
             pm1 = fmaxf(pmax[0][1][row], pmax[1][1][row]);
             pm2 = fmaxf(pmax[0][2][row], pmax[1][2][row]);
+        }
+        if (f16p && p.yp_row_scale) {   // one scale for the whole row (the launch covers every column)
+            const float m = fmaxf(pm0, fmaxf(pm1, pm2));
+            pm0 = pm1 = pm2 = m;
         }
         if (ok && b >= 0 && f16p) {
             // FP16 hi/lo planes of the row scaled by a power of two per 64-column chunk, so that
@@ -1068,9 +1096,11 @@ double host_f16_val(uint16_t h) {
 // rows x cols FP64 (row-major) -> the split planes of the padded rows_p x cols_p operand, in
 // the stage layout [chunk][plane][rows_p x 128 B, SWIZZLE_128B], appended to `out`.  With
 // `f16` the planes are FP16 hi/lo of the operand scaled per chunk by a power of two (largest
-// entry below 2^14); 1 / scale of every chunk is appended to `scales`.
+// entry below 2^14); 1 / scale of every chunk is appended to `scales`.  With `uniform` every
+// chunk gets the scale of the whole operand, so that the chunks of one operator can accumulate
+// in one tensor-memory accumulator.
 static void tc_pack(int prec, bool f16, const double *w, int rows, int cols, int rows_p, int cols_p,
-                    std::vector<unsigned char> &out, std::vector<float> &scales) {
+                    std::vector<unsigned char> &out, std::vector<float> &scales, bool uniform = false) {
     const bool tf32 = prec == FMM_TF32X3;
     const int np = f16 ? 2 : planes_of(prec);
     const int esz = tf32 ? 4 : 2;
@@ -1084,8 +1114,9 @@ static void tc_pack(int prec, bool f16, const double *w, int rows, int cols, int
     if (f16)
         for (int k = 0; k < nchunks; ++k) {
             double mx = 0;
+            const int c_lo = uniform ? 0 : k * ce, c_hi = uniform ? cols : std::min(cols, (k + 1) * ce);
             for (int r = 0; r < rows; ++r)
-                for (int c = k * ce; c < std::min(cols, (k + 1) * ce); ++c) mx = std::max(mx, std::fabs(w[(size_t)r * cols + c]));
+                for (int c = c_lo; c < c_hi; ++c) mx = std::max(mx, std::fabs(w[(size_t)r * cols + c]));
             int ex = 0;
             std::frexp(mx, &ex);
             sc[k] = mx > 0 ? std::ldexp(1.0, 14 - ex) : 1.0;
@@ -1122,11 +1153,11 @@ static void tc_pack(int prec, bool f16, const double *w, int rows, int cols, int
 
 // `count` operators of rows x cols (consecutive in w) packed into one allocation
 static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int rows, int cols,
-                                  int rows_p, int cols_p, TcMat *out, bool f16 = false) {
+                                  int rows_p, int cols_p, TcMat *out, bool f16 = false, bool uniform = false) {
     std::vector<unsigned char> h;
     std::vector<float> scales;
     for (int k = 0; k < count; ++k)
-        tc_pack(ctx->opt.precision, f16, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h, scales);
+        tc_pack(ctx->opt.precision, f16, w + (size_t)k * rows * cols, rows, cols, rows_p, cols_p, h, scales, uniform);
     void *d = nullptr;
     FMM_CUDA_TRY(dev_malloc(&d, h.size()));
     ctx->op_allocs.push_back(d);
@@ -1145,6 +1176,19 @@ static cudaError_t tc_upload_many(fmm_ctx *ctx, const double *w, int count, int 
         out->scale_ld = (int)(scales.size() / count);
     }
     return cudaSuccess;
+}
+
+// FMM_FP16X3 M2L stencil with segment accumulation: every K chunk of one transfer vector's
+// product goes into one tensor-memory accumulator, drained once per segment.  That needs one
+// scale per source row (written by the compress epilogue, so its output must fit one CTA) and
+// one per operator, in both directions.
+static bool stencil_segment_acc(const fmm_ctx *ctx) {
+    if (ctx->opt.precision != FMM_FP16X3) return false;
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        const OpSet &o = ctx->fwd[l];
+        if (o.ns && std::max(o.kinp, o.koutp) > kTcMaxN) return false;
+    }
+    return true;
 }
 
 static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, const OpSet &o, TcOpSet &t) {
@@ -1172,8 +1216,10 @@ static cudaError_t tc_upload_set(fmm_ctx *ctx, const HostOps &h, bool adjoint, c
                                 &t.compress, f16ops));
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_decompress : h.decompress).data(), 1, ns, o.kout, nsp,
                                 o.koutp, &t.decompress, f16ops));
+    // the stencil operators scaled as a whole (see segment accumulation in tc_body)
     FMM_CUDA_TRY(tc_upload_many(ctx, (adjoint ? h.a_stencil : h.stencil).data(), kNumTransfer, o.kout, o.kin,
-                                o.koutp, o.kinp, &t.stencil, ctx->opt.precision == FMM_FP16X3));
+                                o.koutp, o.kinp, &t.stencil, ctx->opt.precision == FMM_FP16X3,
+                                stencil_segment_acc(ctx)));
     return cudaSuccess;
 }
 
@@ -1217,6 +1263,7 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     if (ts.ntiles == 0) return cudaSuccess;
     p.g.tiles = ts.tiles;
     p.g.masks = ts.masks;
+    if (c.mode == GM_STENCIL && ctx->masks_ev) FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->masks_ev, 0));
     switch (op) {
         case OP_UP: p.Wt0 = (const unsigned char *)T.up.planes[0]; p.wt_stride = (long long)T.up.bytes; break;
         case OP_COMPRESS: p.Wt0 = (const unsigned char *)T.compress.planes[0]; break;
@@ -1281,8 +1328,12 @@ cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream
     if (p.nstages < 2) return cudaErrorInvalidValue;
     // two accumulators of ncta columns; the drain reads 32 columns at a time, so the last read
     // of the second accumulator may extend 16 columns past it: keep that inside the allocation
+    p.seg_acc = c.mode == GM_STENCIL && plane && stencil_segment_acc(ctx);
+    p.yp_row_scale = op == OP_COMPRESS && c.Yp && stencil_segment_acc(ctx) && nsplit == 1;
+    if (op == OP_COMPRESS && stencil_segment_acc(ctx) && !p.yp_row_scale) return cudaErrorInvalidValue;
     int cols = 32;
-    while (cols < 2 * p.ncta + 16) cols <<= 1;
+    while (cols < (p.seg_acc ? 3 : 2) * p.ncta + 16) cols <<= 1;
+    if (cols > 512) return cudaErrorInvalidValue;
     p.tmem_cols = cols;
     p.err = ctx->dev_flag;
     p.wait_ns = ctx->tc_wait_ns;

@@ -285,13 +285,82 @@ struct LevelBuild {
     std::vector<double> ll, lr;         // their eigenvalues
 };
 
-LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
+// FFT form of the M2L (Section 2.2 names it beside the BLAS form): with the upward-equivalent
+// and downward-check surfaces on radius alpha = (p - 1)/(p - 2) half-widths, the grid spacing
+// h = 2 alpha / (p - 1) divides the box width 2 (m = p - 2 steps), so every surface point
+// difference between a target box and a V-list source at transfer vector t is a lattice vector
+// h (d - m t), d in [-(p-1), p-1]^3.  The M2L of t is then the convolution of the source's
+// densities (on the p^3 grid, zero off the surface) with K sampled on those vectors, evaluated
+// zero-padded to n = 2p points per axis through the discrete Fourier transform.  Unit box
+// (half-width 1); for Laplace the transforms serve every level (homogeneity: the M2L of check
+// potentials, K(dc, ue) UC2E, is level-invariant).
+double lattice_alpha(int p) { return (double)(p - 1) / (double)(p - 2); }
+
+// Real-to-complex DFT of the sampled kernel of transfer vector (tx, ty, tz): out[(ka n + kb) nh
+// + kc] = sum_{a,b,c} g[a][b][c] e^{-2 pi i (a ka + b kb + c kc) / n}, nh = n/2 + 1, as
+// (re, im) pairs; separable, in FP64.
+void lattice_kernel_transform(int p, int tx, int ty, int tz, int kernel, double kappa_u, double *out) {
+    const int n = 2 * p, nh = n / 2 + 1, m = p - 2;
+    const double h = 2.0 / (p - 2);
+    std::vector<double> g((size_t)n * n * n, 0.0);
+    auto diff = [&](int i) { return i < p ? i : i - n; };   // circular index -> lattice difference
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            for (int c = 0; c < n; ++c) {
+                const int da = diff(a), db = diff(b), dc = diff(c);
+                if (std::abs(da) > p - 1 || std::abs(db) > p - 1 || std::abs(dc) > p - 1) continue;
+                const double x[3] = {h * (da - m * tx), h * (db - m * ty), h * (dc - m * tz)}, z[3] = {0, 0, 0};
+                if (x[0] == 0 && x[1] == 0 && x[2] == 0) continue;
+                g[((size_t)a * n + b) * n + c] = fmm::kernel_matrix(Mat(x, x + 3), Mat(z, z + 3), kernel, kappa_u)[0];
+            }
+    std::vector<double> cr(n), ci(n);
+    for (int k = 0; k < n; ++k) cr[k] = std::cos(2.0 * M_PI * k / n), ci[k] = -std::sin(2.0 * M_PI * k / n);
+    // along c (real -> half spectrum), then b, then a (complex)
+    std::vector<double> s1((size_t)n * n * nh * 2), s2((size_t)n * n * nh * 2);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            for (int kc = 0; kc < nh; ++kc) {
+                double re = 0, im = 0;
+                for (int c = 0; c < n; ++c) {
+                    const double v = g[((size_t)a * n + b) * n + c];
+                    const int w = (c * kc) % n;
+                    re += v * cr[w], im += v * ci[w];
+                }
+                s1[(((size_t)a * n + b) * nh + kc) * 2] = re, s1[(((size_t)a * n + b) * nh + kc) * 2 + 1] = im;
+            }
+    for (int a = 0; a < n; ++a)
+        for (int kb = 0; kb < n; ++kb)
+            for (int kc = 0; kc < nh; ++kc) {
+                double re = 0, im = 0;
+                for (int b = 0; b < n; ++b) {
+                    const double *v = &s1[(((size_t)a * n + b) * nh + kc) * 2];
+                    const int w = (b * kb) % n;
+                    re += v[0] * cr[w] - v[1] * ci[w], im += v[0] * ci[w] + v[1] * cr[w];
+                }
+                s2[(((size_t)a * n + kb) * nh + kc) * 2] = re, s2[(((size_t)a * n + kb) * nh + kc) * 2 + 1] = im;
+            }
+    for (int ka = 0; ka < n; ++ka)
+        for (int kb = 0; kb < n; ++kb)
+            for (int kc = 0; kc < nh; ++kc) {
+                double re = 0, im = 0;
+                for (int a = 0; a < n; ++a) {
+                    const double *v = &s2[(((size_t)a * n + kb) * nh + kc) * 2];
+                    const int w = (a * ka) % n;
+                    re += v[0] * cr[w] - v[1] * ci[w], im += v[0] * ci[w] + v[1] * cr[w];
+                }
+                out[(((size_t)ka * n + kb) * nh + kc) * 2] = re, out[(((size_t)ka * n + kb) * nh + kc) * 2 + 1] = im;
+            }
+}
+
+LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u, bool fft) {
     LevelBuild b;
     b.h = std::make_unique<HostOps>();
     HostOps *h = b.h.get();
     h->p = p;
     h->kernel = kernel;
     h->kappa_u = kappa_u;
+    const double alpha_in = fft ? lattice_alpha(p) : kAlphaInner;
+    h->alpha_inner = alpha_in;
     std::vector<double> grid = surface_grid(p);
     h->npts = (int)grid.size() / 3;
     // ns: the length of a box vector (the surface points, twice that for complex values)
@@ -300,9 +369,9 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     auto kernel_matrix = [&](const Mat &x, const Mat &y, double param) {
         return fmm::kernel_matrix(x, y, kernel, param);
     };
-    Mat ue = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaInner);   // upward equivalent
+    Mat ue = scaled_surface(grid, 0, 0, 0, 1.0, alpha_in);     // upward equivalent
     Mat uc = scaled_surface(grid, 0, 0, 0, 1.0, kAlphaOuter);   // upward check
-    Mat dc = ue;                                                // downward check (1.05)
+    Mat dc = ue;                                                // downward check (the inner radius)
     Mat de = uc;                                                // downward equivalent (2.95)
     h->surf_inner = ue;
     h->surf_outer = uc;
@@ -337,18 +406,29 @@ LevelBuild build_level(int p, double pinv_rtol, int kernel, double kappa_u) {
     for (int c = 0; c < 8; ++c) {
         double cx = ((c >> 2) & 1) ? 0.5 : -0.5, cy = ((c >> 1) & 1) ? 0.5 : -0.5,
                cz = (c & 1) ? 0.5 : -0.5;
-        Mat child_ue = scaled_surface(grid, cx, cy, cz, 0.5, kAlphaInner);
+        Mat child_ue = scaled_surface(grid, cx, cy, cz, 0.5, alpha_in);
         Mat child_dc = child_ue;
         h->up[c] = matmul(kernel_matrix(uc, child_ue, kappa_u), child_uc2e, ns, ns, ns);
         h->down[c] = matmul(kernel_matrix(child_dc, de, kappa_u), dc2e, ns, ns, ns);
     }
 
+    if (fft) {   // the lattice kernel's transforms instead of the compressed operators
+        const int n = 2 * p, nf = n * n * (n / 2 + 1);
+        h->fft_n = n;
+        h->fft_ghat.assign((size_t)kNumTransfer * nf * 2, 0.0);
+        parallel_for(kNumTransfer, [&](int t) {
+            int dx, dy, dz;
+            transfer_vector(t, dx, dy, dz);
+            lattice_kernel_transform(p, dx, dy, dz, kernel, kappa_u, &h->fft_ghat[(size_t)t * nf * 2]);
+        });
+        return b;
+    }
     // M2L operators T_t = K(dc_0, ue_{2t}) UC2E
     b.T.resize(kNumTransfer);
     parallel_for(kNumTransfer, [&](int t) {
         int dx, dy, dz;
         transfer_vector(t, dx, dy, dz);
-        Mat src = scaled_surface(grid, 2.0 * dx, 2.0 * dy, 2.0 * dz, 1.0, kAlphaInner);
+        Mat src = scaled_surface(grid, 2.0 * dx, 2.0 * dy, 2.0 * dz, 1.0, alpha_in);
         b.T[t] = matmul(kernel_matrix(dc, src, kappa_u), uc2e, ns, ns, ns);
     });
     // Gram matrices of the fat [T_1 .. T_316] (left) and tall [T_1; ..; T_316] (right) stacks
@@ -388,6 +468,16 @@ int rank_of(const std::vector<double> &l, double svd_rtol) {
 std::unique_ptr<HostOps> finish_level(LevelBuild &b, int kin, int kout) {
     HostOps *h = b.h.get();
     const int ns = h->ns;
+    if (h->fft_n) {   // FFT M2L: no compressed operators; the surface operators' transposes as below
+        h->kin = h->kout = 0;
+        for (int c = 0; c < 8; ++c) {
+            h->a_up[c] = transpose(h->down[c], ns, ns);
+            h->a_down[c] = transpose(h->up[c], ns, ns);
+        }
+        h->a_close1 = transpose(h->close2, ns, h->rcl);
+        h->a_close2 = transpose(h->close1, h->rcl, ns);
+        return std::move(b.h);
+    }
     h->kout = kout;
     h->kin = kin;
     Mat uo((size_t)ns * kout), vi((size_t)ns * kin);
@@ -445,14 +535,15 @@ std::vector<double> surface_grid(int p) {
 }
 
 std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, double svd_rtol, int kernel,
-                                                  const std::vector<double> &kappa_u, std::string *err) {
+                                                  const std::vector<double> &kappa_u, std::string *err, bool fft) {
     static std::mutex mu;
-    static std::map<std::tuple<int, double, double, int, std::vector<double>>, std::vector<std::unique_ptr<HostOps>>>
+    static std::map<std::tuple<int, double, double, int, std::vector<double>, bool>,
+                    std::vector<std::unique_ptr<HostOps>>>
         cache;
     std::lock_guard<std::mutex> lock(mu);
     std::vector<double> key_k = kappa_u;
     for (auto &k : key_k) k = kernel == FMM_LAPLACE ? 0.0 : std::max(k, 0.0);
-    auto key = std::make_tuple(p, pinv_rtol, svd_rtol, kernel, key_k);
+    auto key = std::make_tuple(p, pinv_rtol, svd_rtol, kernel, key_k, fft);
     auto it = cache.find(key);
     if (it == cache.end()) {
         // distinct kappa_u values only; the M2L ranks are the largest any of them needs, so that
@@ -463,7 +554,8 @@ std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, doubl
         std::vector<LevelBuild> lb;
         int kin = 1, kout = 1;
         for (double k : uniq) {
-            lb.push_back(build_level(p, pinv_rtol, kernel, k));
+            lb.push_back(build_level(p, pinv_rtol, kernel, k, fft));
+            if (fft) continue;
             kin = std::max(kin, rank_of(lb.back().lr, svd_rtol));
             kout = std::max(kout, rank_of(lb.back().ll, svd_rtol));
         }
@@ -486,7 +578,7 @@ std::vector<const HostOps *> host_operator_levels(int p, double pinv_rtol, doubl
 }
 
 const HostOps *host_operators(int p, double pinv_rtol, double svd_rtol, std::string *err) {
-    auto v = host_operator_levels(p, pinv_rtol, svd_rtol, FMM_LAPLACE, {0.0}, err);
+    auto v = host_operator_levels(p, pinv_rtol, svd_rtol, FMM_LAPLACE, {0.0}, err, false);
     return v.empty() ? nullptr : v[0];
 }
 

@@ -244,29 +244,55 @@ __global__ void radix_hist(const uint32_t *keys, int64_t n, int shift, int ntile
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
 }
 
+// Scatter of one 4096-key tile: the tile is first ordered by digit in shared memory (stable:
+// warp, then round, then lane order), then every digit run is written out by consecutive
+// threads to consecutive addresses, so that the global writes are coalesced.
 __global__ void radix_scatter(const uint32_t *keys, const int *vals, int64_t n, int shift,
                               int ntiles, const int *offs, uint32_t *keys_out, int *vals_out) {
-    __shared__ int wcnt[kSortWarps][256];
+    __shared__ int wcnt[kSortWarps][256];   // per-warp digit counts, then tile positions
+    __shared__ int dstart[256];             // tile-local start of each digit's run
+    __shared__ int gbase[256];              // global start of this tile's run of each digit
+    __shared__ int wsum[kSortThreads / 32];
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ int sv[kSortTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSortWarpItems;
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = tbase + (int64_t)warp * kSortWarpItems;
+    const int count = n - tbase < (int64_t)kSortTile ? (int)(n - tbase) : kSortTile;
     // per-warp digit counts
     for (int r = 0; r < kSortRounds; ++r) {
         int64_t k = wbase + r * 32 + lane;
         if (k < n) atomicAdd(&wcnt[warp][(keys[k] >> shift) & 255u], 1);
     }
     __syncthreads();
-    // turn counts into starting positions: tile offset of the digit + earlier warps
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-        int run = offs[(int64_t)d * ntiles + blockIdx.x];
+    // digit totals of the tile and their exclusive scan (one digit per thread: 256 threads)
+    {
+        const int d = threadIdx.x;
+        int tot = 0;
+        for (int w = 0; w < kSortWarps; ++w) tot += wcnt[w][d];
+        int x = tot;   // inclusive scan within the warp, then across warps
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const int start = before + x - tot;
+        dstart[d] = start;
+        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+        int run = start;
         for (int w = 0; w < kSortWarps; ++w) {
-            int c = wcnt[w][d];
+            const int c = wcnt[w][d];
             wcnt[w][d] = run;
             run += c;
         }
     }
     __syncthreads();
+    // tile order in shared memory
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < kSortRounds; ++r) {
         int64_t k = wbase + r * 32 + lane;
@@ -280,9 +306,18 @@ __global__ void radix_scatter(const uint32_t *keys, const int *vals, int64_t n, 
         if (valid && rank == 0) wcnt[warp][digit] += __popc(peers);
         __syncwarp();
         if (valid) {
-            keys_out[pos] = key;
-            vals_out[pos] = vals[k];
+            sk[pos] = key;
+            sv[pos] = vals[k];
         }
+    }
+    __syncthreads();
+    // coalesced write-out: element i of the tile order goes to its digit's global run
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const uint32_t key = sk[i];
+        const int d = (int)((key >> shift) & 255u);
+        const int pos = gbase[d] + (i - dstart[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = sv[i];
     }
 }
 
@@ -444,17 +479,31 @@ __global__ void p2p_work(const int *leaf_off, const int *u_off, const int *u_idx
     }
     long long w = src * (long long)(leaf_off[b + 1] - leaf_off[b]);
     atomicAdd(total, (unsigned long long)w);
-    // descending work order through an ascending sort of the complement (clamped to 32 bits)
-    unsigned long long wc = w > 0xffffffffLL ? 0xffffffffULL : (unsigned long long)w;
-    work_key[b] = 0xffffffffu - (uint32_t)wc;
+    // descending work order through an ascending sort of a 16-bit complement: the top 16 bits
+    // of the work as a float (exponent and 7 mantissa bits, monotone in w), so two radix passes
+    // order the leaves by work to within 1 part in 128 (equal codes keep Morton order)
+    const uint32_t code = __float_as_uint((float)w) >> 16;
+    work_key[b] = 0xffffu - code;
     order[b] = b;
 }
 
-__global__ void octant_keys(const uint32_t *keys, int64_t n, uint32_t *oct, int *idx) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    oct[i] = keys[i] & 7u;
-    idx[i] = (int)i;
+// Class keys of the boxes of every level, concatenated level after level: (level, child
+// octant) as key, the index within the level as value, so that one stable sort gives every
+// level's boxes in class order.
+struct ClassKeyArgs {
+    const uint32_t *keys[kMaxDepth + 1];
+    long long base[kMaxDepth + 2];   // first row of each level; base[depth + 1] = all rows
+    int depth;
+};
+
+__global__ void class_keys(ClassKeyArgs a, uint32_t *cls_key, int *idx) {
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (r >= a.base[a.depth + 1]) return;
+    int l = 0;
+    while (r >= a.base[l + 1]) ++l;
+    const long long i = r - a.base[l];
+    cls_key[r] = ((uint32_t)l << 3) | (a.keys[l][i] & 7u);
+    idx[r] = (int)i;
 }
 
 }  // namespace
@@ -730,18 +779,25 @@ static cudaError_t build_tree_t(fmm_ctx *ctx, const T *xyz) {
         p2p_work<<<blocks_for(nleaf, 256), 256, 0, s>>>(ctx->leaf_off, ctx->u_off, ctx->u_idx, nleaf,
                                                           wk.p, ctx->p2p_order, ctx->dev_pairs); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
-        FMM_CUDA_TRY(radix_sort(wk.p, ctx->p2p_order, nleaf, 32, s));
+        FMM_CUDA_TRY(radix_sort(wk.p, ctx->p2p_order, nleaf, 16, s));
         ctx->p2p_pairs = -1;
     }
-    // class (octant) order per level >= 1: stable sort by octant, class offsets from the counts
-    for (int l = 1; l <= depth; ++l) {
-        LevelTables &T_ = ctx->lev[l];
-        Scratch<uint32_t> oct;
-        FMM_CUDA_TRY(oct.alloc(T_.n, s));
-        FMM_CUDA_TRY(pool_alloc((void **)&T_.cls_rows, std::max<int64_t>(T_.n, 1) * sizeof(int), s));
-        octant_keys<<<blocks_for(T_.n, 256), 256, 0, s>>>(T_.keys, T_.n, oct.p, T_.cls_rows); count_launch();
+    // class (octant) order of every level at once: one stable sort of all boxes by (level,
+    // octant); level l's part starts at its row base, class offsets come from the counts
+    {
+        ClassKeyArgs a{};
+        for (int l = 0; l <= depth; ++l) a.keys[l] = ctx->lev[l].keys, a.base[l] = ctx->lev[l].row_base;
+        a.base[depth + 1] = ctx->total_rows;
+        a.depth = depth;
+        Scratch<uint32_t> ck;
+        FMM_CUDA_TRY(ck.alloc(ctx->total_rows, s));
+        FMM_CUDA_TRY(pool_alloc((void **)&ctx->cls_all, std::max<int64_t>(ctx->total_rows, 1) * sizeof(int), s));
+        class_keys<<<blocks_for(ctx->total_rows, 256), 256, 0, s>>>(a, ck.p, ctx->cls_all); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
-        FMM_CUDA_TRY(radix_sort(oct.p, T_.cls_rows, T_.n, 3, s));
+        int bits = 3;
+        while ((1 << (bits - 3)) <= depth) ++bits;   // level in the bits above the octant
+        FMM_CUDA_TRY(radix_sort(ck.p, ctx->cls_all, ctx->total_rows, bits, s));
+        for (int l = 1; l <= depth; ++l) ctx->lev[l].cls_rows = ctx->cls_all + ctx->lev[l].row_base;
     }
     return cudaSuccess;
 }
@@ -806,15 +862,29 @@ cudaError_t build_tiles(fmm_ctx *ctx, int tile_m) {
         off += c.count;
     }
     FMM_CUDA_TRY(cudaEventRecord(ctx->tiles_ev, s));
+    // The stencil masks are needed only by the VLI, after the upward pass: they are computed on a
+    // side stream (aux[1]) while the evaluation starts, and every stencil contraction waits for
+    // masks_ev first.
     for (int l = 2; l <= depth; ++l) {
+        TileSet &cl = ctx->tiles_cls[l];
+        if (cl.ntiles) FMM_CUDA_TRY(pool_alloc((void **)&cl.masks, (size_t)cl.ntiles * 6 * sizeof(uint32_t), s));
+    }
+    // (a context without the side stream, a virtual rank's, computes them in stream order)
+    const bool side = ctx->aux[1] && ctx->masks_fork_ev && ctx->masks_ev;
+    cudaStream_t ms = side ? ctx->aux[1] : s;
+    if (side) {
+        FMM_CUDA_TRY(cudaEventRecord(ctx->masks_fork_ev, s));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(ms, ctx->masks_fork_ev, 0));
+    }
+    for (int l = depth; l >= 2; --l) {
         LevelTables &T_ = ctx->lev[l];
         TileSet &cl = ctx->tiles_cls[l];
         if (!cl.ntiles) continue;
-        FMM_CUDA_TRY(pool_alloc((void **)&cl.masks, (size_t)cl.ntiles * 6 * sizeof(uint32_t), s));
-        tile_masks<<<cl.ntiles, 256, 0, s>>>(cl.tiles, cl.ntiles, T_.cls_rows, T_.keys, T_.dense, l,
-                                             ctx->class_delta, cl.masks); count_launch();
+        tile_masks<<<cl.ntiles, 256, 0, ms>>>(cl.tiles, cl.ntiles, T_.cls_rows, T_.keys, T_.dense, l,
+                                              ctx->class_delta, cl.masks); count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
     }
+    if (side) FMM_CUDA_TRY(cudaEventRecord(ctx->masks_ev, ms));
     ctx->tile_m = tile_m;
     return cudaSuccess;
 }

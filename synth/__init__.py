@@ -103,6 +103,9 @@ WORKLOADS = {
     "cube262k_p6_d4": Workload("cube262k_p6_d4", 262_144, "cube", "normal", 6, 4, *CUBE, True),
     "cube33m_p8_d8": Workload("cube33m_p8_d8", 33_554_432, "cube", "u01", 8, 8, *CUBE, True),
     "sphere2m_p6_d6": Workload("sphere2m_p6_d6", 2_097_152, "sphere", "u01", 6, 6, *BALL, True),
+    # p = 8 at a size where both forms of the M2L (dense and FFT) run in a bench step: the scale
+    # case's order and cube family at an eighth of its points and depth 6 (16 points per leaf)
+    "cube4m_p8_d6": Workload("cube4m_p8_d6", 4_194_304, "cube", "u01", 8, 6, *CUBE, True),
 }
 
 

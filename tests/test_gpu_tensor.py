@@ -1,7 +1,7 @@
 """Split-precision tensor-core contractions (tcgen05): BF16x3, BF16x6, TF32x3 and FP16x3 forms of
 the surface contractions and of the M2L, against the FP64 oracle and against the FP32 form.
-FP16x3 runs the M2L stencil on power-of-two scaled FP16 hi/lo splits (~2^-22 per term) and the
-other contractions as BF16x6; its bar is that of BF16x6.
+FP16x3 runs every tensor-core contraction (U2U, the M2L compress, stencil and decompress, D2D) on
+power-of-two scaled FP16 hi/lo splits (~2^-22 per term); its bar is that of BF16x6.
 
 Tolerances: 1e-5 (potentials) and 1e-4 (gradients) relative L2, the bar stated for the FMM,
 for BF16x6 and TF32x3 (22 or more significant bits per operand; measured ~1e-6).  BF16x3 keeps
