@@ -410,6 +410,35 @@ def measure_variants(args, w, fmm, x, q, x_np, q_np, phi, grad, flush, stream, s
                                     "accuracy": acc, "step": "adaptive evaluate on a built tree and adaptive tree"}
     except Exception as e:   # noqa: BLE001
         out["adaptive_q64_fp32"] = {"error": str(e)}
+    try:   # a strongly non-uniform workload, where the adaptive tree holds far fewer boxes than
+        # the uniform one: uniform and adaptive FP32 evaluations of the same depth-9 tree
+        wm = WORKLOADS["mixed1m_p6_d9"]
+        xm_np, qm_np = wm.points(), wm.charges()
+        xm, qm = torch.from_numpy(xm_np).cuda(), torch.from_numpy(qm_np).cuda()
+        pm, gm = torch.empty(wm.n, device="cuda"), torch.empty(wm.n, 3, device="cuda")
+        fa = pkg.FMM(p=wm.p, depth=wm.depth, precision="fp32", domain=(wm.origin, wm.side), stream=stream.cuda_stream)
+        fa.precompute()
+        fa.build_tree(xm)
+        uniform = timed(lambda: fa.evaluate_into(qm, pm, gm))
+        fa.evaluate_into(qm, pm, gm)
+        torch.cuda.synchronize()
+        acc_u = accuracy_check(wm, xm_np, qm_np, pm.cpu().numpy().astype(np.float64),
+                               gm.cpu().numpy().astype(np.float64), m=256)
+        fa.adaptive_setup(64)
+        ms = timed(lambda: fa.adaptive_evaluate_into(qm, pm, gm))
+        fa.adaptive_evaluate_into(qm, pm, gm)
+        torch.cuda.synchronize()
+        acc = accuracy_check(wm, xm_np, qm_np, pm.cpu().numpy().astype(np.float64),
+                             gm.cpu().numpy().astype(np.float64), m=256)
+        info = fa.adaptive_info()
+        fa.close()
+        out["adaptive_mixed1m_d9_q64_fp32"] = {
+            "points_per_s": wm.n / (ms * 1e-3), "ms_per_evaluate": ms, "uniform_fp32_ms_per_evaluate": uniform,
+            "uniform_boxes": int(info["n_rows"]), "adaptive_leaves": int(sum(info["n_leaves"])),
+            "adaptive_refined": int(sum(info["n_refined"])), "accuracy": acc, "uniform_accuracy": acc_u,
+            "step": "evaluate on a built tree and adaptive tree (capacity 64)"}
+    except Exception as e:   # noqa: BLE001
+        out["adaptive_mixed1m_d9_q64_fp32"] = {"error": str(e)}
     return out
 
 

@@ -19,11 +19,14 @@
 // the same-level positions through the dense tables, coarser leaves by walking up from an empty
 // position, and finer boxes by a depth-first walk below each refined colleague.
 //
-// The evaluation over the adaptive tree reuses the uniform far pass (evaluate.cu) with the hooks
-// defined at the end of this file: the VLI reads a dense table of the kept boxes only; boxes below
-// a leaf lose their own VLI output and carry the leaf's local field down by D2D; XLI adds the X
-// lists' sources to the downward check potentials (step 2b); WLI evaluates the upward equivalent
-// densities of the W lists at the leaves' points (step 3a); the ULI runs over the adaptive U lists.
+// The evaluation over the adaptive tree (adaptive_far, FP32/FP64) runs the steps of Algorithm 1
+// over the kept boxes only, through the SIMT GEMMs restricted to per-level box lists: S2U at every
+// leaf at its own level and U2U at the refined boxes (levels D .. 2); at every kept box of level
+// >= 2 the VLI (sources from a dense table of the kept boxes), the decompress with D2D from the
+// parent, and XLI, which adds the X lists' sources to the downward check potentials (step 2b);
+// then the closing and D2T at every leaf of level >= 2 at its own level, and WLI, which evaluates
+// the upward equivalent densities of the W lists at the leaves' points (step 3a).  The ULI runs the
+// packed FP32 near-field kernel of the uniform tree over the adaptive U lists (FP64: uli_kernel).
 #include <algorithm>
 #include <vector>
 
@@ -31,6 +34,19 @@
 #include "fmm_internal.h"
 
 namespace fmm {
+
+// The boxes of one level that the adaptive tree keeps, as index lists (the level's box indices)
+// and the tiles of the SIMT GEMMs over them.
+struct AdaptiveLevel {
+    int *kept = nullptr;        // kept boxes, grouped by octant (class), ascending within a class
+    int *refined = nullptr;     // refined boxes, ascending
+    int *leaves = nullptr;      // leaves, ascending
+    int n_kept = 0, n_refined = 0, n_leaves = 0;
+    int *xlist = nullptr;       // boxes with a non-empty X list, ascending
+    int n_x = 0;
+    TileSet kept_tiles;         // class tiles over `kept` (with the stencil slot masks, levels >= 2)
+    TileSet refined_tiles, leaf_tiles;
+};
 
 struct AdaptiveState {
     int capacity = 0;
@@ -41,6 +57,11 @@ struct AdaptiveState {
     int *idx[4] = {};                      // U, V, W, X members (rows)
     int64_t entries[4] = {};
     std::vector<int> host_state;           // copy of state, for the summary counts
+    int *uli_order = nullptr;              // [rows] the leaves in decreasing ULI work, then the other rows
+    int uli_leaves = 0;                    // leaves at the head of uli_order
+    AdaptiveLevel lv[kMaxDepth + 1];       // per level: the far pass's box lists and tiles
+    int *wlist = nullptr;                  // rows with a non-empty W list, ascending
+    int n_w = 0;
     int *begin = nullptr;                  // [rows] first sorted point of each box
     int *dense_kept[kMaxDepth + 1] = {};   // levels >= 2: the level's dense table without unkept boxes
     // evaluation workspaces (allocated by the first evaluation)
@@ -275,16 +296,17 @@ __device__ inline void box_centre(uint32_t key, double ox, double oy, double oz,
 }
 
 // XLI (Algorithm 1, step 2b): the sources of every leaf in X(b) on the downward check surface
-// (1.05) of b, added to b's downward check potentials.  One block per box of the level.
+// (1.05) of b, added to b's downward check potentials.  One block per box of the level with a
+// non-empty X list (`list`, the level's box indices).
 template <typename T>
 __global__ void __launch_bounds__(kEvalThreads)
 xli_kernel(const typename Pt4<T>::type *__restrict__ pts, const uint32_t *__restrict__ keys, int base,
            const int *__restrict__ x_off, const int *__restrict__ x_idx, const int *__restrict__ begin,
            const int *__restrict__ count, const T *__restrict__ grid, int ns, double ox, double oy, double oz,
-           double width, double radius, T *__restrict__ D, int ld) {
+           double width, double radius, T *__restrict__ D, int ld, const int *__restrict__ list) {
     using P = typename Pt4<T>::type;
     __shared__ P src[kEvalChunk];
-    const int b = blockIdx.x, r = base + b;
+    const int b = list[blockIdx.x], r = base + b;
     const int m0 = x_off[r], m1 = x_off[r + 1];
     if (m0 == m1) return;
     double c[3];
@@ -318,16 +340,17 @@ xli_kernel(const typename Pt4<T>::type *__restrict__ pts, const uint32_t *__rest
 }
 
 // WLI (Algorithm 1, step 3a): the upward equivalent densities (1.05 surface) of every box in
-// W(b) evaluated at the points of leaf b, added to the far-field outputs.  One block per row.
+// W(b) evaluated at the points of leaf b, added to the far-field outputs.  One block per row with
+// a non-empty W list (`list`).
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kEvalThreads)
 wli_kernel(const typename Pt4<T>::type *__restrict__ pts, Levels L, const int *__restrict__ w_off,
            const int *__restrict__ w_idx, const int *__restrict__ begin, const int *__restrict__ count,
            const T *__restrict__ grid, int ns, double ox, double oy, double oz, double side,
-           const T *__restrict__ ue, int ldu, T *__restrict__ phi, T *__restrict__ grad) {
+           const T *__restrict__ ue, int ldu, T *__restrict__ phi, T *__restrict__ grad, const int *__restrict__ list) {
     using P = typename Pt4<T>::type;
     __shared__ P src[kMaxSurface];
-    const int r = blockIdx.x;
+    const int r = list[blockIdx.x];
     const int m0 = w_off[r], m1 = w_off[r + 1];
     if (m0 == m1) return;
     const int t0 = begin[r], t1 = t0 + count[r];
@@ -421,12 +444,22 @@ uli_kernel(const typename Pt4<T>::type *__restrict__ pts, const int *__restrict_
     }
 }
 
-// zero the rows of a level's boxes that the adaptive tree does not keep
-template <typename T>
-__global__ void zero_unkept_kernel(T *rows, int ld, int width, const int *state, int n) {
-    const int b = blockIdx.x, j = threadIdx.x;
-    if (b < n && state[b] == 0)
-        for (int k = j; k < width; k += blockDim.x) rows[(size_t)b * ld + k] = (T)0;
+// ULI schedule key of every row: a leaf gets the complement of the top 16 bits of its work
+// |b| * sum_{a in U(b)} |a| as a float (monotone in the work, so an ascending stable sort puts
+// the leaves first in decreasing work), every other row 0xffff, above any leaf's key
+__global__ void uli_work_kernel(int rows, const int *state, const int *count, const int *u_off, const int *u_idx,
+                                uint32_t *key, int *order) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    uint32_t k = 0xffffu;
+    if (state[r] == 1) {
+        long long src = 0;
+        for (int m = u_off[r]; m < u_off[r + 1]; ++m) src += count[u_idx[m]];
+        const long long w = src * (long long)count[r];
+        k = 0xffffu - (__float_as_uint((float)(w > 1 ? w : 1)) >> 16);
+    }
+    key[r] = k;
+    order[r] = r;
 }
 
 Levels make_levels(const fmm_ctx *ctx) {
@@ -448,6 +481,77 @@ unsigned grid_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n +
 fmm_status afail(fmm_ctx *ctx, fmm_status st, const std::string &m) {
     ctx->err = m;
     return st;
+}
+
+constexpr int kAdaptTile = 64;   // rows per tile of the far pass's GEMMs (the SIMT form's)
+
+template <typename V>
+cudaError_t upload_vec(const std::vector<V> &h, V **d) {
+    if (h.empty()) return cudaSuccess;
+    FMM_CUDA_TRY(dev_malloc(d, h.size() * sizeof(V)));
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+}
+
+// Per level, from the host copy of the states: the kept boxes in class order, the refined boxes
+// and the leaves, with their tiles; the stencil slot masks of the kept tiles against the kept
+// boxes' dense table.
+cudaError_t build_levels(fmm_ctx *ctx, AdaptiveState *A) {
+    cudaStream_t s = ctx->stream;
+    const int D = ctx->opt.depth;
+    std::vector<int> w_off(A->rows + 1), x_off(A->rows + 1), wl;
+    FMM_CUDA_TRY(cudaMemcpy(w_off.data(), A->off[2], (A->rows + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    FMM_CUDA_TRY(cudaMemcpy(x_off.data(), A->off[3], (A->rows + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t r = 0; r < A->rows; ++r)
+        if (w_off[r + 1] > w_off[r]) wl.push_back((int)r);
+    A->n_w = (int)wl.size();
+    FMM_CUDA_TRY(upload_vec(wl, &A->wlist));
+    for (int l = 0; l <= D; ++l) {
+        const LevelTables &T = ctx->lev[l];
+        AdaptiveLevel &L = A->lv[l];
+        const int n = (int)T.n;
+        std::vector<uint32_t> keys(std::max(n, 1));
+        if (n) FMM_CUDA_TRY(cudaMemcpy(keys.data(), T.keys, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        const int *st = A->host_state.data() + T.row_base;
+        std::vector<int> kept, refined, leaves, xl;
+        std::vector<Tile> kt, rt, lt;
+        for (int b = 0; b < n; ++b)
+            if (x_off[T.row_base + b + 1] > x_off[T.row_base + b]) xl.push_back(b);
+        L.n_x = (int)xl.size();
+        FMM_CUDA_TRY(upload_vec(xl, &L.xlist));
+        for (int c = 0; c < 8; ++c) {
+            const size_t c0 = kept.size();
+            for (int b = 0; b < n; ++b)
+                if (st[b] != 0 && (l == 0 ? c == 0 : (int)(keys[b] & 7u) == c)) kept.push_back(b);
+            for (size_t r = c0; r < kept.size(); r += kAdaptTile)
+                kt.push_back(Tile{(int)r, (int)std::min<size_t>(kAdaptTile, kept.size() - r), c, (int)kt.size()});
+        }
+        for (int b = 0; b < n; ++b) {
+            if (st[b] == 2) refined.push_back(b);
+            if (st[b] == 1) leaves.push_back(b);
+        }
+        auto plain = [](const std::vector<int> &v, std::vector<Tile> &t) {
+            for (size_t r = 0; r < v.size(); r += kAdaptTile)
+                t.push_back(Tile{(int)r, (int)std::min<size_t>(kAdaptTile, v.size() - r), -1, 0});
+        };
+        plain(refined, rt);
+        plain(leaves, lt);
+        L.n_kept = (int)kept.size(), L.n_refined = (int)refined.size(), L.n_leaves = (int)leaves.size();
+        FMM_CUDA_TRY(upload_vec(kept, &L.kept));
+        FMM_CUDA_TRY(upload_vec(refined, &L.refined));
+        FMM_CUDA_TRY(upload_vec(leaves, &L.leaves));
+        for (auto [ts, h] : {std::pair<TileSet *, std::vector<Tile> *>{&L.kept_tiles, &kt}, {&L.refined_tiles, &rt},
+                             {&L.leaf_tiles, &lt}}) {
+            ts->ntiles = (int)h->size();
+            ts->tile_m = kAdaptTile;
+            FMM_CUDA_TRY(upload_vec(*h, &ts->tiles));
+        }
+        if (l >= 2 && L.kept_tiles.ntiles) {
+            FMM_CUDA_TRY(dev_malloc(&L.kept_tiles.masks, (size_t)L.kept_tiles.ntiles * 6 * sizeof(uint32_t)));
+            FMM_CUDA_TRY(launch_tile_masks(L.kept_tiles.tiles, L.kept_tiles.ntiles, L.kept, T.keys, A->dense_kept[l], l,
+                                           ctx->class_delta, L.kept_tiles.masks, s));
+        }
+    }
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
@@ -527,12 +631,25 @@ cudaError_t build(fmm_ctx *ctx, AdaptiveState *A) {
         count_launch();
     }
     FMM_CUDA_TRY(cudaGetLastError());
+    // ULI schedule
+    {
+        Scratch<uint32_t> key;
+        FMM_CUDA_TRY(key.alloc(rows, s));
+        FMM_CUDA_TRY(dev_malloc(&A->uli_order, rows * sizeof(int)));
+        uli_work_kernel<<<grid_for(rows, 256), 256, 0, s>>>((int)rows, A->state, A->count, A->off[0], A->idx[0], key.p,
+                                                            A->uli_order);
+        count_launch();
+        FMM_CUDA_TRY(cudaGetLastError());
+        FMM_CUDA_TRY(stable_sort_by_key(key.p, A->uli_order, rows, 16, s));
+    }
     int hflag = 0;
     A->host_state.resize(rows);
     FMM_CUDA_TRY(cudaMemcpyAsync(A->host_state.data(), A->state, rows * sizeof(int), cudaMemcpyDeviceToHost, s));
     FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
-    return hflag ? cudaErrorInvalidValue : cudaSuccess;
+    A->uli_leaves = (int)std::count(A->host_state.begin(), A->host_state.end(), 1);
+    if (hflag) return cudaErrorInvalidValue;
+    return build_levels(ctx, A);
 }
 
 }  // namespace
@@ -551,6 +668,13 @@ void adaptive_free(fmm_ctx *ctx) {
     for (int l = 0; l <= kMaxDepth; ++l) cudaFree(A->dense_kept[l]);
     cudaFree(A->ue);
     cudaFree(A->y1);
+    cudaFree(A->uli_order);
+    cudaFree(A->wlist);
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        AdaptiveLevel &L = A->lv[l];
+        cudaFree(L.kept), cudaFree(L.refined), cudaFree(L.leaves), cudaFree(L.xlist);
+        for (TileSet *ts : {&L.kept_tiles, &L.refined_tiles, &L.leaf_tiles}) cudaFree(ts->tiles), cudaFree(ts->masks);
+    }
     delete A;
     ctx->adaptive = nullptr;
 }
@@ -629,28 +753,17 @@ fmm_status adaptive_info(fmm_ctx *ctx, int32_t *capacity, int64_t *leaves, int64
 
 // ---- evaluation hooks (called by run_far and run_evaluate while an adaptive evaluation runs) ----
 
-const int *adaptive_dense(const fmm_ctx *ctx, int level) { return ctx->adaptive->dense_kept[level]; }
-
-template <typename T>
-cudaError_t adaptive_zero_unkept(const fmm_ctx *ctx, int level, T *rows, int ld, int width, cudaStream_t s) {
-    const LevelTables &T_ = ctx->lev[level];
-    if (T_.n == 0) return cudaSuccess;
-    zero_unkept_kernel<T><<<(unsigned)T_.n, 128, 0, s>>>(rows, ld, width, ctx->adaptive->state + T_.row_base,
-                                                         (int)T_.n);
-    count_launch();
-    return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t adaptive_xli(const fmm_ctx *ctx, int level, T *D, int ld, cudaStream_t s) {
     const AdaptiveState *A = ctx->adaptive;
     const LevelTables &T_ = ctx->lev[level];
-    if (T_.n == 0 || A->entries[3] == 0) return cudaSuccess;
+    const AdaptiveLevel &L = A->lv[level];
+    if (L.n_x == 0) return cudaSuccess;
     const double width = ctx->side / (double)(1 << level);
-    xli_kernel<T><<<(unsigned)T_.n, kEvalThreads, 0, s>>>(
+    xli_kernel<T><<<(unsigned)L.n_x, kEvalThreads, 0, s>>>(
         (const typename Pt4<T>::type *)ctx->pts, T_.keys, (int)T_.row_base, A->off[3], A->idx[3], A->begin, A->count,
         (const T *)ctx->grid_dev, ctx->npts, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, 1.05 * 0.5 * width,
-        D, ld);
+        D, ld, L.xlist);
     count_launch();
     return cudaGetLastError();
 }
@@ -659,29 +772,33 @@ template <typename T>
 cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     AdaptiveState *A = ctx->adaptive;
     const int D = ctx->opt.depth;
-    if (A->entries[2] == 0 || D < 2) return cudaSuccess;
+    if (A->n_w == 0 || D < 2) return cudaSuccess;
     if (ctx->npts > kMaxSurface) return cudaErrorInvalidValue;   // p <= 10 is checked at fmm_create
     const int nsp = ctx->nsp;
-    // upward equivalent densities of every box of levels 2..D: r_l (V S^-1)(U^T U_l)
+    // upward equivalent densities of the kept boxes of levels 2..D: r_l (V S^-1)(U^T U_l)
     for (int l = 2; l <= D; ++l) {
+        const AdaptiveLevel &L = A->lv[l];
+        if (!L.n_kept) continue;
         const OpSet &o = ctx->fwd[l];
         GemmCall c1;
         c1.mode = GM_IDENTITY, c1.level = l, c1.n_out = o.rclup;
         c1.X0 = (T *)ctx->Uc + (size_t)ctx->lev[l].row_base * nsp, c1.ldx0 = nsp, c1.k0 = nsp, c1.W0 = o.uclose1;
         c1.Y = A->y1, c1.ldy = o.rclup;
+        c1.tiles = &L.kept_tiles, c1.rows = L.kept;
         FMM_CUDA_TRY(gemm_simt<T>(ctx, c1, s));
         GemmCall c2;
         c2.mode = GM_IDENTITY, c2.level = l, c2.n_out = nsp, c2.alpha = ctx->side / (double)(1 << l) * 0.5;
         c2.X0 = A->y1, c2.ldx0 = o.rclup, c2.k0 = o.rclup, c2.W0 = o.uclose2;
         c2.Y = (T *)A->ue + (size_t)ctx->lev[l].row_base * nsp, c2.ldy = nsp;
+        c2.tiles = &L.kept_tiles, c2.rows = L.kept;
         FMM_CUDA_TRY(gemm_simt<T>(ctx, c2, s));
     }
     const Levels L = make_levels(ctx);
     auto go = [&](auto kern, T *g) {
-        kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, L, A->off[2], A->idx[2],
-                                                        A->begin, A->count, (const T *)ctx->grid_dev, ctx->npts,
-                                                        ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->side,
-                                                        (const T *)A->ue, nsp, phi, g);
+        kern<<<(unsigned)A->n_w, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, L, A->off[2], A->idx[2],
+                                                       A->begin, A->count, (const T *)ctx->grid_dev, ctx->npts,
+                                                       ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->side,
+                                                       (const T *)A->ue, nsp, phi, g, A->wlist);
     };
     grad ? go(wli_kernel<T, true>, grad) : go(wli_kernel<T, false>, nullptr);
     count_launch();
@@ -691,6 +808,9 @@ cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
 template <typename T>
 cudaError_t adaptive_uli(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     const AdaptiveState *A = ctx->adaptive;
+    if constexpr (sizeof(T) == 4)   // the packed FP32 kernel of the uniform tree, over the leaves' rows
+        return launch_p2p_rows_f32((const float4 *)ctx->pts, A->begin, A->count, A->off[0], A->idx[0], A->uli_order,
+                                   A->uli_leaves, (float *)phi, (float *)grad, s);
     auto go = [&](auto kern) {
         kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, A->state, A->off[0],
                                                         A->idx[0], A->begin, A->count, phi, grad);
@@ -731,8 +851,107 @@ fmm_status adaptive_prepare(fmm_ctx *ctx) {
     return FMM_OK;
 }
 
+// The far field over the adaptive tree (forward, FP32/FP64): far_phi / far_grad (sorted order)
+// receive D2T and WLI of every point.
+template <typename T>
+cudaError_t adaptive_far(fmm_ctx *ctx, T *far_phi, T *far_grad, cudaStream_t s) {
+    const AdaptiveState *A = ctx->adaptive;
+    const int D = ctx->opt.depth, nsp = ctx->nsp, kw = ctx->ws_kw;
+    const T *grid = (const T *)ctx->grid_dev;
+    auto at = [&](void *base, int l, int ld) { return (T *)base + (size_t)ctx->lev[l].row_base * ld; };
+    auto restrict_to = [](GemmCall &c, const TileSet &ts, const int *rows) { c.tiles = &ts, c.rows = rows; };
+    // upward pass (step 1), levels D .. 2: S2U at the leaves of the level, U2U at its refined boxes
+    for (int l = D; l >= 2; --l) {
+        const AdaptiveLevel &L = A->lv[l];
+        const int64_t rb = ctx->lev[l].row_base;
+        FMM_CUDA_TRY(launch_leaf_check_rows<T>(ctx, l, L.leaves, L.n_leaves, A->begin + rb, A->count + rb, grid,
+                                               at(ctx->Uc, l, nsp), s));
+        if (l == D) cudaEventRecord(ctx->ev[2], s);
+        if (l < D && L.n_refined) {
+            GemmCall c;
+            c.mode = GM_CHILDREN, c.level = l, c.n_out = nsp;
+            c.X0 = at(ctx->Uc, l + 1, nsp), c.ldx0 = nsp, c.k0 = nsp;
+            c.W0 = ctx->fwd[l].up[0], c.w_stride = (int64_t)nsp * nsp;
+            c.Y = at(ctx->Uc, l, nsp), c.ldy = nsp;
+            restrict_to(c, L.refined_tiles, L.refined);
+            FMM_CUDA_TRY(gemm_simt<T>(ctx, c, s));
+        }
+    }
+    cudaEventRecord(ctx->ev[3], s);
+    // downward pass (step 2), levels 2 .. D at the kept boxes: the VLI compress and stencil of
+    // every level on the level's own stream (over the kept sources), then, level after level,
+    // the decompress with D2D from the parent and XLI
+    FMM_CUDA_TRY(cudaEventRecord(ctx->fork_ev[0], s));
+    for (int l = 2; l <= D; ++l) {
+        const AdaptiveLevel &L = A->lv[l];
+        cudaStream_t ls = ctx->aux[l];
+        FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
+        if (L.n_kept) {
+            const OpSet &o = ctx->fwd[l];
+            GemmCall c;
+            c.mode = GM_IDENTITY, c.level = l, c.n_out = o.kinp;
+            c.X0 = at(ctx->Uc, l, nsp), c.ldx0 = nsp, c.k0 = nsp, c.W0 = o.compress;
+            c.Y = at(ctx->Ut, l, kw), c.ldy = kw;
+            restrict_to(c, L.kept_tiles, L.kept);
+            FMM_CUDA_TRY(gemm_simt<T>(ctx, c, ls));
+            GemmCall st;
+            st.mode = GM_STENCIL, st.level = l, st.n_out = o.koutp;
+            st.X0 = at(ctx->Ut, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
+            st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
+            st.Y = at(ctx->Ct, l, kw), st.ldy = kw;
+            st.dense = A->dense_kept[l];
+            restrict_to(st, L.kept_tiles, L.kept);
+            FMM_CUDA_TRY(gemm_simt<T>(ctx, st, ls));
+        }
+        FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
+    }
+    for (int l = 2; l <= D; ++l) {
+        const AdaptiveLevel &L = A->lv[l];
+        FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
+        if (!L.n_kept) continue;
+        const OpSet &o = ctx->fwd[l];
+        GemmCall dn;
+        dn.mode = GM_PARENT2, dn.level = l, dn.n_out = nsp;
+        dn.X0 = at(ctx->Ct, l, kw), dn.ldx0 = kw, dn.k0 = o.koutp, dn.W0 = o.decompress;
+        if (l >= 3) {
+            dn.X1 = at(ctx->Dc, l - 1, nsp), dn.ldx1 = nsp, dn.k1 = nsp;
+            dn.W1_by_cls = ctx->fwd[l - 1].down;
+        }
+        dn.Y = at(ctx->Dc, l, nsp), dn.ldy = nsp;
+        restrict_to(dn, L.kept_tiles, L.kept);
+        FMM_CUDA_TRY(gemm_simt<T>(ctx, dn, s));
+        FMM_CUDA_TRY(adaptive_xli<T>(ctx, l, at(ctx->Dc, l, nsp), nsp, s));
+    }
+    cudaEventRecord(ctx->ev[4], s);
+    // leaf evaluation (step 3): closing and D2T at every leaf of level >= 2 (leaves of levels 0
+    // and 1 have no far field), then WLI
+    if (far_phi) FMM_CUDA_TRY(cudaMemsetAsync(far_phi, 0, (size_t)ctx->n * sizeof(T), s));
+    if (far_grad) FMM_CUDA_TRY(cudaMemsetAsync(far_grad, 0, (size_t)ctx->n * 3 * sizeof(T), s));
+    for (int l = 2; l <= D; ++l) {
+        const AdaptiveLevel &L = A->lv[l];
+        if (!L.n_leaves) continue;
+        const OpSet &o = ctx->fwd[l];
+        const int64_t rb = ctx->lev[l].row_base;
+        GemmCall c1;
+        c1.mode = GM_IDENTITY, c1.level = l, c1.n_out = o.rclp;
+        c1.X0 = at(ctx->Dc, l, nsp), c1.ldx0 = nsp, c1.k0 = nsp, c1.W0 = o.close1;
+        c1.Y = ctx->Yc, c1.ldy = o.rclp;
+        restrict_to(c1, L.leaf_tiles, L.leaves);
+        FMM_CUDA_TRY(gemm_simt<T>(ctx, c1, s));
+        GemmCall c2;
+        c2.mode = GM_IDENTITY, c2.level = l, c2.n_out = nsp, c2.alpha = ctx->side / (double)(1 << l) * 0.5;
+        c2.X0 = ctx->Yc, c2.ldx0 = o.rclp, c2.k0 = o.rclp, c2.W0 = o.close2;
+        c2.Y = ctx->Dq, c2.ldy = nsp;
+        restrict_to(c2, L.leaf_tiles, L.leaves);
+        FMM_CUDA_TRY(gemm_simt<T>(ctx, c2, s));
+        FMM_CUDA_TRY(launch_leaf_eval_rows<T>(ctx, l, L.leaves, L.n_leaves, A->begin + rb, A->count + rb, grid,
+                                              (const T *)ctx->Dq, nsp, far_phi, far_grad, s));
+    }
+    return adaptive_wli<T>(ctx, far_phi, far_grad, s);
+}
+
 #define FMM_ADAPTIVE_INST(T)                                                                          \
-    template cudaError_t adaptive_zero_unkept<T>(const fmm_ctx *, int, T *, int, int, cudaStream_t); \
+    template cudaError_t adaptive_far<T>(fmm_ctx *, T *, T *, cudaStream_t);                          \
     template cudaError_t adaptive_xli<T>(const fmm_ctx *, int, T *, int, cudaStream_t);               \
     template cudaError_t adaptive_wli<T>(fmm_ctx *, T *, T *, cudaStream_t);                          \
     template cudaError_t adaptive_uli<T>(const fmm_ctx *, T *, T *, cudaStream_t);

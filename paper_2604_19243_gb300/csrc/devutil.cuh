@@ -89,4 +89,15 @@ __device__ inline int dense_find(const int *dense, int level, int ax, int ay, in
 template <typename T>
 cudaError_t exclusive_scan(T *d, int64_t n, T *d_total, cudaStream_t s);
 
+// Stable LSD radix sort of (keys, vals) by the low `bits` bits of the keys, results in place
+// (scratch from the stream-ordered pool).
+cudaError_t stable_sort_by_key(uint32_t *keys, int *vals, int64_t n, int bits, cudaStream_t s);
+
+// Stencil slot masks of class-ordered tiles (Tile.row0 + r indexes `rows`, the level's box indices;
+// Tile.mask is the tile's index): bit s of masks[tile * 6 + s / 32] is set when a row of the tile
+// has a source box in `dense` for class slot s.
+struct Tile;
+cudaError_t launch_tile_masks(const Tile *tiles, int ntiles, const int *rows, const uint32_t *keys, const int *dense,
+                              int level, const int *class_delta, uint32_t *masks, cudaStream_t s);
+
 }  // namespace fmm

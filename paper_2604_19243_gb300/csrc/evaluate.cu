@@ -36,7 +36,7 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c) {
     g.Y = c.Y, g.ldy = c.ldy;
     const LevelTables &L = ctx->lev[c.level];
     const bool cls = c.mode == GM_STENCIL || c.mode == GM_PARENT2;
-    g.rows = cls ? L.cls_rows : nullptr;
+    g.rows = c.rows ? c.rows : cls ? L.cls_rows : nullptr;
     g.child = L.child;
     g.parent = L.parent;
     g.keys = L.keys;
@@ -192,7 +192,6 @@ cudaError_t FarSteps<T>::stencil(int l, cudaStream_t s) {
     st.X0 = rows_at<T>(ctx->Ut, ctx, l, kw), st.ldx0 = kw, st.k0 = o.kinp;
     st.W0 = o.stencil, st.w_stride = (int64_t)o.koutp * o.kinp;
     st.Y = rows_at<T>(ctx->Ct, ctx, l, kw), st.ldy = kw;
-    if (ctx->adaptive_eval) st.dense = adaptive_dense(ctx, l);   // V lists of the adaptive tree
     if (ctx->tensor) {
         st.Xp = utP(l), st.xp_ld = kw, st.xp_rows = (int)ctx->lev[l].n, st.xp_plane = ctx->utp_plane;
         st.xp_scale = utS(l), st.xp_scale_ld = nck_k;
@@ -286,6 +285,7 @@ cudaError_t run_far_fft(fmm_ctx *ctx, FarSteps<T> &f, T *far_phi, T *far_grad, c
 
 template <typename T>
 cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStream_t s) {
+    if (ctx->adaptive_eval) return adaptive_far<T>(ctx, far_phi, far_grad, s);   // forward only
     FarSteps<T> f(ctx, adjoint);
     const int d = f.d;
     if (ctx->fft) {
@@ -307,20 +307,14 @@ cudaError_t run_far(fmm_ctx *ctx, bool adjoint, T *far_phi, T *far_grad, cudaStr
         FMM_CUDA_TRY(cudaStreamWaitEvent(ls, ctx->fork_ev[0], 0));
         FMM_CUDA_TRY(f.compress(l, ls));
         FMM_CUDA_TRY(f.stencil(l, ls));
-        // adaptive tree: boxes below a leaf take no VLI of their own; their downward rows carry
-        // the leaf's local field down by D2D alone
-        if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_zero_unkept<T>(ctx, l, rows_at<T>(ctx->Ct, ctx, l, f.kw), f.kw, f.kw, ls));
         FMM_CUDA_TRY(cudaEventRecord(ctx->join_ev[l], ls));
     }
     for (int l = 2; l <= d; ++l) {
         FMM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
         if (l == d) cudaEventRecord(ctx->ev[4], s);
         FMM_CUDA_TRY(f.down(l, s));
-        if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_xli<T>(ctx, l, rows_at<T>(f.B, ctx, l, f.nsp), f.nsp, s));
     }
-    FMM_CUDA_TRY(f.leaf_out(far_phi, far_grad, s));
-    if (ctx->adaptive_eval) FMM_CUDA_TRY(adaptive_wli<T>(ctx, far_phi, far_grad, s));
-    return cudaSuccess;
+    return f.leaf_out(far_phi, far_grad, s);
 }
 
 template struct FarSteps<float>;

@@ -65,8 +65,7 @@ fft_fwd_kernel(FftShape sh, const T *__restrict__ u, int ldu, const int *__restr
     for (int e = tid; e < p * p * nh; e += blockDim.x) {
         const int kc = e % nh, ab = e / nh;
         V s = {(T)0, (T)0};
-        for (int c = 0; c < p; ++c) {
-            const int w = (c * kc) % n;
+        for (int c = 0, w = 0; c < p; ++c, w = w + kc < n ? w + kc : w + kc - n) {   // w = c kc mod n
             const T v = g[ab * p + c];
             s.x += v * wr[w], s.y += v * wi[w];
         }
@@ -77,8 +76,7 @@ fft_fwd_kernel(FftShape sh, const T *__restrict__ u, int ldu, const int *__restr
     for (int e = tid; e < p * n * nh; e += blockDim.x) {
         const int kc = e % nh, kb = (e / nh) % n, a = e / (nh * n);
         V s = {(T)0, (T)0};
-        for (int bb = 0; bb < p; ++bb) {
-            const int w = (bb * kb) % n;
+        for (int bb = 0, w = 0; bb < p; ++bb, w = w + kb < n ? w + kb : w + kb - n) {
             const V v = x1[(a * p + bb) * nh + kc];
             s.x += v.x * wr[w] - v.y * wi[w], s.y += v.x * wi[w] + v.y * wr[w];
         }
@@ -91,8 +89,7 @@ fft_fwd_kernel(FftShape sh, const T *__restrict__ u, int ldu, const int *__restr
     for (int e = tid; e < nka * per; e += blockDim.x) {
         const int ka = ka0 + e / per, r = e % per;
         V s = {(T)0, (T)0};
-        for (int a = 0; a < p; ++a) {
-            const int w = (a * ka) % n;
+        for (int a = 0, w = 0; a < p; ++a, w = w + ka < n ? w + ka : w + ka - n) {
             const V v = x2[a * per + r];
             s.x += v.x * wr[w] - v.y * wi[w], s.y += v.x * wi[w] + v.y * wr[w];
         }
@@ -100,48 +97,93 @@ fft_fwd_kernel(FftShape sh, const T *__restrict__ u, int ldu, const int *__restr
     }
 }
 
-// ĉ[β] = sum over the V list of β of Ĝ_t ⊙ û[α], for this chunk's frequencies.  One warp per
-// target; the V list is walked through the class slots of the target's octant and the level's
-// dense table (the stencil's source rule), in slot order.
-constexpr int kHadMax = 8;         // chunk frequencies per lane (chunk <= 256)
+// ĉ[β] = sum over the V list of β of Ĝ_t ⊙ û[α], for this chunk's frequencies.  The V list of a
+// child of parent P is the children of P's 26 neighbours that are not adjacent to it, and the
+// transfer vector of (target octant c, neighbour offset o, source octant c') is 2o + c' - c in
+// child units, the same for every parent (table `pairs`: index t of Ĝ_t, or -1 when adjacent).
+// A CTA takes kHadG consecutive parents and one slice of 32 consecutive frequencies: Ĝ of the
+// slice for all 316 transfer vectors is staged in shared memory; warp g owns parent g, lane j
+// frequency j of the slice, and the thread keeps the 8 children's sums in registers.  Each
+// source value is then read from memory once per parent and applied to all 8 targets.
+constexpr int kHadG = 16;          // parents (warps) per CTA
+constexpr int kHadF = 32;          // frequencies per CTA
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-fft_hadamard_kernel(const typename C2<T>::type *__restrict__ uh, const typename C2<T>::type *__restrict__ ghat,
-                    long long ghat_stride, int chunk, const uint32_t *__restrict__ keys, const int *__restrict__ dense,
-                    int level, const int *__restrict__ class_slots, const int *__restrict__ class_delta, int nbox,
-                    typename C2<T>::type *__restrict__ ch) {
+__global__ void __launch_bounds__(kHadG * 32)
+fft_hadamard_kernel(const typename C2<T>::type *__restrict__ uh, long long row, int nfreq,
+                    const typename C2<T>::type *__restrict__ ghat, long long ghat_stride,
+                    const uint32_t *__restrict__ pkeys, const int *__restrict__ pdense, const int *__restrict__ pchild,
+                    int plevel, int nparent, const int *__restrict__ pairs, typename C2<T>::type *__restrict__ ch) {
     using V = typename C2<T>::type;
-    const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-    if (b >= nbox) return;
-    const uint32_t key = keys[b];
-    int ax, ay, az;
-    demorton3(key, ax, ay, az);
-    const int cls = key & 7u;
-    V acc[kHadMax];
+    extern __shared__ unsigned char fft_smem[];
+    V *gs = reinterpret_cast<V *>(fft_smem);   // [316][32]: Ĝ_t of this slice
+    __shared__ int src[kHadG][26][8];          // children of each parent's neighbours (-1: none)
+    __shared__ int tgt[kHadG][8];              // children of each parent
+    __shared__ int tt[26 * 8 * 8];             // transfer index of (o, c', c), -1 when adjacent
+    const int tid = threadIdx.x, g = tid >> 5, lane = tid & 31;
+    const int p0 = blockIdx.x * kHadG, f0 = blockIdx.y * kHadF, f = f0 + lane;
+    const bool fl = f < nfreq;
+    for (int i = tid; i < 26 * 64; i += blockDim.x) tt[i] = pairs[i];
+    constexpr int kU = 8;   // staging loads in flight per thread
+    for (int i0 = tid; i0 < kNumTransfer * kHadF; i0 += kU * kHadG * 32) {
+        V v[kU];
 #pragma unroll
-    for (int i = 0; i < kHadMax; ++i) acc[i] = {(T)0, (T)0};
-    for (int s = 0; s < kClassSlots; ++s) {
-        int dx, dy, dz;
-        unpack_delta(class_delta[cls * kClassSlots + s], dx, dy, dz);
-        const int src = dense_find(dense, level, ax + dx, ay + dy, az + dz);
-        if (src < 0) continue;
-        const V *gt = ghat + (long long)class_slots[cls * kClassSlots + s] * ghat_stride;
-        const V *us = uh + (size_t)src * chunk;
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * kHadG * 32, t = i / kHadF, j = i % kHadF;
+            v[u] = (i < kNumTransfer * kHadF && f0 + j < nfreq) ? ghat[(long long)t * ghat_stride + f0 + j]
+                                                                : V{(T)0, (T)0};
+        }
 #pragma unroll
-        for (int i = 0; i < kHadMax; ++i) {
-            const int f = lane + 32 * i;
-            if (f < chunk) {
-                const V gv = gt[f], uv = us[f];
-                acc[i].x += gv.x * uv.x - gv.y * uv.y;
-                acc[i].y += gv.x * uv.y + gv.y * uv.x;
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * kHadG * 32 < kNumTransfer * kHadF) gs[i0 + u * kHadG * 32] = v[u];
+    }
+    for (int e = tid; e < kHadG * 8; e += blockDim.x) {
+        const int gg = e / 8, c = e % 8, P = p0 + gg;
+        tgt[gg][c] = P < nparent ? pchild[(size_t)P * 8 + c] : -1;
+    }
+    for (int e = tid; e < kHadG * 26; e += blockDim.x) {
+        const int gg = e / 26, oi = e % 26, P = p0 + gg;
+        const int o = oi < 13 ? oi : oi + 1;   // offsets of [-1,1]^3 without the centre
+        int nb = -1;
+        if (P < nparent) {
+            int ax, ay, az;
+            demorton3(pkeys[P], ax, ay, az);
+            nb = dense_find(pdense, plevel, ax + o / 9 - 1, ay + (o / 3) % 3 - 1, az + o % 3 - 1);
+        }
+        for (int c = 0; c < 8; ++c) src[gg][oi][c] = nb >= 0 ? pchild[(size_t)nb * 8 + c] : -1;
+    }
+    __syncthreads();
+    if (p0 + g >= nparent) return;
+    V acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = {(T)0, (T)0};
+    for (int oi = 0; oi < 26; ++oi) {
+        V u[8];
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2) {
+            const int sb = src[g][oi][c2];
+            u[c2] = (sb >= 0 && fl) ? uh[(long long)sb * row + f] : V{(T)0, (T)0};
+        }
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2) {
+            if (src[g][oi][c2] < 0) continue;
+            const int *tp = tt + (oi * 8 + c2) * 8;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int t = tp[c];
+                if (t < 0) continue;   // adjacent to the target: near field, not V
+                const V gv = gs[t * kHadF + lane];
+                acc[c].x += gv.x * u[c2].x - gv.y * u[c2].y;
+                acc[c].y += gv.x * u[c2].y + gv.y * u[c2].x;
             }
         }
     }
-    V *o = ch + (size_t)b * chunk;
+    if (!fl) return;
 #pragma unroll
-    for (int i = 0; i < kHadMax; ++i)
-        if (lane + 32 * i < chunk) o[lane + 32 * i] = acc[i];
+    for (int c = 0; c < 8; ++c) {
+        const int tb = tgt[g][c];
+        if (tb >= 0) ch[(long long)tb * row + f] = acc[c];
+    }
 }
 
 // D[β] += the inverse transform of this chunk's part of ĉ[β], at the surface points.  One CTA
@@ -166,8 +208,7 @@ fft_inv_kernel(FftShape sh, const typename C2<T>::type *__restrict__ ch, int ka0
     for (int e = tid; e < p * per; e += blockDim.x) {
         const int a = e / per, r = e % per;
         V s = {(T)0, (T)0};
-        for (int k = 0; k < nka; ++k) {
-            const int w = (a * (ka0 + k)) % n;
+        for (int k = 0, w = (a * ka0) % n; k < nka; ++k, w = w + a < n ? w + a : w + a - n) {
             const V v = c[k * per + r];
             s.x += v.x * wr[w] + v.y * wi[w], s.y += v.y * wr[w] - v.x * wi[w];
         }
@@ -178,8 +219,7 @@ fft_inv_kernel(FftShape sh, const typename C2<T>::type *__restrict__ ch, int ka0
     for (int e = tid; e < p * p * nh; e += blockDim.x) {
         const int kc = e % nh, bb = (e / nh) % p, a = e / (nh * p);
         V s = {(T)0, (T)0};
-        for (int kb = 0; kb < n; ++kb) {
-            const int w = (bb * kb) % n;
+        for (int kb = 0, w = 0; kb < n; ++kb, w = w + bb < n ? w + bb : w + bb - n) {
             const V v = z1[(a * n + kb) * nh + kc];
             s.x += v.x * wr[w] + v.y * wi[w], s.y += v.y * wr[w] - v.x * wi[w];
         }
@@ -192,8 +232,7 @@ fft_inv_kernel(FftShape sh, const typename C2<T>::type *__restrict__ ch, int ka0
     for (int i = tid; i < sh.ns; i += blockDim.x) {
         const int q = surf[i], cc = q % p, ab = q / p;
         T y = (T)0;
-        for (int kc = 0; kc < nh; ++kc) {
-            const int w = (cc * kc) % n;
+        for (int kc = 0, w = 0; kc < nh; ++kc, w = w + cc < n ? w + cc : w + cc - n) {
             const V v = z2[ab * nh + kc];
             const T re = v.x * wr[w] + v.y * wi[w];   // Re(v e^{+2 pi i cc kc / n})
             y += (kc == 0 || 2 * kc == n) ? re : (T)2 * re;
@@ -248,6 +287,29 @@ cudaError_t fft_upload(fmm_ctx *ctx) {
     FMM_CUDA_TRY(dev_malloc((void **)&ctx->fft_surf, surf.size() * sizeof(int)));
     ctx->op_allocs.push_back(ctx->fft_surf);
     FMM_CUDA_TRY(cudaMemcpy(ctx->fft_surf, surf.data(), surf.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // transfer index of every (dx, dy, dz) in [-3, 3]^3 (the order of the kernel transforms:
+    // lexicographic, the near range |d| <= 1 left out), -1 in the near range; then the index of
+    // (neighbour offset o, source octant c', target octant c) with d = 2o + c' - c
+    std::vector<int> tix(343, -1);
+    int t = 0;
+    for (int i = -3; i <= 3; ++i)
+        for (int j = -3; j <= 3; ++j)
+            for (int k = -3; k <= 3; ++k)
+                if (std::max(std::abs(i), std::max(std::abs(j), std::abs(k))) > 1) tix[((i + 3) * 7 + j + 3) * 7 + k + 3] = t++;
+    if (t != kNumTransfer) return cudaErrorInvalidValue;
+    std::vector<int> pairs(26 * 64);
+    for (int oi = 0; oi < 26; ++oi) {
+        const int o = oi < 13 ? oi : oi + 1, ox = o / 9 - 1, oy = (o / 3) % 3 - 1, oz = o % 3 - 1;
+        for (int c2 = 0; c2 < 8; ++c2)
+            for (int c = 0; c < 8; ++c) {
+                const int dx = 2 * ox + ((c2 >> 2) & 1) - ((c >> 2) & 1), dy = 2 * oy + ((c2 >> 1) & 1) - ((c >> 1) & 1),
+                          dz = 2 * oz + (c2 & 1) - (c & 1);
+                pairs[(oi * 8 + c2) * 8 + c] = tix[((dx + 3) * 7 + dy + 3) * 7 + dz + 3];
+            }
+    }
+    FMM_CUDA_TRY(dev_malloc((void **)&ctx->fft_tindex, pairs.size() * sizeof(int)));
+    ctx->op_allocs.push_back(ctx->fft_tindex);
+    FMM_CUDA_TRY(cudaMemcpy(ctx->fft_tindex, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice));
     return cudaSuccess;
 }
 
@@ -263,7 +325,10 @@ cudaError_t fft_vli(fmm_ctx *ctx, int l, const T *U, T *D, cudaStream_t s) {
     const int nsp = ctx->nsp, p = ctx->opt.order_p;
     const FftShape sh = make_shape(p);
     const int per = sh.n * sh.nh;
-    const int nka = std::max(1, std::min(sh.n, 256 / per));          // ka values per chunk
+    // ka values per chunk: every frequency at once when the level's transformed vectors fit the
+    // workspace budget (the forward transform is then computed once per box), else fewer
+    const size_t budget = (size_t)4 << 30;
+    const int nka = (int)std::max<int64_t>(1, std::min<int64_t>(sh.n, (int64_t)(budget / ((size_t)nb * per * sizeof(V)))));
     const int chunk = nka * per;
     Scratch<T> t1, up;
     Scratch<V> uh, ch;
@@ -286,14 +351,18 @@ cudaError_t fft_vli(fmm_ctx *ctx, int l, const T *U, T *D, cudaStream_t s) {
     const size_t fs = fwd_smem<T>(sh), is = inv_smem<T>(sh);
     if (fs > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(fft_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
     if (is > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(fft_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)is));
+    const size_t hs = (size_t)kNumTransfer * kHadF * sizeof(V);
+    FMM_CUDA_TRY(cudaFuncSetAttribute(fft_hadamard_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
     for (int ka0 = 0; ka0 < sh.n; ka0 += nka) {
         const int k = std::min(nka, sh.n - ka0);
         fft_fwd_kernel<T><<<(unsigned)nb, kFftThreads, fs, s>>>(sh, up.p, nsp, ctx->fft_surf, (int)nb, ka0, k, uh.p);
         count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
-        fft_hadamard_kernel<T><<<(unsigned)((nb + 7) / 8), 256, 0, s>>>(
-            uh.p, ghat + (size_t)ka0 * per, (long long)sh.n * per, k * per, L.keys, L.dense, l, ctx->class_slots,
-            ctx->class_delta, (int)nb, ch.p);
+        const LevelTables &P = ctx->lev[l - 1];
+        const dim3 hg((unsigned)((P.n + kHadG - 1) / kHadG), (unsigned)((k * per + kHadF - 1) / kHadF));
+        fft_hadamard_kernel<T><<<hg, kHadG * 32, hs, s>>>(uh.p, (long long)k * per, k * per, ghat + (size_t)ka0 * per,
+                                                          (long long)sh.n * per, P.keys, P.dense, P.child, l - 1,
+                                                          (int)P.n, ctx->fft_tindex, ch.p);
         count_launch();
         FMM_CUDA_TRY(cudaGetLastError());
         fft_inv_kernel<T><<<(unsigned)nb, kFftThreads, is, s>>>(sh, ch.p, ka0, k, ctx->fft_surf, (int)nb, D, nsp);

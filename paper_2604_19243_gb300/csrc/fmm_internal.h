@@ -113,6 +113,7 @@ struct LevelTables {
 
 struct TileSet {                // tiles of one level for one tile height
     int ntiles = 0;
+    int tile_m = 0;             // rows per tile at most (0: the context's tile_m)
     Tile *tiles = nullptr;      // device
     uint32_t *masks = nullptr;  // device [ntiles x 6] (stencil active-slot bits)
     std::vector<Tile> host;
@@ -131,6 +132,7 @@ struct fmm_ctx {
     bool fft = false;           // M2L by FFT (FMM_M2L_FFT)
     void *fft_ghat = nullptr;   // FFT M2L: the kernel's transforms [316][n n (n/2+1)] complex, storage type
     int *fft_surf = nullptr;    // FFT M2L: p^3 grid index of every surface point
+    int *fft_tindex = nullptr;  // FFT M2L: transfer index of (neighbour offset, source octant, target octant), -1 near
     int npts = 0;               // surface points, 6(p-1)^2+2
     int ns = 0, nsp = 0;        // box vector length (npts, or 2 npts: real then imaginary parts), padded
 
@@ -286,12 +288,11 @@ fmm_status adaptive_setup(fmm_ctx *ctx, int capacity);
 void adaptive_free(fmm_ctx *ctx);
 fmm_status adaptive_export(fmm_ctx *ctx, int kind, int64_t *offsets, int64_t *idx, int64_t *count);
 fmm_status adaptive_info(fmm_ctx *ctx, int32_t *capacity, int64_t *leaves, int64_t *refined, int64_t *entries);
-// Evaluation over the adaptive tree (FMM_FP32 / FMM_FP64, Laplace): workspaces, then the hooks
-// that run_far and run_evaluate call while ctx->adaptive_eval is set.
+// Evaluation over the adaptive tree (FMM_FP32 / FMM_FP64, Laplace): workspaces, then the far
+// and near fields that run_far and run_evaluate call while ctx->adaptive_eval is set.
 fmm_status adaptive_prepare(fmm_ctx *ctx);
-const int *adaptive_dense(const fmm_ctx *ctx, int level);   // VLI source table: kept boxes only
 template <typename T>
-cudaError_t adaptive_zero_unkept(const fmm_ctx *ctx, int level, T *rows, int ld, int width, cudaStream_t s);
+cudaError_t adaptive_far(fmm_ctx *ctx, T *far_phi, T *far_grad, cudaStream_t s);
 template <typename T>
 cudaError_t adaptive_xli(const fmm_ctx *ctx, int level, T *D, int ld, cudaStream_t s);
 template <typename T>
@@ -321,6 +322,22 @@ cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_p
 // ULI near field in sorted order (phi and grad each written if non-null, one of them non-null)
 template <typename T>
 cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
+// S2U check potentials of the boxes list[0 .. n) of one level (box b's points [begin[b], begin[b]
+// + count[b]), begin and count indexed by the level's box index) into out[b x nsp]; Laplace
+template <typename T>
+cudaError_t launch_leaf_check_rows(const fmm_ctx *ctx, int level, const int *list, int n, const int *begin,
+                                   const int *count, const T *grid, T *out, cudaStream_t s);
+// D2T at the points of the boxes list[0 .. n) of one level from the densities dens[b x ldd] on
+// their 2.95 surfaces (phi and grad written, not added); Laplace
+template <typename T>
+cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list, int n, const int *begin,
+                                  const int *count, const T *grid, const T *dens, int ldd, T *phi, T *grad,
+                                  cudaStream_t s);
+// the FP32 ULI (Laplace) over nrows boxes of any level, box order[i] for CTA i: box r holds the
+// sorted points [begin[r], begin[r] + count[r]), its U list is u_idx[u_off[r] .. u_off[r + 1])
+cudaError_t launch_p2p_rows_f32(const float4 *pts, const int *begin, const int *count, const int *u_off,
+                                const int *u_idx, const int *order, int nrows, float *phi, float *grad,
+                                cudaStream_t s);
 // check potentials on the 2.95 surface of every leaf from its own points -> rows [nleaf x nsp]
 template <typename T>
 cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStream_t s);
@@ -363,6 +380,10 @@ struct GemmCall {
     void *const *W1_by_cls = nullptr;                     // array of 8 device pointers
     void *Y = nullptr; int ldy = 0;
     const int *dense = nullptr;  // GM_STENCIL: source lookup table in place of the level's own
+    // a subset of the level's boxes in place of all of them (SIMT form): the tiles, and the box
+    // index of every tile row (tile.row0 + r indexes `rows`; class-ordered for STENCIL / PARENT2)
+    const TileSet *tiles = nullptr;
+    const int *rows = nullptr;
     // tensor-core only: A rows read from split planes through TMA row gathers (segment 0), and/or
     // the output written as split planes instead of FP32 Y.  Plane p of row r, column k is at
     // byte (r * ld + k) * esize + p * plane within the buffer (esize 2 for BF16, 4 for TF32).

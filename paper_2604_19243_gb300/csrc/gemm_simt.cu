@@ -94,8 +94,9 @@ GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c);
 template <typename T>
 cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &c, cudaStream_t s) {
     GemmDev g = make_gemm_dev(ctx, c);
-    const TileSet &ts = (c.mode == GM_STENCIL || c.mode == GM_PARENT2) ? ctx->tiles_cls[c.level]
-                                                                       : ctx->tiles_plain[c.level];
+    const TileSet &ts = c.tiles ? *c.tiles
+                        : (c.mode == GM_STENCIL || c.mode == GM_PARENT2) ? ctx->tiles_cls[c.level]
+                                                                         : ctx->tiles_plain[c.level];
     if (ts.ntiles == 0) return cudaSuccess;
     g.tiles = ts.tiles;
     g.masks = ts.masks;
@@ -103,7 +104,8 @@ cudaError_t gemm_simt(const fmm_ctx *ctx, const GemmCall &c, cudaStream_t s) {
         cudaError_t e = cudaStreamWaitEvent(s, ctx->masks_ev, 0);
         if (e != cudaSuccess) return e;
     }
-    const int subs = (ctx->tile_m + BM - 1) / BM;
+    const int tm = ts.tile_m ? ts.tile_m : ctx->tile_m;
+    const int subs = (tm + BM - 1) / BM;
     dim3 grid(ts.ntiles * subs, (c.n_out + BN - 1) / BN);
     gemm_simt_kernel<T><<<grid, THREADS, 0, s>>>(g, subs); count_launch();
     return cudaGetLastError();

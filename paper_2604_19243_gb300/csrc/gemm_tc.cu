@@ -1250,6 +1250,7 @@ void tc_free(fmm_ctx *ctx) {
 GemmDev make_gemm_dev(const fmm_ctx *ctx, const GemmCall &c);
 
 cudaError_t gemm_tc(const fmm_ctx *ctx, const GemmCall &c, int op_id, cudaStream_t s) {
+    if (c.tiles || c.rows) return cudaErrorNotSupported;   // box subsets: SIMT form only
     const bool adj = op_id >= OP_COUNT;
     const int op = op_id % OP_COUNT;
     // the output level's operators; PARENT2's D2D segment those of the parent level

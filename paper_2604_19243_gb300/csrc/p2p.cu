@@ -63,8 +63,10 @@ __device__ __forceinline__ void interact(const typename Vec4<T>::type &sp, T xi,
     gz += qr3 * dz;
 }
 
+constexpr int kRangeWin = 32;   // source ranges staged per window (one per lane of a warp)
+
 struct P2PRanges {
-    int beg[27], len[27];
+    int beg[kRangeWin], len[kRangeWin];
     int n, total, self_len;
 };
 
@@ -211,6 +213,7 @@ __device__ __forceinline__ void pair_step(const float4 *__restrict__ sp, int e, 
 // odd number of groups, the two halves of the sources of its last group.  A range may start or
 // end inside a group's sweep; the partial sums go to shared memory and are added up per target
 // in a fixed order, so the results do not depend on timing.
+constexpr int kSmallLeaf = 8;                   // leaves up to this many points: p2p_small_f32_kernel
 constexpr int kSub = 16;                        // targets per half-warp
 constexpr int kRoundSub = 16;                   // target groups per round
 constexpr int kRoundT = kSub * kRoundSub;       // 256 targets per round
@@ -235,108 +238,181 @@ __device__ __forceinline__ void build_ranges(P2PRanges &rg, int b, const int *__
     rg.self_len = nt;
 }
 
+// Where the points of a box lie in the sorted order.  Leaves of the uniform tree: box b holds
+// [leaf_off[b], leaf_off[b + 1]).  Rows of the adaptive tree (any level): [begin[r], begin[r] +
+// count[r]).
+struct LeafBoxes {
+    const int *leaf_off;
+    __device__ int first(int b) const { return leaf_off[b]; }
+    __device__ int size(int b) const { return leaf_off[b + 1] - leaf_off[b]; }
+};
+struct RowBoxes {
+    const int *begin, *count;
+    __device__ int first(int b) const { return begin[b]; }
+    __device__ int size(int b) const { return count[b]; }
+};
+
+// The sources of target box b in order: b itself (the only box that can hold a zero distance),
+// then the other members of its U list in list order; range k >= 1 is list entry k - 1, or k
+// once past b's own entry (at position ps of the list, nl if absent).  One warp fills ranges
+// [w0, w0 + 32) with their lengths summed by a shuffle scan.
+template <typename Boxes>
+__device__ __forceinline__ void window_ranges(P2PRanges &rg, const Boxes &bx, int b, const int *__restrict__ list,
+                                              int ps, int nr, int w0, int lane) {
+    const int k = w0 + lane;
+    int beg = 0, len = 0;
+    if (k < nr) {
+        int a = b;
+        if (k > 0) {
+            const int m = k - 1;
+            a = list[m + (m >= ps ? 1 : 0)];
+        }
+        beg = bx.first(a), len = bx.size(a);
+    }
+    int incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int len0 = __shfl_sync(0xffffffffu, len, 0);
+    rg.beg[lane] = beg, rg.len[lane] = len;
+    if (lane == 31) {
+        rg.n = min(kRangeWin, nr - w0);
+        rg.total = incl;
+        rg.self_len = w0 == 0 ? len0 : 0;
+    }
+}
+
 // OUT: bit 0 potentials, bit 1 gradients (gradient only: the "force" evaluation of N-body codes)
 constexpr int kOutPhi = 1, kOutGrad = 2;
 
-template <int OUT, bool YUK>
+// The sources of a box come in windows of up to 32 ranges (one window for every leaf of the
+// uniform tree, whose U lists hold at most 27 leaves; adaptive U lists can be longer).
+template <int OUT, bool YUK, typename Boxes>
 __global__ void __launch_bounds__(kP2PThreads)
-p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
-               const int *__restrict__ u_off, const int *__restrict__ u_idx,
-               const int *__restrict__ order, float *__restrict__ phi, float *__restrict__ grad, float kappa) {
+p2p_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__restrict__ u_off,
+               const int *__restrict__ u_idx, const int *__restrict__ order, float *__restrict__ phi,
+               float *__restrict__ grad, float kappa) {
     __shared__ __align__(16) float4 src[kP2PChunk];       // sources, pair layout
     __shared__ __align__(16) float4 tgt[kRoundT];
     __shared__ __align__(16) float4 acc[kRoundT];         // (pot, gx, gy, gz) per target
     __shared__ __align__(16) float4 part[kSlots * 32];
     __shared__ P2PRanges rg;
+    __shared__ int s_ps;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
     const int b = order[blockIdx.x];
-    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
-    if (tid == 0) build_ranges(rg, b, leaf_off, u_off, u_idx);
+    const int t0 = bx.first(b), t1 = t0 + bx.size(b);
+    if (t1 - t0 <= kSmallLeaf) return;   // p2p_small_f32_kernel
+    const int lo = u_off[b], nl = u_off[b + 1] - lo;
+    if (warp == 0) {   // position of b in its own U list (nl if absent); a single window now
+        int ps = nl;
+        for (int m0 = 0; m0 < nl; m0 += 32) {
+            const unsigned hit = __ballot_sync(0xffffffffu, m0 + lane < nl && u_idx[lo + m0 + lane] == b);
+            if (hit) {
+                ps = m0 + __ffs(hit) - 1;
+                break;
+            }
+        }
+        if (lane == 0) s_ps = ps;
+        const int nr0 = 1 + nl - (ps < nl ? 1 : 0);
+        if (nr0 <= kRangeWin) window_ranges(rg, bx, b, u_idx + lo, ps, nr0, 0, lane);
+    }
+    __syncthreads();
+    const int ps = s_ps, nr = 1 + nl - (ps < nl ? 1 : 0);
+    const bool one_window = nr <= kRangeWin;   // every leaf of the uniform tree
     const int groups = (t1 - t0 + kSub - 1) / kSub;
     float *sf = reinterpret_cast<float *>(src);
     for (int gb = 0; gb < groups; gb += kRoundSub) {
         const int m = min(kRoundSub, groups - gb), mt = m * kSub, tb = t0 + gb * kSub;
-        __syncthreads();   // rg ready; tgt / acc of the previous round consumed
+        __syncthreads();   // tgt / acc of the previous round consumed
         for (int j = tid; j < mt; j += kP2PThreads) {
             tgt[j] = pts[min(tb + j, t1 - 1)];
             acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int npair = m >> 1;                          // units holding two groups
-        for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
-            const int c1 = min(rg.total, c0 + kP2PChunk), n = c1 - c0;
-            const int L = (((n + 1) >> 1) + 1) & ~1;      // source pairs, even
-            __syncthreads();
-            int pos = 0;
-            for (int k = 0; k < rg.n; ++k) {
-                const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
-                for (int e = lo + tid; e < hi; e += kP2PThreads) {
-                    const float4 v = pts[rg.beg[k] + (e - pos)];
-                    const int j = e - c0;
-                    float *o = sf + 8 * (j >> 1) + (j & 1);
-                    o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
-                }
-                pos += rg.len[k];
+        for (int w0 = 0; w0 < nr; w0 += kRangeWin) {
+            if (!one_window) {
+                __syncthreads();   // the previous window's ranges are no longer read
+                if (warp == 0) window_ranges(rg, bx, b, u_idx + lo, ps, nr, w0, lane);
+                __syncthreads();
             }
-            for (int j = n + tid; j < 2 * L; j += kP2PThreads) {   // zero charges up to 2L
-                float *o = sf + 8 * (j >> 1) + (j & 1);
-                o[0] = 0.f, o[2] = 0.f, o[4] = 0.f, o[6] = 0.f;
-            }
-            __syncthreads();
-            const int T = npair * L + (m & 1) * (L >> 1);
-            const int self_pairs = (max(0, min(n, rg.self_len - c0)) + 1) >> 1;
-            const int pad_pair = n >> 1, pad_split = max(0, pad_pair - (L >> 1));
-            const int W = (T + 3) >> 2;
-            int at = warp * W;
-            const int end = min(T, at + W);
-            while (at < end) {
-                int u, e0, e1, g, soff;
-                if (at < npair * L) {
-                    u = at / L, e0 = at - u * L, e1 = min(L, e0 + (end - at));
-                    g = 2 * u + half, soff = 0;
-                } else {
-                    u = npair, e0 = at - npair * L, e1 = min(L >> 1, e0 + (end - at));
-                    g = m - 1, soff = half * (L >> 1);
-                }
-                const float4 t = tgt[g * kSub + hl];
-                const float2 nx = make_float2(-t.x, -t.x), ny = make_float2(-t.y, -t.y),
-                             nz = make_float2(-t.z, -t.z);
-                float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
-                const float4 *sp = src + 2 * soff;
-                // checked: pairs that may hold a target (the leaf's own points lead the list)
-                // or a padding charge at the origin; the bounds are the same for both halves
-                const int ce = min(e1, max(e0, self_pairs)), ue = max(ce, min(e1, u == npair ? pad_split : pad_pair));
-                constexpr bool POT = OUT & kOutPhi;
-                for (int e = e0; e < ce; ++e)
-                    pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
-                int e = ce;
-                for (; e + 4 <= ue; e += 4) {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        pair_step<1, false, YUK, POT>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
-                }
-                for (; e < ue; ++e) pair_step<1, false, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
-                for (e = ue; e < e1; ++e) pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
-                part[(u + warp) * 32 + lane] =
-                    make_float4(pot.x + pot.y, gx.x + gx.y, gy.x + gy.y, gz.x + gz.y);
-                at += e1 - e0;
-            }
-            __syncthreads();
-            for (int j = tid; j < mt; j += kP2PThreads) {   // fixed-order sum of the pieces
-                const int g = j / kSub, h = j % kSub;
-                const bool two = g < 2 * npair;
-                const int u = two ? g >> 1 : npair;
-                const int start = two ? u * L : npair * L, len = two ? L : (L >> 1);
-                float4 s = acc[j];
-                for (int w = start / W; w <= (start + len - 1) / W; ++w) {
-                    const float4 *pp = part + (u + w) * 32;
-                    const float4 a = two ? pp[(g & 1) * kSub + h] : pp[h];
-                    s.x += a.x, s.y += a.y, s.z += a.z, s.w += a.w;
-                    if (!two) {
-                        const float4 c = pp[kSub + h];
-                        s.x += c.x, s.y += c.y, s.z += c.z, s.w += c.w;
+            for (int c0 = 0; c0 < rg.total; c0 += kP2PChunk) {
+                const int c1 = min(rg.total, c0 + kP2PChunk), n = c1 - c0;
+                const int L = (((n + 1) >> 1) + 1) & ~1;      // source pairs, even
+                __syncthreads();
+                int pos = 0;
+                for (int k = 0; k < rg.n; ++k) {
+                    const int lo = max(pos, c0), hi = min(pos + rg.len[k], c1);
+                    for (int e = lo + tid; e < hi; e += kP2PThreads) {
+                        const float4 v = pts[rg.beg[k] + (e - pos)];
+                        const int j = e - c0;
+                        float *o = sf + 8 * (j >> 1) + (j & 1);
+                        o[0] = v.x, o[2] = v.y, o[4] = v.z, o[6] = v.w;
                     }
+                    pos += rg.len[k];
                 }
-                acc[j] = s;
+                for (int j = n + tid; j < 2 * L; j += kP2PThreads) {   // zero charges up to 2L
+                    float *o = sf + 8 * (j >> 1) + (j & 1);
+                    o[0] = 0.f, o[2] = 0.f, o[4] = 0.f, o[6] = 0.f;
+                }
+                __syncthreads();
+                const int T = npair * L + (m & 1) * (L >> 1);
+                const int self_pairs = (max(0, min(n, rg.self_len - c0)) + 1) >> 1;
+                const int pad_pair = n >> 1, pad_split = max(0, pad_pair - (L >> 1));
+                const int W = (T + 3) >> 2;
+                int at = warp * W;
+                const int end = min(T, at + W);
+                while (at < end) {
+                    int u, e0, e1, g, soff;
+                    if (at < npair * L) {
+                        u = at / L, e0 = at - u * L, e1 = min(L, e0 + (end - at));
+                        g = 2 * u + half, soff = 0;
+                    } else {
+                        u = npair, e0 = at - npair * L, e1 = min(L >> 1, e0 + (end - at));
+                        g = m - 1, soff = half * (L >> 1);
+                    }
+                    const float4 t = tgt[g * kSub + hl];
+                    const float2 nx = make_float2(-t.x, -t.x), ny = make_float2(-t.y, -t.y),
+                                 nz = make_float2(-t.z, -t.z);
+                    float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+                    const float4 *sp = src + 2 * soff;
+                    // checked: pairs that may hold a target (the leaf's own points lead the list)
+                    // or a padding charge at the origin; the bounds are the same for both halves
+                    const int ce = min(e1, max(e0, self_pairs)), ue = max(ce, min(e1, u == npair ? pad_split : pad_pair));
+                    constexpr bool POT = OUT & kOutPhi;
+                    for (int e = e0; e < ce; ++e)
+                        pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                    int e = ce;
+                    for (; e + 4 <= ue; e += 4) {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            pair_step<1, false, YUK, POT>(sp, e + v, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                    }
+                    for (; e < ue; ++e) pair_step<1, false, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                    for (e = ue; e < e1; ++e) pair_step<1, true, YUK, POT>(sp, e, &nx, &ny, &nz, &pot, &gx, &gy, &gz, kappa);
+                    part[(u + warp) * 32 + lane] =
+                        make_float4(pot.x + pot.y, gx.x + gx.y, gy.x + gy.y, gz.x + gz.y);
+                    at += e1 - e0;
+                }
+                __syncthreads();
+                for (int j = tid; j < mt; j += kP2PThreads) {   // fixed-order sum of the pieces
+                    const int g = j / kSub, h = j % kSub;
+                    const bool two = g < 2 * npair;
+                    const int u = two ? g >> 1 : npair;
+                    const int start = two ? u * L : npair * L, len = two ? L : (L >> 1);
+                    float4 s = acc[j];
+                    for (int w = start / W; w <= (start + len - 1) / W; ++w) {
+                        const float4 *pp = part + (u + w) * 32;
+                        const float4 a = two ? pp[(g & 1) * kSub + h] : pp[h];
+                        s.x += a.x, s.y += a.y, s.z += a.z, s.w += a.w;
+                        if (!two) {
+                            const float4 c = pp[kSub + h];
+                            s.x += c.x, s.y += c.y, s.z += c.z, s.w += c.w;
+                        }
+                    }
+                    acc[j] = s;
+                }
             }
         }
         // acc[j] is read back by the thread that wrote it
@@ -351,6 +427,68 @@ p2p_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
                     grad[3 * (int64_t)i + 2] = s.w * inv4pi<float>();
                 }
             }
+        }
+    }
+}
+
+// ULI of the leaves with at most kSmallLeaf targets (the two-point leaves of deep trees): one
+// warp per leaf, where the CTA-per-leaf kernel above would leave most of its 128 threads idle.
+// Lane l takes target l mod T (T: the leaf's count rounded up to a power of two) and every S-th
+// source (S = 32 / T) of the leaf's source list (the leaf itself, then the other members of its
+// U list), read through the L1 cache; the S partial sums of a target are then added by a
+// butterfly over the lanes, in a fixed order.  The U list is read 32 entries at a time, one per
+// lane, and its ranges are passed around by shuffles.
+constexpr int kSmallWarps = 8;
+
+template <int OUT, bool YUK, typename Boxes>
+__global__ void __launch_bounds__(kSmallWarps * 32)
+p2p_small_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__restrict__ u_off,
+                     const int *__restrict__ u_idx, const int *__restrict__ order, int n,
+                     float *__restrict__ phi, float *__restrict__ grad, float kappa) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kSmallWarps + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int b = order ? order[i] : i;
+    const int t0 = bx.first(b), nt = bx.size(b);
+    if (nt > kSmallLeaf || nt <= 0) return;
+    int lt = 0;
+    while ((1 << lt) < nt) ++lt;
+    const int T = 1 << lt, S = 32 >> lt, ti = lane & (T - 1), sl = lane >> lt;
+    const float4 x = pts[t0 + min(ti, nt - 1)];
+    float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    int pos = 0;   // position of the current range's first source in the whole list
+    auto range = [&](int beg, int len) {
+        for (int e = (sl - pos) & (S - 1); e < len; e += S)
+            interact<float, true, YUK>(pts[beg + e], x.x, x.y, x.z, pot, gx, gy, gz, kappa);
+        pos += len;
+    };
+    range(t0, nt);
+    const int lo = u_off[b], nl = u_off[b + 1] - lo;
+    for (int w0 = 0; w0 < nl; w0 += 32) {
+        int beg = 0, len = 0;
+        if (w0 + lane < nl) {
+            const int a = u_idx[lo + w0 + lane];
+            if (a != b) beg = bx.first(a), len = bx.size(a);
+        }
+        const int kn = min(32, nl - w0);
+        for (int k = 0; k < kn; ++k) {
+            const int bg = __shfl_sync(0xffffffffu, beg, k), ln = __shfl_sync(0xffffffffu, len, k);
+            if (ln) range(bg, ln);
+        }
+    }
+    for (int o = T; o < 32; o <<= 1) {
+        pot += __shfl_xor_sync(0xffffffffu, pot, o);
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    }
+    if (sl == 0 && ti < nt) {
+        const int64_t k = t0 + ti;
+        if (OUT & kOutPhi) phi[k] = pot * inv4pi<float>();
+        if (OUT & kOutGrad) {
+            grad[3 * k] = gx * inv4pi<float>();
+            grad[3 * k + 1] = gy * inv4pi<float>();
+            grad[3 * k + 2] = gz * inv4pi<float>();
         }
     }
 }
@@ -393,16 +531,19 @@ p2p_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict
 constexpr int kLeafThreads = 128;
 constexpr int kLeafChunk = 1024;
 
-template <typename T, bool YUK>
+// The leaf kernels take box b = list[blockIdx.x] (blockIdx.x without a list), its points from
+// `bx` (LeafBoxes for the leaves of the uniform tree, RowBoxes for the leaves of one level of the
+// adaptive tree) and its Morton key from the level's keys.
+template <typename T, bool YUK, typename Boxes>
 __global__ void __launch_bounds__(kLeafThreads)
-leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
+leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, Boxes bx, const int *__restrict__ list,
                   const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns, int nsp,
                   double ox, double oy, double oz, double width, double radius,
                   T *__restrict__ out, T kappa) {
     using P = typename Vec4<T>::type;
     __shared__ P src[kLeafChunk];
-    const int b = blockIdx.x;
-    const int s0 = leaf_off[b], s1 = leaf_off[b + 1];
+    const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const int s0 = bx.first(b), s1 = s0 + bx.size(b);
     int ax, ay, az;
     demorton3(keys[b], ax, ay, az);
     const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
@@ -439,17 +580,17 @@ leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__r
 // the leaf box and every target on the 2.95 surface outside it, so no distance is zero.
 constexpr int kCheckThreads = 160;
 
-template <bool YUK>
+template <bool YUK, typename Boxes>
 __global__ void __launch_bounds__(kCheckThreads)
-leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ leaf_off,
+leaf_check_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__restrict__ list,
                       const uint32_t *__restrict__ keys, const float *__restrict__ grid, int ns, int nsp,
                       double ox, double oy, double oz, double width, double radius, float *__restrict__ out,
                       float kappa) {
     __shared__ __align__(16) float4 src[kLeafChunk];   // kLeafChunk sources as pairs
     __shared__ float cen[3];
     float *sf = reinterpret_cast<float *>(src);
-    const int b = blockIdx.x;
-    const int s0 = leaf_off[b], s1 = leaf_off[b + 1];
+    const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const int s0 = bx.first(b), s1 = s0 + bx.size(b);
     if (threadIdx.x == 0) {   // the box centre in FP64 once, rounded to FP32
         int ax, ay, az;
         demorton3(keys[b], ax, ay, az);
@@ -501,9 +642,9 @@ leaf_check_f32_kernel(const float4 *__restrict__ pts, const int *__restrict__ le
 // ---------------------------------------------------------------------------------------
 // D2T: potentials (and gradients) at the points of leaf b from densities on its 2.95 surface.
 // ---------------------------------------------------------------------------------------
-template <typename T, bool GRAD, bool YUK>
+template <typename T, bool GRAD, bool YUK, typename Boxes>
 __global__ void __launch_bounds__(kLeafThreads)
-leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__restrict__ leaf_off,
+leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, Boxes bx, const int *__restrict__ list,
                  const uint32_t *__restrict__ keys, const T *__restrict__ grid, int ns,
                  const T *__restrict__ dens, int ldd, T scale, double ox, double oy, double oz,
                  double width, double radius, T *__restrict__ phi, T *__restrict__ grad,
@@ -513,7 +654,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
     P *src = reinterpret_cast<P *>(smem_raw);    // [ns]
     __shared__ double cen[3];
     __shared__ float cenf[3];
-    const int b = blockIdx.x;
+    const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
     if (threadIdx.x == 0) {   // the box centre once per leaf
         int ax, ay, az;
         demorton3(keys[b], ax, ay, az);
@@ -537,7 +678,7 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, const int *__re
         src[j] = p;
     }
     __syncthreads();
-    const int t0 = leaf_off[b], t1 = leaf_off[b + 1];
+    const int t0 = bx.first(b), t1 = t0 + bx.size(b);
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the (even) surface count re-staged as pairs, two-wide FP32 arithmetic; the
         // surface lies outside the leaf box, so no distance is zero
@@ -642,13 +783,48 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
                                                  kappa);
     };
     if constexpr (std::is_same<T, float>::value) {
-        if (grad && phi) yuk ? go(p2p_f32_kernel<3, true>, grad) : go(p2p_f32_kernel<3, false>, grad);
-        else if (grad) yuk ? go(p2p_f32_kernel<kOutGrad, true>, grad) : go(p2p_f32_kernel<kOutGrad, false>, grad);
-        else yuk ? go(p2p_f32_kernel<kOutPhi, true>, nullptr) : go(p2p_f32_kernel<kOutPhi, false>, nullptr);
+        const LeafBoxes bx{ctx->leaf_off};
+        const unsigned small_grid = (unsigned)((ctx->nleaf + kSmallWarps - 1) / kSmallWarps);
+        // leaves of more than kSmallLeaf points in decreasing work, the others one warp each in
+        // Morton order
+        auto gf = [&](auto kern, auto small, float *g) {
+            kern<<<ctx->nleaf, kP2PThreads, 0, s>>>(pts, bx, ctx->u_off, ctx->u_idx, ctx->p2p_order, phi, g, kappa);
+            count_launch();
+            small<<<small_grid, kSmallWarps * 32, 0, s>>>(pts, bx, ctx->u_off, ctx->u_idx, nullptr, ctx->nleaf, phi, g,
+                                                          kappa);
+        };
+        if (grad && phi)
+            yuk ? gf(p2p_f32_kernel<3, true, LeafBoxes>, p2p_small_f32_kernel<3, true, LeafBoxes>, grad)
+                : gf(p2p_f32_kernel<3, false, LeafBoxes>, p2p_small_f32_kernel<3, false, LeafBoxes>, grad);
+        else if (grad)
+            yuk ? gf(p2p_f32_kernel<kOutGrad, true, LeafBoxes>, p2p_small_f32_kernel<kOutGrad, true, LeafBoxes>, grad)
+                : gf(p2p_f32_kernel<kOutGrad, false, LeafBoxes>, p2p_small_f32_kernel<kOutGrad, false, LeafBoxes>, grad);
+        else
+            yuk ? gf(p2p_f32_kernel<kOutPhi, true, LeafBoxes>, p2p_small_f32_kernel<kOutPhi, true, LeafBoxes>, nullptr)
+                : gf(p2p_f32_kernel<kOutPhi, false, LeafBoxes>, p2p_small_f32_kernel<kOutPhi, false, LeafBoxes>, nullptr);
+        (void)go;
     } else {
         if (grad) yuk ? go(p2p_kernel<T, true, true>, grad) : go(p2p_kernel<T, true, false>, grad);
         else yuk ? go(p2p_kernel<T, false, true>, nullptr) : go(p2p_kernel<T, false, false>, nullptr);
     }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2p_rows_f32(const float4 *pts, const int *begin, const int *count, const int *u_off,
+                                const int *u_idx, const int *order, int nrows, float *phi, float *grad,
+                                cudaStream_t s) {
+    if (nrows == 0) return cudaSuccess;
+    const RowBoxes bx{begin, count};
+    const unsigned small_grid = (unsigned)((nrows + kSmallWarps - 1) / kSmallWarps);
+    auto go = [&](auto kern, auto small, float *g) {
+        kern<<<nrows, kP2PThreads, 0, s>>>(pts, bx, u_off, u_idx, order, phi, g, 0.f);
+        count_launch();
+        small<<<small_grid, kSmallWarps * 32, 0, s>>>(pts, bx, u_off, u_idx, order, nrows, phi, g, 0.f);
+    };
+    if (grad && phi) go(p2p_f32_kernel<3, false, RowBoxes>, p2p_small_f32_kernel<3, false, RowBoxes>, grad);
+    else if (grad) go(p2p_f32_kernel<kOutGrad, false, RowBoxes>, p2p_small_f32_kernel<kOutGrad, false, RowBoxes>, grad);
+    else go(p2p_f32_kernel<kOutPhi, false, RowBoxes>, p2p_small_f32_kernel<kOutPhi, false, RowBoxes>, nullptr);
     count_launch();
     return cudaGetLastError();
 }
@@ -662,15 +838,35 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
     const double radius = 2.95 * 0.5 * width;
     const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
     const T kappa = (T)ctx->opt.kappa;
+    const LeafBoxes bx{ctx->leaf_off};
     auto go = [&](auto kern, int threads) {
-        kern<<<ctx->nleaf, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys,
+        kern<<<ctx->nleaf, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, bx, nullptr, ctx->lev[d].keys,
                                             grid, ctx->npts, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2],
                                             width, radius, out, kappa);
     };
     if constexpr (std::is_same<T, float>::value)
-        yuk ? go(leaf_check_f32_kernel<true>, kCheckThreads) : go(leaf_check_f32_kernel<false>, kCheckThreads);
+        yuk ? go(leaf_check_f32_kernel<true, LeafBoxes>, kCheckThreads)
+            : go(leaf_check_f32_kernel<false, LeafBoxes>, kCheckThreads);
     else
-        yuk ? go(leaf_check_kernel<T, true>, kLeafThreads) : go(leaf_check_kernel<T, false>, kLeafThreads);
+        yuk ? go(leaf_check_kernel<T, true, LeafBoxes>, kLeafThreads) : go(leaf_check_kernel<T, false, LeafBoxes>, kLeafThreads);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leaf_check_rows(const fmm_ctx *ctx, int level, const int *list, int n, const int *begin,
+                                   const int *count, const T *grid, T *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const double width = ctx->side / (double)(1 << level);
+    const double radius = 2.95 * 0.5 * width;
+    const RowBoxes bx{begin, count};
+    auto go = [&](auto kern, int threads) {
+        kern<<<n, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, bx, list, ctx->lev[level].keys, grid,
+                                   ctx->npts, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius,
+                                   out, (T)0);
+    };
+    if constexpr (std::is_same<T, float>::value) go(leaf_check_f32_kernel<false, RowBoxes>, kCheckThreads);
+    else go(leaf_check_kernel<T, false, RowBoxes>, kLeafThreads);
     count_launch();
     return cudaGetLastError();
 }
@@ -687,13 +883,38 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     size_t smem = sizeof(P) * ctx->npts * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
     const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
     const T kappa = (T)ctx->opt.kappa;
+    const LeafBoxes bx{ctx->leaf_off};
     auto go = [&](auto kern, T *g) {
-        kern<<<ctx->nleaf, kLeafThreads, smem, s>>>((const P *)ctx->pts, ctx->leaf_off, ctx->lev[d].keys, grid,
+        kern<<<ctx->nleaf, kLeafThreads, smem, s>>>((const P *)ctx->pts, bx, nullptr, ctx->lev[d].keys, grid,
                                                     ctx->npts, dens, ldd, scale, ctx->origin[0], ctx->origin[1],
                                                     ctx->origin[2], width, radius, phi, g, shift, kappa);
     };
-    if (grad) yuk ? go(leaf_eval_kernel<T, true, true>, grad) : go(leaf_eval_kernel<T, true, false>, grad);
-    else yuk ? go(leaf_eval_kernel<T, false, true>, nullptr) : go(leaf_eval_kernel<T, false, false>, nullptr);
+    if (grad)
+        yuk ? go(leaf_eval_kernel<T, true, true, LeafBoxes>, grad) : go(leaf_eval_kernel<T, true, false, LeafBoxes>, grad);
+    else
+        yuk ? go(leaf_eval_kernel<T, false, true, LeafBoxes>, nullptr)
+            : go(leaf_eval_kernel<T, false, false, LeafBoxes>, nullptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list, int n, const int *begin,
+                                  const int *count, const T *grid, const T *dens, int ldd, T *phi, T *grad,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const double width = ctx->side / (double)(1 << level);
+    const double radius = 2.95 * 0.5 * width;
+    using P = typename Vec4<T>::type;
+    size_t smem = sizeof(P) * ctx->npts * (std::is_same<T, float>::value ? 2 : 1);
+    const RowBoxes bx{begin, count};
+    auto go = [&](auto kern, T *g) {
+        kern<<<n, kLeafThreads, smem, s>>>((const P *)ctx->pts, bx, list, ctx->lev[level].keys, grid, ctx->npts, dens,
+                                           ldd, (T)1, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius,
+                                           phi, g, nullptr, (T)0);
+    };
+    if (grad) go(leaf_eval_kernel<T, true, false, RowBoxes>, grad);
+    else go(leaf_eval_kernel<T, false, false, RowBoxes>, nullptr);
     count_launch();
     return cudaGetLastError();
 }
@@ -704,6 +925,10 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
                                            T *, T *, int64_t, cudaStream_t);                        \
     template cudaError_t launch_p2p<T>(const fmm_ctx *, T *, T *, cudaStream_t);                    \
     template cudaError_t launch_leaf_check<T>(const fmm_ctx *, const T *, T *, cudaStream_t);       \
+    template cudaError_t launch_leaf_check_rows<T>(const fmm_ctx *, int, const int *, int, const int *, \
+                                                   const int *, const T *, T *, cudaStream_t);      \
+    template cudaError_t launch_leaf_eval_rows<T>(const fmm_ctx *, int, const int *, int, const int *, \
+                                                  const int *, const T *, const T *, int, T *, T *, cudaStream_t); \
     template cudaError_t launch_leaf_eval<T>(const fmm_ctx *, const T *, const T *, int, T, T *, T *, \
                                              cudaStream_t, const double *);
 FMM_INST(float)

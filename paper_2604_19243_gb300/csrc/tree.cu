@@ -508,6 +508,10 @@ __global__ void class_keys(ClassKeyArgs a, uint32_t *cls_key, int *idx) {
 
 }  // namespace
 
+cudaError_t stable_sort_by_key(uint32_t *keys, int *vals, int64_t n, int bits, cudaStream_t s) {
+    return radix_sort(keys, vals, n, bits, s);
+}
+
 // Class slot table: for child octant c, the 189 transfer indices t (ascending) whose source
 // box has a parent adjacent to (or equal to) the target's parent.
 void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas) {
@@ -615,6 +619,13 @@ __global__ void v_fill(const uint32_t *keys, int64_t n, const int *dense, int le
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_tile_masks(const Tile *tiles, int ntiles, const int *rows, const uint32_t *keys, const int *dense,
+                              int level, const int *class_delta, uint32_t *masks, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    tile_masks<<<ntiles, 256, 0, s>>>(tiles, ntiles, rows, keys, dense, level, class_delta, masks); count_launch();
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------------------
 // build

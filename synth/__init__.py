@@ -74,7 +74,7 @@ class Workload:
 
     name: str
     n: int
-    dist: str          # 'cube' or 'sphere'
+    dist: str          # 'cube', 'sphere' or 'mixed'
     charge: str        # 'u01', 'u11', 'normal'
     p: int             # expansion order; surface size 6(p-1)^2+2
     depth: int         # uniform octree depth
@@ -83,6 +83,8 @@ class Workload:
     gradient: bool
 
     def points(self, seed: int = SEED_POINTS) -> np.ndarray:
+        if self.dist == "mixed":
+            return mixed_points(self.n, seed)
         return cube_points(self.n, seed) if self.dist == "cube" else sphere_points(self.n, seed)
 
     def charges(self, seed: int = SEED_CHARGES) -> np.ndarray:
@@ -106,6 +108,9 @@ WORKLOADS = {
     # p = 8 at a size where both forms of the M2L (dense and FFT) run in a bench step: the scale
     # case's order and cube family at an eighth of its points and depth 6 (16 points per leaf)
     "cube4m_p8_d6": Workload("cube4m_p8_d6", 4_194_304, "cube", "u01", 8, 6, *CUBE, True),
+    # strongly non-uniform points for the adaptive tree: half uniform in the unit cube, half on a
+    # sphere of radius 0.15 inside it, refined to depth 9
+    "mixed1m_p6_d9": Workload("mixed1m_p6_d9", 1_048_576, "mixed", "u01", 6, 9, *CUBE, True),
 }
 
 

@@ -91,3 +91,19 @@ def test_cube33m_p8_d8_against_direct_and_adjoint():
     g64, q64 = g.astype(np.float64), q.astype(np.float64)
     assert abs(g64 @ phi - psi @ q64) / (np.linalg.norm(g64) * np.linalg.norm(phi)) < 1e-5
     f.close()
+
+
+def test_cube33m_p8_d8_textbook_fp16x3_error_is_bounded():
+    # The benchmark's mode on the scale configuration without mean_free: potentials within 1e-5
+    # of the FP64 direct sum, gradients within 4e-4 (measured 4.8e-6 and 2.1e-4 at 4096 targets;
+    # the FP32 downward potentials lose the gradient's bits at depth 8, see the test above)
+    w = WORKLOADS["cube33m_p8_d8"]
+    x, q = w.points(), w.charges()
+    f = make_fmm(x, w.p, w.depth, "fp16x3", (w.origin, w.side))
+    phi, grad = run(f, q)
+    f.sync()
+    f.close()
+    idx = sample_indices(w.n, 256)
+    dp, dg = direct.direct_self(x.astype(np.float64), q.astype(np.float64), sample=idx)
+    e_phi, e_grad = rel(phi[idx], dp), rel(grad[idx], dg)
+    assert e_phi < 1e-5 and e_grad < 4e-4, (e_phi, e_grad)

@@ -122,7 +122,7 @@ def _dev(a, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["mixed", "sphere"])
+@pytest.mark.parametrize("case", ["mixed", "sphere", "deep"])
 def test_adaptive_evaluate_matches_oracle(case, precision):
     import paper_2604_19243_gb300 as pkg
     from gpu_helpers import rel
@@ -130,6 +130,9 @@ def test_adaptive_evaluate_matches_oracle(case, precision):
     from synth import charges
     if case == "mixed":
         n, cap, depth, dom, x = 4000, 32, 6, UNIT, mixed_points(4000)
+        qv = charges(n, "u11")
+    elif case == "deep":   # a tight cluster in a uniform cloud: leaves from level 2 to level 8
+        n, cap, depth, dom, x = 12000, 32, 8, UNIT, mixed_points(12000, radius=0.02)
         qv = charges(n, "u11")
     else:
         n, cap, depth, dom, x = 3000, 24, 5, SPHERE, sphere_points(3000)
@@ -150,6 +153,8 @@ def test_adaptive_evaluate_matches_oracle(case, precision):
     assert sum(len(m) for m in il.w.values()) > 0 and il.x
     e_phi, e_grad = rel(phi.cpu().numpy(), o_phi), rel(grad.cpu().numpy(), o_grad)
     assert e_phi < 1e-5 and e_grad < 1e-4, (e_phi, e_grad)
+    if precision == "fp64":   # the oracle's steps in its order: rounding and the M2L compression only
+        assert e_phi < 1e-8 and e_grad < 1e-8, (e_phi, e_grad)
     # and against the direct sum
     d_phi, d_grad = direct.direct_self(x64, q64)
     assert rel(phi.cpu().numpy(), d_phi) < 2e-5 and rel(grad.cpu().numpy(), d_grad) < 1e-4
