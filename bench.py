@@ -588,7 +588,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fmm.build_tree(xh)
-        fmm.evaluate_into(qh, ph_out, gh)     # host outputs: returns after the device-to-host copy
+        fmm.evaluate_into(qh, ph_out, gh)     # host outputs: returns once the results are in host memory
         e2e_s.append(time.perf_counter() - t0)
     e2e_value = job_rate(w.n, args.steps, ws, slowest(sum(e2e_s), dev, ws))
     es = 8 if fp64 else 4

@@ -384,6 +384,33 @@ fmm_status fmm_sync(fmm_ctx *ctx);
 fmm_status fmm_set_wait_limit(fmm_ctx *ctx, double seconds);
 void fmm_set_alloc_limit(size_t bytes);
 
+/* Consistency checks in place of a memory checker (no counterpart in the paper).
+ *
+ * fmm_debug_check validates every index table of ctx's tree on the device against its bounds
+ * and its definition: the sort permutation, the leaf offsets (increasing from 0 to n), the U
+ * lists (in range, ascending, adjacent, the leaf itself included), every level's keys, dense
+ * table, parent and child indices and class order, and the near-field schedule.  The library
+ * also exists as libfmm_debug.so, built with FMM_DEBUG: there the kernels that compute indices
+ * (the radix scatter, the near-field and leaf kernels' point ranges, the output scatter) check
+ * each one before using it and, instead of trapping, skip the access and record the check; this
+ * call then also returns the checks recorded since its last call, and clears them.
+ * *flags (not NULL) receives the OR of the fmm_debug_bits that failed, 0 if none; *in_kernel (may
+ * be NULL) is set to 1 in libfmm_debug.so, else 0.  ESTATE before fmm_build_tree; ECUDA for a
+ * CUDA error.  It synchronizes ctx's stream. */
+typedef enum {
+    FMM_DEBUG_PERM = 1 << 0,     /* sort permutation */
+    FMM_DEBUG_LEAF = 1 << 1,     /* leaf offsets */
+    FMM_DEBUG_ULIST = 1 << 2,    /* U lists */
+    FMM_DEBUG_KEYS = 1 << 3,     /* level keys and dense tables */
+    FMM_DEBUG_TREE = 1 << 4,     /* parent and child indices */
+    FMM_DEBUG_CLASS = 1 << 5,    /* class (octant) order of a level */
+    FMM_DEBUG_ORDER = 1 << 6,    /* near-field schedule */
+    FMM_DEBUG_P2P = 1 << 7,      /* in-kernel: a point range outside the points */
+    FMM_DEBUG_SCATTER = 1 << 8,  /* in-kernel: an output position outside [0, n) */
+    FMM_DEBUG_SORT = 1 << 9      /* in-kernel: a radix scatter position outside [0, n) */
+} fmm_debug_bits;
+fmm_status fmm_debug_check(fmm_ctx *ctx, uint32_t *flags, int32_t *in_kernel);
+
 /* Morton keys and stable sort of n points, allocating nothing.  The paper has no counterpart:
  * this entry point is for callers that cannot let a library allocate device memory, because
  * one allocator owns all of their device memory or because they reserve their whole budget at

@@ -23,7 +23,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libfmm.so")
+# FMM_LIBRARY selects another build of the library by file name within _build/ (the tests load
+# the bounds-checked libfmm_debug.so this way); the default is libfmm.so
+LIB_PATH = os.path.join(HERE, "_build", os.path.basename(os.environ.get("FMM_LIBRARY", "libfmm.so")))
 
 PRECISIONS = {"fp32": 0, "fp64": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp16x3": 5}
 STATUS = {0: "FMM_OK", 1: "FMM_EINVAL", 2: "FMM_ENOMEM", 3: "FMM_ECUDA", 4: "FMM_ESTATE",
@@ -39,7 +41,9 @@ ENTRY_POINTS = ("fmm_default_options", "fmm_create", "fmm_build_tree", "fmm_prec
                 "fmm_measure_fp32_peak", "fmm_partition_setup", "fmm_partition_evaluate",
                 "fmm_partition_info", "fmm_partition_export", "fmm_partition_timings",
                 "fmm_adaptive_setup", "fmm_adaptive_info", "fmm_adaptive_export", "fmm_adaptive_evaluate",
-                "fmm_set_wait_limit", "fmm_set_alloc_limit", "fmm_last_error", "fmm_destroy")
+                "fmm_set_wait_limit", "fmm_set_alloc_limit", "fmm_debug_check", "fmm_last_error", "fmm_destroy")
+DEBUG_BITS = {"perm": 1 << 0, "leaf": 1 << 1, "ulist": 1 << 2, "keys": 1 << 3, "tree": 1 << 4, "class": 1 << 5,
+              "order": 1 << 6, "p2p": 1 << 7, "scatter": 1 << 8, "sort": 1 << 9}
 
 
 class Options(ctypes.Structure):
@@ -137,6 +141,8 @@ def lib():
             f.restype = ctypes.c_int
         L.fmm_set_wait_limit.argtypes = [vp, ctypes.c_double]
         L.fmm_set_wait_limit.restype = ctypes.c_int
+        L.fmm_debug_check.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32)]
+        L.fmm_debug_check.restype = ctypes.c_int
         L.fmm_set_alloc_limit.argtypes = [ctypes.c_size_t]
         L.fmm_set_alloc_limit.restype = None
         L.fmm_kernel_launches.argtypes = []
@@ -423,6 +429,12 @@ class FMM:
     def adaptive_evaluate_into(self, q, phi, grad=None, parts=PART_ALL):
         """fmm_adaptive_evaluate on caller-owned arrays; phi may be None when grad is given."""
         self._check(lib().fmm_adaptive_evaluate(self._ctx, _ptr(q), _ptr(phi), _ptr(grad), parts))
+
+    def debug_check(self):
+        """fmm_debug_check: (names of the failed checks, whether this library has the in-kernel checks)."""
+        flags, ink = ctypes.c_uint32(0), ctypes.c_int32(0)
+        self._check(lib().fmm_debug_check(self._ctx, ctypes.byref(flags), ctypes.byref(ink)))
+        return sorted(k for k, b in DEBUG_BITS.items() if flags.value & b), bool(ink.value)
 
     def set_wait_limit(self, seconds):
         """Bound on the tensor-core kernels' barrier waits (default 1 s; 0 forces the timeout path)."""

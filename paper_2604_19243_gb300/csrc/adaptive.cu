@@ -809,7 +809,7 @@ template <typename T>
 cudaError_t adaptive_uli(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     const AdaptiveState *A = ctx->adaptive;
     if constexpr (sizeof(T) == 4)   // the packed FP32 kernel of the uniform tree, over the leaves' rows
-        return launch_p2p_rows_f32((const float4 *)ctx->pts, A->begin, A->count, A->off[0], A->idx[0], A->uli_order,
+        return launch_p2p_rows_f32((const float4 *)ctx->pts, ctx->n, A->begin, A->count, A->off[0], A->idx[0], A->uli_order,
                                    A->uli_leaves, (float *)phi, (float *)grad, s);
     auto go = [&](auto kern) {
         kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, A->state, A->off[0],

@@ -89,6 +89,16 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// device view of pinned (page-locked, mapped) host memory; nullptr for any other pointer
+void *mapped_host(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 size_t elem_size(const fmm_ctx *ctx) { return ctx->fp64 ? sizeof(double) : sizeof(float); }
 
 template <typename P>
@@ -125,7 +135,7 @@ void free_workspace(fmm_ctx *ctx) {
 // The workspaces outlive the tree: a new tree reuses them when it fits (see ensure_workspace).
 void free_tree(fmm_ctx *ctx) {
     cudaStream_t s = ctx->stream;
-    free_async(ctx->pts, s), free_async(ctx->perm, s), free_async(ctx->leaf_off, s);
+    free_async(ctx->pts, s), free_async(ctx->perm, s), free_async(ctx->leaf_off, s), free_async(ctx->inv_perm, s);
     free_async(ctx->u_off, s), free_async(ctx->u_idx, s), free_async(ctx->p2p_order, s);
     for (int l = 0; l <= kMaxDepth; ++l) {
         LevelTables &L = ctx->lev[l];
@@ -286,8 +296,23 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     Staged sq, sphi, sgrad;
     fmm_status st;
     if ((st = stage(ctx, q, vn * sizeof(T), true, &ctx->stage_in, &sq)) != FMM_OK) return st;
-    if (phi && (st = stage(ctx, phi, vn * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
-    if (grad && (st = stage(ctx, grad, 3 * vn * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
+    // outputs in pinned host memory (all of them) are written by the output gather straight over
+    // the host link, in the caller's order: no staging buffer and no separate copy
+    const bool want_grad = grad && !adjoint;
+    void *phi_map = (!ctx->cplx && phi) ? mapped_host(phi) : nullptr;
+    void *grad_map = (!ctx->cplx && want_grad) ? mapped_host(grad) : nullptr;
+    const bool direct = !ctx->cplx && (phi || want_grad) && (!phi || phi_map) && (!want_grad || grad_map);
+    if (!direct) {
+        if (phi && (st = stage(ctx, phi, vn * sizeof(T), false, &ctx->stage_out, &sphi)) != FMM_OK) return st;
+        if (grad && (st = stage(ctx, grad, 3 * vn * sizeof(T), false, &ctx->stage_grad, &sgrad)) != FMM_OK) return st;
+    } else if (!ctx->inv_perm) {
+        if (pool_alloc((void **)&ctx->inv_perm, std::max<int64_t>(n, 1) * sizeof(int), s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FMM_ENOMEM, "inverse permutation");
+        }
+        cudaError_t ei = launch_invert_perm(ctx->perm, n, ctx->inv_perm, s);
+        if (ei != cudaSuccess) return cuda_fail(ctx, ei, "inverse permutation");
+    }
     cudaError_t e;
     cudaEventRecord(ctx->ev[0], s);
     e = ctx->cplx ? launch_gather_points_c<T>((const T *)sq.dev, ctx->perm, ctx->pts, (T *)ctx->pts_qi, n, s)
@@ -319,10 +344,24 @@ fmm_status run_evaluate(fmm_ctx *ctx, const void *q, void *phi, void *grad, int 
     cudaEventRecord(ctx->ev[1], ns);
     cudaStreamWaitEvent(s, ctx->ev[5], 0);   // join the far field
     cudaStreamWaitEvent(s, ctx->ev[1], 0);   // join the near field
-    e = (ctx->cplx ? launch_scatter_c<T> : launch_scatter<T>)(
-        near && phi ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
-        far && phi ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->perm, (T *)sphi.dev,
-        (grad && !adjoint) ? (T *)sgrad.dev : nullptr, n, s);
+    if (direct) {
+        e = launch_gather_out<T>(near && phi ? (const T *)ctx->near_phi : nullptr, near ? ng : nullptr,
+                                 far && phi ? (const T *)ctx->far_phi : nullptr, far ? fg : nullptr, ctx->inv_perm,
+                                 (T *)phi_map, (T *)grad_map, n, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "output gather");
+        cudaEventRecord(ctx->ev[6], s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+        ctx->last_adjoint = adjoint;
+        ctx->last_far = far;
+        return FMM_OK;
+    }
+    {
+        const T *a = near && phi ? (const T *)ctx->near_phi : nullptr, *b = near ? ng : nullptr;
+        const T *c = far && phi ? (const T *)ctx->far_phi : nullptr, *d = far ? fg : nullptr;
+        T *go = (grad && !adjoint) ? (T *)sgrad.dev : nullptr;
+        e = ctx->cplx ? launch_scatter_c<T>(a, b, c, d, ctx->perm, (T *)sphi.dev, go, n, s)
+                      : launch_scatter<T>(a, b, c, d, ctx->perm, (T *)sphi.dev, go, n, s);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter");
     cudaEventRecord(ctx->ev[6], s);
     if (phi && sphi.host && (e = cudaMemcpyAsync(phi, sphi.dev, vn * sizeof(T), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -823,6 +862,24 @@ fmm_status fmm_set_wait_limit(fmm_ctx *ctx, double seconds) {
 }
 
 void fmm_set_alloc_limit(size_t bytes) { g_alloc_cap.store(bytes); }
+
+fmm_status fmm_debug_check(fmm_ctx *ctx, uint32_t *flags, int32_t *in_kernel) {
+    if (!ctx || !flags) return ctx ? fail(ctx, FMM_EINVAL, "null flags pointer") : FMM_EINVAL;
+    if (!ctx->have_tree) return fail(ctx, FMM_ESTATE, "fmm_build_tree has not been called");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    uint32_t f = 0;
+    if (e == cudaSuccess) e = validate_tree(ctx, &f);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tree validation");
+    f |= debug_word_tree(true) | debug_word_p2p(true);
+    *flags = f;
+#ifdef FMM_DEBUG
+    if (in_kernel) *in_kernel = 1;
+#else
+    if (in_kernel) *in_kernel = 0;
+#endif
+    return FMM_OK;
+}
 
 const char *fmm_last_error(const fmm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 

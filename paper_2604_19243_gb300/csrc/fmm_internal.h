@@ -143,7 +143,9 @@ struct fmm_ctx {
     double side = 1.0;
     int nleaf = 0;
     void *pts = nullptr;        // sorted (x, y, z, q) as float4 or double4
+    int64_t n_pts_all = -1;     // points in pts when it holds more than n (a rank view's ghosts)
     int *perm = nullptr;        // sorted position -> input index
+    int *inv_perm = nullptr;    // input index -> sorted position (made by the first evaluation with host outputs)
     int *leaf_off = nullptr;    // [nleaf+1]
     int *u_off = nullptr, *u_idx = nullptr;
     int64_t n_u = 0;
@@ -308,6 +310,11 @@ void class_slot_table(std::vector<int> &slots, std::vector<int> &deltas);
 cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, int32_t *tv,
                            int64_t *count);
 cudaError_t build_tiles(fmm_ctx *ctx, int tile_m);
+// fmm_debug_check: the tree's index tables against their bounds and definitions (fmm_debug_bits)
+cudaError_t validate_tree(const fmm_ctx *ctx, uint32_t *flags);
+// the in-kernel checks recorded by a translation unit of the FMM_DEBUG build (0 otherwise)
+uint32_t debug_word_tree(bool clear);
+uint32_t debug_word_p2p(bool clear);
 
 // ---- kernels ----
 // Point kernels (p2p.cu).  T = float or double.
@@ -318,7 +325,13 @@ cudaError_t launch_gather_points(const T *q_in, const int *perm, void *pts, int6
 template <typename T>
 cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_phi,
                            const T *far_grad, const int *perm, T *phi, T *grad, int64_t n,
-                           cudaStream_t s);
+                           cudaStream_t s, int64_t n_out = -1);   // n_out: output length (-1: n)
+// the same sums into the caller's order through the inverse permutation inv (input index ->
+// sorted position), written coalesced: for outputs in mapped host memory
+template <typename T>
+cudaError_t launch_gather_out(const T *near_phi, const T *near_grad, const T *far_phi, const T *far_grad,
+                              const int *inv, T *phi, T *grad, int64_t n, cudaStream_t s);
+cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t s);
 // ULI near field in sorted order (phi and grad each written if non-null, one of them non-null)
 template <typename T>
 cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s);
@@ -335,7 +348,7 @@ cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list
                                   cudaStream_t s);
 // the FP32 ULI (Laplace) over nrows boxes of any level, box order[i] for CTA i: box r holds the
 // sorted points [begin[r], begin[r] + count[r]), its U list is u_idx[u_off[r] .. u_off[r + 1])
-cudaError_t launch_p2p_rows_f32(const float4 *pts, const int *begin, const int *count, const int *u_off,
+cudaError_t launch_p2p_rows_f32(const float4 *pts, int64_t n_points, const int *begin, const int *count, const int *u_off,
                                 const int *u_idx, const int *order, int nrows, float *phi, float *grad,
                                 cudaStream_t s);
 // check potentials on the 2.95 surface of every leaf from its own points -> rows [nleaf x nsp]

@@ -129,6 +129,13 @@ __device__ __forceinline__ uint64_t global_ns() {
 // that finds the phase incomplete).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     const uint32_t a = smem_u32(bar);
+    uint32_t ready = 0;   // a phase that is already complete costs one non-blocking probe
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ready)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ready) return true;
     // Each poll may suspend the thread until the phase completes (at most `hint` ns), so that
     // waiting warps take no issue slots from the warps they wait for on the same SM
     // sub-partition (the MMA issuer above all).

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "debugcheck.cuh"
 #include "devutil.cuh"
 #include "fmm_internal.h"
 
@@ -243,14 +244,23 @@ __device__ __forceinline__ void build_ranges(P2PRanges &rg, int b, const int *__
 // count[r]).
 struct LeafBoxes {
     const int *leaf_off;
+    int npts;                   // points of the sorted arrays (bound of the debug checks)
     __device__ int first(int b) const { return leaf_off[b]; }
     __device__ int size(int b) const { return leaf_off[b + 1] - leaf_off[b]; }
 };
 struct RowBoxes {
     const int *begin, *count;
+    int npts;
     __device__ int first(int b) const { return begin[b]; }
     __device__ int size(int b) const { return count[b]; }
 };
+
+// a box's point range, checked against the point arrays in FMM_DEBUG builds (empty if outside)
+template <typename Boxes>
+__device__ __forceinline__ void box_range(const Boxes &bx, int b, int &beg, int &len) {
+    beg = bx.first(b), len = bx.size(b);
+    if (!dbg_ok(beg >= 0 && len >= 0 && beg + len <= bx.npts, kDbgP2P)) len = 0;
+}
 
 // The sources of target box b in order: b itself (the only box that can hold a zero distance),
 // then the other members of its U list in list order; range k >= 1 is list entry k - 1, or k
@@ -267,7 +277,7 @@ __device__ __forceinline__ void window_ranges(P2PRanges &rg, const Boxes &bx, in
             const int m = k - 1;
             a = list[m + (m >= ps ? 1 : 0)];
         }
-        beg = bx.first(a), len = bx.size(a);
+        box_range(bx, a, beg, len);
     }
     int incl = len;
 #pragma unroll
@@ -302,8 +312,10 @@ p2p_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__restrict__
     __shared__ int s_ps;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
     const int b = order[blockIdx.x];
-    const int t0 = bx.first(b), t1 = t0 + bx.size(b);
-    if (t1 - t0 <= kSmallLeaf) return;   // p2p_small_f32_kernel
+    int t0, tn;
+    box_range(bx, b, t0, tn);
+    const int t1 = t0 + tn;
+    if (tn <= kSmallLeaf) return;   // p2p_small_f32_kernel
     const int lo = u_off[b], nl = u_off[b + 1] - lo;
     if (warp == 0) {   // position of b in its own U list (nl if absent); a single window now
         int ps = nl;
@@ -449,7 +461,8 @@ p2p_small_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__rest
     const int i = blockIdx.x * kSmallWarps + (threadIdx.x >> 5);
     if (i >= n) return;
     const int b = order ? order[i] : i;
-    const int t0 = bx.first(b), nt = bx.size(b);
+    int t0, nt;
+    box_range(bx, b, t0, nt);
     if (nt > kSmallLeaf || nt <= 0) return;
     int lt = 0;
     while ((1 << lt) < nt) ++lt;
@@ -468,7 +481,7 @@ p2p_small_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__rest
         int beg = 0, len = 0;
         if (w0 + lane < nl) {
             const int a = u_idx[lo + w0 + lane];
-            if (a != b) beg = bx.first(a), len = bx.size(a);
+            if (a != b) box_range(bx, a, beg, len);
         }
         const int kn = min(32, nl - w0);
         for (int k = 0; k < kn; ++k) {
@@ -543,7 +556,9 @@ leaf_check_kernel(const typename Vec4<T>::type *__restrict__ pts, Boxes bx, cons
     using P = typename Vec4<T>::type;
     __shared__ P src[kLeafChunk];
     const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
-    const int s0 = bx.first(b), s1 = s0 + bx.size(b);
+    int s0, sn;
+    box_range(bx, b, s0, sn);
+    const int s1 = s0 + sn;
     int ax, ay, az;
     demorton3(keys[b], ax, ay, az);
     const double cx = ox + (ax + 0.5) * width, cy = oy + (ay + 0.5) * width,
@@ -590,7 +605,9 @@ leaf_check_f32_kernel(const float4 *__restrict__ pts, Boxes bx, const int *__res
     __shared__ float cen[3];
     float *sf = reinterpret_cast<float *>(src);
     const int b = list ? list[blockIdx.x] : (int)blockIdx.x;
-    const int s0 = bx.first(b), s1 = s0 + bx.size(b);
+    int s0, sn;
+    box_range(bx, b, s0, sn);
+    const int s1 = s0 + sn;
     if (threadIdx.x == 0) {   // the box centre in FP64 once, rounded to FP32
         int ax, ay, az;
         demorton3(keys[b], ax, ay, az);
@@ -678,7 +695,9 @@ leaf_eval_kernel(const typename Vec4<T>::type *__restrict__ pts, Boxes bx, const
         src[j] = p;
     }
     __syncthreads();
-    const int t0 = bx.first(b), t1 = t0 + bx.size(b);
+    int t0, tn;
+    box_range(bx, b, t0, tn);
+    const int t1 = t0 + tn;
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the (even) surface count re-staged as pairs, two-wide FP32 arithmetic; the
         // surface lies outside the leaf box, so no distance is zero
@@ -730,10 +749,11 @@ template <typename T>
 __global__ void scatter_kernel(const T *__restrict__ near_phi, const T *__restrict__ near_grad,
                                const T *__restrict__ far_phi, const T *__restrict__ far_grad,
                                const int *__restrict__ perm, T *__restrict__ phi,
-                               T *__restrict__ grad, int64_t n) {
+                               T *__restrict__ grad, int64_t n, int64_t n_out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = perm[i];
+    if (!dbg_ok(o >= 0 && o < n_out, kDbgScatter)) return;
     if (phi) {
         T v = 0;
         if (near_phi) v += near_phi[i];
@@ -752,6 +772,42 @@ __global__ void scatter_kernel(const T *__restrict__ near_phi, const T *__restri
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
+// The outputs in the caller's order, written straight into mapped (pinned) host memory: thread o
+// reads the sorted position inv[o] of input o and writes phi[o] and grad[3o .. 3o + 2], so a warp's
+// stores are consecutive and the results cross the host link once, in order, with no staging
+// buffer and no separate copy.
+template <typename T>
+__global__ void gather_out_kernel(const T *__restrict__ near_phi, const T *__restrict__ near_grad,
+                                  const T *__restrict__ far_phi, const T *__restrict__ far_grad,
+                                  const int *__restrict__ inv, T *__restrict__ phi, T *__restrict__ grad, int64_t n) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int i = inv[o];
+    if (!dbg_ok(i >= 0 && i < n, kDbgScatter)) return;
+    if (phi) {
+        T v = 0;
+        if (near_phi) v += near_phi[i];
+        if (far_phi) v += far_phi[i];
+        phi[o] = v;
+    }
+    if (grad)
+        for (int a = 0; a < 3; ++a) {
+            T g = 0;
+            if (near_grad) g += near_grad[3 * (int64_t)i + a];
+            if (far_grad) g += far_grad[3 * (int64_t)i + a];
+            grad[3 * o + a] = g;
+        }
+}
+
+__global__ void invert_perm_kernel(const int *__restrict__ perm, int64_t n, int *__restrict__ inv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int o = perm[i];
+    if (dbg_ok(o >= 0 && o < n, kDbgScatter)) inv[o] = (int)i;
+}
+
+
+
 }  // namespace
 
 template <typename T>
@@ -764,9 +820,23 @@ cudaError_t launch_gather_points(const T *q_in, const int *perm, void *pts, int6
 template <typename T>
 cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_phi,
                            const T *far_grad, const int *perm, T *phi, T *grad, int64_t n,
-                           cudaStream_t s) {
+                           cudaStream_t s, int64_t n_out) {
     scatter_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(near_phi, near_grad, far_phi, far_grad,
-                                                         perm, phi, grad, n); count_launch();
+                                                         perm, phi, grad, n, n_out < 0 ? n : n_out); count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_out(const T *near_phi, const T *near_grad, const T *far_phi, const T *far_grad,
+                              const int *inv, T *phi, T *grad, int64_t n, cudaStream_t s) {
+    gather_out_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(near_phi, near_grad, far_phi, far_grad, inv, phi, grad, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t s) {
+    invert_perm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(perm, n, inv);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -783,7 +853,7 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
                                                  kappa);
     };
     if constexpr (std::is_same<T, float>::value) {
-        const LeafBoxes bx{ctx->leaf_off};
+        const LeafBoxes bx{ctx->leaf_off, (int)std::max<int64_t>(ctx->n, ctx->n_pts_all)};
         const unsigned small_grid = (unsigned)((ctx->nleaf + kSmallWarps - 1) / kSmallWarps);
         // leaves of more than kSmallLeaf points in decreasing work, the others one warp each in
         // Morton order
@@ -811,11 +881,11 @@ cudaError_t launch_p2p(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_p2p_rows_f32(const float4 *pts, const int *begin, const int *count, const int *u_off,
+cudaError_t launch_p2p_rows_f32(const float4 *pts, int64_t n_points, const int *begin, const int *count, const int *u_off,
                                 const int *u_idx, const int *order, int nrows, float *phi, float *grad,
                                 cudaStream_t s) {
     if (nrows == 0) return cudaSuccess;
-    const RowBoxes bx{begin, count};
+    const RowBoxes bx{begin, count, (int)n_points};
     const unsigned small_grid = (unsigned)((nrows + kSmallWarps - 1) / kSmallWarps);
     auto go = [&](auto kern, auto small, float *g) {
         kern<<<nrows, kP2PThreads, 0, s>>>(pts, bx, u_off, u_idx, order, phi, g, 0.f);
@@ -838,7 +908,7 @@ cudaError_t launch_leaf_check(const fmm_ctx *ctx, const T *grid, T *out, cudaStr
     const double radius = 2.95 * 0.5 * width;
     const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
     const T kappa = (T)ctx->opt.kappa;
-    const LeafBoxes bx{ctx->leaf_off};
+    const LeafBoxes bx{ctx->leaf_off, (int)std::max<int64_t>(ctx->n, ctx->n_pts_all)};
     auto go = [&](auto kern, int threads) {
         kern<<<ctx->nleaf, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, bx, nullptr, ctx->lev[d].keys,
                                             grid, ctx->npts, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2],
@@ -859,7 +929,7 @@ cudaError_t launch_leaf_check_rows(const fmm_ctx *ctx, int level, const int *lis
     if (n == 0) return cudaSuccess;
     const double width = ctx->side / (double)(1 << level);
     const double radius = 2.95 * 0.5 * width;
-    const RowBoxes bx{begin, count};
+    const RowBoxes bx{begin, count, (int)std::max<int64_t>(ctx->n, ctx->n_pts_all)};
     auto go = [&](auto kern, int threads) {
         kern<<<n, threads, 0, s>>>((const typename Vec4<T>::type *)ctx->pts, bx, list, ctx->lev[level].keys, grid,
                                    ctx->npts, ctx->nsp, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius,
@@ -883,7 +953,7 @@ cudaError_t launch_leaf_eval(const fmm_ctx *ctx, const T *grid, const T *dens, i
     size_t smem = sizeof(P) * ctx->npts * (std::is_same<T, float>::value ? 2 : 1);   // FP32: + the pair layout
     const bool yuk = ctx->opt.kernel == FMM_YUKAWA;
     const T kappa = (T)ctx->opt.kappa;
-    const LeafBoxes bx{ctx->leaf_off};
+    const LeafBoxes bx{ctx->leaf_off, (int)std::max<int64_t>(ctx->n, ctx->n_pts_all)};
     auto go = [&](auto kern, T *g) {
         kern<<<ctx->nleaf, kLeafThreads, smem, s>>>((const P *)ctx->pts, bx, nullptr, ctx->lev[d].keys, grid,
                                                     ctx->npts, dens, ldd, scale, ctx->origin[0], ctx->origin[1],
@@ -907,7 +977,7 @@ cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list
     const double radius = 2.95 * 0.5 * width;
     using P = typename Vec4<T>::type;
     size_t smem = sizeof(P) * ctx->npts * (std::is_same<T, float>::value ? 2 : 1);
-    const RowBoxes bx{begin, count};
+    const RowBoxes bx{begin, count, (int)std::max<int64_t>(ctx->n, ctx->n_pts_all)};
     auto go = [&](auto kern, T *g) {
         kern<<<n, kLeafThreads, smem, s>>>((const P *)ctx->pts, bx, list, ctx->lev[level].keys, grid, ctx->npts, dens,
                                            ldd, (T)1, ctx->origin[0], ctx->origin[1], ctx->origin[2], width, radius,
@@ -921,8 +991,10 @@ cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list
 
 #define FMM_INST(T)                                                                                \
     template cudaError_t launch_gather_points<T>(const T *, const int *, void *, int64_t, cudaStream_t); \
+    template cudaError_t launch_gather_out<T>(const T *, const T *, const T *, const T *, const int *, T *, T *, \
+                                              int64_t, cudaStream_t);                                    \
     template cudaError_t launch_scatter<T>(const T *, const T *, const T *, const T *, const int *,   \
-                                           T *, T *, int64_t, cudaStream_t);                        \
+                                           T *, T *, int64_t, cudaStream_t, int64_t);               \
     template cudaError_t launch_p2p<T>(const fmm_ctx *, T *, T *, cudaStream_t);                    \
     template cudaError_t launch_leaf_check<T>(const fmm_ctx *, const T *, T *, cudaStream_t);       \
     template cudaError_t launch_leaf_check_rows<T>(const fmm_ctx *, int, const int *, int, const int *, \
@@ -934,5 +1006,7 @@ cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list
 FMM_INST(float)
 FMM_INST(double)
 #undef FMM_INST
+
+FMM_DEBUG_UNIT(p2p)
 
 }  // namespace fmm

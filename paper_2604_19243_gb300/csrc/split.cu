@@ -526,6 +526,7 @@ fmm_status split_setup(fmm_ctx *ctx, int dg, int P) {
         v->total_rows = H.rows;
         v->nleaf = (int)(S->hi[r][d] - S->lo[r][d]);
         v->n = H.n_own_pts;
+        v->n_pts_all = H.n_pts;
         if (e == cudaSuccess) e = upload(H.leaf_off, &v->leaf_off, own, s);
         if (e == cudaSuccess) e = upload(H.u_off, &v->u_off, own, s);
         if (e == cudaSuccess) e = upload(H.u_idx, &v->u_idx, own, s);
@@ -782,7 +783,7 @@ cudaError_t split_enqueue(fmm_ctx *ctx, SplitState &S, bool want_phi, bool want_
                                        want_grad ? (const T *)v->near_grad : nullptr,
                                        want_phi ? (const T *)v->far_phi : nullptr,
                                        want_grad ? (const T *)v->far_grad : nullptr, ctx->perm + S.pt_lo[r], phi_o,
-                                       grad_o, v->n, S.far_s[r % K]));
+                                       grad_o, v->n, S.far_s[r % K], ctx->n));
     }
     FMM_CUDA_TRY(join(S.far_s, S.ev_far, K));
     FMM_CUDA_TRY(mark(S.ev[9]));

@@ -14,6 +14,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "debugcheck.cuh"
 #include "devutil.cuh"
 #include "fmm_internal.h"
 
@@ -316,6 +317,7 @@ __global__ void radix_scatter(const uint32_t *keys, const int *vals, int64_t n, 
         const uint32_t key = sk[i];
         const int d = (int)((key >> shift) & 255u);
         const int pos = gbase[d] + (i - dstart[d]);
+        if (!dbg_ok(pos >= 0 && pos < n, kDbgSort)) continue;
         keys_out[pos] = key;
         vals_out[pos] = sv[i];
     }
@@ -940,6 +942,161 @@ cudaError_t export_v_lists(fmm_ctx *ctx, int level, int64_t *off, int64_t *idx, 
     }
     return cudaSuccess;
 }
+
+// ---------------------------------------------------------------------------------------
+// Table validation (fmm_debug_check): every index table of the built tree against its bounds
+// and its definition, one thread per entry; a violation ORs its bit (debugcheck.cuh) into *flag.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+__global__ void val_count(const int *v, int64_t n, int64_t range, int *cnt, uint32_t bit, uint32_t *flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = v[i];
+    if (x < 0 || x >= range) atomicOr(flag, bit);
+    else atomicAdd(&cnt[x], 1);
+}
+
+__global__ void val_once(const int *cnt, int64_t n, uint32_t bit, uint32_t *flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && cnt[i] != 1) atomicOr(flag, bit);
+}
+
+__global__ void val_leaf(const int *leaf_off, int nleaf, int64_t n, uint32_t *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    if (leaf_off[i] >= leaf_off[i + 1] || (i == 0 && leaf_off[0] != 0) || (i == nleaf - 1 && leaf_off[nleaf] != n))
+        atomicOr(flag, kDbgLeaf);
+}
+
+__global__ void val_ulist(const uint32_t *keys, const int *u_off, const int *u_idx, int nleaf, int64_t n_u,
+                          uint32_t *flag) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const int o0 = u_off[b], o1 = u_off[b + 1];
+    if (o0 < 0 || o1 < o0 || o1 > n_u || o1 - o0 > 27) {
+        atomicOr(flag, kDbgUList);
+        return;
+    }
+    int bx, by, bz;
+    demorton3(keys[b], bx, by, bz);
+    bool self = false;
+    for (int m = o0, prev = -1; m < o1; ++m) {
+        const int a = u_idx[m];
+        if (a < 0 || a >= nleaf || a <= prev) {
+            atomicOr(flag, kDbgUList);
+            return;
+        }
+        prev = a, self = self || a == b;
+        int ax, ay, az;
+        demorton3(keys[a], ax, ay, az);
+        if (abs(ax - bx) > 1 || abs(ay - by) > 1 || abs(az - bz) > 1) atomicOr(flag, kDbgUList);
+    }
+    if (!self) atomicOr(flag, kDbgUList);
+}
+
+// level l: keys strictly increasing and inside the level, the dense table, the parent
+__global__ void val_level(const uint32_t *keys, int n, int level, const int *dense, const int *parent,
+                          const uint32_t *pkeys, int np, uint32_t *flag) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const uint32_t k = keys[b];
+    if ((b > 0 && keys[b - 1] >= k) || k >= (1u << (3 * level)) || dense[k] != b) atomicOr(flag, kDbgKeys);
+    if (level > 0) {
+        const int pp = parent[b];
+        if (pp < 0 || pp >= np || pkeys[pp] != (k >> 3)) atomicOr(flag, kDbgTree);
+    }
+}
+
+// every slot of the dense table: -1 or the box of that key
+__global__ void val_dense(const int *dense, int64_t slots, const uint32_t *keys, int n, uint32_t *flag) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= slots) return;
+    const int d = dense[j];
+    if (d != -1 && (d < 0 || d >= n || keys[d] != (uint32_t)j)) atomicOr(flag, kDbgKeys);
+}
+
+__global__ void val_child(const uint32_t *keys, int n, const int *child, const uint32_t *ckeys, const int *cparent,
+                          int nc, uint32_t *flag) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * 8) return;
+    const int b = (int)(e >> 3), c = (int)(e & 7), ch = child[e];
+    if (ch == -1) return;
+    if (ch < 0 || ch >= nc || cparent[ch] != b || ckeys[ch] != ((keys[b] << 3) | (uint32_t)c)) atomicOr(flag, kDbgTree);
+}
+
+struct ClassOff {
+    int off[9];
+};
+
+// the class order of a level: rows [off[c], off[c + 1]) hold the boxes of octant c
+__global__ void val_class(const int *cls_rows, int n, const uint32_t *keys, ClassOff co, uint32_t *flag) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int c = 0;
+    while (c < 8 && r >= co.off[c + 1]) ++c;
+    const int b = cls_rows[r];
+    if (c == 8 || b < 0 || b >= n || (int)(keys[b] & 7u) != c) atomicOr(flag, kDbgClass);
+}
+
+unsigned vblocks(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
+
+}  // namespace
+
+cudaError_t validate_tree(const fmm_ctx *ctx, uint32_t *flags) {
+    cudaStream_t s = ctx->stream;
+    const int depth = ctx->opt.depth;
+    const int64_t n = ctx->n;
+    const int nleaf = ctx->nleaf;
+    uint32_t hflags = 0;
+    Scratch<uint32_t> flag;
+    Scratch<int> cnt;
+    FMM_CUDA_TRY(flag.alloc(1, s));
+    FMM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(uint32_t), s));
+    FMM_CUDA_TRY(cnt.alloc(std::max<int64_t>(n, ctx->total_rows), s));
+    auto permutation = [&](const int *v, int64_t m, uint32_t bit) -> cudaError_t {
+        FMM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, std::max<int64_t>(m, 1) * sizeof(int), s));
+        val_count<<<vblocks(m), 256, 0, s>>>(v, m, m, cnt.p, bit, flag.p); count_launch();
+        val_once<<<vblocks(m), 256, 0, s>>>(cnt.p, m, bit, flag.p); count_launch();
+        return cudaGetLastError();
+    };
+    FMM_CUDA_TRY(permutation(ctx->perm, n, kDbgPerm));
+    val_leaf<<<vblocks(nleaf), 256, 0, s>>>(ctx->leaf_off, nleaf, n, flag.p); count_launch();
+    val_ulist<<<vblocks(nleaf), 256, 0, s>>>(ctx->lev[depth].keys, ctx->u_off, ctx->u_idx, nleaf, ctx->n_u, flag.p);
+    count_launch();
+    FMM_CUDA_TRY(permutation(ctx->p2p_order, nleaf, kDbgOrder));
+    for (int l = 0; l <= depth; ++l) {
+        const LevelTables &T = ctx->lev[l];
+        const int nl = (int)T.n;
+        if (!nl) continue;
+        const LevelTables *P = l > 0 ? &ctx->lev[l - 1] : nullptr;
+        val_level<<<vblocks(nl), 256, 0, s>>>(T.keys, nl, l, T.dense, T.parent, P ? P->keys : nullptr,
+                                             P ? (int)P->n : 0, flag.p);
+        count_launch();
+        val_dense<<<vblocks((int64_t)1 << (3 * l)), 256, 0, s>>>(T.dense, (int64_t)1 << (3 * l), T.keys, nl, flag.p);
+        count_launch();
+        if (l < depth) {
+            const LevelTables &C = ctx->lev[l + 1];
+            val_child<<<vblocks((int64_t)nl * 8), 256, 0, s>>>(T.keys, nl, T.child, C.keys, C.parent, (int)C.n, flag.p);
+            count_launch();
+        }
+        if (l >= 1 && T.cls_rows) {
+            ClassOff co;
+            for (int c = 0; c < 9; ++c) co.off[c] = T.cls_off[c];
+            if (co.off[0] != 0 || co.off[8] != nl) hflags |= kDbgClass;
+            val_class<<<vblocks(nl), 256, 0, s>>>(T.cls_rows, nl, T.keys, co, flag.p); count_launch();
+            FMM_CUDA_TRY(permutation(T.cls_rows, nl, kDbgClass));
+        }
+    }
+    FMM_CUDA_TRY(cudaGetLastError());
+    uint32_t h = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&h, flag.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    *flags = h | hflags;
+    return cudaSuccess;
+}
+
+FMM_DEBUG_UNIT(tree)
 
 }  // namespace fmm
 

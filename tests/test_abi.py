@@ -29,8 +29,11 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
-def test_library_exports_every_declared_symbol(libpath):
-    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+@pytest.mark.parametrize("name", ["libfmm.so", "libfmm_debug.so"])
+def test_library_exports_every_declared_symbol(libpath, name):
+    # libfmm_debug.so: the same sources built with FMM_DEBUG (in-kernel bounds checks)
+    path = os.path.join(os.path.dirname(libpath), name)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(fmm_[a-z_0-9]+)$", out, re.M))
     missing = [n for n in declared_functions() if n not in exported]

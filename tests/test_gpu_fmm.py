@@ -135,6 +135,30 @@ def test_host_pointers_match_device_pointers():
     np.testing.assert_array_equal(grad_h, grad_d.astype(np.float32))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16x3"])
+def test_pinned_host_outputs_match_device_outputs(precision):
+    # outputs in pinned host memory are written by the output gather straight over the host link
+    # (no staging copy); they equal the device outputs bit for bit, the gradient-only form too
+    import torch
+    n = 20_000
+    x, q = cube_points(n), charges(n, "u11")
+    f = make_fmm(x, 4, 3, precision, CUBE)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    qd = torch.from_numpy(q).to("cuda", dt)
+    pd, gd = f.evaluate(qd)
+    ph, gh = torch.empty(n, dtype=dt).pin_memory(), torch.empty(n, 3, dtype=dt).pin_memory()
+    f.evaluate_into(qd, ph, gh)
+    assert torch.equal(ph, pd.cpu()) and torch.equal(gh, gd.cpu())
+    gh2 = torch.zeros(n, 3, dtype=dt).pin_memory()
+    f.evaluate_into(qd.cpu().pin_memory(), None, gh2)   # pinned input too, gradient only
+    assert torch.equal(gh2, gd.cpu())
+    f.build_tree(torch.from_numpy(x[::-1].copy()).to("cuda", dt))   # a new tree: a new inverse permutation
+    pd2, _ = f.evaluate(qd.flip(0))
+    f.evaluate_into(qd.flip(0).contiguous(), ph, gh)
+    assert torch.equal(ph, pd2.cpu())
+    f.close()
+
+
 def test_tree_reuse_with_new_densities():
     x = cube_points(20_000)
     f = make_fmm(x, 4, 3, "fp32", CUBE)
