@@ -871,7 +871,7 @@ fmm_status fmm_debug_check(fmm_ctx *ctx, uint32_t *flags, int32_t *in_kernel) {
     uint32_t f = 0;
     if (e == cudaSuccess) e = validate_tree(ctx, &f);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tree validation");
-    f |= debug_word_tree(true) | debug_word_p2p(true);
+    f |= debug_word_tree(true) | debug_word_p2p(true) | debug_word_output(true);
     *flags = f;
 #ifdef FMM_DEBUG
     if (in_kernel) *in_kernel = 1;

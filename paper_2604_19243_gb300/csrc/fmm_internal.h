@@ -315,6 +315,7 @@ cudaError_t validate_tree(const fmm_ctx *ctx, uint32_t *flags);
 // the in-kernel checks recorded by a translation unit of the FMM_DEBUG build (0 otherwise)
 uint32_t debug_word_tree(bool clear);
 uint32_t debug_word_p2p(bool clear);
+uint32_t debug_word_output(bool clear);
 
 // ---- kernels ----
 // Point kernels (p2p.cu).  T = float or double.

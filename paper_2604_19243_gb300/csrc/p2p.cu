@@ -772,42 +772,6 @@ __global__ void scatter_kernel(const T *__restrict__ near_phi, const T *__restri
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
-// The outputs in the caller's order, written straight into mapped (pinned) host memory: thread o
-// reads the sorted position inv[o] of input o and writes phi[o] and grad[3o .. 3o + 2], so a warp's
-// stores are consecutive and the results cross the host link once, in order, with no staging
-// buffer and no separate copy.
-template <typename T>
-__global__ void gather_out_kernel(const T *__restrict__ near_phi, const T *__restrict__ near_grad,
-                                  const T *__restrict__ far_phi, const T *__restrict__ far_grad,
-                                  const int *__restrict__ inv, T *__restrict__ phi, T *__restrict__ grad, int64_t n) {
-    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    const int i = inv[o];
-    if (!dbg_ok(i >= 0 && i < n, kDbgScatter)) return;
-    if (phi) {
-        T v = 0;
-        if (near_phi) v += near_phi[i];
-        if (far_phi) v += far_phi[i];
-        phi[o] = v;
-    }
-    if (grad)
-        for (int a = 0; a < 3; ++a) {
-            T g = 0;
-            if (near_grad) g += near_grad[3 * (int64_t)i + a];
-            if (far_grad) g += far_grad[3 * (int64_t)i + a];
-            grad[3 * o + a] = g;
-        }
-}
-
-__global__ void invert_perm_kernel(const int *__restrict__ perm, int64_t n, int *__restrict__ inv) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int o = perm[i];
-    if (dbg_ok(o >= 0 && o < n, kDbgScatter)) inv[o] = (int)i;
-}
-
-
-
 }  // namespace
 
 template <typename T>
@@ -823,20 +787,6 @@ cudaError_t launch_scatter(const T *near_phi, const T *near_grad, const T *far_p
                            cudaStream_t s, int64_t n_out) {
     scatter_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(near_phi, near_grad, far_phi, far_grad,
                                                          perm, phi, grad, n, n_out < 0 ? n : n_out); count_launch();
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_gather_out(const T *near_phi, const T *near_grad, const T *far_phi, const T *far_grad,
-                              const int *inv, T *phi, T *grad, int64_t n, cudaStream_t s) {
-    gather_out_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(near_phi, near_grad, far_phi, far_grad, inv, phi, grad, n);
-    count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t s) {
-    invert_perm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(perm, n, inv);
-    count_launch();
     return cudaGetLastError();
 }
 
@@ -991,8 +941,6 @@ cudaError_t launch_leaf_eval_rows(const fmm_ctx *ctx, int level, const int *list
 
 #define FMM_INST(T)                                                                                \
     template cudaError_t launch_gather_points<T>(const T *, const int *, void *, int64_t, cudaStream_t); \
-    template cudaError_t launch_gather_out<T>(const T *, const T *, const T *, const T *, const int *, T *, T *, \
-                                              int64_t, cudaStream_t);                                    \
     template cudaError_t launch_scatter<T>(const T *, const T *, const T *, const T *, const int *,   \
                                            T *, T *, int64_t, cudaStream_t, int64_t);               \
     template cudaError_t launch_p2p<T>(const fmm_ctx *, T *, T *, cudaStream_t);                    \
