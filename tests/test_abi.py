@@ -3,6 +3,7 @@
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -86,6 +87,8 @@ def test_default_options_and_validation_without_gpu(libpath):
     assert lib.fmm_adaptive_export(None, pkg.ADAPTIVE_U, None, None, None) == 1
     assert lib.fmm_adaptive_evaluate(None, None, None, None, pkg.PART_ALL) == 1
     assert lib.fmm_partition_setup(None, 2, 4) == 1
+    flags, ink = ctypes.c_uint32(7), ctypes.c_int32(7)
+    assert lib.fmm_debug_check(None, ctypes.byref(flags), ctypes.byref(ink)) == 1
     assert lib.fmm_last_error(None) == b"null context"
     lib.fmm_destroy(None)
 
@@ -97,3 +100,15 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", text), f
+
+
+def test_library_selection_loads_the_bounds_checked_build(libpath):
+    # FMM_LIBRARY picks a build within _build/ by file name; the child loads it and reports the
+    # path and the outcome of a null-context call (no CUDA call is made)
+    code = ("import ctypes, paper_2604_19243_gb300 as pkg; L = pkg.lib(); "
+            "f = ctypes.c_uint32(); print(pkg.LIB_PATH, L.fmm_debug_check(None, ctypes.byref(f), None))")
+    for name in ("libfmm.so", "libfmm_debug.so", "../../../libfmm_debug.so"):
+        env = dict(os.environ, FMM_LIBRARY=name)
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             check=True).stdout.split()
+        assert out[0] == os.path.join(os.path.dirname(libpath), os.path.basename(name)) and out[1] == "1"
