@@ -396,15 +396,15 @@ wli_kernel(const typename Pt4<T>::type *__restrict__ pts, Levels L, const int *_
 }
 
 // ULI over the adaptive U lists: every point of leaf b against the points of every leaf in
-// U(b) (pairs at distance zero skipped).  One block per row; rows that are not leaves return.
+// U(b) (pairs at distance zero skipped).  One block per leaf, row order[blockIdx.x] (the FP64 form).
 template <typename T, bool POT, bool GRAD>
 __global__ void __launch_bounds__(kEvalThreads)
 uli_kernel(const typename Pt4<T>::type *__restrict__ pts, const int *__restrict__ state,
            const int *__restrict__ u_off, const int *__restrict__ u_idx, const int *__restrict__ begin,
-           const int *__restrict__ count, T *__restrict__ phi, T *__restrict__ grad) {
+           const int *__restrict__ count, T *__restrict__ phi, T *__restrict__ grad, const int *__restrict__ order) {
     using P = typename Pt4<T>::type;
     __shared__ P src[kEvalChunk];
-    const int r = blockIdx.x;
+    const int r = order[blockIdx.x];
     if (state[r] != 1) return;
     const int t0 = begin[r], t1 = t0 + count[r];
     for (int i0 = t0; i0 < t1; i0 += kEvalThreads) {
@@ -808,18 +808,22 @@ cudaError_t adaptive_wli(fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
 template <typename T>
 cudaError_t adaptive_uli(const fmm_ctx *ctx, T *phi, T *grad, cudaStream_t s) {
     const AdaptiveState *A = ctx->adaptive;
-    if constexpr (sizeof(T) == 4)   // the packed FP32 kernel of the uniform tree, over the leaves' rows
-        return launch_p2p_rows_f32((const float4 *)ctx->pts, ctx->n, A->begin, A->count, A->off[0], A->idx[0], A->uli_order,
-                                   A->uli_leaves, (float *)phi, (float *)grad, s);
-    auto go = [&](auto kern) {
-        kern<<<(unsigned)A->rows, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, A->state, A->off[0],
-                                                        A->idx[0], A->begin, A->count, phi, grad);
-    };
-    if (phi && grad) go(uli_kernel<T, true, true>);
-    else if (grad) go(uli_kernel<T, false, true>);
-    else go(uli_kernel<T, true, false>);
-    count_launch();
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {   // the packed FP32 kernels of the uniform tree, over the leaves' rows
+        return launch_p2p_rows_f32((const float4 *)ctx->pts, ctx->n, A->begin, A->count, A->off[0], A->idx[0],
+                                   A->uli_order, A->uli_leaves, (float *)phi, (float *)grad, s);
+    } else {   // FP64: one block per leaf, in the ULI schedule's order
+        if (A->uli_leaves == 0) return cudaSuccess;
+        auto go = [&](auto kern) {
+            kern<<<(unsigned)A->uli_leaves, kEvalThreads, 0, s>>>((const typename Pt4<T>::type *)ctx->pts, A->state,
+                                                                 A->off[0], A->idx[0], A->begin, A->count, phi, grad,
+                                                                 A->uli_order);
+        };
+        if (phi && grad) go(uli_kernel<T, true, true>);
+        else if (grad) go(uli_kernel<T, false, true>);
+        else go(uli_kernel<T, true, false>);
+        count_launch();
+        return cudaGetLastError();
+    }
 }
 
 // workspaces of the W-list step for the current operators
