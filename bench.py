@@ -653,18 +653,22 @@ def main():
     # M2L algorithmic flops: compress + stencil products over the real V pairs
     # ns: entries of a box vector (twice the surface points for the Helmholtz kernel's complex rows)
     kin, kout, ns = info["m2l_rank_in"], info["m2l_rank_out"], info["n_surface"] * (2 if helm else 1)
-    vpairs = 0
+    vpairs = vpairs_upper = 0
     compress_flops = stencil_flops = 0.0
     for level in range(2, w.depth + 1):
         nl = info["n_boxes"][level]
         nv = fmm.v_count(level)
         vpairs += nv
+        vpairs_upper += nv if level < w.depth else 0
         compress_flops += 2.0 * kin * ns * nl
         stencil_flops += 2.0 * kout * kin * nv
     m2l_flops = compress_flops + stencil_flops
-    if args.m2l == "fft":   # products with the kernel's transforms: one complex multiply-add (8 flops)
-        nfft = 2 * w.p          # per frequency of the half spectrum, per V pair
-        m2l_flops = 8.0 * vpairs * nfft * nfft * (nfft // 2 + 1)
+    if args.m2l == "fft":
+        # products with the kernel's transforms: one complex multiply-add (8 flops) per frequency of
+        # the half spectrum and V pair; the phase's events hold levels 2 .. depth - 1 (the leaf
+        # level's transforms and products run after the event that closes the phase)
+        nfft = 2 * w.p
+        m2l_flops = 8.0 * vpairs_upper * nfft * nfft * (nfft // 2 + 1)
     tensor = args.precision in ("bf16x3", "bf16x6", "tf32x3", "fp16x3")
     if tensor:
         # products per contraction: BF16x6 six, the other split modes three (FP16X3 runs every
@@ -683,7 +687,13 @@ def main():
         m2l = {"bound": "alu", "achieved": m2l_flops / (m2l_ms * 1e-3) / 1e12,
                "peak": fp32_peak_tf if not fp64 else None, "unit": "TFLOP/s",
                "peak_basis": "measured FP32 FMA throughput (SIMT contraction)"}
-    m2l.update({"kernel": "M2L phase: compress + stencil GEMMs of all levels (gemm_tc_kernel)",
+    if args.m2l == "fft":
+        m2l_kernel = ("M2L phase, FFT form: transforms (fft_fwd_kernel, fft_inv_kernel), products "
+                      "(fft_hadamard_kernel) and the equivalent-density GEMMs of levels 2 to depth - 1")
+    else:
+        m2l_kernel = ("M2L phase: compress + stencil GEMMs of all levels ("
+                      + ("gemm_tc_plane_kernel / gemm_tc_kernel" if tensor else "gemm_simt_kernel") + ")")
+    m2l.update({"kernel": m2l_kernel,
                 "ms": m2l_ms, "v_pairs": vpairs, "algorithmic_flops": m2l_flops,
                 "timing": "CUDA events on the far-field stream: end of the upward pass to the start "
                           "of the leaf level's downward step"})
