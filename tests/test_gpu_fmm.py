@@ -159,27 +159,6 @@ def test_pinned_host_outputs_match_device_outputs(precision):
     f.close()
 
 
-def test_pinned_host_outputs_of_the_adaptive_and_fft_evaluations():
-    # the same output path for the other evaluations that end in run_evaluate
-    import torch
-    from synth import mixed_points
-    n = 12_000
-    x, q = mixed_points(n, radius=0.02), charges(n, "u11")
-    qd = torch.from_numpy(q).cuda()
-    ph, gh = torch.empty(n).pin_memory(), torch.empty(n, 3).pin_memory()
-    f = make_fmm(x, 4, 7, "fp32", CUBE)
-    f.adaptive_setup(16)
-    pd, gd = f.adaptive_evaluate(qd)
-    f.adaptive_evaluate_into(qd, ph, gh)
-    assert torch.equal(ph, pd.cpu()) and torch.equal(gh, gd.cpu())
-    f.close()
-    g = make_fmm(x, 6, 4, "fp32", CUBE, m2l="fft")
-    pd, gd = g.evaluate(qd)
-    g.evaluate_into(qd, ph, gh)
-    assert torch.equal(ph, pd.cpu()) and torch.equal(gh, gd.cpu())
-    g.close()
-
-
 def test_tree_reuse_with_new_densities():
     x = cube_points(20_000)
     f = make_fmm(x, 4, 3, "fp32", CUBE)
