@@ -19,7 +19,10 @@
  *  - Array arguments may be device pointers or host pointers (pageable or pinned); the library
  *    detects which with cudaPointerGetAttributes.  With device pointers a call returns as soon
  *    as its work is enqueued; with host pointers it copies through library-owned device
- *    buffers and returns after the results are back in host memory.
+ *    buffers and returns after the results are back in host memory.  Outputs of an evaluation
+ *    (fmm_evaluate, fmm_evaluate_parts, fmm_adjoint's psi, fmm_adaptive_evaluate; real
+ *    kernels) that are all in pinned host memory are written there directly by a kernel, in the
+ *    caller's order, with no staging buffer.
  *  - Floating-point arrays are float (4 bytes) unless the context's precision is FMM_FP64,
  *    in which case they are double.  Coordinates are N x 3 row-major (x0 y0 z0 x1 y1 z1 ...).
  *  - The caller owns every array it passes; the library keeps no caller pointer after a call
